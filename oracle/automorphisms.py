@@ -1,0 +1,36 @@
+"""Brute-force automorphism group and edge orbits (test infrastructure).
+
+For small graphs (n <= 8) every one of the n! vertex permutations is tested
+against the definition of an automorphism (Sec. 2: (phi(u), phi(v)) is an edge
+iff (u, v) is). The edge orbits are then the classes of edges under the whole
+group, which pins the generator search plus Algorithm 1 of the package's
+orbit finder.
+"""
+from __future__ import annotations
+
+from itertools import permutations
+
+import numpy as np
+
+
+def automorphism_group(n, edges):
+    es = {(min(int(u), int(v)), max(int(u), int(v))) for u, v in np.asarray(edges).reshape(-1, 2)}
+    group = []
+    for perm in permutations(range(n)):
+        if all((min(perm[u], perm[v]), max(perm[u], perm[v])) in es for u, v in es):
+            group.append(perm)
+    return group
+
+
+def edge_orbit_partition(n, edges):
+    """The set of edge orbits, each a frozenset of (u, v) tuples."""
+    es = sorted({(min(int(u), int(v)), max(int(u), int(v))) for u, v in np.asarray(edges).reshape(-1, 2)})
+    group = automorphism_group(n, edges)
+    seen, orbits = set(), []
+    for e in es:
+        if e in seen:
+            continue
+        orb = frozenset((min(g[e[0]], g[e[1]]), max(g[e[0]], g[e[1]])) for g in group)
+        seen |= orb
+        orbits.append(orb)
+    return set(orbits), group

@@ -1,0 +1,187 @@
+"""CPU oracle: ctypes front end of ``qaoa_oracle.c`` (test infrastructure).
+
+Only the tests, the package smoke check and the benchmark's CPU-baseline leg
+may import this module. It never calls into the CUDA library and the CUDA
+library never calls into it.
+
+Observables are given as weighted edge lists ``(obs_edges, weights)`` standing
+for 1/2 sum_k w_k (1 - Z_{u_k} Z_{v_k}): all edges at weight 1 is H_C, the
+orbit representatives at weight |S~_m| is H_red (Sec. 3.3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qaoa_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (plain -O2, no fast-math)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def load_library(path):
+    """Bind the oracle's C entry points from the shared object at ``path``."""
+    lib = ctypes.CDLL(path)
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+    c128p = np.ctypeslib.ndpointer(np.complex128, flags="C_CONTIGUOUS")
+    lib.oracle_cut_value.restype = ctypes.c_int64
+    lib.oracle_cut_value.argtypes = [ctypes.c_int, i32p, ctypes.c_uint64]
+    lib.oracle_observable_value.restype = ctypes.c_double
+    lib.oracle_observable_value.argtypes = [ctypes.c_int, i32p, f64p, ctypes.c_uint64]
+    lib.oracle_plus_state.restype = None
+    lib.oracle_plus_state.argtypes = [ctypes.c_int, c128p]
+    lib.oracle_apply_cost.restype = None
+    lib.oracle_apply_cost.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_double, c128p]
+    lib.oracle_apply_rx.restype = None
+    lib.oracle_apply_rx.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, c128p]
+    lib.oracle_apply_mixer.restype = None
+    lib.oracle_apply_mixer.argtypes = [ctypes.c_int, ctypes.c_double, c128p]
+    lib.oracle_qaoa_state.restype = None
+    lib.oracle_qaoa_state.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, f64p, f64p, c128p]
+    lib.oracle_expect_diag.restype = ctypes.c_double
+    lib.oracle_expect_diag.argtypes = [ctypes.c_int, c128p, ctypes.c_int, i32p, f64p]
+    lib.oracle_zz.restype = ctypes.c_double
+    lib.oracle_zz.argtypes = [ctypes.c_int, c128p, ctypes.c_int, ctypes.c_int]
+    lib.oracle_expect_terms.restype = ctypes.c_double
+    lib.oracle_expect_terms.argtypes = [ctypes.c_int, c128p, ctypes.c_int, i32p, f64p]
+    lib.oracle_energy_grad.restype = ctypes.c_double
+    lib.oracle_energy_grad.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, f64p, f64p,
+                                       ctypes.c_int, i32p, f64p, f64p, f64p, c128p, c128p]
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+def _edges(e):
+    return np.ascontiguousarray(np.asarray(e, dtype=np.int32).reshape(-1, 2))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+
+
+def full_observable(edges):
+    """H_C as a weighted edge list: every edge at weight 1."""
+    e = _edges(edges)
+    return e, np.ones(len(e), dtype=np.float64)
+
+
+def reduced_observable(edges, rep, weight):
+    """H_red (Sec. 3.3): one representative edge per orbit at weight |S~_m|."""
+    e = _edges(edges)
+    return _edges(e[np.asarray(rep, dtype=np.int64)]), _f64(weight)
+
+
+def cut_value(edges, x: int) -> int:
+    e = _edges(edges)
+    return int(_load().oracle_cut_value(len(e), e, x))
+
+
+def observable_value(obs, x: int) -> float:
+    oe, w = obs
+    return float(_load().oracle_observable_value(len(oe), _edges(oe), _f64(w), x))
+
+
+def plus_state(n):
+    psi = np.empty(1 << n, dtype=np.complex128)
+    _load().oracle_plus_state(n, psi)
+    return psi
+
+
+def apply_cost(n, edges, gamma, psi):
+    e = _edges(edges)
+    _load().oracle_apply_cost(n, len(e), e, float(gamma), psi)
+    return psi
+
+
+def apply_rx(n, q, beta, psi):
+    _load().oracle_apply_rx(n, q, float(beta), psi)
+    return psi
+
+
+def apply_mixer(n, beta, psi):
+    _load().oracle_apply_mixer(n, float(beta), psi)
+    return psi
+
+
+def qaoa_state(n, edges, gamma, beta):
+    """The p-layer state of Eq. (1) as a complex128 vector of 2^n amplitudes."""
+    e = _edges(edges)
+    g, b = _f64(gamma), _f64(beta)
+    psi = np.empty(1 << n, dtype=np.complex128)
+    _load().oracle_qaoa_state(n, len(e), e, len(g), g, b, psi)
+    return psi
+
+
+def expect_diag(n, psi, obs):
+    oe, w = obs
+    return float(_load().oracle_expect_diag(n, psi, len(oe), _edges(oe), _f64(w)))
+
+
+def zz(n, psi, u, v):
+    return float(_load().oracle_zz(n, psi, int(u), int(v)))
+
+
+def expect_terms(n, psi, obs):
+    oe, w = obs
+    return float(_load().oracle_expect_terms(n, psi, len(oe), _edges(oe), _f64(w)))
+
+
+def energy(n, edges, gamma, beta, obs=None):
+    """E = <psi|O|psi>; O defaults to H_C."""
+    if obs is None:
+        obs = full_observable(edges)
+    return expect_diag(n, qaoa_state(n, edges, gamma, beta), obs)
+
+
+def energy_grad(n, edges, gamma, beta, obs=None):
+    """(E, dE/dgamma, dE/dbeta) by the adjoint recursion, FP64."""
+    if obs is None:
+        obs = full_observable(edges)
+    e = _edges(edges)
+    g, b = _f64(gamma), _f64(beta)
+    p = len(g)
+    oe, w = obs
+    dg = np.zeros(p)
+    db = np.zeros(p)
+    phi = np.empty(1 << n, dtype=np.complex128)
+    lam = np.empty(1 << n, dtype=np.complex128)
+    E = _load().oracle_energy_grad(n, len(e), e, p, g, b, len(oe), _edges(oe), _f64(w), dg, db, phi, lam)
+    return float(E), dg, db
+
+
+def finite_difference_grad(n, edges, gamma, beta, obs=None, h=1e-6):
+    """Central finite differences of the oracle energy (FP64)."""
+    g, b = _f64(gamma).copy(), _f64(beta).copy()
+    dg, db = np.zeros_like(g), np.zeros_like(b)
+    for vec, out in ((g, dg), (b, db)):
+        for i in range(len(vec)):
+            old = vec[i]
+            vec[i] = old + h
+            ep = energy(n, edges, g, b, obs)
+            vec[i] = old - h
+            em = energy(n, edges, g, b, obs)
+            vec[i] = old
+            out[i] = (ep - em) / (2 * h)
+    return dg, db

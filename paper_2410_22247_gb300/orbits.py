@@ -1,0 +1,218 @@
+"""Host-side edge-orbit computation (the input to the reduced observable H_red).
+
+The paper obtains generators of Aut(G) from nauty's ``sparsenauty`` and then
+groups edges into equivalence classes by a breadth-first closure under those
+generators (Sec. 4, Algorithm 1). nauty is third-party, so the generators here
+come from this module's own individualisation-refinement search:
+
+* colour refinement to the coarsest equitable ordered partition (an
+  isomorphism-invariant labelling step);
+* a first path of individualisations down to a discrete partition, giving a
+  reference leaf;
+* for every level of that path, a search of each sibling subtree (pruned by
+  the orbits of the generators found so far) for a leaf that differs from the
+  reference leaf by an automorphism. The automorphisms found this way form a
+  generating set of Aut(G) (one transversal per level of the stabiliser chain).
+
+Every generator is checked to map the edge set onto itself before it is used.
+The edge classes then follow Algorithm 1 literally: edges (u, v), u < v, in
+sorted order; each unclassified edge seeds a class; a queue applies every
+generator to every dequeued edge, normalising the image to (min, max), and
+adds images that are unclassified edges.
+
+The representative of each class is its seed edge, which is the lowest-indexed
+edge of the class (the paper picks a random representative, Sec. 3.3; any
+member gives the same expectation because of Eq. (A3)).
+"""
+from __future__ import annotations
+
+from collections import deque
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = ["EdgeOrbits", "automorphism_generators", "edge_orbits", "is_automorphism"]
+
+
+def _adjacency(n, edges):
+    adj = [[] for _ in range(n)]
+    for u, v in edges:
+        adj[u].append(v)
+        adj[v].append(u)
+    return adj
+
+
+def _rank(keys):
+    order = {k: i for i, k in enumerate(sorted(set(keys)))}
+    return [order[k] for k in keys]
+
+
+def _refine(adj, col):
+    """Colour refinement to the coarsest equitable partition refining ``col``."""
+    ncells = len(set(col))
+    while True:
+        sig = [(col[v], tuple(sorted(col[u] for u in adj[v]))) for v in range(len(col))]
+        new = _rank(sig)
+        k = len(set(new))
+        if k == ncells:
+            return new
+        col, ncells = new, k
+
+
+def _individualise(adj, col, v):
+    keys = [(col[u], 0 if u == v else 1) for u in range(len(col))]
+    return _refine(adj, _rank(keys))
+
+
+def _target_cell(col):
+    sizes = {}
+    for v, c in enumerate(col):
+        sizes.setdefault(c, []).append(v)
+    for c in sorted(sizes):
+        if len(sizes[c]) > 1:
+            return sizes[c]
+    return None
+
+
+def _cell_sizes(col):
+    sizes = [0] * len(col)
+    for c in col:
+        sizes[c] += 1
+    return tuple(sizes)
+
+
+def is_automorphism(perm, edge_set) -> bool:
+    """True when the vertex permutation maps the edge set onto itself."""
+    for u, v in edge_set:
+        a, b = perm[u], perm[v]
+        if (min(a, b), max(a, b)) not in edge_set:
+            return False
+    return True
+
+
+def _orbit_ids(n, gens):
+    parent = list(range(n))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for g in gens:
+        for a in range(n):
+            ra, rb = find(a), find(g[a])
+            if ra != rb:
+                parent[ra] = rb
+    return [find(a) for a in range(n)]
+
+
+def automorphism_generators(n, edges):
+    """A generating set of Aut(G) as a list of permutations (lists of length n)."""
+    edges = [tuple(map(int, e)) for e in np.asarray(edges).reshape(-1, 2)]
+    edge_set = {(min(u, v), max(u, v)) for u, v in edges}
+    adj = _adjacency(n, edges)
+    if n == 0:
+        return []
+    col = _refine(adj, [0] * n)
+    path = []
+    while True:
+        cell = _target_cell(col)
+        if cell is None:
+            break
+        path.append((col, cell, cell[0]))
+        col = _individualise(adj, col, cell[0])
+    leaf0 = col
+    inv0 = [0] * n
+    for v, c in enumerate(leaf0):
+        inv0[c] = v
+    depth_sizes = [_cell_sizes(c) for c, _, _ in path] + [_cell_sizes(leaf0)]
+
+    def leaf_map(leaf):
+        # the permutation taking the reference leaf to this leaf: a vertex of
+        # colour c in leaf0 goes to the vertex of colour c in ``leaf``
+        inv = [0] * n
+        for v, c in enumerate(leaf):
+            inv[c] = v
+        return [inv[leaf0[u]] for u in range(n)]
+
+    def search(col, depth):
+        if _cell_sizes(col) != depth_sizes[depth]:
+            return None
+        cell = _target_cell(col)
+        if cell is None:
+            g = leaf_map(col)
+            return g if is_automorphism(g, edge_set) else None
+        for x in cell:
+            r = search(_individualise(adj, col, x), depth + 1)
+            if r is not None:
+                return r
+        return None
+
+    gens = []
+    for level in range(len(path) - 1, -1, -1):
+        col_k, cell, v_k = path[level]
+        for w in cell:
+            if w == v_k:
+                continue
+            orb = _orbit_ids(n, gens)
+            if orb[w] == orb[v_k]:
+                continue
+            g = search(_individualise(adj, col_k, w), level + 1)
+            if g is not None:
+                assert is_automorphism(g, edge_set)
+                gens.append(g)
+    return gens
+
+
+@dataclass
+class EdgeOrbits:
+    """Edge classes of Algorithm 1.
+
+    ``edge_orbit[e]`` is the class of edge e (edges in canonical sorted order),
+    ``rep[m]`` the edge index of the representative of class m (its seed) and
+    ``weight[m]`` the class size |S~_m|.
+    """
+    edge_orbit: np.ndarray
+    rep: np.ndarray
+    weight: np.ndarray
+    generators: list
+
+    @property
+    def num_orbits(self) -> int:
+        return len(self.rep)
+
+
+def edge_orbits(n, edges, generators=None) -> EdgeOrbits:
+    """Algorithm 1: breadth-first closure of the edges under the generators."""
+    edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    canon = [(int(min(u, v)), int(max(u, v))) for u, v in edges]
+    if canon != sorted(canon):
+        raise ValueError("edges must be in canonical sorted order (u < v, lexicographic)")
+    index = {e: i for i, e in enumerate(canon)}
+    if generators is None:
+        generators = automorphism_generators(n, edges)
+    m = len(canon)
+    cls = np.full(m, -1, dtype=np.int64)
+    reps, weights = [], []
+    for seed in range(m):
+        if cls[seed] >= 0:
+            continue
+        c = len(reps)
+        cls[seed] = c
+        reps.append(seed)
+        size = 1
+        queue = deque([canon[seed]])
+        while queue:
+            a, b = queue.popleft()
+            for g in generators:
+                ga, gb = g[a], g[b]
+                img = (min(ga, gb), max(ga, gb))
+                j = index.get(img)
+                if j is not None and cls[j] < 0:
+                    cls[j] = c
+                    size += 1
+                    queue.append(img)
+        weights.append(size)
+    return EdgeOrbits(cls.astype(np.int32), np.asarray(reps, dtype=np.int32),
+                      np.asarray(weights, dtype=np.int32), generators)

@@ -1,0 +1,188 @@
+"""Checks that pin the CPU oracle to things other than itself.
+
+Each check returns the largest relative discrepancy it saw, so the same checks
+serve the pin tests (discrepancy must be tiny) and the planted-mistake tests
+(a mutated oracle must make at least one of them large).
+
+What pins what:
+  * dense brute force: scipy.linalg.expm of the 2^n x 2^n matrices of H_C and
+    H_M built from Kronecker products of Pauli matrices (Eq. (1), Eq. (A2) for
+    the layer order, qubit i = bit i) -- pins the state amplitude by amplitude;
+  * the published p = 1 closed form (degrees and triangles) -- pins E and its
+    gradient on arbitrary graphs;
+  * the Dicke / star symmetric-subspace models -- pin E and gradient at p > 1;
+  * central finite differences -- pin the adjoint gradient;
+  * invariants that hold for every graph (norm, gamma = 0, beta = 0, periods,
+    time reversal, global bit flip, <Z_i> = 0, automorphism invariance of the
+    state (Eq. (A2)), equal <ZZ> within an edge orbit (Eq. (A3)),
+    <H_red> = <H_C> (Eq. (exact)), term-by-term aggregation (Eq. (agg))
+    equal to the diagonal sum, bounds 0 <= E <= C_max).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.linalg import expm
+
+from oracle import oracle as O
+from oracle import closed_form as CF
+from oracle import symmetric as SYM
+from oracle import automorphisms as AUT
+from paper_2410_22247_gb300 import workloads as W
+
+
+def _rel(a, b, scale=None):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    s = np.maximum(np.abs(b), 1.0) if scale is None else scale
+    return float(np.max(np.abs(a - b) / s)) if a.size else 0.0
+
+
+def _op_on(n, q, a):
+    """Dense operator acting with 2x2 matrix a on qubit q (qubit q = bit q)."""
+    m = np.array([[1.0]])
+    for k in range(n - 1, -1, -1):
+        m = np.kron(m, a if k == q else np.eye(2))
+    return m
+
+
+def dense_state(n, edges, gamma, beta):
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+    dim = 1 << n
+    HC = np.zeros((dim, dim), dtype=np.complex128)
+    for u, v in np.asarray(edges).reshape(-1, 2):
+        HC += 0.5 * (np.eye(dim) - _op_on(n, int(u), Z) @ _op_on(n, int(v), Z))
+    HM = sum(_op_on(n, q, X) for q in range(n))
+    psi = np.ones(dim, dtype=np.complex128) / math.sqrt(dim)
+    for g, b in zip(gamma, beta):
+        psi = expm(-1j * g * HC) @ psi
+        psi = expm(-1j * b * HM) @ psi
+    return psi
+
+
+def small_graphs():
+    return [
+        W.cycle_graph(5), W.complete_graph(4), W.star_graph(6), W.prufer_tree(7, 3),
+        W.random_regular(6, 3, 1), (3, W.canonical_edges([(0, 2)])), W.heap_binary_tree(7),
+    ]
+
+
+def check_bruteforce():
+    worst = 0.0
+    for k, (n, e) in enumerate(small_graphs()):
+        g, b = W.random_angles(2, 100 + k)
+        ref = dense_state(n, e, g, b)
+        got = O.qaoa_state(n, e, g, b)
+        worst = max(worst, float(np.max(np.abs(got - ref))))
+    return worst
+
+
+def closed_form_graphs():
+    gs = [W.random_regular(12, 3, 5), W.prufer_tree(11, 2), W.complete_graph(9), W.cycle_graph(10),
+          W.generalized_petersen(5, 2), W.circulant_graph(11, (1, 3)), W.star_graph(9)]
+    r = W.rng(77)
+    # an Erdos-Renyi-style graph with triangles and uneven degrees
+    e = [(i, j) for i in range(10) for j in range(i + 1, 10) if r.uniform() < 0.4]
+    gs.append((10, W.canonical_edges(e)))
+    return gs
+
+
+def check_closed_form():
+    worst = 0.0
+    for k, (n, e) in enumerate(closed_form_graphs()):
+        g, b = W.random_angles(1, 200 + k)
+        E, dg, db = O.energy_grad(n, e, g, b)
+        Ec, dgc, dbc = CF.energy_grad_p1(n, e, g, b)
+        scale = max(abs(Ec), 1.0)
+        worst = max(worst, abs(E - Ec) / scale, _rel(dg, dgc, scale), _rel(db, dbc, scale))
+    return worst
+
+
+def check_symmetric():
+    worst = 0.0
+    for k, (kind, n) in enumerate((("complete", 7), ("complete", 10), ("star", 8), ("star", 11))):
+        p = 1 + k % 3
+        g, b = W.random_angles(p, 300 + k)
+        if kind == "complete":
+            _, e = W.complete_graph(n)
+            model = SYM.complete_graph_model(n)
+        else:
+            _, e = W.star_graph(n)
+            model = SYM.star_model(n)
+        E, dg, db = O.energy_grad(n, e, g, b)
+        Es, dgs, dbs = SYM.energy_grad(model, g, b)
+        scale = max(abs(Es), 1.0)
+        worst = max(worst, abs(E - Es) / scale, _rel(dg, dgs, scale), _rel(db, dbs, scale))
+    return worst
+
+
+def check_finite_difference():
+    worst = 0.0
+    for k, (n, e) in enumerate((W.random_regular(10, 3, 8), W.prufer_tree(9, 4))):
+        g, b = W.random_angles(3, 400 + k)
+        E, dg, db = O.energy_grad(n, e, g, b)
+        fg, fb = O.finite_difference_grad(n, e, g, b, h=1e-5)
+        scale = max(abs(E), 1.0)
+        worst = max(worst, _rel(dg, fg, scale), _rel(db, fb, scale))
+    return worst
+
+
+def check_invariants():
+    """Largest violation over a set of exact identities (all should be ~1e-13)."""
+    worst = 0.0
+    cases = [W.cycle_graph(7), W.prufer_tree(8, 1), W.random_regular(8, 3, 2), W.star_graph(7),
+             W.complete_graph(6), W.heap_binary_tree(8)]
+    for k, (n, e) in enumerate(cases):
+        m = len(e)
+        g, b = W.random_angles(2, 500 + k)
+        psi = O.qaoa_state(n, e, g, b)
+        E = O.energy(n, e, g, b)
+        worst = max(worst, abs(np.vdot(psi, psi).real - 1.0))
+        worst = max(worst, abs(O.energy(n, e, np.zeros(2), b) - m / 2) / m)
+        worst = max(worst, abs(O.energy(n, e, g, np.zeros(2)) - m / 2) / m)
+        worst = max(worst, abs(O.energy(n, e, g, b + np.array([math.pi / 2, 0.0])) - E) / m)
+        worst = max(worst, abs(O.energy(n, e, g + np.array([0.0, 2 * math.pi]), b) - E) / m)
+        worst = max(worst, abs(O.energy(n, e, -g, -b) - E) / m)
+        flip = (1 << n) - 1
+        worst = max(worst, float(np.max(np.abs(psi - psi[np.arange(1 << n) ^ flip]))))
+        for i in range(n):
+            zi = np.sum(np.abs(psi) ** 2 * (1 - 2 * ((np.arange(1 << n) >> i) & 1)))
+            worst = max(worst, abs(zi))
+        # Eq. (A2): psi(pi x) = psi(x) for each automorphism pi
+        group = AUT.automorphism_group(n, e)
+        xs = np.arange(1 << n)
+        for perm in group[: min(len(group), 12)]:
+            px = np.zeros_like(xs)
+            for i in range(n):
+                px |= ((xs >> i) & 1) << perm[i]
+            worst = max(worst, float(np.max(np.abs(psi[px] - psi))))
+        # Eq. (A3): equal <ZZ> inside an edge orbit; Eq. (exact): <H_red> = <H_C>
+        orbits, _ = AUT.edge_orbit_partition(n, e)
+        for orb in orbits:
+            vals = [O.zz(n, psi, u, v) for u, v in orb]
+            worst = max(worst, max(vals) - min(vals))
+        idx = {tuple(map(int, x)): i for i, x in enumerate(e)}
+        reps = [idx[min(orb)] for orb in orbits]
+        wts = [len(orb) for orb in orbits]
+        red = O.reduced_observable(e, reps, wts)
+        Ered, dgr, dbr = O.energy_grad(n, e, g, b, red)
+        Efull, dgf, dbf = O.energy_grad(n, e, g, b)
+        worst = max(worst, abs(Ered - Efull) / m, _rel(dgr, dgf, m), _rel(dbr, dbf, m))
+        # Eq. (agg): term-by-term aggregation equals the diagonal sum
+        worst = max(worst, abs(O.expect_terms(n, psi, O.full_observable(e)) - E) / m)
+        worst = max(worst, abs(O.expect_terms(n, psi, red) - E) / m)
+        # 0 <= E <= C_max (max cut by brute force)
+        cmax = max(O.cut_value(e, x) for x in range(1 << n))
+        worst = max(worst, max(0.0, -E), max(0.0, E - cmax))
+    return worst
+
+
+ALL_CHECKS = {
+    "bruteforce": check_bruteforce,
+    "closed_form": check_closed_form,
+    "symmetric": check_symmetric,
+    "finite_difference": check_finite_difference,
+    "invariants": check_invariants,
+}
