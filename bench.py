@@ -1,0 +1,434 @@
+"""Benchmark: QAOA energy + adjoint-gradient evaluations per second at n = 30.
+
+Workload (one "step" = one evaluation of the whole hot path): the star S_29
+(n = 30 qubits, 29 edges, one edge orbit of weight 29), p = 2 layers,
+complex64 amplitudes with FP64 reductions, observable H_red, energy and the
+adjoint gradient with respect to all 2p angles. The statevector (8.6 GB) is
+far larger than L2, so no flush is needed between steps.
+
+Printed as one JSON line (rank 0). ``value`` is measured with the angles
+already in device memory (CUDA events on the library's stream); ``e2e`` is
+the same metric through the host-pointer C call (pinned host angles in,
+energy and gradient out, copies inside the timed region). ``roofline`` is
+the dominant kernel's achieved HBM bandwidth, ``cpu_baseline`` the FP64 CPU
+oracle on a bounded sample. ``--impl reference`` times that oracle alone.
+
+Multi-GPU (torchrun): every rank evaluates its own parameter points on its
+own GPU (independent evaluations, no collective on the data path) and
+``value`` is the total over ranks ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_QUBITS = 30
+P_LAYERS = 2
+WORKLOAD = "star S_29 (n=30), p=2, complex64, H_red, energy + adjoint gradient"
+METRIC = "QAOA energy+grad evals/s at n=30 (GB/s vs HBM peak); H_red vs H_C agg time"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def graph():
+    from paper_2410_22247_gb300 import orbits as ORB
+    from paper_2410_22247_gb300 import workloads as W
+    n, e = W.star_graph(N_QUBITS)
+    return n, e, ORB.edge_orbits(n, e)
+
+
+def angle_sets(count, seed):
+    from paper_2410_22247_gb300 import workloads as W
+    out = [W.random_angles(P_LAYERS, seed + k) for k in range(count)]
+    return np.array([o[0] for o in out]), np.array([o[1] for o in out])
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(max_seconds=20.0):
+    """FP64 oracle energy + adjoint gradient on a bounded sample.
+
+    The full n = 30 evaluation would take the single-threaded oracle tens of
+    minutes, so the sample is the same graph family and depth at n_s qubits
+    (star S_{n_s - 1}, p = 2), timed end to end, then scaled to n = 30 by the
+    ratio of amplitude-qubit work (30 * 2^30) / (n_s * 2^n_s): every oracle
+    step is a loop over all amplitudes per qubit or per edge, and the star's
+    edge count grows like n.
+    """
+    from oracle import oracle as O
+    from paper_2410_22247_gb300 import orbits as ORB
+    from paper_2410_22247_gb300 import workloads as W
+    O.build()
+    ns = 18
+    times = []
+    while True:
+        n, e = W.star_graph(ns)
+        orb = ORB.edge_orbits(n, e)
+        obs = O.reduced_observable(e, orb.rep, orb.weight)
+        g, b = W.random_angles(P_LAYERS, 1)
+        t0 = time.perf_counter()
+        O.energy_grad(n, e, g, b, obs)
+        dt = time.perf_counter() - t0
+        times.append((ns, dt))
+        if dt * 4.4 > max_seconds or ns >= 24:
+            break
+        ns += 2
+    ns, dt = times[-1]
+    scale = (N_QUBITS * 2.0 ** N_QUBITS) / (ns * 2.0 ** ns)
+    evals_per_s = 1.0 / (dt * scale)
+    return {"value": evals_per_s, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle energy+adjoint gradient of star S_{ns - 1} (n={ns}), p=2, FP64, 1 thread, "
+                      f"{dt:.2f} s, scaled by (30*2^30)/({ns}*2^{ns}) to the n=30 workload"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(max_seconds=8.0)
+    for _ in range(args.steps):
+        vals.append(oracle_sample(max_seconds=8.0))
+    v = float(np.median([x["value"] for x in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_QUBITS, "p": P_LAYERS, "graph": "star S_29"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[-1]["sample"], "value": v},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- native
+def run_native(args, rank, world, local):
+    import torch
+    from paper_2410_22247_gb300.api import Plan
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    n, e, orb = graph()
+    plan = Plan(n, e, P_LAYERS, orbits=orb, precision="c64", with_grad=True, stream=stream, device=dev)
+    K, Wm = args.steps, args.warmup
+    gs, bs = angle_sets(K + Wm, 1000 * (rank + 1))
+    d_g = torch.tensor(gs, dtype=torch.float64, device=dev)
+    d_b = torch.tensor(bs, dtype=torch.float64, device=dev)
+    d_out = torch.zeros((K + Wm, 1 + 2 * P_LAYERS), dtype=torch.float64, device=dev)
+
+    for k in range(Wm):
+        plan.grad_device(d_g[k], d_b[k], d_out[k], "red")
+    plan.sync()
+    from paper_2410_22247_gb300 import _native as N
+    N.check(N.aaqaoa_profile_enable(plan.handle, 1), "profile")
+    launches = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for k in range(Wm, Wm + K):
+                plan.grad_device(d_g[k], d_b[k], d_out[k], "red")
+                launches += plan.launch_count()
+            ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, world)
+    prof = {}
+    names = {0: "forward_pass", 1: "adjoint_pass", 2: "whole_circuit", 3: "aggregation", 4: "param_tables"}
+    import ctypes
+    for kind, nm in names.items():
+        t, c, by = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+        N.check(N.aaqaoa_profile_read(plan.handle, kind, ctypes.byref(t), ctypes.byref(c), ctypes.byref(by)),
+                "profile read")
+        if c.value:
+            prof[nm] = {"ms": t.value, "launches": c.value, "bytes": by.value}
+    N.check(N.aaqaoa_profile_enable(plan.handle, 0), "profile")
+    plan.sync()
+    # results of the timed steps are finite
+    res = d_out[Wm:].cpu().numpy()
+    assert np.all(np.isfinite(res)), "non-finite results"
+
+    # end to end through the host-pointer call with pinned host buffers
+    hg = torch.tensor(gs[0], dtype=torch.float64).pin_memory()
+    hb = torch.tensor(bs[0], dtype=torch.float64).pin_memory()
+    E_host = ctypes.c_double()
+    dg_host = torch.zeros(P_LAYERS, dtype=torch.float64).pin_memory()
+    db_host = torch.zeros(P_LAYERS, dtype=torch.float64).pin_memory()
+    fp = lambda t: ctypes.cast(ctypes.c_void_p(t.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    for _ in range(2):
+        N.check(N.aaqaoa_grad(plan.handle, fp(hg), fp(hb), 1, ctypes.byref(E_host), fp(dg_host), fp(db_host)), "grad")
+    barrier(world)
+    t0 = time.perf_counter()
+    k_e2e = max(3, K // 2)
+    for k in range(k_e2e):
+        hg.copy_(torch.from_numpy(gs[k % len(gs)]))
+        hb.copy_(torch.from_numpy(bs[k % len(bs)]))
+        N.check(N.aaqaoa_grad(plan.handle, fp(hg), fp(hb), 1, ctypes.byref(E_host), fp(dg_host), fp(db_host)), "grad")
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+
+    result = {
+        "ms": ms_max, "evals_per_s": world * K / (ms_max / 1000.0), "prof": prof, "launches": launches,
+        "clocks": clk.summary(), "e2e_evals_per_s": world * k_e2e / t_e2e,
+        "E0": float(res[0, 0]),
+    }
+    extra = {}
+    if rank == 0 and not args.quick:
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+        extra = extras(dev, stream)
+    return result, extra
+
+
+def timed(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extras(dev, stream):
+    """Side-by-side figures at n = 30: c128, energy only, the 3-regular
+    control, and the aggregation modes for H_C vs H_red."""
+    import torch
+    from paper_2410_22247_gb300 import orbits as ORB
+    from paper_2410_22247_gb300 import workloads as W
+    from paper_2410_22247_gb300.api import Plan
+
+    out = {}
+    g, b = W.random_angles(P_LAYERS, 5)
+    dg = torch.tensor(g, device=dev)
+    db = torch.tensor(b, device=dev)
+    o = torch.zeros(1 + 2 * P_LAYERS, dtype=torch.float64, device=dev)
+    oe = torch.zeros(1, dtype=torch.float64, device=dev)
+    graphs = {"star_S29": W.star_graph(30), "regular3_n30": W.random_regular(30, 3, 0)}
+    for name, (n, e) in graphs.items():
+        orb = ORB.edge_orbits(n, e)
+        rec = {"edges": int(len(e)), "orbits": int(orb.num_orbits)}
+        for prec in ("c64", "c128"):
+            pl = Plan(n, e, P_LAYERS, orbits=orb, precision=prec, with_grad=True, stream=stream, device=dev)
+            with torch.cuda.stream(stream):
+                reps = 3 if prec == "c64" else 1
+                t_grad = timed(lambda: pl.grad_device(dg, db, o, "red"), reps, stream)
+                t_fwd = timed(lambda: pl.expect_device(dg, db, oe, "red"), reps, stream)
+            r = {"grad_ms": t_grad, "grad_evals_per_s": 1000.0 / t_grad, "energy_ms": t_fwd,
+                 "energy_evals_per_s": 1000.0 / t_fwd}
+            # aggregation alone on the stored final state, H_C vs H_red
+            pl.expect(g, b, "full", "singlepass")
+            agg = {}
+            for obs in ("full", "red"):
+                for mode in ("singlepass", "perterm"):
+                    t0 = time.perf_counter()
+                    pl.aggregate_only(obs, mode)
+                    agg[f"{obs}_{mode}_ms"] = (time.perf_counter() - t0) * 1000.0
+            r["aggregation_only"] = agg
+            r["energy_red_vs_full_abs_diff"] = abs(pl.expect(g, b, "red") - pl.expect(g, b, "full"))
+            rec[prec] = r
+            pl.close()
+            del pl
+            torch.cuda.empty_cache()
+        out[name] = rec
+    return out
+
+
+def traffic_from_profiles():
+    """dram bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "adjoint_pass_n30_c64_traffic.txt")
+    try:
+        for ln in open(path):
+            if ln.startswith("dram_bytes_per_launch:"):
+                return float(ln.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def profile_case(n):
+    """Two energy+gradient evaluations (p = 2, complex64, H_red) of the star on n qubits."""
+    import torch
+    from paper_2410_22247_gb300 import orbits as ORB
+    from paper_2410_22247_gb300 import workloads as W
+    from paper_2410_22247_gb300.api import Plan
+    nn, e = W.star_graph(n)
+    pl = Plan(nn, e, P_LAYERS, orbits=ORB.edge_orbits(nn, e), precision="c64", with_grad=True)
+    g, b = W.random_angles(P_LAYERS, 3)
+    for _ in range(2):
+        E, dg, db = pl.grad(g, b, "red")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": n, "E": E, "dgamma": list(dg), "dbeta": list(db)}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the side-by-side extras")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="N",
+                    help="run two energy+gradient evaluations of the star on N qubits (a small case for ncu) and exit")
+    args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    result, extra = run_native(args, rank, world, local)
+    if rank != 0:
+        return
+    peak, peak_kind = peaks()
+    prof = result["prof"]
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dom_name, d = dom
+    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+    S = (1 << N_QUBITS) * 8
+    B_alg = (6 * P_LAYERS + 1) * S
+    cpu = oracle_sample()
+    line = {
+        "metric": METRIC,
+        "value": result["evals_per_s"],
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": result["ms"] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 (FP64 reductions)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_QUBITS, "p": P_LAYERS, "graph": "star S_29", "observable": "H_red",
+                   "precision": "complex64", "l2": "statevector 8.6 GB >> 129 MB L2; no flush needed",
+                   "parallelism": f"independent evaluations per GPU x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": traffic_from_profiles(),
+                     "bytes_per_launch": d["bytes"] / d["launches"], "launches": d["launches"]},
+        "step_algorithmic": {"bytes": B_alg, "formula": "(6p+1)*2^n*8",
+                             "GBps": B_alg / (result["ms"] / args.steps / 1000.0) / 1e9},
+        "kernels": prof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": result["e2e_evals_per_s"], "unit": "evals/s", "h2d_bytes_per_step": 2 * P_LAYERS * 8,
+                "d2h_bytes_per_step": 4 + (1 + 2 * P_LAYERS) * 8},
+        "gpu_launches": result["launches"],
+        "clocks": result["clocks"],
+        "extra": extra,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * aaqaoa.h -- C ABI of the GB300 (sm_103a) AA-QAOA hot path.
+ *
+ * What it computes (Automorphism-Assisted QAOA, arXiv:2410.22247):
+ *   |psi_p(gamma, beta)> = prod_{l=1..p} exp(-i beta_l H_M) exp(-i gamma_l H_C) |+>^n
+ * (Eq. (1); layer 1 acts first on |+>^n, as Eq. (A2) writes the product out),
+ * with the unweighted MaxCut cost H_C = 1/2 sum_{(i,j) in E} (1 - Z_i Z_j)
+ * (Eq. for H_P with w_ij in {0, 1}) and the mixer H_M = sum_i X_i, followed by
+ * the cost expectation (F_p, Eq. (2)) aggregated over all 2^n amplitudes
+ * with one of two observables:
+ *   AAQAOA_OBS_FULL  H_C itself;
+ *   AAQAOA_OBS_RED   H_red = 1/2 sum_m |S~_m| (1 - Z_{i_m} Z_{j_m}), one
+ *                    representative edge per edge orbit weighted by the orbit
+ *                    size (Sec. 5, equation for H_red). The ansatz is always
+ *                    built from the full H_C; only the measured observable is
+ *                    reduced, and <H_red> = <H_C> exactly (Eq. (exact)).
+ *
+ * Conventions: qubit i is bit i of the basis-state index (little-endian).
+ * Amplitudes are complex64 (AAQAOA_C64: float re/im pairs) or complex128
+ * (AAQAOA_C128: double re/im pairs); every reduction (energy, gradient,
+ * <Z Z>) accumulates in FP64 and every phase gamma*C(x) is reduced mod 2*pi
+ * in FP64 before it is rounded to the storage precision. The returned energy
+ * is E = <psi| O |psi> (the expected cut, >= 0); minimising or maximising it is
+ * the caller's business.
+ *
+ * Threading and streams: a plan is not thread-safe; calls on one plan must be
+ * serialised by the caller. All device work of a plan is issued on the plan's
+ * CUDA stream (set at prepare time or with aaqaoa_set_stream). Calls that
+ * take host pointers synchronise that stream before they return; calls that
+ * take device pointers only enqueue work.
+ *
+ * Errors: every int-returning entry point returns AAQAOA_OK (0) or a negative
+ * AAQAOA_ERR_* code and never aborts the process. aaqaoa_strerror() gives a
+ * fixed description of a code; aaqaoa_last_error_detail() gives the message
+ * recorded by the last failing call on the calling thread.
+ */
+#ifndef AAQAOA_H
+#define AAQAOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aaqaoa_plan aaqaoa_plan; /* opaque, owned by the library */
+
+/* prepare() flags: amplitude precision */
+#define AAQAOA_C64  0u
+#define AAQAOA_C128 1u
+
+/* observables */
+#define AAQAOA_OBS_FULL 0
+#define AAQAOA_OBS_RED  1
+
+/* aggregation modes of aaqaoa_expect():
+ *   FUSED      one FP64 sum of |psi_x|^2 O(x) folded into the last pass of the
+ *              circuit (no extra read of the state);
+ *   PERTERM    the estimator aggregation of Eq. (agg): one full pass over the
+ *              amplitudes per ZZ term (|E| passes for H_C, |O_E| for H_red),
+ *              the cost model whose term count the paper reduces;
+ *   SINGLEPASS one pass over the stored state that evaluates all terms of
+ *              the observable per amplitude (sum_x |psi_x|^2 O(x) with
+ *              O(x) = sum_terms w [x_u != x_v]), i.e. the whole aggregation
+ *              in a single read. */
+#define AAQAOA_AGG_FUSED      0
+#define AAQAOA_AGG_PERTERM    1
+#define AAQAOA_AGG_SINGLEPASS 2
+
+/* error codes */
+#define AAQAOA_OK               0
+#define AAQAOA_ERR_INVALID_ARG  (-1) /* bad n, p, edge list, pointer or size      */
+#define AAQAOA_ERR_BAD_ORBITS   (-2) /* orbit data do not partition the edges     */
+#define AAQAOA_ERR_WORKSPACE    (-3) /* no workspace, or one too small/misaligned */
+#define AAQAOA_ERR_CUDA         (-4) /* a CUDA call failed (detail recorded)      */
+#define AAQAOA_ERR_TIMEOUT      (-5) /* a bounded device wait expired             */
+#define AAQAOA_ERR_UNSUPPORTED  (-6) /* valid request this build does not serve   */
+
+#define AAQAOA_MAX_QUBITS 34
+
+/*
+ * aaqaoa_prepare -- validate a graph and its edge orbits, build a plan.
+ *
+ * n            number of vertices = qubits, 1 <= n <= 34.
+ * num_edges    |E| >= 0.
+ * edges        host, 2*num_edges int32: edge e joins edges[2e] and edges[2e+1].
+ *              Vertices in [0, n); no self-loops; no repeated edge (in either
+ *              orientation). Any order; the plan keeps the caller's edge
+ *              indexing for orbit_rep / edge_orbit.
+ * num_orbits   |O_E| (0 if no reduced observable is wanted).
+ * orbit_rep    host, num_orbits int32: index (into edges) of the representative
+ *              (i_m, j_m) of each orbit S~_m (Sec. 5). May be NULL if
+ *              num_orbits == 0.
+ * orbit_weight host, num_orbits int32: |S~_m| >= 1; must sum to num_edges.
+ * edge_orbit   host, num_edges int32 or NULL: the orbit of each edge. When
+ *              given, it must be a partition consistent with orbit_rep (each
+ *              representative lies in its own orbit) and orbit_weight (class
+ *              sizes). The library cannot check that the classes are true
+ *              Aut(G) orbits (Algorithm 1); exactness of H_red relies on it.
+ * p            number of QAOA layers, 1 <= p <= 64.
+ * flags        AAQAOA_C64 or AAQAOA_C128.
+ * stream       cudaStream_t (as void*) for all device work; NULL = legacy
+ *              default stream.
+ * out          receives the plan; *out is NULL on error.
+ *
+ * All host arrays are copied; the caller may free them on return. No device
+ * memory is allocated: device buffers come from aaqaoa_set_workspace().
+ * Errors: INVALID_ARG, BAD_ORBITS.
+ */
+int aaqaoa_prepare(int n, int num_edges, const int32_t *edges,
+                   int num_orbits, const int32_t *orbit_rep, const int32_t *orbit_weight,
+                   const int32_t *edge_orbit, int p, unsigned flags, void *stream,
+                   aaqaoa_plan **out);
+
+/*
+ * aaqaoa_workspace_bytes -- device bytes needed for a workspace able to hold
+ * `batch` statevectors (batch >= 1), with room for the adjoint gradient's
+ * second statevector when with_grad != 0. Writes *bytes.
+ */
+int aaqaoa_workspace_bytes(const aaqaoa_plan *plan, int batch, int with_grad, size_t *bytes);
+
+/*
+ * aaqaoa_set_workspace -- hand the plan a device buffer (caller-owned; e.g. a
+ * torch tensor) of at least aaqaoa_workspace_bytes(plan, batch, with_grad)
+ * bytes, 256-byte aligned. The plan keeps the pointer until the next call or
+ * aaqaoa_destroy; the caller must keep the memory alive meanwhile.
+ * Errors: INVALID_ARG, WORKSPACE (too small / misaligned), CUDA.
+ */
+int aaqaoa_set_workspace(aaqaoa_plan *plan, void *device_ptr, size_t bytes, int batch, int with_grad);
+
+/* aaqaoa_set_stream -- change the plan's CUDA stream (cudaStream_t as void*). */
+int aaqaoa_set_stream(aaqaoa_plan *plan, void *stream);
+
+/*
+ * aaqaoa_expect -- E = <psi_p(gamma, beta)| O |psi_p(gamma, beta)>.
+ *
+ * gamma, beta  host, p doubles each.
+ * observable   AAQAOA_OBS_FULL or AAQAOA_OBS_RED (RED needs num_orbits > 0).
+ * agg_mode     AAQAOA_AGG_FUSED / PERTERM / SINGLEPASS (see above).
+ * energy       host, 1 double.
+ * Synchronises the plan's stream. Errors: INVALID_ARG, WORKSPACE, CUDA, TIMEOUT.
+ */
+int aaqaoa_expect(aaqaoa_plan *plan, const double *gamma, const double *beta,
+                  int observable, int agg_mode, double *energy);
+
+/*
+ * aaqaoa_grad -- energy and its gradient by the adjoint method.
+ *
+ * With phi = psi_p and lambda = O psi_p, for l = p..1 the library applies the
+ * inverse mixer and cost layers to both vectors and accumulates
+ * dE/dbeta_l = 2 Im <lambda| H_M |phi> and dE/dgamma_l = 2 Im <lambda| H_C |phi>
+ * (derivative of F_p, Eq. (2)). Two statevectors; the workspace must have
+ * been set with with_grad != 0.
+ * gamma, beta, dgamma, dbeta: host, p doubles each; energy: host, 1 double.
+ * Synchronises the plan's stream.
+ */
+int aaqaoa_grad(aaqaoa_plan *plan, const double *gamma, const double *beta, int observable,
+                double *energy, double *dgamma, double *dbeta);
+
+/*
+ * aaqaoa_expect_batch -- energies of B parameter points on the plan's graph.
+ * gamma, beta: host, B*p doubles (point-major: point b uses gamma[b*p .. b*p+p-1]).
+ * energy: host, B doubles. Points are processed in groups of the workspace's
+ * batch capacity. Fused aggregation. Synchronises the plan's stream.
+ */
+int aaqaoa_expect_batch(aaqaoa_plan *plan, int B, const double *gamma, const double *beta,
+                        int observable, double *energy);
+
+/*
+ * Device-pointer forms: the same computations with every argument already in
+ * device memory. They only enqueue work on the plan's stream and return; the
+ * results are valid once that stream has reached them. A device-side timeout
+ * is reported by the next call of aaqaoa_sync().
+ *
+ * aaqaoa_expect_device: d_gamma, d_beta: B*p doubles; d_energy: B doubles
+ *   (B <= the workspace's batch capacity). Fused aggregation.
+ * aaqaoa_grad_device: d_gamma, d_beta: p doubles; d_out: 1 + 2p doubles laid
+ *   out as [E, dE/dgamma_1..p, dE/dbeta_1..p].
+ */
+int aaqaoa_expect_device(aaqaoa_plan *plan, int B, const double *d_gamma, const double *d_beta,
+                         int observable, double *d_energy);
+int aaqaoa_grad_device(aaqaoa_plan *plan, const double *d_gamma, const double *d_beta,
+                       int observable, double *d_out);
+
+/* aaqaoa_sync -- wait for the plan's stream and report any device-side error. */
+int aaqaoa_sync(aaqaoa_plan *plan);
+
+/*
+ * aaqaoa_edge_zz -- <Z_u Z_v> for every edge of the graph in one pass over the
+ * final state (the per-term values that Eq. (agg) sums; equal within an edge
+ * orbit by Eq. (A3)). zz: host, num_edges doubles, in the caller's edge order.
+ */
+int aaqaoa_edge_zz(aaqaoa_plan *plan, const double *gamma, const double *beta, double *zz);
+
+/*
+ * aaqaoa_statevector -- the final state psi_p itself, copied to host memory:
+ * 2^n complex amplitudes in the plan's precision (interleaved re, im as float
+ * for C64 or double for C128). host_out must hold 2^n * 8 (C64) or
+ * 2^n * 16 (C128) bytes.
+ */
+int aaqaoa_statevector(aaqaoa_plan *plan, const double *gamma, const double *beta, void *host_out);
+
+/*
+ * aaqaoa_aggregate_only -- time-isolated aggregation: evaluate
+ * <psi|O|psi> on the state left in the workspace by the last
+ * aaqaoa_statevector / aaqaoa_edge_zz / non-fused aaqaoa_expect call, with
+ * the given observable and aggregation mode, without re-running the circuit.
+ * energy: host, 1 double. Synchronises the plan's stream.
+ */
+int aaqaoa_aggregate_only(aaqaoa_plan *plan, int observable, int agg_mode, double *energy);
+
+/* Plan properties: qubits, layers, edges, orbits, precision flag. */
+int aaqaoa_plan_info(const aaqaoa_plan *plan, int *n, int *p, int *num_edges, int *num_orbits,
+                     unsigned *flags);
+
+/*
+ * aaqaoa_launch_count -- number of kernel launches the last completed call on
+ * this plan enqueued (for launch accounting in benchmarks).
+ */
+int aaqaoa_launch_count(const aaqaoa_plan *plan, int *launches);
+
+/*
+ * Launch profiling. While enabled, the plan records a CUDA event pair on its
+ * stream around every kernel launch and keeps, per kernel kind, the launch
+ * count and the bytes each launch has to move (statevector tiles loaded plus
+ * stored). aaqaoa_profile_read synchronises the stream and returns the summed
+ * event durations (ms), launches and bytes of one kind:
+ *   0 forward tiled pass, 1 adjoint tiled pass, 2 whole-circuit (small n)
+ *   kernel, 3 aggregation over a stored state, 4 parameter tables.
+ * aaqaoa_profile_enable(plan, 0) stops recording; enabling clears the record.
+ */
+int aaqaoa_profile_enable(aaqaoa_plan *plan, int enable);
+int aaqaoa_profile_read(aaqaoa_plan *plan, int kind, double *ms_total, int *launches, double *bytes);
+
+/* Release a plan (not the workspace, which the caller owns). NULL is a no-op. */
+void aaqaoa_destroy(aaqaoa_plan *plan);
+
+/* Fixed description of an error code. */
+const char *aaqaoa_strerror(int code);
+
+/* Message recorded by the last failing call on this thread ("" if none). */
+const char *aaqaoa_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AAQAOA_H */

@@ -1,7 +1,7 @@
 """Brute-force automorphism group and edge orbits (test infrastructure).
 
 For small graphs (n <= 8) every one of the n! vertex permutations is tested
-against the definition of an automorphism (Sec. 2: (phi(u), phi(v)) is an edge
+against the definition of an automorphism (Sec. 3, "Graph Automorphisms": (phi(u), phi(v)) is an edge
 iff (u, v) is). The edge orbits are then the classes of edges under the whole
 group, which pins the generator search plus Algorithm 1 of the package's
 orbit finder.

@@ -3,7 +3,7 @@
 At depth p the expectation <Z_u Z_v> depends only on the qubits within graph
 distance p of {u, v}: in the Heisenberg picture each of the p cost layers
 widens the support by one neighbourhood, and every gate outside that ball
-commutes through and cancels (this is the reverse causal cone of Sec. 3.4,
+commutes through and cancels (this is the reverse causal cone of Sec. 5.1,
 Eqs. (rcc1)-(rcc4)). Edges between two vertices at distance exactly p also
 cancel, so the induced subgraph on the ball gives the same value.
 

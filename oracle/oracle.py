@@ -6,7 +6,7 @@ library never calls into it.
 
 Observables are given as weighted edge lists ``(obs_edges, weights)`` standing
 for 1/2 sum_k w_k (1 - Z_{u_k} Z_{v_k}): all edges at weight 1 is H_C, the
-orbit representatives at weight |S~_m| is H_red (Sec. 3.3).
+orbit representatives at weight |S~_m| is H_red (Sec. 5, "Reducing the Hamiltonian").
 """
 from __future__ import annotations
 
@@ -88,7 +88,7 @@ def full_observable(edges):
 
 
 def reduced_observable(edges, rep, weight):
-    """H_red (Sec. 3.3): one representative edge per orbit at weight |S~_m|."""
+    """H_red (Sec. 5, equation for H_red): one representative edge per orbit at weight |S~_m|."""
     e = _edges(edges)
     return _edges(e[np.asarray(rep, dtype=np.int64)]), _f64(weight)
 

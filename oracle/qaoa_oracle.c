@@ -18,7 +18,7 @@
  *     RX(2 beta) = [[cos b, -i sin b], [-i sin b, cos b]];
  *   - an observable is a weighted list of edges (u, v, w) standing for
  *     1/2 sum w (1 - Z_u Z_v). With every edge at weight 1 it is H_C; with the
- *     orbit representatives at weight |S~_m| it is H_red (Sec. 3.3).
+ *     orbit representatives at weight |S~_m| it is H_red (Sec. 5, "Reducing the Hamiltonian").
  *
  * Nothing is blocked, fused or reordered: each function is the textbook loop
  * over basis states.
@@ -46,7 +46,7 @@ int64_t oracle_cut_value(int m, const int32_t *edges, uint64_t x)
 
 /* Diagonal of a weighted observable 1/2 sum_k w_k (1 - Z_{u_k} Z_{v_k}) at x:
  * sum_k w_k [x_{u_k} != x_{v_k}]. With the orbit representatives and orbit
- * sizes this is the diagonal of H_red (Sec. 3.3, equation for H_red). */
+ * sizes this is the diagonal of H_red (Sec. 5, equation for H_red). */
 double oracle_observable_value(int k, const int32_t *obs_edges, const double *w, uint64_t x)
 {
     double s = 0.0;

@@ -1,0 +1,194 @@
+"""Python front end of the C ABI: a plan object and a torch.autograd.Function.
+
+PyTorch supplies device memory (the plan's workspace is a uint8 CUDA tensor)
+and the CUDA stream; every computation runs in ``libaaqaoa.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+
+OBSERVABLES = {"full": N.AAQAOA_OBS_FULL, "red": N.AAQAOA_OBS_RED,
+               N.AAQAOA_OBS_FULL: N.AAQAOA_OBS_FULL, N.AAQAOA_OBS_RED: N.AAQAOA_OBS_RED}
+AGG_MODES = {"fused": N.AAQAOA_AGG_FUSED, "perterm": N.AAQAOA_AGG_PERTERM, "singlepass": N.AAQAOA_AGG_SINGLEPASS}
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t)) if a is not None and a.size else None
+
+
+class Plan:
+    """A prepared graph (and its edge orbits) with a device workspace.
+
+    ``orbits`` is an object with ``rep``, ``weight`` and ``edge_orbit``
+    attributes (e.g. :class:`paper_2410_22247_gb300.orbits.EdgeOrbits`), a
+    ``(rep, weight[, edge_orbit])`` tuple, or None for no reduced observable.
+    """
+
+    def __init__(self, n, edges, p, orbits=None, precision="c64", batch=1, with_grad=True,
+                 stream=None, device=None):
+        import torch
+
+        self._lib = N.load()
+        self.n, self.p = int(n), int(p)
+        self.precision = precision
+        self.edges = _i32(edges).reshape(-1, 2)
+        flags = N.AAQAOA_C128 if precision == "c128" else N.AAQAOA_C64
+        rep = weight = eo = None
+        if orbits is not None:
+            if hasattr(orbits, "rep"):
+                rep, weight, eo = orbits.rep, orbits.weight, getattr(orbits, "edge_orbit", None)
+            else:
+                rep, weight = orbits[0], orbits[1]
+                eo = orbits[2] if len(orbits) > 2 else None
+            rep, weight = _i32(rep), _i32(weight)
+            eo = None if eo is None else _i32(eo)
+        self.num_orbits = 0 if rep is None else len(rep)
+        e = _i32(self.edges)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        handle = ctypes.c_void_p()
+        N.check(N.aaqaoa_prepare(self.n, len(self.edges), _ptr(e, ctypes.c_int32), self.num_orbits,
+                                 _ptr(rep, ctypes.c_int32), _ptr(weight, ctypes.c_int32), _ptr(eo, ctypes.c_int32),
+                                 self.p, flags, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)),
+                "aaqaoa_prepare")
+        self.handle = handle
+        self.batch = int(batch)
+        self.with_grad = bool(with_grad)
+        size = ctypes.c_size_t()
+        N.check(N.aaqaoa_workspace_bytes(self.handle, self.batch, int(self.with_grad), ctypes.byref(size)),
+                "aaqaoa_workspace_bytes")
+        self.workspace = torch.empty(int(size.value), dtype=torch.uint8, device=self.device)
+        N.check(N.aaqaoa_set_workspace(self.handle, ctypes.c_void_p(self.workspace.data_ptr()), size.value,
+                                       self.batch, int(self.with_grad)), "aaqaoa_set_workspace")
+
+    # -- host-pointer calls (synchronising) --------------------------------
+    def expect(self, gamma, beta, observable="full", agg="fused") -> float:
+        g, b = _f64(gamma), _f64(beta)
+        out = ctypes.c_double()
+        N.check(N.aaqaoa_expect(self.handle, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                OBSERVABLES[observable], AGG_MODES[agg], ctypes.byref(out)), "aaqaoa_expect")
+        return out.value
+
+    def grad(self, gamma, beta, observable="full"):
+        g, b = _f64(gamma), _f64(beta)
+        E = ctypes.c_double()
+        dg = np.zeros(self.p)
+        db = np.zeros(self.p)
+        N.check(N.aaqaoa_grad(self.handle, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
+                              OBSERVABLES[observable], ctypes.byref(E), _ptr(dg, ctypes.c_double),
+                              _ptr(db, ctypes.c_double)), "aaqaoa_grad")
+        return E.value, dg, db
+
+    def expect_batch(self, gammas, betas, observable="full"):
+        g = _f64(gammas)
+        b = _f64(betas)
+        B = len(g) // self.p
+        out = np.zeros(B)
+        N.check(N.aaqaoa_expect_batch(self.handle, B, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                      OBSERVABLES[observable], _ptr(out, ctypes.c_double)), "aaqaoa_expect_batch")
+        return out
+
+    def edge_zz(self, gamma, beta):
+        g, b = _f64(gamma), _f64(beta)
+        out = np.zeros(len(self.edges))
+        N.check(N.aaqaoa_edge_zz(self.handle, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                 _ptr(out, ctypes.c_double) if len(out) else ctypes.cast(ctypes.pointer(ctypes.c_double()), ctypes.POINTER(ctypes.c_double))),
+                "aaqaoa_edge_zz")
+        return out
+
+    def statevector(self, gamma, beta):
+        g, b = _f64(gamma), _f64(beta)
+        dt = np.complex128 if self.precision == "c128" else np.complex64
+        out = np.zeros(1 << self.n, dtype=dt)
+        N.check(N.aaqaoa_statevector(self.handle, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                     ctypes.c_void_p(out.ctypes.data)), "aaqaoa_statevector")
+        return out
+
+    def aggregate_only(self, observable="full", agg="singlepass") -> float:
+        out = ctypes.c_double()
+        N.check(N.aaqaoa_aggregate_only(self.handle, OBSERVABLES[observable], AGG_MODES[agg], ctypes.byref(out)),
+                "aaqaoa_aggregate_only")
+        return out.value
+
+    # -- device-pointer calls (asynchronous on the plan's stream) ----------
+    def expect_device(self, d_gamma, d_beta, d_energy, observable="full"):
+        B = d_gamma.numel() // self.p
+        N.check(N.aaqaoa_expect_device(self.handle, B, ctypes.c_void_p(d_gamma.data_ptr()),
+                                       ctypes.c_void_p(d_beta.data_ptr()), OBSERVABLES[observable],
+                                       ctypes.c_void_p(d_energy.data_ptr())), "aaqaoa_expect_device")
+
+    def grad_device(self, d_gamma, d_beta, d_out, observable="full"):
+        N.check(N.aaqaoa_grad_device(self.handle, ctypes.c_void_p(d_gamma.data_ptr()),
+                                     ctypes.c_void_p(d_beta.data_ptr()), OBSERVABLES[observable],
+                                     ctypes.c_void_p(d_out.data_ptr())), "aaqaoa_grad_device")
+
+    def sync(self):
+        N.check(N.aaqaoa_sync(self.handle), "aaqaoa_sync")
+
+    def launch_count(self) -> int:
+        c = ctypes.c_int()
+        N.check(N.aaqaoa_launch_count(self.handle, ctypes.byref(c)), "aaqaoa_launch_count")
+        return c.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            N.aaqaoa_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _autograd_function():
+    import torch
+
+    class AAQAOAFunction(torch.autograd.Function):
+        """E(gamma, beta) with the adjoint gradient of ``aaqaoa_grad_device``.
+
+        ``gamma`` and ``beta`` are float64 CUDA tensors of length p. The
+        forward pass computes the energy and both gradients in one call; the
+        backward pass only scales them by the incoming gradient.
+        """
+
+        @staticmethod
+        def forward(ctx, gamma, beta, plan, observable="full"):
+            g = gamma.detach().to(dtype=torch.float64).contiguous()
+            b = beta.detach().to(dtype=torch.float64).contiguous()
+            out = torch.empty(1 + 2 * plan.p, dtype=torch.float64, device=g.device)
+            plan.grad_device(g, b, out, observable)
+            ctx.save_for_backward(out[1:1 + plan.p].clone(), out[1 + plan.p:].clone())
+            return out[0].clone()
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dg, db = ctx.saved_tensors
+            return grad_out * dg, grad_out * db, None, None
+
+    return AAQAOAFunction
+
+
+_FN = None
+
+
+def energy(gamma, beta, plan, observable="full"):
+    """Differentiable energy: ``AAQAOAFunction.apply(gamma, beta, plan, observable)``."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_function()
+    return _FN.apply(gamma, beta, plan, observable)

@@ -1,0 +1,981 @@
+// Host side of the AA-QAOA C ABI (include/aaqaoa.h): input validation, plans,
+// workspace layout, TMA tensor maps and the order of kernel launches.
+//
+// Pass schedule for n above the tile size (T = 13 qubits for C64, 12 for C128):
+//   forward, layer l = 1..p:  low pass (cost phase T_l[C(x)] then butterflies
+//     on qubits 0..T-1), then high passes of 9 qubits each; the last pass of
+//     layer p folds in the reduction (and, for the gradient, lambda = O psi).
+//   adjoint, layer l = p..1:  the same passes on (phi, lambda) in reverse
+//     order with the inverse mixer, accumulating 2 Im <lambda|X_q|phi>; the
+//     last pass of the layer adds 2 Im <lambda|C|phi> and applies the inverse
+//     cost phase (skipped, with the store, for l = 1).
+// For n <= T one CTA per parameter point runs the whole circuit in shared
+// memory.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "aaqaoa.h"
+#include "aaqaoa_internal.h"
+
+using namespace aaq;
+
+namespace {
+
+thread_local std::string g_detail;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_detail = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(AAQAOA_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess)                        \
+            return cuda_fail(e_, #call);              \
+    } while (0)
+
+#define CKL(code, what)                                          \
+    do {                                                         \
+        int c_ = (code);                                         \
+        if (c_ != 0)                                             \
+            return cuda_fail((cudaError_t)c_, what);             \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+struct Pass {
+    int s, is_low, hmask;
+};
+
+struct Layout {
+    size_t ctrl, out, params, cs, tab, partials, zz, phi, lam, total;
+    size_t partial_count;
+};
+
+}  // namespace
+
+struct aaqaoa_plan {
+    int n = 0, m = 0, p = 0, num_orbits = 0;
+    bool c128 = false;
+    std::vector<int32_t> edges;  // normalised (u < v), caller's edge order
+    std::vector<int32_t> orbit_rep, orbit_weight;
+    CostFn cost{};
+    CutFn obs[2]{};
+    cudaStream_t stream = nullptr;
+    // workspace
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    int cap = 0;
+    bool ws_grad = false;
+    Layout L{};
+    std::vector<Pass> passes;
+    std::vector<CUtensorMap> map_phi, map_lam;
+    int launches = 0;
+    bool state_valid = false;
+    // launch profiling
+    bool prof = false;
+    struct ProfRec {
+        int kind;
+        double bytes;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+
+    int T() const { return tile_bits(c128); }
+    int CB() const { return c128 ? 3 : 4; }
+    size_t amp() const { return c128 ? 16 : 8; }
+    int tab_len() const { return m + 1; }
+    int out_stride() const { return 1 + 2 * p; }
+    bool small() const { return n <= T(); }
+    int tiles() const { return small() ? 1 : 1 << (n - T()); }
+    int *d_err() const { return reinterpret_cast<int *>(ws + L.ctrl); }
+    unsigned *d_counter_pass() const { return reinterpret_cast<unsigned *>(ws + L.ctrl + 8); }
+    unsigned *d_counter_agg() const { return reinterpret_cast<unsigned *>(ws + L.ctrl + 16); }
+    double *d_out() const { return reinterpret_cast<double *>(ws + L.out); }
+    double *d_params() const { return reinterpret_cast<double *>(ws + L.params); }
+    double2 *d_cs() const { return reinterpret_cast<double2 *>(ws + L.cs); }
+    void *d_tab() const { return ws + L.tab; }
+    double *d_partials() const { return reinterpret_cast<double *>(ws + L.partials); }
+    double *d_zz() const { return reinterpret_cast<double *>(ws + L.zz); }
+    void *d_phi() const { return ws + L.phi; }
+    void *d_lam() const { return ws + L.lam; }
+};
+
+namespace {
+
+enum ProfKind { PK_FWD = 0, PK_ADJ = 1, PK_SMALL = 2, PK_AGG = 3, PK_PARAMS = 4, PK_COUNT = 5 };
+
+cudaEvent_t prof_event(aaqaoa_plan *pl)
+{
+    if (!pl->prof_pool.empty()) {
+        cudaEvent_t e = pl->prof_pool.back();
+        pl->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// brackets one launch with an event pair when profiling is on
+struct ProfScope {
+    aaqaoa_plan *pl;
+    int kind;
+    double bytes;
+    cudaEvent_t a = nullptr;
+    ProfScope(aaqaoa_plan *p, int k, double by) : pl(p), kind(k), bytes(by)
+    {
+        if (pl->prof) {
+            a = prof_event(pl);
+            cudaEventRecord(a, pl->stream);
+        }
+    }
+    ~ProfScope()
+    {
+        if (pl->prof) {
+            cudaEvent_t b = prof_event(pl);
+            cudaEventRecord(b, pl->stream);
+            pl->prof_recs.push_back({kind, bytes, a, b});
+        }
+    }
+};
+
+Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
+{
+    Layout L{};
+    size_t off = 0;
+    const size_t B = (size_t)batch;
+    L.ctrl = off;
+    off += 256;
+    L.out = off;
+    off = align256(off + B * pl->out_stride() * sizeof(double));
+    L.params = off;
+    off = align256(off + 2 * B * pl->p * sizeof(double));
+    L.cs = off;
+    off = align256(off + B * pl->p * sizeof(double2));
+    L.tab = off;
+    off = align256(off + B * pl->p * pl->tab_len() * pl->amp());
+    const size_t pass_partials = pl->small() ? 0 : 2 * B * (size_t)pl->tiles();
+    const size_t agg_partials = 64 * (size_t)agg_grid(pl->c128);
+    L.partial_count = pass_partials > agg_partials ? pass_partials : agg_partials;
+    L.partials = off;
+    off = align256(off + L.partial_count * sizeof(double));
+    L.zz = off;
+    off = align256(off + (size_t)(pl->m > 0 ? pl->m : 1) * sizeof(double));
+    L.phi = off;
+    off = align256(off + B * ((size_t)1 << pl->n) * pl->amp());
+    L.lam = off;
+    if (grad && !pl->small())
+        off = align256(off + B * ((size_t)1 << pl->n) * pl->amp());
+    L.total = off;
+    return L;
+}
+
+int make_map(CUtensorMap *map, void *base, int n, int s, int cb, size_t amp, int B)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return fail(AAQAOA_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable from the driver");
+    cuuint64_t dims[5] = {16, (cuuint64_t)1 << (s - cb), 32, 16, ((cuuint64_t)1 << (n - s - 9)) * (cuuint64_t)B};
+    cuuint64_t strides[4] = {128, ((cuuint64_t)1 << s) * amp, ((cuuint64_t)1 << (s + 5)) * amp,
+                             ((cuuint64_t)1 << (s + 9)) * amp};
+    cuuint32_t box[5] = {16, 1, 32, 16, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(AAQAOA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for n=%d s=%d", (int)r, n, s);
+    return AAQAOA_OK;
+}
+
+void build_passes(aaqaoa_plan *pl)
+{
+    pl->passes.clear();
+    if (pl->small())
+        return;
+    const int T = pl->T(), CB = pl->CB(), n = pl->n;
+    pl->passes.push_back({CB, 1, 0x1FF});
+    int covered = T;
+    while (covered < n) {
+        const int s = covered < n - 9 ? covered : n - 9;
+        int hm = 0;
+        for (int j = 0; j < 9; j++)
+            if (s + j >= covered && s + j < n)
+                hm |= 1 << j;
+        pl->passes.push_back({s, 0, hm});
+        covered = s + 9;
+    }
+}
+
+PassArgs base_args(const aaqaoa_plan *pl, int obs)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = pl->n;
+    a.tiles = pl->tiles();
+    a.p = pl->p;
+    a.tab_len = pl->tab_len();
+    a.amp0 = std::pow(2.0, -0.5 * pl->n);
+    a.tab = pl->d_tab();
+    a.cs = pl->d_cs();
+    a.partials = pl->d_partials();
+    a.counter = pl->d_counter_pass();
+    a.out = pl->d_out();
+    a.out_stride = pl->out_stride();
+    a.slot_idx[0] = a.slot_idx[1] = -1;
+    a.err = pl->d_err();
+    a.obs = pl->obs[obs];
+    a.cost = pl->cost;
+    return a;
+}
+
+enum FwdMode { FWD_ENERGY, FWD_GRAD, FWD_STATE };
+
+int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
+{
+    const int np = (int)pl->passes.size();
+    for (int l = 0; l < pl->p; l++) {
+        for (int k = 0; k < np; k++) {
+            const Pass &ps = pl->passes[k];
+            PassArgs a = base_args(pl, obs);
+            a.s = ps.s;
+            a.is_low = ps.is_low;
+            a.hmask = ps.hmask;
+            a.layer = l;
+            a.sign_s = 1.0;
+            a.load = !(l == 0 && k == 0);
+            a.pre_phase = (k == 0);
+            a.nvec_io = 1;
+            const bool last = (l == pl->p - 1 && k == np - 1);
+            a.write = !(last && mode == FWD_ENERGY);
+            a.post = !last ? 0 : mode == FWD_ENERGY ? POST_REDUCE : mode == FWD_GRAD ? (POST_REDUCE | POST_LAMBDA) : 0;
+            if (last && mode != FWD_STATE) {
+                a.slot_idx[0] = 0;
+                a.slot_scale[0] = 1.0;
+            }
+            const int nbuf = (a.post & POST_LAMBDA) ? 2 : 1;
+            const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
+            ProfScope ps_(pl, PK_FWD, S * ((a.load ? 1 : 0) + (a.write ? nbuf : 0)));
+            CKL(launch_pass(pl->c128, 1, nbuf, pl->map_phi[k], pl->map_lam[k], a, B, pl->stream), "forward pass");
+            pl->launches++;
+        }
+    }
+    return AAQAOA_OK;
+}
+
+int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
+{
+    const int np = (int)pl->passes.size();
+    for (int l = pl->p - 1; l >= 0; l--) {
+        for (int kk = np - 1; kk >= 0; kk--) {
+            const Pass &ps = pl->passes[kk];
+            const bool last_of_layer = (kk == 0);
+            PassArgs a = base_args(pl, obs);
+            a.s = ps.s;
+            a.is_low = ps.is_low;
+            a.hmask = ps.hmask;
+            a.layer = l;
+            a.sign_s = -1.0;
+            a.load = 1;
+            a.pre_phase = 0;
+            a.nvec_io = 2;
+            a.post = last_of_layer ? (POST_GAMMA | (l > 0 ? POST_PHASE_CONJ : 0)) : 0;
+            a.write = !(last_of_layer && l == 0);
+            a.slot_idx[0] = 1 + pl->p + l;
+            a.slot_scale[0] = 2.0;
+            if (last_of_layer) {
+                a.slot_idx[1] = 1 + l;
+                a.slot_scale[1] = 2.0;
+            }
+            const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
+            ProfScope ps_(pl, PK_ADJ, S * (2 + (a.write ? 2 : 0)));
+            CKL(launch_pass(pl->c128, 2, 2, pl->map_phi[kk], pl->map_lam[kk], a, B, pl->stream), "adjoint pass");
+            pl->launches++;
+        }
+    }
+    return AAQAOA_OK;
+}
+
+SmallArgs small_args(const aaqaoa_plan *pl, int obs, int mode, int write_state)
+{
+    SmallArgs s;
+    memset(&s, 0, sizeof s);
+    s.n = pl->n;
+    s.p = pl->p;
+    s.tab_len = pl->tab_len();
+    s.mode = mode;
+    s.write_state = write_state;
+    s.amp0 = std::pow(2.0, -0.5 * pl->n);
+    s.tab = pl->d_tab();
+    s.cs = pl->d_cs();
+    s.out = pl->d_out();
+    s.out_stride = pl->out_stride();
+    s.state = pl->d_phi();
+    s.obs = pl->obs[obs];
+    s.cost = pl->cost;
+    return s;
+}
+
+int check_ready(aaqaoa_plan *pl, int obs, bool grad, int B)
+{
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    if (!pl->ws)
+        return fail(AAQAOA_ERR_WORKSPACE, "no workspace set (aaqaoa_set_workspace)");
+    if (obs != AAQAOA_OBS_FULL && obs != AAQAOA_OBS_RED)
+        return fail(AAQAOA_ERR_INVALID_ARG, "observable %d unknown", obs);
+    if (obs == AAQAOA_OBS_RED && pl->num_orbits == 0)
+        return fail(AAQAOA_ERR_INVALID_ARG, "H_red requested but the plan has no edge orbits");
+    if (grad && !pl->ws_grad)
+        return fail(AAQAOA_ERR_WORKSPACE, "workspace was set without room for the gradient");
+    if (B < 1 || B > pl->cap)
+        return fail(AAQAOA_ERR_INVALID_ARG, "batch %d outside [1, %d] (workspace capacity)", B, pl->cap);
+    return AAQAOA_OK;
+}
+
+// parameters already in device memory (point-major B x p)
+int enqueue_params(aaqaoa_plan *pl, int B, const double *d_gamma, const double *d_beta)
+{
+    (void)cudaGetLastError();  // a stale error of an unrelated earlier call must not be reported here
+    ProfScope ps_(pl, PK_PARAMS, 0.0);
+    CKL(launch_params(pl->c128, B, pl->p, pl->tab_len(), d_gamma, d_beta, pl->d_tab(), pl->d_cs(), pl->stream),
+        "parameter tables");
+    pl->launches++;
+    CK(cudaMemsetAsync(pl->d_out(), 0, (size_t)B * pl->out_stride() * sizeof(double), pl->stream));
+    return AAQAOA_OK;
+}
+
+int enqueue_aggregate(aaqaoa_plan *pl, int obs, int agg)
+{
+    const bool c128 = pl->c128;
+    const int grid = pl->n < 10 ? 1 : agg_grid(c128);
+    CK(cudaMemsetAsync(pl->d_out(), 0, sizeof(double), pl->stream));
+    AggArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = pl->n;
+    a.chunks = pl->n < 10 ? 0 : ((uint64_t)1 << (pl->n - 10));
+    a.state = pl->d_phi();
+    a.partials = pl->d_partials();
+    a.counter = pl->d_counter_agg();
+    a.out_energy = pl->d_out();
+    const double S = (double)((size_t)1 << pl->n) * (double)pl->amp();
+    if (agg == AAQAOA_AGG_SINGLEPASS) {
+        a.obs = pl->obs[obs];
+        ProfScope ps_(pl, PK_AGG, S);
+        CKL(launch_agg_fused(c128, a, pl->stream, grid), "single-pass aggregation");
+        pl->launches++;
+        return AAQAOA_OK;
+    }
+    // per-term passes: Eq. (agg) over all edges (H_C) or the representatives (H_red)
+    const int nterms = obs == AAQAOA_OBS_FULL ? pl->m : pl->num_orbits;
+    for (int t = 0; t < nterms; t++) {
+        const int e = obs == AAQAOA_OBS_FULL ? t : pl->orbit_rep[t];
+        a.num_terms = 1;
+        a.term_u[0] = pl->edges[2 * e];
+        a.term_v[0] = pl->edges[2 * e + 1];
+        a.term_w[0] = obs == AAQAOA_OBS_FULL ? 1.0 : (double)pl->orbit_weight[t];
+        ProfScope ps_(pl, PK_AGG, S);
+        CKL(launch_agg_terms(c128, a, pl->stream, grid), "per-term aggregation");
+        pl->launches++;
+    }
+    return AAQAOA_OK;
+}
+
+int enqueue_expect(aaqaoa_plan *pl, int B, const double *d_gamma, const double *d_beta, int obs, int agg)
+{
+    int r = enqueue_params(pl, B, d_gamma, d_beta);
+    if (r)
+        return r;
+    const bool materialise = agg != AAQAOA_AGG_FUSED;
+    if (pl->small()) {
+        SmallArgs s = small_args(pl, obs, SMALL_ENERGY, materialise ? 1 : 0);
+        ProfScope ps_(pl, PK_SMALL, materialise ? (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp() : 0.0);
+        CKL(launch_small(pl->c128, s, B, pl->stream), "whole-circuit kernel");
+        pl->launches++;
+    } else {
+        r = enqueue_forward(pl, B, obs, materialise ? FWD_STATE : FWD_ENERGY);
+        if (r)
+            return r;
+    }
+    if (materialise) {
+        pl->state_valid = true;
+        return enqueue_aggregate(pl, obs, agg);
+    }
+    return AAQAOA_OK;
+}
+
+int enqueue_grad(aaqaoa_plan *pl, const double *d_gamma, const double *d_beta, int obs)
+{
+    int r = enqueue_params(pl, 1, d_gamma, d_beta);
+    if (r)
+        return r;
+    if (pl->small()) {
+        SmallArgs s = small_args(pl, obs, SMALL_GRAD, 0);
+        ProfScope ps_(pl, PK_SMALL, 0.0);
+        CKL(launch_small(pl->c128, s, 1, pl->stream), "whole-circuit kernel");
+        pl->launches++;
+        return AAQAOA_OK;
+    }
+    r = enqueue_forward(pl, 1, obs, FWD_GRAD);
+    if (r)
+        return r;
+    pl->state_valid = false;
+    return enqueue_backward(pl, 1, obs);
+}
+
+// copy [err | pad | out rows] back and check the device error flag
+int fetch_out(aaqaoa_plan *pl, int B, std::vector<double> &rows)
+{
+    const size_t nout = (size_t)B * pl->out_stride();
+    rows.resize(nout);
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, pl->d_err(), sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
+    CK(cudaMemcpyAsync(rows.data(), pl->d_out(), nout * sizeof(double), cudaMemcpyDeviceToHost, pl->stream));
+    CK(cudaStreamSynchronize(pl->stream));
+    if (err) {
+        cudaMemsetAsync(pl->ws + pl->L.ctrl, 0, 256, pl->stream);
+        cudaStreamSynchronize(pl->stream);
+        return fail(AAQAOA_ERR_TIMEOUT, "a bounded device wait expired (TMA tile never arrived)");
+    }
+    return AAQAOA_OK;
+}
+
+int upload_params(aaqaoa_plan *pl, int B, const double *gamma, const double *beta)
+{
+    if (!gamma || !beta)
+        return fail(AAQAOA_ERR_INVALID_ARG, "gamma/beta is NULL");
+    const size_t bytes = (size_t)B * pl->p * sizeof(double);
+    double *dg = pl->d_params(), *db = pl->d_params() + (size_t)B * pl->p;
+    CK(cudaMemcpyAsync(dg, gamma, bytes, cudaMemcpyHostToDevice, pl->stream));
+    CK(cudaMemcpyAsync(db, beta, bytes, cudaMemcpyHostToDevice, pl->stream));
+    return AAQAOA_OK;
+}
+
+CutFn make_cutfn(int n, const std::vector<std::pair<std::pair<int, int>, int>> &wedges)
+{
+    CutFn f;
+    memset(&f, 0, sizeof f);
+    std::map<int, int> cls;
+    for (auto &we : wedges)
+        cls.emplace(we.second, 0);
+    if ((int)cls.size() <= MAXK) {
+        int c = 0;
+        for (auto &kv : cls) {
+            kv.second = c;
+            f.w[c] = kv.first;
+            c++;
+        }
+        f.K = c;
+        for (auto &we : wedges) {
+            const int c2 = cls[we.second], u = we.first.first, v = we.first.second;
+            f.nbr[c2][u] |= 1ull << v;
+            f.nbr[c2][v] |= 1ull << u;
+        }
+    } else {  // binary digits of the weights (all < 2^10 because they sum to |E| <= 561)
+        f.K = MAXK;
+        for (int bit = 0; bit < MAXK; bit++)
+            f.w[bit] = 1 << bit;
+        for (auto &we : wedges)
+            for (int bit = 0; bit < MAXK; bit++)
+                if ((we.second >> bit) & 1) {
+                    f.nbr[bit][we.first.first] |= 1ull << we.first.second;
+                    f.nbr[bit][we.first.second] |= 1ull << we.first.first;
+                }
+    }
+    (void)n;
+    return f;
+}
+
+}  // namespace
+
+// ================================================================== ABI
+extern "C" {
+
+const char *aaqaoa_strerror(int code)
+{
+    switch (code) {
+    case AAQAOA_OK: return "success";
+    case AAQAOA_ERR_INVALID_ARG: return "invalid argument";
+    case AAQAOA_ERR_BAD_ORBITS: return "edge-orbit data do not partition the edge set";
+    case AAQAOA_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case AAQAOA_ERR_CUDA: return "CUDA error";
+    case AAQAOA_ERR_TIMEOUT: return "bounded device wait expired";
+    case AAQAOA_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown error code";
+    }
+}
+
+const char *aaqaoa_last_error_detail(void) { return g_detail.c_str(); }
+
+int aaqaoa_prepare(int n, int num_edges, const int32_t *edges, int num_orbits, const int32_t *orbit_rep,
+                   const int32_t *orbit_weight, const int32_t *edge_orbit, int p, unsigned flags, void *stream,
+                   aaqaoa_plan **out)
+{
+    g_detail.clear();
+    if (!out)
+        return fail(AAQAOA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > AAQAOA_MAX_QUBITS)
+        return fail(AAQAOA_ERR_INVALID_ARG, "n=%d outside [1, %d]", n, AAQAOA_MAX_QUBITS);
+    if (p < 1 || p > 64)
+        return fail(AAQAOA_ERR_INVALID_ARG, "p=%d outside [1, 64]", p);
+    if (flags != AAQAOA_C64 && flags != AAQAOA_C128)
+        return fail(AAQAOA_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    if (num_edges < 0 || (long long)num_edges > (long long)n * (n - 1) / 2)
+        return fail(AAQAOA_ERR_INVALID_ARG, "num_edges=%d impossible for n=%d", num_edges, n);
+    if (num_edges > 0 && !edges)
+        return fail(AAQAOA_ERR_INVALID_ARG, "edges is NULL");
+    std::vector<int32_t> e(2 * (size_t)num_edges);
+    uint64_t adj[AAQAOA_MAX_QUBITS] = {0};
+    for (int i = 0; i < num_edges; i++) {
+        int u = edges[2 * i], v = edges[2 * i + 1];
+        if (u < 0 || u >= n || v < 0 || v >= n)
+            return fail(AAQAOA_ERR_INVALID_ARG, "edge %d = (%d, %d) has a vertex outside [0, %d)", i, u, v, n);
+        if (u == v)
+            return fail(AAQAOA_ERR_INVALID_ARG, "edge %d is a self-loop on %d", i, u);
+        if (u > v)
+            std::swap(u, v);
+        if ((adj[u] >> v) & 1ull)
+            return fail(AAQAOA_ERR_INVALID_ARG, "edge %d = (%d, %d) is repeated", i, u, v);
+        adj[u] |= 1ull << v;
+        adj[v] |= 1ull << u;
+        e[2 * i] = u;
+        e[2 * i + 1] = v;
+    }
+    if (num_orbits < 0)
+        return fail(AAQAOA_ERR_BAD_ORBITS, "num_orbits=%d < 0", num_orbits);
+    if (num_orbits > 0) {
+        if (!orbit_rep || !orbit_weight)
+            return fail(AAQAOA_ERR_BAD_ORBITS, "orbit_rep / orbit_weight is NULL");
+        if (num_orbits > num_edges)
+            return fail(AAQAOA_ERR_BAD_ORBITS, "more orbits (%d) than edges (%d)", num_orbits, num_edges);
+        long long sum = 0;
+        std::vector<char> isrep(num_edges, 0);
+        for (int c = 0; c < num_orbits; c++) {
+            if (orbit_rep[c] < 0 || orbit_rep[c] >= num_edges)
+                return fail(AAQAOA_ERR_BAD_ORBITS, "orbit %d representative %d is not an edge index", c, orbit_rep[c]);
+            if (isrep[orbit_rep[c]])
+                return fail(AAQAOA_ERR_BAD_ORBITS, "edge %d represents two orbits", orbit_rep[c]);
+            isrep[orbit_rep[c]] = 1;
+            if (orbit_weight[c] < 1)
+                return fail(AAQAOA_ERR_BAD_ORBITS, "orbit %d has weight %d < 1", c, orbit_weight[c]);
+            sum += orbit_weight[c];
+        }
+        if (sum != num_edges)
+            return fail(AAQAOA_ERR_BAD_ORBITS, "orbit weights sum to %lld, not |E| = %d", sum, num_edges);
+        if (edge_orbit) {
+            std::vector<int> count(num_orbits, 0);
+            for (int i = 0; i < num_edges; i++) {
+                if (edge_orbit[i] < 0 || edge_orbit[i] >= num_orbits)
+                    return fail(AAQAOA_ERR_BAD_ORBITS, "edge %d has orbit %d outside [0, %d)", i, edge_orbit[i],
+                                num_orbits);
+                count[edge_orbit[i]]++;
+            }
+            for (int c = 0; c < num_orbits; c++) {
+                if (edge_orbit[orbit_rep[c]] != c)
+                    return fail(AAQAOA_ERR_BAD_ORBITS, "representative of orbit %d lies in orbit %d", c,
+                                edge_orbit[orbit_rep[c]]);
+                if (count[c] != orbit_weight[c])
+                    return fail(AAQAOA_ERR_BAD_ORBITS, "orbit %d has %d edges but weight %d", c, count[c],
+                                orbit_weight[c]);
+            }
+        }
+    } else if (edge_orbit) {
+        return fail(AAQAOA_ERR_BAD_ORBITS, "edge_orbit given without orbits");
+    }
+
+    aaqaoa_plan *pl = new (std::nothrow) aaqaoa_plan();
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "out of host memory");
+    pl->n = n;
+    pl->m = num_edges;
+    pl->p = p;
+    pl->num_orbits = num_orbits;
+    pl->c128 = (flags == AAQAOA_C128);
+    pl->edges = e;
+    pl->orbit_rep.assign(orbit_rep, orbit_rep + num_orbits);
+    pl->orbit_weight.assign(orbit_weight, orbit_weight + num_orbits);
+    pl->stream = (cudaStream_t)stream;
+    for (int u = 0; u < n; u++)
+        pl->cost.nbr[u] = adj[u];
+    std::vector<std::pair<std::pair<int, int>, int>> full, red;
+    for (int i = 0; i < num_edges; i++)
+        full.push_back({{e[2 * i], e[2 * i + 1]}, 1});
+    for (int c = 0; c < num_orbits; c++) {
+        const int i = orbit_rep[c];
+        red.push_back({{e[2 * i], e[2 * i + 1]}, orbit_weight[c]});
+    }
+    pl->obs[AAQAOA_OBS_FULL] = make_cutfn(n, full);
+    pl->obs[AAQAOA_OBS_RED] = make_cutfn(n, red);
+    build_passes(pl);
+    *out = pl;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_workspace_bytes(const aaqaoa_plan *plan, int batch, int with_grad, size_t *bytes)
+{
+    if (!plan || !bytes || batch < 1)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan/bytes NULL or batch < 1");
+    *bytes = layout(plan, batch, with_grad != 0).total;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_set_workspace(aaqaoa_plan *pl, void *device_ptr, size_t bytes, int batch, int with_grad)
+{
+    if (!pl || batch < 1)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan NULL or batch < 1");
+    if (!device_ptr || ((uintptr_t)device_ptr & 255))
+        return fail(AAQAOA_ERR_WORKSPACE, "workspace pointer NULL or not 256-byte aligned");
+    Layout L = layout(pl, batch, with_grad != 0);
+    if (bytes < L.total)
+        return fail(AAQAOA_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", bytes, L.total);
+    pl->ws = (unsigned char *)device_ptr;
+    pl->ws_bytes = bytes;
+    pl->cap = batch;
+    pl->ws_grad = with_grad != 0;
+    pl->L = L;
+    pl->state_valid = false;
+    pl->map_phi.assign(pl->passes.size(), CUtensorMap{});
+    pl->map_lam.assign(pl->passes.size(), CUtensorMap{});
+    for (size_t k = 0; k < pl->passes.size(); k++) {
+        int r = make_map(&pl->map_phi[k], pl->d_phi(), pl->n, pl->passes[k].s, pl->CB(), pl->amp(), batch);
+        if (r)
+            return r;
+        // the lambda map is used by gradient launches and by the forward pass that writes lambda
+        void *lam = with_grad ? pl->d_lam() : pl->d_phi();
+        r = make_map(&pl->map_lam[k], lam, pl->n, pl->passes[k].s, pl->CB(), pl->amp(), batch);
+        if (r)
+            return r;
+    }
+    CK(cudaMemsetAsync(pl->ws + L.ctrl, 0, 256, pl->stream));
+    CK(cudaStreamSynchronize(pl->stream));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_set_stream(aaqaoa_plan *pl, void *stream)
+{
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    pl->stream = (cudaStream_t)stream;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_expect(aaqaoa_plan *pl, const double *gamma, const double *beta, int observable, int agg_mode,
+                  double *energy)
+{
+    g_detail.clear();
+    int r = check_ready(pl, observable, false, 1);
+    if (r)
+        return r;
+    if (agg_mode < AAQAOA_AGG_FUSED || agg_mode > AAQAOA_AGG_SINGLEPASS)
+        return fail(AAQAOA_ERR_INVALID_ARG, "agg_mode %d unknown", agg_mode);
+    if (!energy)
+        return fail(AAQAOA_ERR_INVALID_ARG, "energy is NULL");
+    pl->launches = 0;
+    if ((r = upload_params(pl, 1, gamma, beta)))
+        return r;
+    if ((r = enqueue_expect(pl, 1, pl->d_params(), pl->d_params() + pl->p, observable, agg_mode)))
+        return r;
+    std::vector<double> rows;
+    if ((r = fetch_out(pl, 1, rows)))
+        return r;
+    *energy = rows[0];
+    return AAQAOA_OK;
+}
+
+int aaqaoa_grad(aaqaoa_plan *pl, const double *gamma, const double *beta, int observable, double *energy,
+                double *dgamma, double *dbeta)
+{
+    g_detail.clear();
+    int r = check_ready(pl, observable, true, 1);
+    if (r)
+        return r;
+    if (!energy || !dgamma || !dbeta)
+        return fail(AAQAOA_ERR_INVALID_ARG, "output pointer is NULL");
+    pl->launches = 0;
+    if ((r = upload_params(pl, 1, gamma, beta)))
+        return r;
+    if ((r = enqueue_grad(pl, pl->d_params(), pl->d_params() + pl->p, observable)))
+        return r;
+    std::vector<double> rows;
+    if ((r = fetch_out(pl, 1, rows)))
+        return r;
+    *energy = rows[0];
+    for (int l = 0; l < pl->p; l++) {
+        dgamma[l] = rows[1 + l];
+        dbeta[l] = rows[1 + pl->p + l];
+    }
+    return AAQAOA_OK;
+}
+
+int aaqaoa_expect_batch(aaqaoa_plan *pl, int B, const double *gamma, const double *beta, int observable,
+                        double *energy)
+{
+    g_detail.clear();
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    if (B < 1 || !energy)
+        return fail(AAQAOA_ERR_INVALID_ARG, "B < 1 or energy NULL");
+    int r = check_ready(pl, observable, false, 1);
+    if (r)
+        return r;
+    pl->launches = 0;
+    std::vector<double> rows;
+    for (int b0 = 0; b0 < B; b0 += pl->cap) {
+        const int Bw = B - b0 < pl->cap ? B - b0 : pl->cap;
+        if ((r = upload_params(pl, Bw, gamma + (size_t)b0 * pl->p, beta + (size_t)b0 * pl->p)))
+            return r;
+        if ((r = enqueue_expect(pl, Bw, pl->d_params(), pl->d_params() + (size_t)Bw * pl->p, observable,
+                                AAQAOA_AGG_FUSED)))
+            return r;
+        if ((r = fetch_out(pl, Bw, rows)))
+            return r;
+        for (int b = 0; b < Bw; b++)
+            energy[b0 + b] = rows[(size_t)b * pl->out_stride()];
+    }
+    return AAQAOA_OK;
+}
+
+int aaqaoa_expect_device(aaqaoa_plan *pl, int B, const double *d_gamma, const double *d_beta, int observable,
+                         double *d_energy)
+{
+    g_detail.clear();
+    int r = check_ready(pl, observable, false, B);
+    if (r)
+        return r;
+    if (!d_gamma || !d_beta || !d_energy)
+        return fail(AAQAOA_ERR_INVALID_ARG, "device pointer is NULL");
+    pl->launches = 0;
+    if ((r = enqueue_expect(pl, B, d_gamma, d_beta, observable, AAQAOA_AGG_FUSED)))
+        return r;
+    CK(cudaMemcpy2DAsync(d_energy, sizeof(double), pl->d_out(), pl->out_stride() * sizeof(double), sizeof(double),
+                         B, cudaMemcpyDeviceToDevice, pl->stream));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_grad_device(aaqaoa_plan *pl, const double *d_gamma, const double *d_beta, int observable, double *d_out)
+{
+    g_detail.clear();
+    int r = check_ready(pl, observable, true, 1);
+    if (r)
+        return r;
+    if (!d_gamma || !d_beta || !d_out)
+        return fail(AAQAOA_ERR_INVALID_ARG, "device pointer is NULL");
+    pl->launches = 0;
+    if ((r = enqueue_grad(pl, d_gamma, d_beta, observable)))
+        return r;
+    CK(cudaMemcpyAsync(d_out, pl->d_out(), pl->out_stride() * sizeof(double), cudaMemcpyDeviceToDevice, pl->stream));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_sync(aaqaoa_plan *pl)
+{
+    if (!pl || !pl->ws)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan NULL or without workspace");
+    std::vector<double> rows;
+    return fetch_out(pl, 1, rows);
+}
+
+int aaqaoa_statevector(aaqaoa_plan *pl, const double *gamma, const double *beta, void *host_out)
+{
+    g_detail.clear();
+    int r = check_ready(pl, AAQAOA_OBS_FULL, false, 1);
+    if (r)
+        return r;
+    if (!host_out)
+        return fail(AAQAOA_ERR_INVALID_ARG, "host_out is NULL");
+    pl->launches = 0;
+    if ((r = upload_params(pl, 1, gamma, beta)))
+        return r;
+    if ((r = enqueue_params(pl, 1, pl->d_params(), pl->d_params() + pl->p)))
+        return r;
+    if (pl->small()) {
+        SmallArgs s = small_args(pl, AAQAOA_OBS_FULL, SMALL_ENERGY, 1);
+        CKL(launch_small(pl->c128, s, 1, pl->stream), "whole-circuit kernel");
+        pl->launches++;
+    } else if ((r = enqueue_forward(pl, 1, AAQAOA_OBS_FULL, FWD_STATE))) {
+        return r;
+    }
+    pl->state_valid = true;
+    std::vector<double> rows;
+    if ((r = fetch_out(pl, 1, rows)))
+        return r;
+    CK(cudaMemcpy(host_out, pl->d_phi(), ((size_t)1 << pl->n) * pl->amp(), cudaMemcpyDeviceToHost));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_edge_zz(aaqaoa_plan *pl, const double *gamma, const double *beta, double *zz)
+{
+    g_detail.clear();
+    int r = check_ready(pl, AAQAOA_OBS_FULL, false, 1);
+    if (r)
+        return r;
+    if (!zz)
+        return fail(AAQAOA_ERR_INVALID_ARG, "zz is NULL");
+    pl->launches = 0;
+    if ((r = upload_params(pl, 1, gamma, beta)))
+        return r;
+    if ((r = enqueue_params(pl, 1, pl->d_params(), pl->d_params() + pl->p)))
+        return r;
+    if (pl->small()) {
+        SmallArgs s = small_args(pl, AAQAOA_OBS_FULL, SMALL_ENERGY, 1);
+        CKL(launch_small(pl->c128, s, 1, pl->stream), "whole-circuit kernel");
+        pl->launches++;
+    } else if ((r = enqueue_forward(pl, 1, AAQAOA_OBS_FULL, FWD_STATE))) {
+        return r;
+    }
+    pl->state_valid = true;
+    const int grid = pl->n < 10 ? 1 : agg_grid(pl->c128);
+    for (int t0 = 0; t0 < pl->m; t0 += 64) {
+        AggArgs a;
+        memset(&a, 0, sizeof a);
+        a.n = pl->n;
+        a.chunks = pl->n < 10 ? 0 : ((uint64_t)1 << (pl->n - 10));
+        a.state = pl->d_phi();
+        a.partials = pl->d_partials();
+        a.counter = pl->d_counter_agg();
+        a.out_terms = pl->d_zz() + t0;
+        a.out_energy = pl->d_out();
+        a.num_terms = pl->m - t0 < 64 ? pl->m - t0 : 64;
+        for (int t = 0; t < a.num_terms; t++) {
+            a.term_u[t] = pl->edges[2 * (t0 + t)];
+            a.term_v[t] = pl->edges[2 * (t0 + t) + 1];
+            a.term_w[t] = 1.0;
+        }
+        CKL(launch_agg_terms(pl->c128, a, pl->stream, grid), "edge <ZZ> pass");
+        pl->launches++;
+    }
+    std::vector<double> rows;
+    if ((r = fetch_out(pl, 1, rows)))
+        return r;
+    if (pl->m > 0)
+        CK(cudaMemcpy(zz, pl->d_zz(), pl->m * sizeof(double), cudaMemcpyDeviceToHost));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_aggregate_only(aaqaoa_plan *pl, int observable, int agg_mode, double *energy)
+{
+    g_detail.clear();
+    int r = check_ready(pl, observable, false, 1);
+    if (r)
+        return r;
+    if (!energy)
+        return fail(AAQAOA_ERR_INVALID_ARG, "energy is NULL");
+    if (agg_mode != AAQAOA_AGG_PERTERM && agg_mode != AAQAOA_AGG_SINGLEPASS)
+        return fail(AAQAOA_ERR_INVALID_ARG, "aggregate_only needs PERTERM or SINGLEPASS");
+    if (!pl->state_valid)
+        return fail(AAQAOA_ERR_INVALID_ARG, "no stored state: run aaqaoa_statevector or a non-fused expect first");
+    pl->launches = 0;
+    if ((r = enqueue_aggregate(pl, observable, agg_mode)))
+        return r;
+    std::vector<double> rows;
+    if ((r = fetch_out(pl, 1, rows)))
+        return r;
+    *energy = rows[0];
+    return AAQAOA_OK;
+}
+
+int aaqaoa_plan_info(const aaqaoa_plan *pl, int *n, int *p, int *num_edges, int *num_orbits, unsigned *flags)
+{
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    if (n) *n = pl->n;
+    if (p) *p = pl->p;
+    if (num_edges) *num_edges = pl->m;
+    if (num_orbits) *num_orbits = pl->num_orbits;
+    if (flags) *flags = pl->c128 ? AAQAOA_C128 : AAQAOA_C64;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_launch_count(const aaqaoa_plan *pl, int *launches)
+{
+    if (!pl || !launches)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan or launches NULL");
+    *launches = pl->launches;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_profile_enable(aaqaoa_plan *pl, int enable)
+{
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    for (auto &r : pl->prof_recs) {
+        pl->prof_pool.push_back(r.a);
+        pl->prof_pool.push_back(r.b);
+    }
+    pl->prof_recs.clear();
+    pl->prof = enable != 0;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_profile_read(aaqaoa_plan *pl, int kind, double *ms_total, int *launches, double *bytes)
+{
+    if (!pl || kind < 0 || kind >= PK_COUNT)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan NULL or kind %d unknown", kind);
+    CK(cudaStreamSynchronize(pl->stream));
+    double ms = 0.0, by = 0.0;
+    int cnt = 0;
+    for (auto &r : pl->prof_recs) {
+        if (r.kind != kind)
+            continue;
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, r.a, r.b));
+        ms += t;
+        by += r.bytes;
+        cnt++;
+    }
+    if (ms_total) *ms_total = ms;
+    if (launches) *launches = cnt;
+    if (bytes) *bytes = by;
+    return AAQAOA_OK;
+}
+
+void aaqaoa_destroy(aaqaoa_plan *pl)
+{
+    if (!pl)
+        return;
+    for (auto &r : pl->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : pl->prof_pool)
+        cudaEventDestroy(e);
+    delete pl;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the host side (aaqaoa_host.cu) and the
+// kernels (aaqaoa_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aaq {
+
+constexpr int MAXN = 34;   // qubits
+constexpr int MAXK = 10;   // weight classes of a weighted cut function
+constexpr int MAXTAB = 562; // |E| + 1 for K_34
+
+// A weighted cut function O(x) = sum_c w[c] * sum_{edges (u,v) of class c} [x_u != x_v],
+// stored as per-class vertex neighbour masks. H_C is the single class of all
+// edges at weight 1; H_red groups the orbit representatives by weight.
+struct CutFn {
+    int K;
+    int w[MAXK];
+    uint64_t nbr[MAXK][MAXN];
+};
+
+// The cost function C(x) of the ansatz: one class, unit weight.
+struct CostFn {
+    uint64_t nbr[MAXN];
+};
+
+// Operations of one tiled pass over the statevector(s).
+enum PostOp : int {
+    POST_REDUCE = 1,      // acc0 += |phi|^2 O(x)                 (energy)
+    POST_LAMBDA = 2,      // write lambda = O(x) phi as a second vector
+    POST_GAMMA = 4,       // acc1 += C(x) Im(conj(lambda) phi)     (dE/dgamma)
+    POST_PHASE_CONJ = 8,  // phi, lambda *= exp(+i gamma_l C(x))   (undo cost layer)
+};
+
+struct PassArgs {
+    int n;            // qubits
+    int s;            // global bit of local high bit 0
+    int is_low;       // tile is contiguous and the low bits are transformed here
+    int hmask;        // which of the 9 local high bits receive a butterfly
+    int tiles;        // tiles per statevector = 2^(n - tile_bits)
+    int load;         // 1: TMA-load the tile(s); 0: generate |+>^n
+    int pre_phase;    // multiply by the cost-layer phase before any butterfly
+    int write;        // TMA-store the tile(s) after the last stage
+    int post;         // PostOp flags
+    int nvec_io;      // vectors loaded (1 or 2)
+    int layer;        // layer l (0-based): selects the phase table and (cos, sin)
+    int p;            // number of layers
+    int tab_len;      // |E| + 1
+    double sign_s;    // +1: exp(-i beta H_M); -1: its inverse
+    double amp0;      // 2^(-n/2) for the generated |+>^n
+    const void *tab;  // phase tables [B][p][tab_len], complex in the amplitude precision
+    const double2 *cs;  // [B][p] (cos beta_l, sin beta_l)
+    double *partials; // [2][B][tiles]
+    unsigned *counter;  // last-block counter (zero between launches)
+    double *out;      // [B][out_stride]
+    int out_stride;
+    int slot_idx[2];  // output index (within a point's row) of slot 0 / 1, or -1
+    double slot_scale[2];
+    int *err;         // device error flag
+    CutFn obs;        // observable of the reduction / lambda
+    CostFn cost;      // C(x) for the phase and dE/dgamma
+};
+
+// Whole-circuit kernel for states that fit one CTA's shared memory.
+enum SmallMode : int { SMALL_ENERGY = 0, SMALL_GRAD = 1 };
+
+struct SmallArgs {
+    int n, p, tab_len, mode;
+    int write_state;   // also store psi_p to `state`
+    double amp0;
+    const void *tab;
+    const double2 *cs;
+    double *out;       // [B][out_stride]
+    int out_stride;
+    void *state;       // [B][2^n] (optional)
+    CutFn obs;
+    CostFn cost;
+};
+
+// Aggregation over a stored statevector.
+struct AggArgs {
+    int n;
+    uint64_t chunks;     // number of 1024-amplitude chunks (per state)
+    const void *state;
+    double *partials;    // [T][grid]
+    unsigned *counter;
+    double *out_terms;   // per-term <Z_u Z_v>, or nullptr
+    double *out_energy;  // accumulates sum_t w_t (1 - zz_t)/2 or sum |psi|^2 O(x)
+    int num_terms;       // terms of this launch
+    int term_u[64], term_v[64];
+    double term_w[64];
+    CutFn obs;           // fused mode
+};
+
+// Launchers (aaqaoa_kernels.cu). They return a cudaError_t as int.
+int tile_bits(bool c128);
+size_t pass_smem_bytes(bool c128, int nvec_buffers);
+int launch_params(bool c128, int B, int p, int tab_len, const double *d_gamma, const double *d_beta,
+                  void *d_tab, double2 *d_cs, cudaStream_t st);
+int launch_pass(bool c128, int nv_kernel, int nbuf, const CUtensorMap &m0, const CUtensorMap &m1,
+                const PassArgs &a, int B, cudaStream_t st);
+int launch_small(bool c128, const SmallArgs &a, int B, cudaStream_t st);
+size_t small_smem_bytes(bool c128, int n, int mode);
+int small_max_qubits(bool c128, int mode);
+int launch_agg_fused(bool c128, const AggArgs &a, cudaStream_t st, int grid);
+int launch_agg_terms(bool c128, const AggArgs &a, cudaStream_t st, int grid);
+int agg_grid(bool c128);
+
+}  // namespace aaq

@@ -21,7 +21,7 @@ generator to every dequeued edge, normalising the image to (min, max), and
 adds images that are unclassified edges.
 
 The representative of each class is its seed edge, which is the lowest-indexed
-edge of the class (the paper picks a random representative, Sec. 3.3; any
+edge of the class (the paper picks a random representative, Sec. 5.4; any
 member gives the same expectation because of Eq. (A3)).
 """
 from __future__ import annotations

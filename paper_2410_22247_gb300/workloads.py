@@ -4,8 +4,8 @@ This module only builds inputs (edge lists, angle vectors, batches). It holds
 none of the QAOA arithmetic, so both the CUDA path and the CPU oracle may take
 their inputs from it.
 
-Graph families follow the ones the paper benchmarks on (Sec. 5, Tables 1-5 and
-the diagnostic-control / non-tree tables of Sec. 5.1): heap-ordered binary
+Graph families follow the ones the paper benchmarks on (Sec. 6, Tables 1-5 and
+the diagnostic-control / non-tree tables of Sec. 6.1): heap-ordered binary
 trees, complete r-ary ("balanced") trees, stars, complete graphs K_n, cycles,
 the generalized Petersen graph GP(5,2), circulants, random 3-regular graphs and
 uniformly random labelled trees (Pruefer sequences). The paper does not publish

@@ -1,0 +1,116 @@
+"""The C-ABI library without a GPU: it loads, exports every declared symbol,
+and its host-side validation (no device calls) rejects malformed inputs."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2410_22247_gb300 import _native as N
+from paper_2410_22247_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "aaqaoa.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(aaqaoa_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = N.load()
+    decl = declared_symbols()
+    assert len(decl) >= 15
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(N.EXPORTED) == decl
+
+
+def _prepare(n, edges, p=1, orbits=None, flags=0):
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    h = ctypes.c_void_p()
+    rep = weight = eo = None
+    k = 0
+    if orbits is not None:
+        rep = np.ascontiguousarray(orbits[0], dtype=np.int32)
+        weight = np.ascontiguousarray(orbits[1], dtype=np.int32)
+        eo = None if len(orbits) < 3 or orbits[2] is None else np.ascontiguousarray(orbits[2], dtype=np.int32)
+        k = len(rep)
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if a is not None and a.size else None
+    rc = N.aaqaoa_prepare(n, len(e) // 2, P(e), k, P(rep), P(weight), P(eo), p, flags, None, ctypes.byref(h))
+    if rc == 0:
+        N.aaqaoa_destroy(h)
+    return rc
+
+
+def test_prepare_accepts_valid_graphs():
+    n, e = W.star_graph(6)
+    assert _prepare(n, e, orbits=([0], [5], [0] * 5)) == 0
+    assert _prepare(n, e, orbits=([0], [5])) == 0
+    assert _prepare(1, np.zeros((0, 2))) == 0
+    assert _prepare(34, W.heap_binary_tree(34)[1], p=4, flags=1) == 0
+
+
+@pytest.mark.parametrize("case,code", [
+    ("n0", -1), ("n35", -1), ("p0", -1), ("selfloop", -1), ("dup", -1), ("dup_rev", -1), ("range", -1),
+    ("flags", -1), ("wsum", -2), ("rep_range", -2), ("rep_dup", -2), ("w0", -2), ("eo_rep", -2),
+    ("eo_count", -2),
+])
+def test_prepare_rejects(case, code):
+    path = [(0, 1), (1, 2), (2, 3)]
+    args = dict(n=4, edges=path)
+    if case == "n0":
+        args = dict(n=0, edges=np.zeros((0, 2)))
+    elif case == "n35":
+        args = dict(n=35, edges=[(0, 1)])
+    elif case == "p0":
+        args["p"] = 0
+    elif case == "selfloop":
+        args["edges"] = [(0, 1), (2, 2)]
+    elif case == "dup":
+        args["edges"] = [(0, 1), (0, 1)]
+    elif case == "dup_rev":
+        args["edges"] = [(0, 1), (1, 0)]
+    elif case == "range":
+        args["edges"] = [(0, 4)]
+    elif case == "flags":
+        args["flags"] = 7
+    elif case == "wsum":
+        args["orbits"] = ([0, 1], [1, 1])
+    elif case == "rep_range":
+        args["orbits"] = ([0, 5], [2, 1])
+    elif case == "rep_dup":
+        args["orbits"] = ([0, 0], [2, 1])
+    elif case == "w0":
+        args["orbits"] = ([0, 1], [3, 0])
+    elif case == "eo_rep":
+        args["orbits"] = ([0, 1], [2, 1], [1, 1, 0])
+    elif case == "eo_count":
+        args["orbits"] = ([0, 1], [2, 1], [0, 1, 1])
+    assert _prepare(**args) == code
+    assert N.aaqaoa_last_error_detail()  # a message was recorded
+
+
+def test_workspace_size_grows_with_batch_and_gradient():
+    n, e = W.random_regular(20, 3, 1)
+    ee = np.ascontiguousarray(e.reshape(-1), dtype=np.int32)
+    h = ctypes.c_void_p()
+    assert N.aaqaoa_prepare(n, len(e), ee.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0, None, None, None,
+                            2, 0, None, ctypes.byref(h)) == 0
+    sizes = {}
+    for batch in (1, 4):
+        for grad in (0, 1):
+            s = ctypes.c_size_t()
+            assert N.aaqaoa_workspace_bytes(h, batch, grad, ctypes.byref(s)) == 0
+            sizes[batch, grad] = s.value
+    N.aaqaoa_destroy(h)
+    state = (1 << 20) * 8
+    assert sizes[1, 0] > state and sizes[1, 1] > 2 * state
+    assert sizes[4, 0] > 4 * state
+
+
+def test_strerror_covers_codes():
+    for c in [0, -1, -2, -3, -4, -5, -6]:
+        assert N.aaqaoa_strerror(c)

@@ -1,0 +1,310 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (stated in the problem for this method): complex128 results agree
+with the oracle to 1e-10 relative, complex64 to 1e-5 relative. Energies are
+compared relative to max(|E_ref|, 1); gradient components relative to
+max(|g_ref|, 1e-3 |E_ref|) because a component can be exactly zero;
+amplitudes relative to the largest reference amplitude.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import lightcone as LC
+from oracle import symmetric as SYM
+from oracle import closed_form as CF
+from paper_2410_22247_gb300 import workloads as W
+from paper_2410_22247_gb300 import orbits as ORB
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64": 1e-5, "c128": 1e-10}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_22247_gb300 import _native
+    _native.load()
+
+
+def plan_for(n, e, p, precision, batch=1, grad=True, orbits=True):
+    from paper_2410_22247_gb300.api import Plan
+    orb = ORB.edge_orbits(n, e) if orbits and len(e) else None
+    return Plan(n, e, p, orbits=orb, precision=precision, batch=batch, with_grad=grad), orb
+
+
+def e_rel(a, b):
+    return abs(a - b) / max(abs(b), 1.0)
+
+
+def g_rel(g, gref, E, precision="c128"):
+    """Gradient error per component. FP64: relative to max(|g_ref|, 1e-3 |E|).
+    complex64: relative to max(|g_ref|, |E|): a gradient component is a
+    cancelling sum of terms of size up to ~|E|, so FP32 amplitudes carry an
+    absolute error on the energy's scale, not the component's."""
+    g, gref = np.asarray(g), np.asarray(gref)
+    floor = (1.0 if precision == "c64" else 1e-3) * max(abs(E), 1.0)
+    return float(np.max(np.abs(g - gref) / np.maximum(np.abs(gref), floor)))
+
+
+# graphs spanning: whole state in one CTA (n <= 12/13), one tile plus
+# partial high pass (14, 15), several tiles and one or two high passes (16..23)
+CASES = [
+    ("empty1", lambda: (1, W.canonical_edges([]))),
+    ("edge2", lambda: (2, W.canonical_edges([(0, 1)]))),
+    ("cycle5", lambda: W.cycle_graph(5)),
+    ("petersen", lambda: W.generalized_petersen(5, 2)),
+    ("k12", lambda: W.complete_graph(12)),
+    ("star13", lambda: W.star_graph(13)),
+    ("reg14", lambda: W.random_regular(14, 3, 3)),
+    ("prufer15", lambda: W.prufer_tree(15, 5)),
+    ("reg16", lambda: W.random_regular(16, 3, 1)),
+    ("bintree20", lambda: W.heap_binary_tree(20)),
+    ("circ21", lambda: W.circulant_graph(21, (1, 4))),
+    ("prufer22", lambda: W.prufer_tree(22, 9)),
+    ("star23", lambda: W.star_graph(23)),
+]
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("case", [c[0] for c in CASES if c[0] not in ("star23",)])
+def test_statevector_matches_oracle(case, precision):
+    n, e = dict(CASES)[case]()
+    p = 2
+    g, b = W.random_angles(p, 11)
+    pl, _ = plan_for(n, e, p, precision, grad=False)
+    psi = pl.statevector(g, b)
+    ref = O.qaoa_state(n, e, g, b)
+    err = np.max(np.abs(psi.astype(np.complex128) - ref)) / np.max(np.abs(ref))
+    assert err < TOL[precision], err
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("case", [c[0] for c in CASES])
+def test_energy_full_and_reduced_match_oracle(case, precision):
+    n, e = dict(CASES)[case]()
+    for p in (1, 3):
+        g, b = W.random_angles(p, 100 + p)
+        pl, orb = plan_for(n, e, p, precision, grad=False)
+        Eref = O.energy(n, e, g, b)
+        Ef = pl.expect(g, b, "full")
+        assert e_rel(Ef, Eref) < TOL[precision], (Ef, Eref)
+        if orb is not None:
+            Er = pl.expect(g, b, "red")
+            assert e_rel(Er, Eref) < TOL[precision], (Er, Eref)
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("case", ["edge2", "cycle5", "k12", "reg14", "prufer15", "reg16", "bintree20", "prufer22"])
+def test_gradient_matches_oracle(case, precision):
+    n, e = dict(CASES)[case]()
+    p = 3
+    g, b = W.random_angles(p, 7)
+    pl, orb = plan_for(n, e, p, precision)
+    for obs in ("full", "red"):
+        E, dg, db = pl.grad(g, b, obs)
+        oobs = O.full_observable(e) if obs == "full" else O.reduced_observable(e, orb.rep, orb.weight)
+        Er, dgr, dbr = O.energy_grad(n, e, g, b, oobs)
+        assert e_rel(E, Er) < TOL[precision]
+        assert g_rel(dg, dgr, Er, precision) < TOL[precision], (dg, dgr)
+        assert g_rel(db, dbr, Er, precision) < TOL[precision], (db, dbr)
+
+
+def test_gradient_matches_finite_differences_c128():
+    n, e = W.prufer_tree(16, 2)
+    g, b = W.random_angles(2, 5)
+    pl, _ = plan_for(n, e, 2, "c128")
+    E, dg, db = pl.grad(g, b)
+    h = 1e-6
+    for vec, got in ((g, dg), (b, db)):
+        for i in range(len(vec)):
+            old = vec[i]
+            vec[i] = old + h
+            ep = pl.expect(g, b)
+            vec[i] = old - h
+            em = pl.expect(g, b)
+            vec[i] = old
+            assert abs((ep - em) / (2 * h) - got[i]) < 1e-6 * max(abs(E), 1.0)
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("n,maker", [(9, lambda: W.cycle_graph(9)), (12, lambda: W.complete_graph(12)),
+                                     (18, lambda: W.random_regular(18, 3, 2)), (19, lambda: W.star_graph(19))])
+def test_aggregation_modes_agree(n, maker, precision):
+    _, e = maker()
+    g, b = W.random_angles(2, 21)
+    pl, orb = plan_for(n, e, 2, precision, grad=False)
+    Eref = O.energy(n, e, g, b)
+    for obs in ("full", "red"):
+        for agg in ("fused", "perterm", "singlepass"):
+            E = pl.expect(g, b, obs, agg)
+            assert e_rel(E, Eref) < TOL[precision], (obs, agg, E, Eref)
+        # aggregation alone on the stored state
+        for agg in ("perterm", "singlepass"):
+            assert e_rel(pl.aggregate_only(obs, agg), Eref) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("maker", [lambda: W.prufer_tree(8, 1), lambda: W.random_regular(12, 3, 4),
+                                   lambda: W.circulant_graph(15, (1, 2)), lambda: W.heap_binary_tree(17)],
+                         ids=["prufer8", "reg12", "circ15", "bintree17"])
+def test_edge_zz_matches_oracle(maker, precision):
+    n, e = maker()
+    g, b = W.random_angles(2, 3)
+    pl, orb = plan_for(n, e, 2, precision, grad=False)
+    zz = pl.edge_zz(g, b)
+    psi = O.qaoa_state(n, e, g, b)
+    ref = np.array([O.zz(n, psi, u, v) for u, v in e])
+    assert np.max(np.abs(zz - ref)) < TOL[precision]
+    # Eq. (A3): equal <ZZ> inside each orbit
+    for c in range(orb.num_orbits):
+        vals = zz[orb.edge_orbit == c]
+        assert np.ptp(vals) < 10 * TOL[precision]
+
+
+def test_batch_grid_k12_c128():
+    # K_12, p = 1: the inclusive 16 x 16 grid, FP64 throughout
+    n, e = W.complete_graph(12)
+    gs, bs = W.angle_grid(16)
+    pl, _ = plan_for(n, e, 1, "c128", batch=256, grad=False)
+    E = pl.expect_batch(gs, bs, "red")
+    model = SYM.complete_graph_model(12)
+    ref = np.array([SYM.energy(model, [g], [b]) for g, b in zip(gs, bs)])
+    assert np.max(np.abs(E - ref) / np.maximum(np.abs(ref), 1.0)) < 1e-10
+    assert abs(pl.expect([0.4], [0.3], "red") - O.energy(n, e, [0.4], [0.3])) < 1e-10 * 34
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_batch_waves_match_single_calls(precision):
+    n, e = W.random_regular(16, 3, 5)
+    B, p = 5, 2
+    rng = W.rng(9)
+    gs = rng.uniform(0, np.pi, size=(B, p))
+    bs = rng.uniform(0, np.pi / 2, size=(B, p))
+    pl, _ = plan_for(n, e, p, precision, batch=2, grad=False)
+    E = pl.expect_batch(gs, bs)
+    for k in range(B):
+        assert e_rel(E[k], O.energy(n, e, gs[k], bs[k])) < TOL[precision]
+
+
+def test_results_are_bit_reproducible():
+    n, e = W.random_regular(18, 3, 8)
+    g, b = W.random_angles(2, 8)
+    pl, _ = plan_for(n, e, 2, "c64")
+    r1 = pl.grad(g, b, "red")
+    r2 = pl.grad(g, b, "red")
+    assert r1[0] == r2[0] and np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+
+
+def test_errors_reported_not_raised_on_device():
+    from paper_2410_22247_gb300._native import AAQAOAError
+    n, e = W.cycle_graph(14)
+    from paper_2410_22247_gb300.api import Plan
+    pl = Plan(n, e, 1, orbits=None, with_grad=False)
+    with pytest.raises(AAQAOAError, match="INVALID_ARG"):
+        pl.expect([0.1], [0.2], "red")
+    with pytest.raises(AAQAOAError, match="WORKSPACE"):
+        pl.grad([0.1], [0.2])
+    with pytest.raises(AAQAOAError, match="INVALID_ARG"):
+        pl.aggregate_only("full", "singlepass")
+
+
+def test_autograd_function_matches_grad():
+    torch = pytest.importorskip("torch")
+    from paper_2410_22247_gb300.api import energy
+    n, e = W.prufer_tree(15, 3)
+    g, b = W.random_angles(2, 2)
+    pl, _ = plan_for(n, e, 2, "c128")
+    gt = torch.tensor(g, device="cuda", requires_grad=True)
+    bt = torch.tensor(b, device="cuda", requires_grad=True)
+    E = energy(gt, bt, pl, "red")
+    E.backward()
+    Er, dgr, dbr = O.energy_grad(n, e, g, b)
+    assert e_rel(E.item(), Er) < 1e-10
+    assert g_rel(gt.grad.cpu().numpy(), dgr, Er) < 1e-10
+    assert g_rel(bt.grad.cpu().numpy(), dbr, Er) < 1e-10
+
+
+# ----------------------------------------------------------- full sizes
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_full_size_random_3regular_n30_p2(precision):
+    # per-edge light cones have <= 14 qubits, so the oracle is exact here
+    n, e = W.random_regular(30, 3, 0)
+    g, b = W.random_angles(2, 30)
+    pl, orb = plan_for(n, e, 2, precision)
+    E, dg, db = pl.grad(g, b, "red")
+    Er, dgr, dbr = LC.energy_grad(n, e, g, b)
+    assert e_rel(E, Er) < TOL[precision]
+    assert g_rel(dg, dgr, Er, precision) < TOL[precision]
+    assert g_rel(db, dbr, Er, precision) < TOL[precision]
+    assert e_rel(pl.expect(g, b, "full"), Er) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_full_size_star_s29_n30_p2(precision):
+    n, e = W.star_graph(30)
+    g, b = W.random_angles(2, 29)
+    pl, orb = plan_for(n, e, 2, precision)
+    assert orb.num_orbits == 1 and orb.weight[0] == 29
+    Er, dgr, dbr = SYM.energy_grad(SYM.star_model(30), g, b)
+    for obs in ("red", "full"):
+        E, dg, db = pl.grad(g, b, obs)
+        assert e_rel(E, Er) < TOL[precision]
+        assert g_rel(dg, dgr, Er, precision) < TOL[precision]
+        assert g_rel(db, dbr, Er, precision) < TOL[precision]
+
+
+def test_full_size_k16_p1():
+    n, e = W.complete_graph(16)
+    g, b = [0.37], [0.21]
+    pl, _ = plan_for(n, e, 1, "c128", grad=False)
+    Ec = CF.energy_p1(n, e, g[0], b[0])
+    assert e_rel(pl.expect(g, b, "red"), Ec) < 1e-10
+    assert e_rel(SYM.energy(SYM.complete_graph_model(16), g, b), Ec) < 1e-12
+
+
+def test_full_size_binary_tree_n34_p1_c64():
+    torch = pytest.importorskip("torch")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 150e9:
+        pytest.skip("needs ~140 GB of free device memory")
+    n, e = W.heap_binary_tree(34)
+    g, b = [0.63], [0.29]
+    pl, orb = plan_for(n, e, 1, "c64", grad=False)
+    assert orb.num_orbits == 16
+    Ec = CF.energy_p1(n, e, g[0], b[0])
+    assert e_rel(pl.expect(g, b, "red"), Ec) < 1e-5
+    assert e_rel(pl.expect(g, b, "full"), Ec) < 1e-5
+    pl.close()
+    torch.cuda.empty_cache()
+
+
+def test_full_size_prufer_n32_p4_c64_sampled_edges():
+    torch = pytest.importorskip("torch")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 80e9:
+        pytest.skip("needs ~70 GB of free device memory")
+    n, e = W.prufer_tree(32, 0)
+    g, b = W.random_angles(4, 32)
+    pl, orb = plan_for(n, e, 4, "c64", grad=True)
+    E, dg, db = pl.grad(g, b, "red")
+    Ef, dgf, dbf = pl.grad(g, b, "full")
+    assert e_rel(E, Ef) < 1e-5 and g_rel(dg, dgf, Ef, "c64") < 1e-5 and g_rel(db, dbf, Ef, "c64") < 1e-5
+    assert 0.0 <= E <= len(e)
+    zz = pl.edge_zz(g, b)
+    # sampled outputs: per-edge <ZZ> of edges whose light cone is small
+    checked = 0
+    for k, (u, v) in enumerate(e):
+        if len(LC.ball(n, e, int(u), int(v), 4)) <= 16:
+            ns, se, us, vs = LC.edge_subproblem(n, e, int(u), int(v), 4)
+            psi = O.qaoa_state(ns, se, g, b)
+            assert abs(zz[k] - O.zz(ns, psi, us, vs)) < 1e-5
+            checked += 1
+    assert checked >= 3
+    # the energy is the orbit-weighted sum of the per-edge values
+    assert e_rel(float(np.sum(0.5 * (1 - zz))), E) < 1e-5
+    pl.close()
+    torch.cuda.empty_cache()
