@@ -210,6 +210,36 @@ int aaqaoa_statevector(aaqaoa_plan *plan, const double *gamma, const double *bet
  */
 int aaqaoa_aggregate_only(aaqaoa_plan *plan, int observable, int agg_mode, double *energy);
 
+/*
+ * aaqaoa_expect_static -- aaqaoa_expect (fused aggregation) without a
+ * workspace and without any device allocation by the library.
+ *
+ * The paper has no counterpart: this serves callers that cannot allocate
+ * device memory at the point where they evaluate an energy -- for example code
+ * that runs under a host application which owns every device allocation, or a
+ * process that has used up its device-memory budget and still needs energies
+ * of small graphs -- so they cannot provide a workspace.
+ *
+ * Device scratch (control words, phase tables, parameters, partial sums and
+ * one statevector) lives in a file-scope static device array of 33 MiB
+ * compiled into the library; every GPU that loads the library holds it until
+ * the process exits. It fits one statevector of up to 2^22 complex64 or 2^21
+ * complex128 amplitudes: n <= 22 for AAQAOA_C64, n <= 21 for AAQAOA_C128;
+ * larger n returns AAQAOA_ERR_UNSUPPORTED with a message.
+ *
+ * The first call on a device looks up the array's device address (and so
+ * makes the CUDA runtime load the library's device module); make that first
+ * call before any stream capture. Every call shares the one array: the entry
+ * point clears what must start at zero, but calls that overlap on the GPU
+ * (other streams, other host threads, concurrent graph replays) race on it.
+ *
+ * plan: prepared graph (no workspace needed). gamma, beta: host, p doubles.
+ * observable: AAQAOA_OBS_FULL or AAQAOA_OBS_RED. energy: host, 1 double.
+ * Synchronises the plan's stream. Calls no cudaMalloc/cudaFree.
+ */
+int aaqaoa_expect_static(aaqaoa_plan *plan, const double *gamma, const double *beta, int observable,
+                         double *energy);
+
 /* Plan properties: qubits, layers, edges, orbits, precision flag. */
 int aaqaoa_plan_info(const aaqaoa_plan *plan, int *n, int *p, int *num_edges, int *num_orbits,
                      unsigned *flags);

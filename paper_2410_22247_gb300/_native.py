@@ -45,6 +45,7 @@ _PROTOS = [
     ("aaqaoa_edge_zz", ctypes.c_int, [_vp, _f64p, _f64p, _f64p]),
     ("aaqaoa_statevector", ctypes.c_int, [_vp, _f64p, _f64p, _vp]),
     ("aaqaoa_aggregate_only", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _f64p]),
+    ("aaqaoa_expect_static", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_int, _f64p]),
     ("aaqaoa_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_uint)]),

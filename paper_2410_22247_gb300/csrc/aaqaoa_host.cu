@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -979,3 +980,163 @@ void aaqaoa_destroy(aaqaoa_plan *pl)
 }
 
 }  // extern "C"
+
+// ====================================================== static scratch
+// An energy evaluation for callers that cannot allocate device memory. All of
+// its device scratch (control words, phase tables, parameters, partial sums
+// and one statevector) lives in this file-scope array, which every GPU that
+// loads the library holds until the process exits.
+namespace {
+
+constexpr size_t STATIC_FIXED_BYTES = (size_t)1 << 20;   // control, outputs, tables, partials
+constexpr size_t STATIC_STATE_BYTES = (size_t)32 << 20;  // one statevector
+constexpr size_t STATIC_SCRATCH_BYTES = STATIC_FIXED_BYTES + STATIC_STATE_BYTES;
+constexpr int STATIC_MAX_DEVICES = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mutex;
+unsigned char *g_static_ptr[STATIC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name of a __device__ array is not a device
+// address).
+int static_scratch(unsigned char **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "device ordinal %d beyond the static scratch table", dev);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return AAQAOA_OK;
+}
+
+}  // namespace
+
+extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const double *beta, int observable,
+                                    double *energy)
+{
+    g_detail.clear();
+    if (!pl || !gamma || !beta || !energy)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan, gamma, beta or energy is NULL");
+    if (observable != AAQAOA_OBS_FULL && observable != AAQAOA_OBS_RED)
+        return fail(AAQAOA_ERR_INVALID_ARG, "observable %d unknown", observable);
+    if (observable == AAQAOA_OBS_RED && pl->num_orbits == 0)
+        return fail(AAQAOA_ERR_INVALID_ARG, "H_red requested but the plan has no edge orbits");
+    const size_t state_bytes = ((size_t)1 << pl->n) * pl->amp();
+    if (state_bytes > STATIC_STATE_BYTES)
+        return fail(AAQAOA_ERR_UNSUPPORTED,
+                    "static scratch holds one statevector of at most %zu bytes (n <= %d for %s); n = %d needs %zu",
+                    STATIC_STATE_BYTES, pl->c128 ? 21 : 22, pl->c128 ? "complex128" : "complex64", pl->n,
+                    state_bytes);
+    unsigned char *base = nullptr;
+    int r = static_scratch(&base);
+    if (r)
+        return r;
+
+    // fixed region: [ctrl 256 | out | gamma, beta | cs | tables | partials]
+    const int p = pl->p;
+    size_t off = 256;
+    double *d_out = reinterpret_cast<double *>(base + off);
+    off = align256(off + (size_t)pl->out_stride() * sizeof(double));
+    double *d_par = reinterpret_cast<double *>(base + off);
+    off = align256(off + 2 * (size_t)p * sizeof(double));
+    double2 *d_cs = reinterpret_cast<double2 *>(base + off);
+    off = align256(off + (size_t)p * sizeof(double2));
+    void *d_tab = base + off;
+    off = align256(off + (size_t)p * pl->tab_len() * pl->amp());
+    double *d_part = reinterpret_cast<double *>(base + off);
+    off = align256(off + 2 * (size_t)pl->tiles() * sizeof(double));
+    if (off > STATIC_FIXED_BYTES)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "tables for p = %d and |E| = %d exceed the static scratch", p, pl->m);
+    int *d_err = reinterpret_cast<int *>(base);
+    unsigned *d_counter = reinterpret_cast<unsigned *>(base + 8);
+    void *d_phi = base + STATIC_FIXED_BYTES;
+
+    cudaStream_t st = pl->stream;
+    (void)cudaGetLastError();
+    // what must start at zero: error flag, last-block counters, the output row
+    CK(cudaMemsetAsync(base, 0, 256, st));
+    CK(cudaMemsetAsync(d_out, 0, (size_t)pl->out_stride() * sizeof(double), st));
+    CK(cudaMemcpyAsync(d_par, gamma, (size_t)p * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_par + p, beta, (size_t)p * sizeof(double), cudaMemcpyHostToDevice, st));
+    CKL(launch_params(pl->c128, 1, p, pl->tab_len(), d_par, d_par + p, d_tab, d_cs, st), "parameter tables");
+
+    if (pl->small()) {
+        SmallArgs s;
+        memset(&s, 0, sizeof s);
+        s.n = pl->n;
+        s.p = p;
+        s.tab_len = pl->tab_len();
+        s.mode = SMALL_ENERGY;
+        s.write_state = 0;
+        s.amp0 = std::pow(2.0, -0.5 * pl->n);
+        s.tab = d_tab;
+        s.cs = d_cs;
+        s.out = d_out;
+        s.out_stride = pl->out_stride();
+        s.state = d_phi;
+        s.obs = pl->obs[observable];
+        s.cost = pl->cost;
+        CKL(launch_small(pl->c128, s, 1, st), "whole-circuit kernel");
+    } else {
+        const int np = (int)pl->passes.size();
+        CUtensorMap maps[8];
+        if (np > 8)
+            return fail(AAQAOA_ERR_UNSUPPORTED, "%d passes per layer", np);
+        for (int k = 0; k < np; k++)
+            if ((r = make_map(&maps[k], d_phi, pl->n, pl->passes[k].s, pl->CB(), pl->amp(), 1)))
+                return r;
+        for (int l = 0; l < p; l++) {
+            for (int k = 0; k < np; k++) {
+                const Pass &ps = pl->passes[k];
+                PassArgs a;
+                memset(&a, 0, sizeof a);
+                a.n = pl->n;
+                a.s = ps.s;
+                a.is_low = ps.is_low;
+                a.hmask = ps.hmask;
+                a.tiles = pl->tiles();
+                a.load = !(l == 0 && k == 0);
+                a.pre_phase = (k == 0);
+                const bool last = (l == p - 1 && k == np - 1);
+                a.write = !last;
+                a.post = last ? POST_REDUCE : 0;
+                a.nvec_io = 1;
+                a.layer = l;
+                a.p = p;
+                a.tab_len = pl->tab_len();
+                a.sign_s = 1.0;
+                a.amp0 = std::pow(2.0, -0.5 * pl->n);
+                a.tab = d_tab;
+                a.cs = d_cs;
+                a.partials = d_part;
+                a.counter = d_counter;
+                a.out = d_out;
+                a.out_stride = pl->out_stride();
+                a.slot_idx[0] = last ? 0 : -1;
+                a.slot_idx[1] = -1;
+                a.slot_scale[0] = 1.0;
+                a.err = d_err;
+                a.obs = pl->obs[observable];
+                a.cost = pl->cost;
+                CKL(launch_pass(pl->c128, 1, 1, maps[k], maps[k], a, 1, st), "forward pass");
+            }
+        }
+    }
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(energy, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err)
+        return fail(AAQAOA_ERR_TIMEOUT, "a bounded device wait expired (TMA tile never arrived)");
+    return AAQAOA_OK;
+}
