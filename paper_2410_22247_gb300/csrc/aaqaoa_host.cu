@@ -102,8 +102,10 @@ struct aaqaoa_plan {
     int cap = 0;
     bool ws_grad = false;
     Layout L{};
-    std::vector<Pass> passes;
-    std::vector<CUtensorMap> map_phi, map_lam;
+    std::vector<Pass> passes;      // forward passes (one-vector tile geometry)
+    std::vector<Pass> bwd_passes;  // adjoint passes (two-vector tile geometry)
+    std::vector<CUtensorMap> map_phi;            // forward, per pass
+    std::vector<CUtensorMap> map_bphi, map_blam; // adjoint, per pass
     int launches = 0;
     bool state_valid = false;
     // launch profiling
@@ -117,7 +119,8 @@ struct aaqaoa_plan {
     std::vector<cudaEvent_t> prof_pool;
 
     int T() const { return tile_bits(c128); }
-    int CB() const { return c128 ? 3 : 4; }
+    int CB() const { int t, c, h; pass_geometry(c128, 1, &t, &c, &h); return c; }
+    int HB() const { int t, c, h; pass_geometry(c128, 1, &t, &c, &h); return h; }
     size_t amp() const { return c128 ? 16 : 8; }
     int tab_len() const { return m + 1; }
     int out_stride() const { return 1 + 2 * p; }
@@ -190,7 +193,7 @@ Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
     off = align256(off + B * pl->p * sizeof(double2));
     L.tab = off;
     off = align256(off + B * pl->p * pl->tab_len() * pl->amp());
-    const size_t pass_partials = pl->small() ? 0 : 2 * B * (size_t)pl->tiles();
+    const size_t pass_partials = pl->small() ? 0 : 2 * B * (size_t)device_sms();
     const size_t agg_partials = 64 * (size_t)agg_grid(pl->c128);
     L.partial_count = pass_partials > agg_partials ? pass_partials : agg_partials;
     L.partials = off;
@@ -206,15 +209,20 @@ Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
     return L;
 }
 
-int make_map(CUtensorMap *map, void *base, int n, int s, int cb, size_t amp, int B)
+// 5-D view of B statevectors for tiles of one 128-byte row (local bits
+// 0..cb-1) times 2^hb rows along qubits s..s+hb-1: dims (16 x 8 B, mid bits
+// cb..s-1, 2^(hb-4), 16, fixed high bits and batch).
+int make_map(CUtensorMap *map, void *base, int n, int s, int cb, int hb, size_t amp, int B)
 {
     auto fn = encode_fn();
     if (!fn)
         return fail(AAQAOA_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable from the driver");
-    cuuint64_t dims[5] = {16, (cuuint64_t)1 << (s - cb), 32, 16, ((cuuint64_t)1 << (n - s - 9)) * (cuuint64_t)B};
-    cuuint64_t strides[4] = {128, ((cuuint64_t)1 << s) * amp, ((cuuint64_t)1 << (s + 5)) * amp,
-                             ((cuuint64_t)1 << (s + 9)) * amp};
-    cuuint32_t box[5] = {16, 1, 32, 16, 1};
+    const int h1 = hb - 4;
+    cuuint64_t dims[5] = {16, (cuuint64_t)1 << (s - cb), (cuuint64_t)1 << h1, 16,
+                          ((cuuint64_t)1 << (n - s - hb)) * (cuuint64_t)B};
+    cuuint64_t strides[4] = {128, ((cuuint64_t)1 << s) * amp, ((cuuint64_t)1 << (s + h1)) * amp,
+                             ((cuuint64_t)1 << (s + hb)) * amp};
+    cuuint32_t box[5] = {16, 1, (cuuint32_t)1 << h1, 16, 1};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -224,23 +232,35 @@ int make_map(CUtensorMap *map, void *base, int n, int s, int cb, size_t amp, int
     return AAQAOA_OK;
 }
 
-void build_passes(aaqaoa_plan *pl)
+// Passes of one layer for tiles of T qubits (CB contiguous + HB high): a low
+// pass over qubits 0..T-1, then high passes of HB qubits; the last high pass
+// is shifted down to end at qubit n-1 and only transforms qubits not yet done.
+std::vector<Pass> make_passes(int n, int T, int CB, int HB)
 {
-    pl->passes.clear();
-    if (pl->small())
-        return;
-    const int T = pl->T(), CB = pl->CB(), n = pl->n;
-    pl->passes.push_back({CB, 1, 0x1FF});
+    std::vector<Pass> v;
+    if (n <= T)
+        return v;
+    v.push_back({CB, 1, (1 << HB) - 1});
     int covered = T;
     while (covered < n) {
-        const int s = covered < n - 9 ? covered : n - 9;
+        const int s = covered < n - HB ? covered : n - HB;
         int hm = 0;
-        for (int j = 0; j < 9; j++)
+        for (int j = 0; j < HB; j++)
             if (s + j >= covered && s + j < n)
                 hm |= 1 << j;
-        pl->passes.push_back({s, 0, hm});
-        covered = s + 9;
+        v.push_back({s, 0, hm});
+        covered = s + HB;
     }
+    return v;
+}
+
+void build_passes(aaqaoa_plan *pl)
+{
+    int T, CB, HB;
+    pass_geometry(pl->c128, 1, &T, &CB, &HB);
+    pl->passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB);
+    pass_geometry(pl->c128, 2, &T, &CB, &HB);
+    pl->bwd_passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB);
 }
 
 PassArgs base_args(const aaqaoa_plan *pl, int obs)
@@ -249,6 +269,7 @@ PassArgs base_args(const aaqaoa_plan *pl, int obs)
     memset(&a, 0, sizeof a);
     a.n = pl->n;
     a.tiles = pl->tiles();
+    a.B = 1;
     a.p = pl->p;
     a.tab_len = pl->tab_len();
     a.amp0 = std::pow(2.0, -0.5 * pl->n);
@@ -270,10 +291,12 @@ enum FwdMode { FWD_ENERGY, FWD_GRAD, FWD_STATE };
 int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
 {
     const int np = (int)pl->passes.size();
+    const int grid = pass_grid((long long)pl->tiles() * B);
     for (int l = 0; l < pl->p; l++) {
         for (int k = 0; k < np; k++) {
             const Pass &ps = pl->passes[k];
             PassArgs a = base_args(pl, obs);
+            a.B = B;
             a.s = ps.s;
             a.is_low = ps.is_low;
             a.hmask = ps.hmask;
@@ -284,29 +307,36 @@ int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
             a.nvec_io = 1;
             const bool last = (l == pl->p - 1 && k == np - 1);
             a.write = !(last && mode == FWD_ENERGY);
-            a.post = !last ? 0 : mode == FWD_ENERGY ? POST_REDUCE : mode == FWD_GRAD ? (POST_REDUCE | POST_LAMBDA) : 0;
+            a.post = (last && mode != FWD_STATE) ? POST_REDUCE : 0;
             if (last && mode != FWD_STATE) {
                 a.slot_idx[0] = 0;
                 a.slot_scale[0] = 1.0;
             }
-            const int nbuf = (a.post & POST_LAMBDA) ? 2 : 1;
             const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
-            ProfScope ps_(pl, PK_FWD, S * ((a.load ? 1 : 0) + (a.write ? nbuf : 0)));
-            CKL(launch_pass(pl->c128, 1, nbuf, pl->map_phi[k], pl->map_lam[k], a, B, pl->stream), "forward pass");
+            ProfScope ps_(pl, PK_FWD, S * ((a.load ? 1 : 0) + (a.write ? 1 : 0)));
+            CKL(launch_pass(pl->c128, 1, pl->map_phi[k], pl->map_phi[k], a, grid, pl->stream), "forward pass");
             pl->launches++;
         }
     }
     return AAQAOA_OK;
 }
 
+// adjoint passes on (phi, lambda); the first one forms lambda = O phi itself
 int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
 {
-    const int np = (int)pl->passes.size();
+    int T, CB, HB;
+    pass_geometry(pl->c128, 2, &T, &CB, &HB);
+    const int tiles = 1 << (pl->n - T);
+    const int grid = pass_grid((long long)tiles * B);
+    const int np = (int)pl->bwd_passes.size();
+    bool first = true;
     for (int l = pl->p - 1; l >= 0; l--) {
         for (int kk = np - 1; kk >= 0; kk--) {
-            const Pass &ps = pl->passes[kk];
+            const Pass &ps = pl->bwd_passes[kk];
             const bool last_of_layer = (kk == 0);
             PassArgs a = base_args(pl, obs);
+            a.B = B;
+            a.tiles = tiles;
             a.s = ps.s;
             a.is_low = ps.is_low;
             a.hmask = ps.hmask;
@@ -314,7 +344,8 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
             a.sign_s = -1.0;
             a.load = 1;
             a.pre_phase = 0;
-            a.nvec_io = 2;
+            a.pre_lambda = first ? 1 : 0;
+            a.nvec_io = first ? 1 : 2;
             a.post = last_of_layer ? (POST_GAMMA | (l > 0 ? POST_PHASE_CONJ : 0)) : 0;
             a.write = !(last_of_layer && l == 0);
             a.slot_idx[0] = 1 + pl->p + l;
@@ -324,9 +355,10 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
                 a.slot_scale[1] = 2.0;
             }
             const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
-            ProfScope ps_(pl, PK_ADJ, S * (2 + (a.write ? 2 : 0)));
-            CKL(launch_pass(pl->c128, 2, 2, pl->map_phi[kk], pl->map_lam[kk], a, B, pl->stream), "adjoint pass");
+            ProfScope ps_(pl, PK_ADJ, S * (a.nvec_io + (a.write ? 2 : 0)));
+            CKL(launch_pass(pl->c128, 2, pl->map_bphi[kk], pl->map_blam[kk], a, grid, pl->stream), "adjoint pass");
             pl->launches++;
+            first = false;
         }
     }
     return AAQAOA_OK;
@@ -672,16 +704,25 @@ int aaqaoa_set_workspace(aaqaoa_plan *pl, void *device_ptr, size_t bytes, int ba
     pl->L = L;
     pl->state_valid = false;
     pl->map_phi.assign(pl->passes.size(), CUtensorMap{});
-    pl->map_lam.assign(pl->passes.size(), CUtensorMap{});
+    pl->map_bphi.assign(pl->bwd_passes.size(), CUtensorMap{});
+    pl->map_blam.assign(pl->bwd_passes.size(), CUtensorMap{});
+    int T, CB, HB;
+    pass_geometry(pl->c128, 1, &T, &CB, &HB);
     for (size_t k = 0; k < pl->passes.size(); k++) {
-        int r = make_map(&pl->map_phi[k], pl->d_phi(), pl->n, pl->passes[k].s, pl->CB(), pl->amp(), batch);
+        int r = make_map(&pl->map_phi[k], pl->d_phi(), pl->n, pl->passes[k].s, CB, HB, pl->amp(), batch);
         if (r)
             return r;
-        // the lambda map is used by gradient launches and by the forward pass that writes lambda
-        void *lam = with_grad ? pl->d_lam() : pl->d_phi();
-        r = make_map(&pl->map_lam[k], lam, pl->n, pl->passes[k].s, pl->CB(), pl->amp(), batch);
-        if (r)
-            return r;
+    }
+    if (with_grad) {
+        pass_geometry(pl->c128, 2, &T, &CB, &HB);
+        for (size_t k = 0; k < pl->bwd_passes.size(); k++) {
+            int r = make_map(&pl->map_bphi[k], pl->d_phi(), pl->n, pl->bwd_passes[k].s, CB, HB, pl->amp(), batch);
+            if (r)
+                return r;
+            r = make_map(&pl->map_blam[k], pl->d_lam(), pl->n, pl->bwd_passes[k].s, CB, HB, pl->amp(), batch);
+            if (r)
+                return r;
+        }
     }
     CK(cudaMemsetAsync(pl->ws + L.ctrl, 0, 256, pl->stream));
     CK(cudaStreamSynchronize(pl->stream));
@@ -1054,7 +1095,7 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
     void *d_tab = base + off;
     off = align256(off + (size_t)p * pl->tab_len() * pl->amp());
     double *d_part = reinterpret_cast<double *>(base + off);
-    off = align256(off + 2 * (size_t)pl->tiles() * sizeof(double));
+    off = align256(off + 2 * (size_t)device_sms() * sizeof(double));
     if (off > STATIC_FIXED_BYTES)
         return fail(AAQAOA_ERR_UNSUPPORTED, "tables for p = %d and |E| = %d exceed the static scratch", p, pl->m);
     int *d_err = reinterpret_cast<int *>(base);
@@ -1093,8 +1134,9 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
         if (np > 8)
             return fail(AAQAOA_ERR_UNSUPPORTED, "%d passes per layer", np);
         for (int k = 0; k < np; k++)
-            if ((r = make_map(&maps[k], d_phi, pl->n, pl->passes[k].s, pl->CB(), pl->amp(), 1)))
+            if ((r = make_map(&maps[k], d_phi, pl->n, pl->passes[k].s, pl->CB(), pl->HB(), pl->amp(), 1)))
                 return r;
+        const int grid = pass_grid(pl->tiles());
         for (int l = 0; l < p; l++) {
             for (int k = 0; k < np; k++) {
                 const Pass &ps = pl->passes[k];
@@ -1105,6 +1147,7 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
                 a.is_low = ps.is_low;
                 a.hmask = ps.hmask;
                 a.tiles = pl->tiles();
+                a.B = 1;
                 a.load = !(l == 0 && k == 0);
                 a.pre_phase = (k == 0);
                 const bool last = (l == p - 1 && k == np - 1);
@@ -1128,7 +1171,7 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
                 a.err = d_err;
                 a.obs = pl->obs[observable];
                 a.cost = pl->cost;
-                CKL(launch_pass(pl->c128, 1, 1, maps[k], maps[k], a, 1, st), "forward pass");
+                CKL(launch_pass(pl->c128, 1, maps[k], maps[k], a, grid, st), "forward pass");
             }
         }
     }

@@ -29,7 +29,6 @@ struct CostFn {
 // Operations of one tiled pass over the statevector(s).
 enum PostOp : int {
     POST_REDUCE = 1,      // acc0 += |phi|^2 O(x)                 (energy)
-    POST_LAMBDA = 2,      // write lambda = O(x) phi as a second vector
     POST_GAMMA = 4,       // acc1 += C(x) Im(conj(lambda) phi)     (dE/dgamma)
     POST_PHASE_CONJ = 8,  // phi, lambda *= exp(+i gamma_l C(x))   (undo cost layer)
 };
@@ -37,11 +36,13 @@ enum PostOp : int {
 struct PassArgs {
     int n;            // qubits
     int s;            // global bit of local high bit 0
-    int is_low;       // tile is contiguous and the low bits are transformed here
-    int hmask;        // which of the 9 local high bits receive a butterfly
-    int tiles;        // tiles per statevector = 2^(n - tile_bits)
+    int is_low;       // tile is contiguous and its low bits are transformed here
+    int hmask;        // which local high bits receive a butterfly
+    int tiles;        // tiles per statevector = 2^(n - tile bits)
+    int B;            // statevectors (parameter points) in this launch
     int load;         // 1: TMA-load the tile(s); 0: generate |+>^n
     int pre_phase;    // multiply by the cost-layer phase before any butterfly
+    int pre_lambda;   // adjoint: load phi only and form lambda = O(x) phi first
     int write;        // TMA-store the tile(s) after the last stage
     int post;         // PostOp flags
     int nvec_io;      // vectors loaded (1 or 2)
@@ -52,7 +53,7 @@ struct PassArgs {
     double amp0;      // 2^(-n/2) for the generated |+>^n
     const void *tab;  // phase tables [B][p][tab_len], complex in the amplitude precision
     const double2 *cs;  // [B][p] (cos beta_l, sin beta_l)
-    double *partials; // [2][B][tiles]
+    double *partials; // [2][B][grid]
     unsigned *counter;  // last-block counter (zero between launches)
     double *out;      // [B][out_stride]
     int out_stride;
@@ -96,11 +97,13 @@ struct AggArgs {
 
 // Launchers (aaqaoa_kernels.cu). They return a cudaError_t as int.
 int tile_bits(bool c128);
-size_t pass_smem_bytes(bool c128, int nvec_buffers);
+void pass_geometry(bool c128, int nv, int *T, int *CB, int *HB);
+int device_sms();
+int pass_grid(long long total_tiles);
 int launch_params(bool c128, int B, int p, int tab_len, const double *d_gamma, const double *d_beta,
                   void *d_tab, double2 *d_cs, cudaStream_t st);
-int launch_pass(bool c128, int nv_kernel, int nbuf, const CUtensorMap &m0, const CUtensorMap &m1,
-                const PassArgs &a, int B, cudaStream_t st);
+int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a,
+                int grid, cudaStream_t st);
 int launch_small(bool c128, const SmallArgs &a, int B, cudaStream_t st);
 size_t small_smem_bytes(bool c128, int n, int mode);
 int small_max_qubits(bool c128, int mode);

@@ -79,6 +79,30 @@ __device__ __forceinline__ void bfly(C &a, C &b, R c, R s)
     b = b2;
 }
 
+// RX(2 beta) up to a real factor f, with one FMA per output component:
+//   |cos| >= |sin|: f = cos, t = tan:  (a, b) <- (a - i t b, b - i t a)
+//   |cos| <  |sin|: f = sin, u = cot:  (a, b) <- (u a - i b, u b - i a)
+// so c a - i s b = f * (new a). The caller rescales by f^k after k of them.
+template <typename C, typename R>
+__device__ __forceinline__ void bfly_tan(C &a, C &b, R t)
+{
+    const C a0 = a, b0 = b;
+    a.x = fma(t, b0.y, a0.x);
+    a.y = fma(-t, b0.x, a0.y);
+    b.x = fma(t, a0.y, b0.x);
+    b.y = fma(-t, a0.x, b0.y);
+}
+
+template <typename C, typename R>
+__device__ __forceinline__ void bfly_cot(C &a, C &b, R u)
+{
+    const C a0 = a, b0 = b;
+    a.x = fma(u, a0.x, b0.y);
+    a.y = fma(u, a0.y, -b0.x);
+    b.x = fma(u, b0.x, a0.y);
+    b.y = fma(u, b0.y, -a0.x);
+}
+
 // Im(conj(l) f)
 template <typename C>
 __device__ __forceinline__ auto im_conj_mul(C l, C f) -> decltype(l.x) { return l.x * f.y - l.y * f.x; }
@@ -261,18 +285,77 @@ __device__ __forceinline__ void eval_cut(const CutFn &f, int n, uint64_t x0, con
     finish_cut<RB>(base, d, W, v);
 }
 
+// Smem-resident copies of the cut functions: cost masks nbr[u]; observable
+// masks nbr[c * MAXN + u] with integer class weights w[c].
+template <int RB>
+__device__ __forceinline__ void eval_cost_s(const uint64_t *nbr, int n, uint64_t x0, const int (&gp)[RB],
+                                            int (&v)[1 << RB])
+{
+    int base = 0;
+    for (int u = 0; u < n; u++) {
+        const uint64_t nb = nbr[u];
+        base += ((x0 >> u) & 1ull) ? __popcll(nb & ~x0) : 0;
+    }
+    int d[RB], W[RB][RB];
+#pragma unroll
+    for (int k = 0; k < RB; k++) {
+        const uint64_t nb = nbr[gp[k]];
+        d[k] = __popcll(nb) - 2 * __popcll(nb & x0);
+#pragma unroll
+        for (int k2 = 0; k2 < RB; k2++)
+            W[k][k2] = (int)((nb >> gp[k2]) & 1ull);
+    }
+    finish_cut<RB>(base, d, W, v);
+}
+
+template <int RB>
+__device__ __forceinline__ void eval_cut_s(const uint64_t *nbr, const int *w, int K, int n, uint64_t x0,
+                                           const int (&gp)[RB], int (&v)[1 << RB])
+{
+    int base = 0, d[RB], W[RB][RB];
+#pragma unroll
+    for (int k = 0; k < RB; k++) {
+        d[k] = 0;
+#pragma unroll
+        for (int k2 = 0; k2 < RB; k2++)
+            W[k][k2] = 0;
+    }
+    for (int c = 0; c < K; c++) {
+        const int wc = w[c];
+        const uint64_t *nc = nbr + c * MAXN;
+        int bc = 0;
+        for (int u = 0; u < n; u++) {
+            const uint64_t nb = nc[u];
+            bc += ((x0 >> u) & 1ull) ? __popcll(nb & ~x0) : 0;
+        }
+        base += wc * bc;
+#pragma unroll
+        for (int k = 0; k < RB; k++) {
+            const uint64_t nb = nc[gp[k]];
+            d[k] += wc * (__popcll(nb) - 2 * __popcll(nb & x0));
+#pragma unroll
+            for (int k2 = 0; k2 < RB; k2++)
+                W[k][k2] += wc * (int)((nb >> gp[k2]) & 1ull);
+        }
+    }
+    finish_cut<RB>(base, d, W, v);
+}
+
 // ---------------------------------------------------------- tile geometry
-// Stage plans: reg(st, k) is the local tile bit held in register slot bit k,
+// A tile holds 2^T amplitudes per vector: local bits 0..CB-1 are one 128-byte
+// row of contiguous amplitudes, local bits CB..CB+HB-1 are HB consecutive
+// qubits s..s+HB-1 (rows at stride 2^s). NSTAGE tiles are in flight per CTA.
+// Register stages: reg(st, k) is the local bit held in register-slot bit k,
 // thr(st, j) the local bit given by thread-index bit j (lane bits first),
-// own(st) the register bits whose butterflies this stage applies. Local bits
-// 0..CB-1 are the contiguous row; CB..CB+8 the high bits. swz() is the TMA
-// 128-byte swizzle expressed on amplitude indices (16-byte chunk index XOR
-// row mod 8). The plans are chosen so every shared-memory access of a warp is
-// free of bank conflicts (16 lanes x 8 B or 8 lanes x 16 B per wavefront).
+// own(st) the register bits whose butterflies stage st applies. swz() is the
+// TMA 128-byte swizzle on amplitude indices (16-byte chunk XOR row mod 8).
+// Every plan keeps each warp's shared-memory accesses free of bank conflicts
+// (16 lanes x 8 B or 8 lanes x 16 B per wavefront).
 template <typename R, int NV> struct Geo;
 
-template <int NV> struct Geo<float, NV> {
-    static constexpr int CB = 4, HB = 9, T = 13, RB = 5, NTHR = 256, NST = 3;
+// complex64, one vector: 64 KB tiles (13 qubits), 32 amplitudes per thread
+template <> struct Geo<float, 1> {
+    static constexpr int CB = 4, HB = 9, T = 13, RB = 5, NTHR = 256, NST = 3, NSTAGE = 3;
     __host__ __device__ static constexpr int reg(int st, int k)
     {
         return st == 0 ? (k < 4 ? k : 7) : st == 1 ? 4 + k : (k == 0 ? 0 : 8 + k);
@@ -285,8 +368,21 @@ template <int NV> struct Geo<float, NV> {
     __host__ __device__ static constexpr uint32_t swz(uint32_t i) { return i ^ (((i >> 4) & 7u) << 1); }
 };
 
+// complex64, two vectors (adjoint): 2 x 32 KB tiles (12 qubits), 16 per thread
+template <> struct Geo<float, 2> {
+    static constexpr int CB = 4, HB = 8, T = 12, RB = 4, NTHR = 256, NST = 3, NSTAGE = 3;
+    __host__ __device__ static constexpr int reg(int st, int k) { return st == 0 ? k : st == 1 ? 4 + k : 8 + k; }
+    __host__ __device__ static constexpr int thr(int st, int j)
+    {
+        return st == 0 ? 4 + j : st == 1 ? (j < 4 ? j : 4 + j) : j;
+    }
+    __host__ __device__ static constexpr int own(int st) { return 0xF; }
+    __host__ __device__ static constexpr uint32_t swz(uint32_t i) { return i ^ (((i >> 4) & 7u) << 1); }
+};
+
+// complex128, one vector: 64 KB tiles (12 qubits), 32 amplitudes per thread
 template <> struct Geo<double, 1> {
-    static constexpr int CB = 3, HB = 9, T = 12, RB = 5, NTHR = 128, NST = 3;
+    static constexpr int CB = 3, HB = 9, T = 12, RB = 5, NTHR = 128, NST = 3, NSTAGE = 3;
     __host__ __device__ static constexpr int reg(int st, int k)
     {
         return st == 0 ? (k < 3 ? k : 3 + k) : st == 1 ? 3 + k : (k == 0 ? 0 : 7 + k);
@@ -299,23 +395,24 @@ template <> struct Geo<double, 1> {
     __host__ __device__ static constexpr uint32_t swz(uint32_t i) { return i ^ ((i >> 3) & 7u); }
 };
 
+// complex128, two vectors (adjoint): 2 x 32 KB tiles (11 qubits), 16 per thread
 template <> struct Geo<double, 2> {
-    static constexpr int CB = 3, HB = 9, T = 12, RB = 4, NTHR = 256, NST = 4;
+    static constexpr int CB = 3, HB = 8, T = 11, RB = 4, NTHR = 128, NST = 3, NSTAGE = 3;
     __host__ __device__ static constexpr int reg(int st, int k)
     {
-        return st == 0 ? (k < 3 ? k : 6) : st == 1 ? 3 + k : st == 2 ? 7 + k : (k == 0 ? 11 : 2 + k);
+        return st == 0 ? (k < 3 ? k : 6) : st == 1 ? 3 + k : 7 + k;
     }
     __host__ __device__ static constexpr int thr(int st, int j)
     {
-        return st == 0 ? (j < 3 ? 3 + j : 4 + j) : st == 1 ? (j < 3 ? j : 4 + j) : st == 2 ? (j < 7 ? j : 11)
-                                                                                   : (j < 3 ? j : 3 + j);
+        return st == 0 ? (j < 3 ? 3 + j : 4 + j) : st == 1 ? (j < 3 ? j : 4 + j) : j;
     }
-    __host__ __device__ static constexpr int own(int st) { return st == 0 ? 0x7 : st == 3 ? 0x1 : 0xF; }
+    __host__ __device__ static constexpr int own(int st) { return st == 0 ? 0x7 : 0xF; }
     __host__ __device__ static constexpr uint32_t swz(uint32_t i) { return i ^ ((i >> 3) & 7u); }
 };
 
 // compile-time checks: each stage's register and thread bits partition the
-// tile, and the stages' butterflies cover every tile bit exactly once.
+// tile, the stages' butterflies cover every tile bit exactly once, and the
+// pipeline fits the 227 KB of shared memory.
 template <typename G>
 constexpr bool stages_partition()
 {
@@ -337,11 +434,27 @@ constexpr bool stages_partition()
                     return false;
                 cover |= bit;
             }
-    return cover == (1u << G::T) - 1u;
+    return cover == (1u << G::T) - 1u && G::CB + G::HB == G::T && (1 << (G::T - G::RB)) == G::NTHR;
 }
 static_assert(stages_partition<Geo<float, 1>>(), "c64 stage plan");
+static_assert(stages_partition<Geo<float, 2>>(), "c64 two-vector stage plan");
 static_assert(stages_partition<Geo<double, 1>>(), "c128 stage plan");
 static_assert(stages_partition<Geo<double, 2>>(), "c128 two-vector stage plan");
+
+template <typename R, int NV>
+__host__ __device__ constexpr size_t tile_bytes() { return ((size_t)1 << Geo<R, NV>::T) * sizeof(R) * 2; }
+
+// shared memory of one pass CTA: pipeline buffers, phase table, cut masks
+template <typename R, int NV>
+__host__ __device__ constexpr size_t pass_smem_total()
+{
+    return (size_t)Geo<R, NV>::NSTAGE * NV * tile_bytes<R, NV>() + (size_t)MAXTAB * sizeof(R) * 2 +
+           (size_t)(MAXK + 1) * MAXN * 8 + 1024;
+}
+static_assert(pass_smem_total<float, 1>() <= 227 * 1024, "c64 pipeline smem");
+static_assert(pass_smem_total<float, 2>() <= 227 * 1024, "c64 adjoint pipeline smem");
+static_assert(pass_smem_total<double, 1>() <= 227 * 1024, "c128 pipeline smem");
+static_assert(pass_smem_total<double, 2>() <= 227 * 1024, "c128 adjoint pipeline smem");
 
 template <typename G>
 __host__ __device__ constexpr uint32_t reg_offset(int st, int m)
@@ -390,18 +503,31 @@ __device__ __forceinline__ void store_regs(typename CT<R>::T *sv, uint32_t sb,
     }
 }
 
+// The pass's scalar controls, copied from the parameter space into registers
+// once per CTA.
+struct PassRegs {
+    int n, s, is_low, hmask, load, pre_phase, pre_lambda, write, post;
+    double amp0;
+};
+
 template <typename R>
 struct StageCtx {
     typename CT<R>::T *sv0, *sv1;
     const typename CT<R>::T *tab;
+    const uint64_t *cost_nbr, *obs_nbr;
+    const int *obs_w;
+    int obs_k;
     uint64_t fixed;
     int s, tid;
-    R cb, sb;
+    bool first;
+    bool use_cot;  // which butterfly form (|sin beta| > |cos beta|)
+    R tq;          // tan beta or cot beta (the inverse mixer flips the sign)
+    R f;           // factor dropped by one butterfly: cos beta or sin beta
 };
 
-// One register stage of a pass. NV = vectors carried (1: forward, 2: adjoint).
+// One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
 template <typename R, int NV, int ST>
-__device__ __forceinline__ void run_stage(const PassArgs &A, const StageCtx<R> &X,
+__device__ __forceinline__ void run_stage(const PassRegs &A, const StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                           typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc0,
                                           double &acc1)
@@ -409,7 +535,7 @@ __device__ __forceinline__ void run_stage(const PassArgs &A, const StageCtx<R> &
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
     constexpr int RB = G::RB, NR = 1 << RB, NTB = G::T - RB;
-    constexpr bool FIRST = (ST == 0), LAST = (ST == G::NST - 1);
+    constexpr bool LAST = (ST == G::NST - 1);
 
     uint32_t base = 0;
 #pragma unroll
@@ -417,14 +543,15 @@ __device__ __forceinline__ void run_stage(const PassArgs &A, const StageCtx<R> &
         base |= ((uint32_t(X.tid) >> j) & 1u) << G::thr(ST, j);
     const uint32_t sb = G::swz(base);
 
-    if (FIRST && !A.load) {
+    if (ST == 0 && !A.load) {
 #pragma unroll
         for (int m = 0; m < NR; m++)
             a[m] = mkc<C>((R)A.amp0, (R)0);
     } else {
         load_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
-            load_regs<R, NV, ST>(X.sv1, sb, l);
+            if (!(X.first && A.pre_lambda))
+                load_regs<R, NV, ST>(X.sv1, sb, l);
     }
 
     int gp[RB];
@@ -435,85 +562,111 @@ __device__ __forceinline__ void run_stage(const PassArgs &A, const StageCtx<R> &
     }
     const uint64_t x0 = X.fixed | (uint64_t)(base & ((1u << G::CB) - 1u)) | ((uint64_t)(base >> G::CB) << X.s);
 
-    if (FIRST && A.pre_phase) {
+    if (ST == 0 && A.pre_phase) {
         int cv[NR];
-        eval_cost<RB>(A.cost, A.n, x0, gp, cv);
+        eval_cost_s<RB>(X.cost_nbr, A.n, x0, gp, cv);
 #pragma unroll
         for (int m = 0; m < NR; m++)
             a[m] = cmul(a[m], X.tab[cv[m]]);
     }
+    if constexpr (NV == 2) {
+        if (X.first && A.pre_lambda) {  // lambda = O phi, from the stored final state
+            int ov[NR];
+            eval_cut_s<RB>(X.obs_nbr, X.obs_w, X.obs_k, A.n, x0, gp, ov);
+#pragma unroll
+            for (int m = 0; m < NR; m++)
+                l[m] = mkc<C>(a[m].x * (R)ov[m], a[m].y * (R)ov[m]);
+        }
+    }
 
-    R gb = 0;
+    // butterflies in tan/cot form; after j of them the vectors carry 1/f^j,
+    // so an inner product taken before butterfly j+1 is scaled by f^(2j)
+    R gb = 0, scale = 1;
 #pragma unroll
     for (int k = 0; k < RB; k++) {
         if (!((G::own(ST) >> k) & 1))
             continue;
         bool due = true;
-        if (ST != 0)
+        if (G::reg(ST, k) >= G::CB)
             due = (A.hmask >> (G::reg(ST, k) - G::CB)) & 1;
+        else
+            due = A.is_low;
         if (!due)
             continue;
+        R ip = 0;
+        if (X.use_cot) {
+#pragma unroll
+            for (int m = 0; m < NR; m++) {
+                if (m & (1 << k))
+                    continue;
+                const int m1 = m | (1 << k);
+                if constexpr (NV == 2) {
+                    ip += im_conj_mul(l[m], a[m1]) + im_conj_mul(l[m1], a[m]);
+                    bfly_cot(l[m], l[m1], X.tq);
+                }
+                bfly_cot(a[m], a[m1], X.tq);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < NR; m++) {
+                if (m & (1 << k))
+                    continue;
+                const int m1 = m | (1 << k);
+                if constexpr (NV == 2) {
+                    ip += im_conj_mul(l[m], a[m1]) + im_conj_mul(l[m1], a[m]);
+                    bfly_tan(l[m], l[m1], X.tq);
+                }
+                bfly_tan(a[m], a[m1], X.tq);
+            }
+        }
+        if constexpr (NV == 2)
+            gb = fma(ip, scale * scale, gb);
+        scale *= X.f;
+    }
+    if (scale != (R)1) {  // restore the true amplitudes: multiply by f^j
 #pragma unroll
         for (int m = 0; m < NR; m++) {
-            if (m & (1 << k))
-                continue;
-            const int m1 = m | (1 << k);
+            a[m].x *= scale;
+            a[m].y *= scale;
             if constexpr (NV == 2) {
-                gb += im_conj_mul(l[m], a[m1]) + im_conj_mul(l[m1], a[m]);
-                bfly(l[m], l[m1], X.cb, X.sb);
+                l[m].x *= scale;
+                l[m].y *= scale;
             }
-            bfly(a[m], a[m1], X.cb, X.sb);
         }
     }
     if constexpr (NV == 2)
         acc0 += (double)gb;
 
-    bool lambda_out = false;
-    if (LAST && A.post) {
-        if (A.post & (POST_REDUCE | POST_LAMBDA)) {
-            int ov[NR];
-            eval_cut<RB>(A.obs, A.n, x0, gp, ov);
-            if (A.post & POST_REDUCE) {
-                R e = 0;
+    if (LAST && (A.post & POST_REDUCE)) {
+        int ov[NR];
+        eval_cut_s<RB>(X.obs_nbr, X.obs_w, X.obs_k, A.n, x0, gp, ov);
+        R e = 0;
+#pragma unroll
+        for (int m = 0; m < NR; m++)
+            e += (a[m].x * a[m].x + a[m].y * a[m].y) * (R)ov[m];
+        acc0 += (double)e;
+    }
+    if constexpr (NV == 2) {
+        if (LAST && (A.post & (POST_GAMMA | POST_PHASE_CONJ))) {
+            int cv[NR];
+            eval_cost_s<RB>(X.cost_nbr, A.n, x0, gp, cv);
+            if (A.post & POST_GAMMA) {
+                R g = 0;
 #pragma unroll
                 for (int m = 0; m < NR; m++)
-                    e += (a[m].x * a[m].x + a[m].y * a[m].y) * (R)ov[m];
-                acc0 += (double)e;
+                    g += (R)cv[m] * im_conj_mul(l[m], a[m]);
+                acc1 += (double)g;
             }
-            if constexpr (NV == 1) {
-                if (A.post & POST_LAMBDA) {
-                    C lam[NR];
+            if (A.post & POST_PHASE_CONJ) {
 #pragma unroll
-                    for (int m = 0; m < NR; m++)
-                        lam[m] = mkc<C>(a[m].x * (R)ov[m], a[m].y * (R)ov[m]);
-                    store_regs<R, NV, ST>(X.sv1, sb, lam);
-                    lambda_out = true;
-                }
-            }
-        }
-        if constexpr (NV == 2) {
-            if (A.post & (POST_GAMMA | POST_PHASE_CONJ)) {
-                int cv[NR];
-                eval_cost<RB>(A.cost, A.n, x0, gp, cv);
-                if (A.post & POST_GAMMA) {
-                    R g = 0;
-#pragma unroll
-                    for (int m = 0; m < NR; m++)
-                        g += (R)cv[m] * im_conj_mul(l[m], a[m]);
-                    acc1 += (double)g;
-                }
-                if (A.post & POST_PHASE_CONJ) {
-#pragma unroll
-                    for (int m = 0; m < NR; m++) {
-                        const C t = X.tab[cv[m]];
-                        a[m] = cmul_conj(a[m], t);
-                        l[m] = cmul_conj(l[m], t);
-                    }
+                for (int m = 0; m < NR; m++) {
+                    const C t = X.tab[cv[m]];
+                    a[m] = cmul_conj(a[m], t);
+                    l[m] = cmul_conj(l[m], t);
                 }
             }
         }
     }
-    (void)lambda_out;
     if (!LAST || A.write) {
         store_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
@@ -521,142 +674,229 @@ __device__ __forceinline__ void run_stage(const PassArgs &A, const StageCtx<R> &
     }
 }
 
-// Fixed-order sum of the per-block partials by the last block to finish.
+// Was any tile of point b processed by CTA c? (CTA c takes tiles c, c+G, ...)
+__device__ __forceinline__ bool cta_touches(unsigned c, unsigned b, unsigned tiles, unsigned grid, unsigned total)
+{
+    const unsigned lo = b * tiles, hi = lo + tiles;
+    unsigned g0 = c;
+    if (g0 < lo)
+        g0 += ((lo - c + grid - 1) / grid) * grid;
+    return g0 < hi && g0 < total;
+}
+
+// partials[slot][b][cta]; the last CTA to finish sums them in a fixed order
 template <int NTHR>
-__device__ void last_block_reduce(const PassArgs &A, double s0, double s1, double (*red)[32], unsigned tile,
-                                  int b, int B)
+__device__ void pass_final_reduce(const PassArgs &A, double (*red)[32], unsigned total)
 {
     __shared__ unsigned s_last;
-    const size_t plane = (size_t)B * A.tiles;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        A.partials[(size_t)b * A.tiles + tile] = s0;
-        A.partials[plane + (size_t)b * A.tiles + tile] = s1;
         __threadfence();
-        const unsigned total = gridDim.x * gridDim.y;
-        s_last = (atomicAdd(A.counter, 1u) == total - 1u) ? 1u : 0u;
+        s_last = (atomicAdd(A.counter, 1u) == gridDim.x - 1u) ? 1u : 0u;
     }
     __syncthreads();
     if (!s_last)
         return;
     __threadfence();
+    const unsigned G = gridDim.x;
     for (int slot = 0; slot < 2; slot++) {
         if (A.slot_idx[slot] < 0)
             continue;
-        for (int bb = 0; bb < B; bb++) {
-            const double *src = A.partials + slot * plane + (size_t)bb * A.tiles;
+        for (int b = 0; b < A.B; b++) {
+            const double *src = A.partials + ((size_t)slot * A.B + b) * G;
             double a = 0.0, dummy = 0.0;
-            for (int t = threadIdx.x; t < A.tiles; t += NTHR)
-                a += __ldcg(src + t);
+            for (unsigned c = threadIdx.x; c < G; c += NTHR)
+                if (cta_touches(c, (unsigned)b, (unsigned)A.tiles, G, total))
+                    a += __ldcg(src + c);
             block_sum2<NTHR>(a, dummy, red);
             if (threadIdx.x == 0)
-                A.out[(size_t)bb * A.out_stride + A.slot_idx[slot]] += A.slot_scale[slot] * a;
+                A.out[(size_t)b * A.out_stride + A.slot_idx[slot]] += A.slot_scale[slot] * a;
         }
     }
     if (threadIdx.x == 0)
         *A.counter = 0u;
 }
 
-// One tiled pass over B statevectors: grid (tiles, B), one 64 KB tile per
-// vector per block.
+// Persistent tiled pass over A.B statevectors. CTA c handles tiles c, c+G,
+// c+2G, ... (G = gridDim.x) of the B x tiles sequence; NSTAGE tiles are in
+// flight: thread 0 issues the TMA load of tile k+NSTAGE-1 while tile k is in
+// the register stages, and the TMA store of tile k from the same buffer.
 template <typename R, int NV>
-__global__ void __launch_bounds__(Geo<R, NV>::NTHR)
+__global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
     k_pass(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
            const __grid_constant__ PassArgs A)
 {
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
-    constexpr int NR = 1 << G::RB;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar;
+    constexpr int NR = 1 << G::RB, NS = G::NSTAGE;
+    constexpr uint32_t TB = (uint32_t)tile_bytes<R, NV>();
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment (TMA 128-byte swizzle) by pointer arithmetic on the
+    // shared array itself, so every tile access stays a shared-memory access
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    __shared__ __align__(8) uint64_t bars[NS];
     __shared__ double red[2][32];
-    __shared__ int s_abort;
+    __shared__ int s_flag;
 
     const int tid = threadIdx.x;
-    const int b = blockIdx.y;
-    const unsigned tile = blockIdx.x;
-    const int nbuf = (NV == 2 || (A.post & POST_LAMBDA)) ? 2 : 1;
-    C *sv0 = reinterpret_cast<C *>(sm);
-    C *sv1 = reinterpret_cast<C *>(sm + 65536);
-    C *tab = reinterpret_cast<C *>(sm + nbuf * 65536);
+    C *tab = reinterpret_cast<C *>(sm + (size_t)NS * NV * TB);
+    uint64_t *cost_nbr = reinterpret_cast<uint64_t *>(tab + MAXTAB);
+    uint64_t *obs_nbr = cost_nbr + MAXN;
+    __shared__ int obs_w[MAXK];
 
+    const unsigned total = (unsigned)A.tiles * (unsigned)A.B;
+    const unsigned grid = gridDim.x;
+    const unsigned niter = blockIdx.x < total ? (total - blockIdx.x + grid - 1) / grid : 0;
     const int midbits = A.s - G::CB;
-    const unsigned mid = tile & ((1u << midbits) - 1u);
-    const unsigned hi = tile >> midbits;
-    const uint64_t fixed = ((uint64_t)mid << G::CB) | ((uint64_t)hi << (A.s + G::HB));
-    const int c4 = (int)(hi + (unsigned)b * ((unsigned)A.tiles >> midbits));
+    const unsigned tiles_per_hi = (unsigned)A.tiles >> midbits;  // 2^(n - s - HB)
 
     if (tid == 0) {
-        // a block that starts after another one timed out does no work
-        s_abort = *reinterpret_cast<volatile int *>(A.err) ? 1 : 0;
-        mbar_init(&bar, 1);
+        s_flag = *reinterpret_cast<volatile int *>(A.err) ? 1 : 0;
+        for (int s = 0; s < NS; s++)
+            mbar_init(&bars[s], 1);
         fence_barrier_init();
     }
+    for (int i = tid; i < MAXN; i += G::NTHR)
+        cost_nbr[i] = A.cost.nbr[i];
+    for (int i = tid; i < A.obs.K * MAXN; i += G::NTHR)
+        obs_nbr[i] = A.obs.nbr[i / MAXN][i % MAXN];
+    if (tid < MAXK)
+        obs_w[tid] = A.obs.w[tid];
     __syncthreads();
-    if (s_abort)
+    if (s_flag)
         return;
-    if (tid == 0 && A.load) {
-        mbar_arrive_expect_tx(&bar, (uint32_t)A.nvec_io * 65536u);
-        tma_load_5d(sv0, &map0, &bar, 0, (int)mid, 0, 0, c4);
+
+    auto tile_coords = [&](unsigned k, unsigned &b, unsigned &t, unsigned &mid, int &c4) {
+        const unsigned g = blockIdx.x + k * grid;
+        b = g / (unsigned)A.tiles;
+        t = g - b * (unsigned)A.tiles;
+        mid = t & ((1u << midbits) - 1u);
+        const unsigned hi = t >> midbits;
+        c4 = (int)(hi + b * tiles_per_hi);
+    };
+    auto issue_load = [&](unsigned k) {
+        unsigned b, t, mid;
+        int c4;
+        tile_coords(k, b, t, mid, c4);
+        const int s = (int)(k % NS);
+        unsigned char *buf = sm + (size_t)s * NV * TB;
+        mbar_arrive_expect_tx(&bars[s], (uint32_t)A.nvec_io * TB);
+        tma_load_5d(buf, &map0, &bars[s], 0, (int)mid, 0, 0, c4);
         if (A.nvec_io == 2)
-            tma_load_5d(sv1, &map1, &bar, 0, (int)mid, 0, 0, c4);
-    }
-    if (A.pre_phase || (A.post & POST_PHASE_CONJ)) {
-        const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.layer) * A.tab_len;
-        for (int i = tid; i < A.tab_len; i += G::NTHR)
-            tab[i] = src[i];
-    }
-    const double2 csd = A.cs[(size_t)b * A.p + A.layer];
+            tma_load_5d(buf + TB, &map1, &bars[s], 0, (int)mid, 0, 0, c4);
+    };
+    if (tid == 0 && A.load)
+        for (unsigned k = 0; k < (unsigned)(NS - 1) && k < niter; k++)
+            issue_load(k);
+
+    const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.amp0};
+    double acc0 = 0.0, acc1 = 0.0;
+    int cur_b = -1;
     StageCtx<R> X;
-    X.sv0 = sv0;
-    X.sv1 = sv1;
     X.tab = tab;
-    X.fixed = fixed;
+    X.cost_nbr = cost_nbr;
+    X.obs_nbr = obs_nbr;
+    X.obs_w = obs_w;
+    X.obs_k = A.obs.K;
     X.s = A.s;
     X.tid = tid;
-    X.cb = (R)csd.x;
-    X.sb = (R)(A.sign_s * csd.y);
+    X.first = true;
 
-    if (A.load) {
-        if (!mbar_wait_bounded(&bar, 0))
-            atomicOr(&s_abort, 1);
-    }
-    __syncthreads();
-    if (s_abort) {
-        if (tid == 0) {
-            atomicExch(A.err, 1);
-            mbar_wait_bounded(&bar, 0);
-        }
-        return;
-    }
-
-    C a[NR], l[NR];
-    double acc0 = 0.0, acc1 = 0.0;
-    if (A.is_low) {
-        run_stage<R, NV, 0>(A, X, a, l, acc0, acc1);
-        __syncthreads();
-    }
-    run_stage<R, NV, 1>(A, X, a, l, acc0, acc1);
-    __syncthreads();
-    run_stage<R, NV, 2>(A, X, a, l, acc0, acc1);
-    if constexpr (G::NST == 4) {
-        __syncthreads();
-        run_stage<R, NV, 3>(A, X, a, l, acc0, acc1);
-    }
-
-    if (A.write) {
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tma_store_5d(&map0, sv0, 0, (int)mid, 0, 0, c4);
-            if (nbuf == 2)
-                tma_store_5d(&map1, sv1, 0, (int)mid, 0, 0, c4);
-            tma_store_commit_and_wait_read();
-        }
-    }
-    if (A.slot_idx[0] >= 0 || A.slot_idx[1] >= 0) {
+    auto flush = [&](int b) {  // this CTA's sums for point b -> partials
         block_sum2<G::NTHR>(acc0, acc1, red);
-        last_block_reduce<G::NTHR>(A, acc0, acc1, red, tile, b, gridDim.y);
+        if (tid == 0) {
+            A.partials[((size_t)0 * A.B + b) * grid + blockIdx.x] = acc0;
+            A.partials[((size_t)1 * A.B + b) * grid + blockIdx.x] = acc1;
+        }
+        acc0 = acc1 = 0.0;
+    };
+    const bool reduce = A.slot_idx[0] >= 0 || A.slot_idx[1] >= 0;
+
+    for (unsigned k = 0; k < niter; k++) {
+        unsigned b, t, mid;
+        int c4;
+        tile_coords(k, b, t, mid, c4);
+        const int s = (int)(k % NS);
+        unsigned char *buf = sm + (size_t)s * NV * TB;
+        if ((int)b != cur_b) {  // new parameter point: its phase table and mixer angle
+            if (cur_b >= 0 && reduce)
+                flush(cur_b);
+            __syncthreads();
+            if (A.pre_phase || (A.post & POST_PHASE_CONJ)) {
+                const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.layer) * A.tab_len;
+                for (int i = tid; i < A.tab_len; i += G::NTHR)
+                    tab[i] = src[i];
+            }
+            const double2 csd = A.cs[(size_t)b * A.p + A.layer];
+            const double cb = csd.x, sb = A.sign_s * csd.y;
+            X.use_cot = fabs(sb) > fabs(cb);
+            X.tq = X.use_cot ? (R)(cb / sb) : (R)(sb / cb);
+            X.f = X.use_cot ? (R)sb : (R)cb;
+            cur_b = (int)b;
+            __syncthreads();
+        }
+        X.sv0 = reinterpret_cast<C *>(buf);
+        X.sv1 = reinterpret_cast<C *>(buf + TB);
+        X.fixed = ((uint64_t)mid << G::CB) | ((uint64_t)(t >> midbits) << (A.s + G::HB));
+
+        if (A.load) {
+            if (!mbar_wait_bounded(&bars[s], (k / NS) & 1u))
+                atomicOr(&s_flag, 1);
+        } else if (tid == 0 && A.write) {
+            // the stage buffer is rewritten by this tile's threads: the store
+            // of tile k-NS from it must have finished reading (at most NS-1
+            // younger store groups may still be pending)
+            asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory");
+            static_assert(NS == 3, "wait_group immediate assumes three stages");
+        }
+        __syncthreads();
+        if (s_flag) {  // a tile never arrived: record, drain our own copies, stop
+            if (tid == 0) {
+                atomicExch(A.err, 1);
+                for (unsigned q = k; q < k + NS - 1 && q < niter; q++)
+                    mbar_wait_bounded(&bars[q % NS], (q / NS) & 1u);
+                asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+            }
+            return;
+        }
+
+        C a[NR], l[NR];
+        X.first = true;
+        if (P.is_low) {
+            run_stage<R, NV, 0>(P, X, a, l, acc0, acc1);
+            X.first = false;
+            __syncthreads();
+        }
+        run_stage<R, NV, 1>(P, X, a, l, acc0, acc1);
+        X.first = false;
+        __syncthreads();
+        // refill the buffer freed by tile k-1: its store was committed two
+        // register stages ago and has finished reading shared memory by now
+        if (tid == 0 && A.load && k + NS - 1 < niter) {
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            issue_load(k + NS - 1);
+        }
+        run_stage<R, NV, 2>(P, X, a, l, acc0, acc1);
+        if (P.write) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tma_store_5d(&map0, buf, 0, (int)mid, 0, 0, c4);
+                if (NV == 2)
+                    tma_store_5d(&map1, buf + TB, 0, (int)mid, 0, 0, c4);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+        } else {
+            fence_proxy_async_smem();  // generic reads before the buffer's next TMA load
+            __syncthreads();
+        }
+    }
+    if (tid == 0)
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (reduce) {
+        if (cur_b >= 0)
+            flush(cur_b);
+        pass_final_reduce<G::NTHR>(A, red, total);
     }
 }
 
@@ -988,9 +1228,37 @@ __global__ void __launch_bounds__(256) k_agg_terms(const __grid_constant__ AggAr
 // ------------------------------------------------------------- launchers
 int tile_bits(bool c128) { return c128 ? Geo<double, 1>::T : Geo<float, 1>::T; }
 
-size_t pass_smem_bytes(bool c128, int nbuf)
+void pass_geometry(bool c128, int nv, int *T, int *CB, int *HB)
 {
-    return (size_t)nbuf * 65536 + (size_t)MAXTAB * (c128 ? 16 : 8) + 1024;
+    if (c128) {
+        *T = nv == 2 ? Geo<double, 2>::T : Geo<double, 1>::T;
+        *CB = nv == 2 ? Geo<double, 2>::CB : Geo<double, 1>::CB;
+        *HB = nv == 2 ? Geo<double, 2>::HB : Geo<double, 1>::HB;
+    } else {
+        *T = nv == 2 ? Geo<float, 2>::T : Geo<float, 1>::T;
+        *CB = nv == 2 ? Geo<float, 2>::CB : Geo<float, 1>::CB;
+        *HB = nv == 2 ? Geo<float, 2>::HB : Geo<float, 1>::HB;
+    }
+}
+
+int device_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) ==
+                                                       cudaSuccess && v > 0)
+            sms = v;
+        else
+            return 152;
+    }
+    return sms;
+}
+
+int pass_grid(long long total_tiles)
+{
+    const long long g = device_sms();
+    return (int)(total_tiles < g ? total_tiles : g);
 }
 
 int launch_params(bool c128, int B, int p, int tab_len, const double *d_gamma, const double *d_beta, void *d_tab,
@@ -1006,30 +1274,28 @@ int launch_params(bool c128, int B, int p, int tab_len, const double *d_gamma, c
 }
 
 template <typename R, int NV>
-static int launch_pass_t(int nbuf, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int B,
-                         cudaStream_t st)
+static int launch_pass_t(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid, cudaStream_t st)
 {
-    const size_t smem = pass_smem_bytes(sizeof(R) == 8, nbuf);
-    static bool attr_done[3] = {false, false, false};
-    if (!attr_done[nbuf]) {
+    const size_t smem = pass_smem_total<R, NV>();
+    static bool attr_done = false;
+    if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_pass<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return (int)e;
-        attr_done[nbuf] = true;
+        attr_done = true;
     }
-    dim3 grid((unsigned)a.tiles, (unsigned)B);
     k_pass<R, NV><<<grid, Geo<R, NV>::NTHR, smem, st>>>(m0, m1, a);
     return (int)cudaGetLastError();
 }
 
-int launch_pass(bool c128, int nv_kernel, int nbuf, const CUtensorMap &m0, const CUtensorMap &m1,
-                const PassArgs &a, int B, cudaStream_t st)
+int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
+                cudaStream_t st)
 {
     if (c128)
-        return nv_kernel == 2 ? launch_pass_t<double, 2>(nbuf, m0, m1, a, B, st)
-                              : launch_pass_t<double, 1>(nbuf, m0, m1, a, B, st);
-    return nv_kernel == 2 ? launch_pass_t<float, 2>(nbuf, m0, m1, a, B, st)
-                          : launch_pass_t<float, 1>(nbuf, m0, m1, a, B, st);
+        return nv_kernel == 2 ? launch_pass_t<double, 2>(m0, m1, a, grid, st)
+                              : launch_pass_t<double, 1>(m0, m1, a, grid, st);
+    return nv_kernel == 2 ? launch_pass_t<float, 2>(m0, m1, a, grid, st)
+                          : launch_pass_t<float, 1>(m0, m1, a, grid, st);
 }
 
 size_t small_smem_bytes(bool c128, int n, int mode)
