@@ -78,7 +78,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 struct Pass {
-    int s, is_low, hmask;
+    int s;       // first qubit of the tile rows
+    int cb;      // contiguous bits per row
+    int is_low;  // contiguous tile whose low qubits are transformed
+    int hmask;   // high local bits that receive a butterfly
+    int wide;    // tensor-map form (rows of more than 128 bytes)
 };
 
 struct Layout {
@@ -191,8 +195,8 @@ Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
     off = align256(off + 2 * B * pl->p * sizeof(double));
     L.cs = off;
     off = align256(off + B * pl->p * sizeof(double2));
-    L.tab = off;
-    off = align256(off + B * pl->p * pl->tab_len() * pl->amp());
+    L.tab = off;  // three tables: exact, forward-scaled, inverse layer
+    off = align256(off + 3 * B * pl->p * pl->tab_len() * pl->amp());
     const size_t pass_partials = pl->small() ? 0 : 2 * B * (size_t)device_sms();
     const size_t agg_partials = 64 * (size_t)agg_grid(pl->c128);
     L.partial_count = pass_partials > agg_partials ? pass_partials : agg_partials;
@@ -209,47 +213,62 @@ Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
     return L;
 }
 
-// 5-D view of B statevectors for tiles of one 128-byte row (local bits
-// 0..cb-1) times 2^hb rows along qubits s..s+hb-1: dims (16 x 8 B, mid bits
-// cb..s-1, 2^(hb-4), 16, fixed high bits and batch).
-int make_map(CUtensorMap *map, void *base, int n, int s, int cb, int hb, size_t amp, int B)
+// 5-D view of B statevectors for tiles of 2^T amplitudes: rows of 2^cb
+// contiguous amplitudes along qubits s..s+T-cb-1. A 128-byte segment holds
+// 2^cbmin amplitudes. Nine row qubits (cb = cbmin) need two box dimensions
+// (32 x 16 rows); up to eight fit one (wide form, rows of 2^(cb-cbmin)
+// segments).
+int make_map(CUtensorMap *map, void *base, int n, int s, int cb, int T, int cbmin, size_t amp, int B, int *wide)
 {
     auto fn = encode_fn();
     if (!fn)
         return fail(AAQAOA_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable from the driver");
-    const int h1 = hb - 4;
-    cuuint64_t dims[5] = {16, (cuuint64_t)1 << (s - cb), (cuuint64_t)1 << h1, 16,
-                          ((cuuint64_t)1 << (n - s - hb)) * (cuuint64_t)B};
-    cuuint64_t strides[4] = {128, ((cuuint64_t)1 << s) * amp, ((cuuint64_t)1 << (s + h1)) * amp,
-                             ((cuuint64_t)1 << (s + hb)) * amp};
-    cuuint32_t box[5] = {16, 1, (cuuint32_t)1 << h1, 16, 1};
+    const int h = T - cb;
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5];
+    if (h == 9) {
+        dims[0] = 16; dims[1] = (cuuint64_t)1 << (s - cb); dims[2] = 32; dims[3] = 16;
+        dims[4] = ((cuuint64_t)1 << (n - s - 9)) * (cuuint64_t)B;
+        strides[0] = 128; strides[1] = ((cuuint64_t)1 << s) * amp; strides[2] = ((cuuint64_t)1 << (s + 5)) * amp;
+        strides[3] = ((cuuint64_t)1 << (s + 9)) * amp;
+        box[0] = 16; box[1] = 1; box[2] = 32; box[3] = 16; box[4] = 1;
+        *wide = 0;
+    } else if (h >= 0 && h <= 8 && cb >= cbmin) {
+        dims[0] = 16; dims[1] = (cuuint64_t)1 << (cb - cbmin); dims[2] = (cuuint64_t)1 << (s - cb);
+        dims[3] = (cuuint64_t)1 << h; dims[4] = ((cuuint64_t)1 << (n - s - h)) * (cuuint64_t)B;
+        strides[0] = 128; strides[1] = ((cuuint64_t)1 << cb) * amp; strides[2] = ((cuuint64_t)1 << s) * amp;
+        strides[3] = ((cuuint64_t)1 << (s + h)) * amp;
+        box[0] = 16; box[1] = (cuuint32_t)1 << (cb - cbmin); box[2] = 1; box[3] = (cuuint32_t)1 << h; box[4] = 1;
+        *wide = 1;
+    } else {
+        return fail(AAQAOA_ERR_UNSUPPORTED, "tile of %d row qubits", h);
+    }
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
-        return fail(AAQAOA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for n=%d s=%d", (int)r, n, s);
+        return fail(AAQAOA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for n=%d s=%d cb=%d", (int)r, n, s, cb);
     return AAQAOA_OK;
 }
 
-// Passes of one layer for tiles of T qubits (CB contiguous + HB high): a low
-// pass over qubits 0..T-1, then high passes of HB qubits; the last high pass
-// is shifted down to end at qubit n-1 and only transforms qubits not yet done.
-std::vector<Pass> make_passes(int n, int T, int CB, int HB)
+// Passes of one layer for tiles of T qubits: a low pass over qubits
+// 0..T-1 (contiguous tiles), then K = ceil((n-T)/hbmax) high passes that
+// share the remaining n-T qubits evenly. A high pass with h < hbmax row qubits
+// spends the spare tile bits on longer contiguous rows (cb = T-h), which keeps
+// the strided passes close to streaming bandwidth.
+std::vector<Pass> make_passes(int n, int T, int cbmin, int hbmax)
 {
     std::vector<Pass> v;
     if (n <= T)
         return v;
-    v.push_back({CB, 1, (1 << HB) - 1});
-    int covered = T;
-    while (covered < n) {
-        const int s = covered < n - HB ? covered : n - HB;
-        int hm = 0;
-        for (int j = 0; j < HB; j++)
-            if (s + j >= covered && s + j < n)
-                hm |= 1 << j;
-        v.push_back({s, 0, hm});
-        covered = s + HB;
+    v.push_back({cbmin, cbmin, 1, (1 << (T - cbmin)) - 1, 0});
+    const int r = n - T, K = (r + hbmax - 1) / hbmax;
+    int s = T;
+    for (int k = 0; k < K; k++) {
+        const int h = r / K + (k < r % K ? 1 : 0);
+        v.push_back({s, T - h, 0, (1 << h) - 1, 0});
+        s += h;
     }
     return v;
 }
@@ -261,6 +280,12 @@ void build_passes(aaqaoa_plan *pl)
     pl->passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB);
     pass_geometry(pl->c128, 2, &T, &CB, &HB);
     pl->bwd_passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB);
+}
+
+// table `kind` (0 exact, 1 forward-scaled, 2 inverse) of a call with B points
+const void *tab_kind(const aaqaoa_plan *pl, const void *base, int B, int kind)
+{
+    return static_cast<const unsigned char *>(base) + (size_t)kind * B * pl->p * pl->tab_len() * pl->amp();
 }
 
 PassArgs base_args(const aaqaoa_plan *pl, int obs)
@@ -298,16 +323,21 @@ int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
             PassArgs a = base_args(pl, obs);
             a.B = B;
             a.s = ps.s;
+            a.cb = ps.cb;
+            a.wide_rows = ps.wide;
             a.is_low = ps.is_low;
             a.hmask = ps.hmask;
             a.layer = l;
             a.sign_s = 1.0;
+            a.tab = tab_kind(pl, pl->d_tab(), B, 1);
             a.load = !(l == 0 && k == 0);
             a.pre_phase = (k == 0);
             a.nvec_io = 1;
             const bool last = (l == pl->p - 1 && k == np - 1);
             a.write = !(last && mode == FWD_ENERGY);
             a.post = (last && mode != FWD_STATE) ? POST_REDUCE : 0;
+            if (last && a.write)
+                a.post |= POST_RESCALE;
             if (last && mode != FWD_STATE) {
                 a.slot_idx[0] = 0;
                 a.slot_scale[0] = 1.0;
@@ -331,6 +361,7 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
     const int np = (int)pl->bwd_passes.size();
     bool first = true;
     for (int l = pl->p - 1; l >= 0; l--) {
+        int j0 = 0;  // qubits of this layer's inverse mixer done by earlier passes
         for (int kk = np - 1; kk >= 0; kk--) {
             const Pass &ps = pl->bwd_passes[kk];
             const bool last_of_layer = (kk == 0);
@@ -338,10 +369,15 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
             a.B = B;
             a.tiles = tiles;
             a.s = ps.s;
+            a.cb = ps.cb;
+            a.wide_rows = ps.wide;
             a.is_low = ps.is_low;
             a.hmask = ps.hmask;
             a.layer = l;
             a.sign_s = -1.0;
+            a.tab = tab_kind(pl, pl->d_tab(), B, 2);
+            a.j0 = j0;
+            j0 += ps.is_low ? T : __builtin_popcount((unsigned)ps.hmask);
             a.load = 1;
             a.pre_phase = 0;
             a.pre_lambda = first ? 1 : 0;
@@ -406,7 +442,7 @@ int enqueue_params(aaqaoa_plan *pl, int B, const double *d_gamma, const double *
 {
     (void)cudaGetLastError();  // a stale error of an unrelated earlier call must not be reported here
     ProfScope ps_(pl, PK_PARAMS, 0.0);
-    CKL(launch_params(pl->c128, B, pl->p, pl->tab_len(), d_gamma, d_beta, pl->d_tab(), pl->d_cs(), pl->stream),
+    CKL(launch_params(pl->c128, B, pl->p, pl->tab_len(), pl->n, d_gamma, d_beta, pl->d_tab(), pl->d_cs(), pl->stream),
         "parameter tables");
     pl->launches++;
     CK(cudaMemsetAsync(pl->d_out(), 0, (size_t)B * pl->out_stride() * sizeof(double), pl->stream));
@@ -709,17 +745,19 @@ int aaqaoa_set_workspace(aaqaoa_plan *pl, void *device_ptr, size_t bytes, int ba
     int T, CB, HB;
     pass_geometry(pl->c128, 1, &T, &CB, &HB);
     for (size_t k = 0; k < pl->passes.size(); k++) {
-        int r = make_map(&pl->map_phi[k], pl->d_phi(), pl->n, pl->passes[k].s, CB, HB, pl->amp(), batch);
+        Pass &ps = pl->passes[k];
+        int r = make_map(&pl->map_phi[k], pl->d_phi(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), batch, &ps.wide);
         if (r)
             return r;
     }
     if (with_grad) {
         pass_geometry(pl->c128, 2, &T, &CB, &HB);
         for (size_t k = 0; k < pl->bwd_passes.size(); k++) {
-            int r = make_map(&pl->map_bphi[k], pl->d_phi(), pl->n, pl->bwd_passes[k].s, CB, HB, pl->amp(), batch);
+            Pass &ps = pl->bwd_passes[k];
+            int r = make_map(&pl->map_bphi[k], pl->d_phi(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), batch, &ps.wide);
             if (r)
                 return r;
-            r = make_map(&pl->map_blam[k], pl->d_lam(), pl->n, pl->bwd_passes[k].s, CB, HB, pl->amp(), batch);
+            r = make_map(&pl->map_blam[k], pl->d_lam(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), batch, &ps.wide);
             if (r)
                 return r;
         }
@@ -1092,8 +1130,8 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
     off = align256(off + 2 * (size_t)p * sizeof(double));
     double2 *d_cs = reinterpret_cast<double2 *>(base + off);
     off = align256(off + (size_t)p * sizeof(double2));
-    void *d_tab = base + off;
-    off = align256(off + (size_t)p * pl->tab_len() * pl->amp());
+    void *d_tab = base + off;  // exact, forward-scaled and inverse tables
+    off = align256(off + 3 * (size_t)p * pl->tab_len() * pl->amp());
     double *d_part = reinterpret_cast<double *>(base + off);
     off = align256(off + 2 * (size_t)device_sms() * sizeof(double));
     if (off > STATIC_FIXED_BYTES)
@@ -1109,7 +1147,7 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
     CK(cudaMemsetAsync(d_out, 0, (size_t)pl->out_stride() * sizeof(double), st));
     CK(cudaMemcpyAsync(d_par, gamma, (size_t)p * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_par + p, beta, (size_t)p * sizeof(double), cudaMemcpyHostToDevice, st));
-    CKL(launch_params(pl->c128, 1, p, pl->tab_len(), d_par, d_par + p, d_tab, d_cs, st), "parameter tables");
+    CKL(launch_params(pl->c128, 1, p, pl->tab_len(), pl->n, d_par, d_par + p, d_tab, d_cs, st), "parameter tables");
 
     if (pl->small()) {
         SmallArgs s;
@@ -1133,8 +1171,10 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
         CUtensorMap maps[8];
         if (np > 8)
             return fail(AAQAOA_ERR_UNSUPPORTED, "%d passes per layer", np);
+        int wide[8];
         for (int k = 0; k < np; k++)
-            if ((r = make_map(&maps[k], d_phi, pl->n, pl->passes[k].s, pl->CB(), pl->HB(), pl->amp(), 1)))
+            if ((r = make_map(&maps[k], d_phi, pl->n, pl->passes[k].s, pl->passes[k].cb, pl->T(), pl->CB(), pl->amp(),
+                              1, &wide[k])))
                 return r;
         const int grid = pass_grid(pl->tiles());
         for (int l = 0; l < p; l++) {
@@ -1144,6 +1184,8 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
                 memset(&a, 0, sizeof a);
                 a.n = pl->n;
                 a.s = ps.s;
+                a.cb = ps.cb;
+                a.wide_rows = wide[k];
                 a.is_low = ps.is_low;
                 a.hmask = ps.hmask;
                 a.tiles = pl->tiles();
@@ -1159,7 +1201,7 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
                 a.tab_len = pl->tab_len();
                 a.sign_s = 1.0;
                 a.amp0 = std::pow(2.0, -0.5 * pl->n);
-                a.tab = d_tab;
+                a.tab = tab_kind(pl, d_tab, 1, 1);
                 a.cs = d_cs;
                 a.partials = d_part;
                 a.counter = d_counter;

@@ -29,15 +29,18 @@ struct CostFn {
 // Operations of one tiled pass over the statevector(s).
 enum PostOp : int {
     POST_REDUCE = 1,      // acc0 += |phi|^2 O(x)                 (energy)
+    POST_RESCALE = 2,     // multiply by f^n: the stored final state is exact
     POST_GAMMA = 4,       // acc1 += C(x) Im(conj(lambda) phi)     (dE/dgamma)
-    POST_PHASE_CONJ = 8,  // phi, lambda *= exp(+i gamma_l C(x))   (undo cost layer)
+    POST_PHASE_CONJ = 8,  // phi, lambda *= inverse-layer table    (undo cost layer)
 };
 
 struct PassArgs {
     int n;            // qubits
     int s;            // global bit of local high bit 0
+    int cb;           // contiguous bits of a tile row (local bits 0..cb-1 = qubits 0..cb-1)
+    int wide_rows;    // tensor map form: 1 when a row spans more than 128 bytes
     int is_low;       // tile is contiguous and its low bits are transformed here
-    int hmask;        // which local high bits receive a butterfly
+    int hmask;        // which local high bits (bit j = local bit cb + j) get a butterfly
     int tiles;        // tiles per statevector = 2^(n - tile bits)
     int B;            // statevectors (parameter points) in this launch
     int load;         // 1: TMA-load the tile(s); 0: generate |+>^n
@@ -47,11 +50,12 @@ struct PassArgs {
     int post;         // PostOp flags
     int nvec_io;      // vectors loaded (1 or 2)
     int layer;        // layer l (0-based): selects the phase table and (cos, sin)
+    int j0;           // butterflies of this layer applied by earlier passes (adjoint)
     int p;            // number of layers
     int tab_len;      // |E| + 1
     double sign_s;    // +1: exp(-i beta H_M); -1: its inverse
     double amp0;      // 2^(-n/2) for the generated |+>^n
-    const void *tab;  // phase tables [B][p][tab_len], complex in the amplitude precision
+    const void *tab;  // this pass's phase tables [B][p][tab_len]: forward-scaled or inverse
     const double2 *cs;  // [B][p] (cos beta_l, sin beta_l)
     double *partials; // [2][B][grid]
     unsigned *counter;  // last-block counter (zero between launches)
@@ -100,7 +104,7 @@ int tile_bits(bool c128);
 void pass_geometry(bool c128, int nv, int *T, int *CB, int *HB);
 int device_sms();
 int pass_grid(long long total_tiles);
-int launch_params(bool c128, int B, int p, int tab_len, const double *d_gamma, const double *d_beta,
+int launch_params(bool c128, int B, int p, int tab_len, int n, const double *d_gamma, const double *d_beta,
                   void *d_tab, double2 *d_cs, cudaStream_t st);
 int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a,
                 int grid, cudaStream_t st);

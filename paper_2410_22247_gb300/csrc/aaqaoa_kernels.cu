@@ -506,7 +506,7 @@ __device__ __forceinline__ void store_regs(typename CT<R>::T *sv, uint32_t sb,
 // The pass's scalar controls, copied from the parameter space into registers
 // once per CTA.
 struct PassRegs {
-    int n, s, is_low, hmask, load, pre_phase, pre_lambda, write, post;
+    int n, s, is_low, hmask, load, pre_phase, pre_lambda, write, post, j0;
     double amp0;
 };
 
@@ -518,16 +518,19 @@ struct StageCtx {
     const int *obs_w;
     int obs_k;
     uint64_t fixed;
-    int s, tid;
+    int s, cb, tid;  // high qubit s and contiguous bits cb of this pass's tiles
     bool first;
     bool use_cot;  // which butterfly form (|sin beta| > |cos beta|)
     R tq;          // tan beta or cot beta (the inverse mixer flips the sign)
     R f;           // factor dropped by one butterfly: cos beta or sin beta
+    R fn, fn2;     // f^n and f^(2n): one whole layer of butterflies
+    R scale0;      // f^j0: butterflies of this layer applied by earlier passes
+    R run;         // f^j for the current tile (advanced by every butterfly)
 };
 
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
 template <typename R, int NV, int ST>
-__device__ __forceinline__ void run_stage(const PassRegs &A, const StageCtx<R> &X,
+__device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                           typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc0,
                                           double &acc1)
@@ -558,9 +561,9 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, const StageCtx<R> &
 #pragma unroll
     for (int k = 0; k < RB; k++) {
         const int L = G::reg(ST, k);
-        gp[k] = L < G::CB ? L : X.s + L - G::CB;
+        gp[k] = L < X.cb ? L : X.s + L - X.cb;
     }
-    const uint64_t x0 = X.fixed | (uint64_t)(base & ((1u << G::CB) - 1u)) | ((uint64_t)(base >> G::CB) << X.s);
+    const uint64_t x0 = X.fixed | (uint64_t)(base & ((1u << X.cb) - 1u)) | ((uint64_t)(base >> X.cb) << X.s);
 
     if (ST == 0 && A.pre_phase) {
         int cv[NR];
@@ -579,21 +582,23 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, const StageCtx<R> &
         }
     }
 
-    // butterflies in tan/cot form; after j of them the vectors carry 1/f^j,
-    // so an inner product taken before butterfly j+1 is scaled by f^(2j)
-    R gb = 0, scale = 1;
+    // Butterflies in tan/cot form, no rescaling: after j butterflies of this
+    // layer the vectors carry 1/f^j (restored by the next phase table or the
+    // last pass), so an inner product taken before butterfly j+1 is scaled
+    // by f^(2j). Four independent FMA chains per inner product.
+    R gb = 0, sc = X.run;
 #pragma unroll
     for (int k = 0; k < RB; k++) {
         if (!((G::own(ST) >> k) & 1))
             continue;
         bool due = true;
-        if (G::reg(ST, k) >= G::CB)
-            due = (A.hmask >> (G::reg(ST, k) - G::CB)) & 1;
+        if (G::reg(ST, k) >= X.cb)
+            due = (A.hmask >> (G::reg(ST, k) - X.cb)) & 1;
         else
             due = A.is_low;
         if (!due)
             continue;
-        R ip = 0;
+        R ip[4] = {0, 0, 0, 0};
         if (X.use_cot) {
 #pragma unroll
             for (int m = 0; m < NR; m++) {
@@ -601,7 +606,11 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, const StageCtx<R> &
                     continue;
                 const int m1 = m | (1 << k);
                 if constexpr (NV == 2) {
-                    ip += im_conj_mul(l[m], a[m1]) + im_conj_mul(l[m1], a[m]);
+                    R &q = ip[(m >> (k == 0 ? 1 : 0)) & 3];
+                    q = fma(l[m].x, a[m1].y, q);
+                    q = fma(-l[m].y, a[m1].x, q);
+                    q = fma(l[m1].x, a[m].y, q);
+                    q = fma(-l[m1].y, a[m].x, q);
                     bfly_cot(l[m], l[m1], X.tq);
                 }
                 bfly_cot(a[m], a[m1], X.tq);
@@ -613,29 +622,31 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, const StageCtx<R> &
                     continue;
                 const int m1 = m | (1 << k);
                 if constexpr (NV == 2) {
-                    ip += im_conj_mul(l[m], a[m1]) + im_conj_mul(l[m1], a[m]);
+                    R &q = ip[(m >> (k == 0 ? 1 : 0)) & 3];
+                    q = fma(l[m].x, a[m1].y, q);
+                    q = fma(-l[m].y, a[m1].x, q);
+                    q = fma(l[m1].x, a[m].y, q);
+                    q = fma(-l[m1].y, a[m].x, q);
                     bfly_tan(l[m], l[m1], X.tq);
                 }
                 bfly_tan(a[m], a[m1], X.tq);
             }
         }
         if constexpr (NV == 2)
-            gb = fma(ip, scale * scale, gb);
-        scale *= X.f;
+            gb = fma((ip[0] + ip[1]) + (ip[2] + ip[3]), sc * sc, gb);
+        sc *= X.f;
     }
-    if (scale != (R)1) {  // restore the true amplitudes: multiply by f^j
-#pragma unroll
-        for (int m = 0; m < NR; m++) {
-            a[m].x *= scale;
-            a[m].y *= scale;
-            if constexpr (NV == 2) {
-                l[m].x *= scale;
-                l[m].y *= scale;
-            }
-        }
-    }
+    X.run = sc;
     if constexpr (NV == 2)
         acc0 += (double)gb;
+
+    if (LAST && (A.post & POST_RESCALE)) {  // the stored state is the exact one
+#pragma unroll
+        for (int m = 0; m < NR; m++) {
+            a[m].x *= X.fn;
+            a[m].y *= X.fn;
+        }
+    }
 
     if (LAST && (A.post & POST_REDUCE)) {
         int ov[NR];
@@ -644,7 +655,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, const StageCtx<R> &
 #pragma unroll
         for (int m = 0; m < NR; m++)
             e += (a[m].x * a[m].x + a[m].y * a[m].y) * (R)ov[m];
-        acc0 += (double)e;
+        acc0 += (A.post & POST_RESCALE) ? (double)e : (double)e * (double)X.fn2;
     }
     if constexpr (NV == 2) {
         if (LAST && (A.post & (POST_GAMMA | POST_PHASE_CONJ))) {
@@ -655,14 +666,14 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, const StageCtx<R> &
 #pragma unroll
                 for (int m = 0; m < NR; m++)
                     g += (R)cv[m] * im_conj_mul(l[m], a[m]);
-                acc1 += (double)g;
+                acc1 += (double)g * (double)X.fn2;  // both vectors carry 1/f^n here
             }
-            if (A.post & POST_PHASE_CONJ) {
+            if (A.post & POST_PHASE_CONJ) {  // inverse cost layer, restoring f^n
 #pragma unroll
                 for (int m = 0; m < NR; m++) {
                     const C t = X.tab[cv[m]];
-                    a[m] = cmul_conj(a[m], t);
-                    l[m] = cmul_conj(l[m], t);
+                    a[m] = cmul(a[m], t);
+                    l[m] = cmul(l[m], t);
                 }
             }
         }
@@ -747,8 +758,10 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
     const unsigned total = (unsigned)A.tiles * (unsigned)A.B;
     const unsigned grid = gridDim.x;
     const unsigned niter = blockIdx.x < total ? (total - blockIdx.x + grid - 1) / grid : 0;
-    const int midbits = A.s - G::CB;
-    const unsigned tiles_per_hi = (unsigned)A.tiles >> midbits;  // 2^(n - s - HB)
+    // tile = 2^cb contiguous amplitudes x 2^(T-cb) rows along qubits s..
+    const int cb = A.cb, hb = G::T - A.cb;
+    const int midbits = A.s - cb;
+    const unsigned tiles_per_hi = (unsigned)A.tiles >> midbits;  // 2^(n - s - hb)
 
     if (tid == 0) {
         s_flag = *reinterpret_cast<volatile int *>(A.err) ? 1 : 0;
@@ -781,15 +794,16 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
         const int s = (int)(k % NS);
         unsigned char *buf = sm + (size_t)s * NV * TB;
         mbar_arrive_expect_tx(&bars[s], (uint32_t)A.nvec_io * TB);
-        tma_load_5d(buf, &map0, &bars[s], 0, (int)mid, 0, 0, c4);
+        const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
+        tma_load_5d(buf, &map0, &bars[s], 0, c1, c2, 0, c4);
         if (A.nvec_io == 2)
-            tma_load_5d(buf + TB, &map1, &bars[s], 0, (int)mid, 0, 0, c4);
+            tma_load_5d(buf + TB, &map1, &bars[s], 0, c1, c2, 0, c4);
     };
     if (tid == 0 && A.load)
         for (unsigned k = 0; k < (unsigned)(NS - 1) && k < niter; k++)
             issue_load(k);
 
-    const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.amp0};
+    const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.j0, A.amp0};
     double acc0 = 0.0, acc1 = 0.0;
     int cur_b = -1;
     StageCtx<R> X;
@@ -799,6 +813,7 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
     X.obs_w = obs_w;
     X.obs_k = A.obs.K;
     X.s = A.s;
+    X.cb = cb;
     X.tid = tid;
     X.first = true;
 
@@ -831,13 +846,23 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
             const double cb = csd.x, sb = A.sign_s * csd.y;
             X.use_cot = fabs(sb) > fabs(cb);
             X.tq = X.use_cot ? (R)(cb / sb) : (R)(sb / cb);
-            X.f = X.use_cot ? (R)sb : (R)cb;
+            const double f = X.use_cot ? sb : cb;
+            double fj = 1.0, fn = 1.0;
+            for (int i = 0; i < A.n; i++) {
+                if (i < A.j0)
+                    fj *= f;
+                fn *= f;
+            }
+            X.f = (R)f;
+            X.fn = (R)fn;
+            X.fn2 = (R)(fn * fn);
+            X.scale0 = (R)fj;
             cur_b = (int)b;
             __syncthreads();
         }
         X.sv0 = reinterpret_cast<C *>(buf);
         X.sv1 = reinterpret_cast<C *>(buf + TB);
-        X.fixed = ((uint64_t)mid << G::CB) | ((uint64_t)(t >> midbits) << (A.s + G::HB));
+        X.fixed = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
 
         if (A.load) {
             if (!mbar_wait_bounded(&bars[s], (k / NS) & 1u))
@@ -862,6 +887,7 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
 
         C a[NR], l[NR];
         X.first = true;
+        X.run = X.scale0;
         if (P.is_low) {
             run_stage<R, NV, 0>(P, X, a, l, acc0, acc1);
             X.first = false;
@@ -881,9 +907,10 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
             fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
-                tma_store_5d(&map0, buf, 0, (int)mid, 0, 0, c4);
+                const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
+                tma_store_5d(&map0, buf, 0, c1, c2, 0, c4);
                 if (NV == 2)
-                    tma_store_5d(&map1, buf + TB, 0, (int)mid, 0, 0, c4);
+                    tma_store_5d(&map1, buf + TB, 0, c1, c2, 0, c4);
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
         } else {
@@ -901,25 +928,60 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
 }
 
 // ------------------------------------------------------ parameter tables
-// T_l[c] = exp(-i ((gamma_l c) mod 2 pi)) for c = 0..tab_len-1, in FP64 then
-// rounded once to the amplitude precision; (cos beta_l, sin beta_l) in FP64.
+// The factor dropped by one tan/cot butterfly of the (inverse, sign = -1)
+// mixer: cos beta if |sin| <= |cos| else sign * sin beta. Mirrors the choice
+// the pass kernel makes from the same (cos, sin) pair.
+__device__ __forceinline__ double butterfly_factor(double cn, double sn, double sign)
+{
+    const double s = sign * sn;
+    return fabs(s) > fabs(cn) ? s : cn;
+}
+
+__device__ __forceinline__ double ipow(double f, int k)
+{
+    double r = 1.0;
+    for (int i = 0; i < k; i++)
+        r *= f;
+    return r;
+}
+
+// Three phase tables per (point, layer), each exp(-i ((gamma_l c) mod 2 pi))
+// for c = 0..tab_len-1 computed in FP64 and rounded once:
+//   tab[0]: exact, for the whole-circuit kernel;
+//   tab[1]: times f_{l-1}^n, the factor the previous layer's n tan/cot
+//           butterflies left on the state (forward passes);
+//   tab[2]: conjugated and times f'_l^n for the inverse layer (adjoint).
+// cs[b][l] = (cos beta_l, sin beta_l) in FP64.
 template <typename R>
-__global__ void k_params(int B, int p, int tab_len, const double *__restrict__ gamma,
+__global__ void k_params(int B, int p, int tab_len, int n, const double *__restrict__ gamma,
                          const double *__restrict__ beta, typename CT<R>::T *__restrict__ tab,
                          double2 *__restrict__ cs)
 {
+    using C = typename CT<R>::T;
     const double TWO_PI = 6.283185307179586476925286766559;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)B * p * tab_len;
-    if (i < total) {
+    const long long N = (long long)B * p * tab_len;
+    if (i < N) {
         const long long bl = i / tab_len;
         const int c = (int)(i - bl * tab_len);
+        const int l = (int)(bl % p);
         double ang = fmod(gamma[bl] * (double)c, TWO_PI);
         if (ang < 0.0)
             ang += TWO_PI;
         double sn, cn;
         sincos(ang, &sn, &cn);
-        tab[i] = mkc<typename CT<R>::T>((R)cn, (R)(-sn));
+        double fs = 1.0;
+        if (l > 0) {
+            double bs, bc;
+            sincos(beta[bl - 1], &bs, &bc);
+            fs = ipow(butterfly_factor(bc, bs, 1.0), n);
+        }
+        double bs, bc;
+        sincos(beta[bl], &bs, &bc);
+        const double fb = ipow(butterfly_factor(bc, bs, -1.0), n);
+        tab[i] = mkc<C>((R)cn, (R)(-sn));
+        tab[N + i] = mkc<C>((R)(cn * fs), (R)(-sn * fs));
+        tab[2 * N + i] = mkc<C>((R)(cn * fb), (R)(sn * fb));
     }
     if (i < (long long)B * p) {
         double sn, cn;
@@ -1261,15 +1323,15 @@ int pass_grid(long long total_tiles)
     return (int)(total_tiles < g ? total_tiles : g);
 }
 
-int launch_params(bool c128, int B, int p, int tab_len, const double *d_gamma, const double *d_beta, void *d_tab,
-                  double2 *d_cs, cudaStream_t st)
+int launch_params(bool c128, int B, int p, int tab_len, int n, const double *d_gamma, const double *d_beta,
+                  void *d_tab, double2 *d_cs, cudaStream_t st)
 {
     const long long total = (long long)B * p * (tab_len > 1 ? tab_len : 1);
     const int grid = (int)((total + 255) / 256);
     if (c128)
-        k_params<double><<<grid, 256, 0, st>>>(B, p, tab_len, d_gamma, d_beta, (double2 *)d_tab, d_cs);
+        k_params<double><<<grid, 256, 0, st>>>(B, p, tab_len, n, d_gamma, d_beta, (double2 *)d_tab, d_cs);
     else
-        k_params<float><<<grid, 256, 0, st>>>(B, p, tab_len, d_gamma, d_beta, (float2 *)d_tab, d_cs);
+        k_params<float><<<grid, 256, 0, st>>>(B, p, tab_len, n, d_gamma, d_beta, (float2 *)d_tab, d_cs);
     return (int)cudaGetLastError();
 }
 
