@@ -356,6 +356,7 @@ template <typename R, int NV> struct Geo;
 // complex64, one vector: 64 KB tiles (13 qubits), 32 amplitudes per thread
 template <> struct Geo<float, 1> {
     static constexpr int CB = 4, HB = 9, T = 13, RB = 5, NTHR = 256, NST = 3, NSTAGE = 3;
+    static constexpr int MAXREG = 168;  // 9 warps: 3 share a sub-partition's 16K registers
     __host__ __device__ static constexpr int reg(int st, int k)
     {
         return st == 0 ? (k < 4 ? k : 7) : st == 1 ? 4 + k : (k == 0 ? 0 : 8 + k);
@@ -371,6 +372,7 @@ template <> struct Geo<float, 1> {
 // complex64, two vectors (adjoint): 2 x 32 KB tiles (12 qubits), 16 per thread
 template <> struct Geo<float, 2> {
     static constexpr int CB = 4, HB = 8, T = 12, RB = 4, NTHR = 256, NST = 3, NSTAGE = 3;
+    static constexpr int MAXREG = 168;  // 9 warps: 3 share a sub-partition's 16K registers
     __host__ __device__ static constexpr int reg(int st, int k) { return st == 0 ? k : st == 1 ? 4 + k : 8 + k; }
     __host__ __device__ static constexpr int thr(int st, int j)
     {
@@ -383,6 +385,7 @@ template <> struct Geo<float, 2> {
 // complex128, one vector: 64 KB tiles (12 qubits), 32 amplitudes per thread
 template <> struct Geo<double, 1> {
     static constexpr int CB = 3, HB = 9, T = 12, RB = 5, NTHR = 128, NST = 3, NSTAGE = 3;
+    static constexpr int MAXREG = 255;  // 5 warps: at most 2 per sub-partition
     __host__ __device__ static constexpr int reg(int st, int k)
     {
         return st == 0 ? (k < 3 ? k : 3 + k) : st == 1 ? 3 + k : (k == 0 ? 0 : 7 + k);
@@ -398,6 +401,7 @@ template <> struct Geo<double, 1> {
 // complex128, two vectors (adjoint): 2 x 32 KB tiles (11 qubits), 16 per thread
 template <> struct Geo<double, 2> {
     static constexpr int CB = 3, HB = 8, T = 11, RB = 4, NTHR = 128, NST = 3, NSTAGE = 3;
+    static constexpr int MAXREG = 255;  // 5 warps: at most 2 per sub-partition
     __host__ __device__ static constexpr int reg(int st, int k)
     {
         return st == 0 ? (k < 3 ? k : 6) : st == 1 ? 3 + k : 7 + k;
@@ -529,7 +533,7 @@ struct StageCtx {
 };
 
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
-template <typename R, int NV, int ST>
+template <typename R, int NV, int ST, bool OPS>
 __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                           typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc0,
@@ -553,7 +557,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     } else {
         load_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
-            if (!(X.first && A.pre_lambda))
+            if (!(OPS && X.first && A.pre_lambda))
                 load_regs<R, NV, ST>(X.sv1, sb, l);
     }
 
@@ -565,7 +569,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     }
     const uint64_t x0 = X.fixed | (uint64_t)(base & ((1u << X.cb) - 1u)) | ((uint64_t)(base >> X.cb) << X.s);
 
-    if (ST == 0 && A.pre_phase) {
+    if (OPS && ST == 0 && A.pre_phase) {
         int cv[NR];
         eval_cost_s<RB>(X.cost_nbr, A.n, x0, gp, cv);
 #pragma unroll
@@ -573,7 +577,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
             a[m] = cmul(a[m], X.tab[cv[m]]);
     }
     if constexpr (NV == 2) {
-        if (X.first && A.pre_lambda) {  // lambda = O phi, from the stored final state
+        if (OPS && X.first && A.pre_lambda) {  // lambda = O phi, from the stored final state
             int ov[NR];
             eval_cut_s<RB>(X.obs_nbr, X.obs_w, X.obs_k, A.n, x0, gp, ov);
 #pragma unroll
@@ -640,7 +644,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     if constexpr (NV == 2)
         acc0 += (double)gb;
 
-    if (LAST && (A.post & POST_RESCALE)) {  // the stored state is the exact one
+    if (OPS && LAST && (A.post & POST_RESCALE)) {  // the stored state is the exact one
 #pragma unroll
         for (int m = 0; m < NR; m++) {
             a[m].x *= X.fn;
@@ -648,7 +652,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         }
     }
 
-    if (LAST && (A.post & POST_REDUCE)) {
+    if (OPS && LAST && (A.post & POST_REDUCE)) {
         int ov[NR];
         eval_cut_s<RB>(X.obs_nbr, X.obs_w, X.obs_k, A.n, x0, gp, ov);
         R e = 0;
@@ -658,7 +662,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         acc0 += (A.post & POST_RESCALE) ? (double)e : (double)e * (double)X.fn2;
     }
     if constexpr (NV == 2) {
-        if (LAST && (A.post & (POST_GAMMA | POST_PHASE_CONJ))) {
+        if (OPS && LAST && (A.post & (POST_GAMMA | POST_PHASE_CONJ))) {
             int cv[NR];
             eval_cost_s<RB>(X.cost_nbr, A.n, x0, gp, cv);
             if (A.post & POST_GAMMA) {
@@ -685,6 +689,67 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     }
 }
 
+// Sums over all threads of the block (any multiple of 32 threads).
+__device__ __forceinline__ double block_sum_all(double a, double (*red)[32])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+        red[0][w] = a;
+    __syncthreads();
+    if (w == 0) {
+        a = lane < nw ? red[0][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+    }
+    return a;
+}
+
+// Named barrier 1 spans the NTHR compute threads only (the producer warp
+// never takes part).
+template <int NTHR>
+__device__ __forceinline__ void compute_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(NTHR) : "memory");
+}
+
+// (a, b) summed over the NTHR compute threads; valid in thread 0.
+template <int NTHR>
+__device__ __forceinline__ void compute_sum2(double &a, double &b, double (*red)[32])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    compute_sync<NTHR>();
+    if (lane == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+    }
+    compute_sync<NTHR>();
+    if (w == 0) {
+        constexpr int NW = NTHR / 32;
+        a = lane < NW ? red[0][lane] : 0.0;
+        b = lane < NW ? red[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Was any tile of point b processed by CTA c? (CTA c takes tiles c, c+G, ...)
 __device__ __forceinline__ bool cta_touches(unsigned c, unsigned b, unsigned tiles, unsigned grid, unsigned total)
 {
@@ -696,7 +761,6 @@ __device__ __forceinline__ bool cta_touches(unsigned c, unsigned b, unsigned til
 }
 
 // partials[slot][b][cta]; the last CTA to finish sums them in a fixed order
-template <int NTHR>
 __device__ void pass_final_reduce(const PassArgs &A, double (*red)[32], unsigned total)
 {
     __shared__ unsigned s_last;
@@ -715,11 +779,11 @@ __device__ void pass_final_reduce(const PassArgs &A, double (*red)[32], unsigned
             continue;
         for (int b = 0; b < A.B; b++) {
             const double *src = A.partials + ((size_t)slot * A.B + b) * G;
-            double a = 0.0, dummy = 0.0;
-            for (unsigned c = threadIdx.x; c < G; c += NTHR)
+            double a = 0.0;
+            for (unsigned c = threadIdx.x; c < G; c += blockDim.x)
                 if (cta_touches(c, (unsigned)b, (unsigned)A.tiles, G, total))
                     a += __ldcg(src + c);
-            block_sum2<NTHR>(a, dummy, red);
+            a = block_sum_all(a, red);
             if (threadIdx.x == 0)
                 A.out[(size_t)b * A.out_stride + A.slot_idx[slot]] += A.slot_scale[slot] * a;
         }
@@ -728,32 +792,35 @@ __device__ void pass_final_reduce(const PassArgs &A, double (*red)[32], unsigned
         *A.counter = 0u;
 }
 
-// Persistent tiled pass over A.B statevectors. CTA c handles tiles c, c+G,
-// c+2G, ... (G = gridDim.x) of the B x tiles sequence; NSTAGE tiles are in
-// flight: thread 0 issues the TMA load of tile k+NSTAGE-1 while tile k is in
-// the register stages, and the TMA store of tile k from the same buffer.
-template <typename R, int NV>
-__global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
+// Persistent tiled pass over A.B statevectors, warp-specialised. CTA c takes
+// tiles c, c+G, c+2G, ... (G = gridDim.x) of the B x tiles sequence. The last
+// warp is the producer: its lane 0 keeps NSTAGE tiles in flight (TMA loads)
+// and writes finished tiles back (TMA stores). The NTHR compute threads run
+// the register stages. Per stage buffer s two mbarriers hand the buffer over:
+// full[s] (producer -> compute: tile loaded, or buffer free in a generating
+// pass) and done[s] (compute -> producer: results in shared memory).
+template <typename R, int NV, bool OPS>
+__global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     k_pass(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
            const __grid_constant__ PassArgs A)
 {
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
-    constexpr int NR = 1 << G::RB, NS = G::NSTAGE;
+    constexpr int NR = 1 << G::RB, NS = G::NSTAGE, NTHR = G::NTHR;
     constexpr uint32_t TB = (uint32_t)tile_bytes<R, NV>();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment (TMA 128-byte swizzle) by pointer arithmetic on the
     // shared array itself, so every tile access stays a shared-memory access
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    __shared__ __align__(8) uint64_t bars[NS];
+    __shared__ __align__(8) uint64_t full[NS], done[NS];
     __shared__ double red[2][32];
     __shared__ int s_flag;
+    __shared__ int obs_w[MAXK];
 
     const int tid = threadIdx.x;
     C *tab = reinterpret_cast<C *>(sm + (size_t)NS * NV * TB);
     uint64_t *cost_nbr = reinterpret_cast<uint64_t *>(tab + MAXTAB);
     uint64_t *obs_nbr = cost_nbr + MAXN;
-    __shared__ int obs_w[MAXK];
 
     const unsigned total = (unsigned)A.tiles * (unsigned)A.B;
     const unsigned grid = gridDim.x;
@@ -762,16 +829,19 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
     const int cb = A.cb, hb = G::T - A.cb;
     const int midbits = A.s - cb;
     const unsigned tiles_per_hi = (unsigned)A.tiles >> midbits;  // 2^(n - s - hb)
+    const bool reduce = A.slot_idx[0] >= 0 || A.slot_idx[1] >= 0;
 
     if (tid == 0) {
         s_flag = *reinterpret_cast<volatile int *>(A.err) ? 1 : 0;
-        for (int s = 0; s < NS; s++)
-            mbar_init(&bars[s], 1);
+        for (int s = 0; s < NS; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&done[s], NTHR);
+        }
         fence_barrier_init();
     }
-    for (int i = tid; i < MAXN; i += G::NTHR)
+    for (int i = tid; i < MAXN; i += blockDim.x)
         cost_nbr[i] = A.cost.nbr[i];
-    for (int i = tid; i < A.obs.K * MAXN; i += G::NTHR)
+    for (int i = tid; i < A.obs.K * MAXN; i += blockDim.x)
         obs_nbr[i] = A.obs.nbr[i / MAXN][i % MAXN];
     if (tid < MAXK)
         obs_w[tid] = A.obs.w[tid];
@@ -787,144 +857,163 @@ __global__ void __launch_bounds__(Geo<R, NV>::NTHR, 1)
         const unsigned hi = t >> midbits;
         c4 = (int)(hi + b * tiles_per_hi);
     };
-    auto issue_load = [&](unsigned k) {
-        unsigned b, t, mid;
-        int c4;
-        tile_coords(k, b, t, mid, c4);
-        const int s = (int)(k % NS);
-        unsigned char *buf = sm + (size_t)s * NV * TB;
-        mbar_arrive_expect_tx(&bars[s], (uint32_t)A.nvec_io * TB);
-        const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
-        tma_load_5d(buf, &map0, &bars[s], 0, c1, c2, 0, c4);
-        if (A.nvec_io == 2)
-            tma_load_5d(buf + TB, &map1, &bars[s], 0, c1, c2, 0, c4);
-    };
-    if (tid == 0 && A.load)
-        for (unsigned k = 0; k < (unsigned)(NS - 1) && k < niter; k++)
-            issue_load(k);
 
-    const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.j0, A.amp0};
-    double acc0 = 0.0, acc1 = 0.0;
-    int cur_b = -1;
-    StageCtx<R> X;
-    X.tab = tab;
-    X.cost_nbr = cost_nbr;
-    X.obs_nbr = obs_nbr;
-    X.obs_w = obs_w;
-    X.obs_k = A.obs.K;
-    X.s = A.s;
-    X.cb = cb;
-    X.tid = tid;
-    X.first = true;
-
-    auto flush = [&](int b) {  // this CTA's sums for point b -> partials
-        block_sum2<G::NTHR>(acc0, acc1, red);
-        if (tid == 0) {
-            A.partials[((size_t)0 * A.B + b) * grid + blockIdx.x] = acc0;
-            A.partials[((size_t)1 * A.B + b) * grid + blockIdx.x] = acc1;
-        }
-        acc0 = acc1 = 0.0;
-    };
-    const bool reduce = A.slot_idx[0] >= 0 || A.slot_idx[1] >= 0;
-
-    for (unsigned k = 0; k < niter; k++) {
-        unsigned b, t, mid;
-        int c4;
-        tile_coords(k, b, t, mid, c4);
-        const int s = (int)(k % NS);
-        unsigned char *buf = sm + (size_t)s * NV * TB;
-        if ((int)b != cur_b) {  // new parameter point: its phase table and mixer angle
-            if (cur_b >= 0 && reduce)
-                flush(cur_b);
-            __syncthreads();
-            if (A.pre_phase || (A.post & POST_PHASE_CONJ)) {
-                const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.layer) * A.tab_len;
-                for (int i = tid; i < A.tab_len; i += G::NTHR)
-                    tab[i] = src[i];
+    if (tid >= NTHR) {
+        // ------------------------------------------------------ producer
+        if (tid == NTHR) {
+            bool ok = true;
+            long long last_fill[NS];  // newest tile loaded into each buffer
+            for (int s = 0; s < NS; s++)
+                last_fill[s] = -1;
+            auto fill = [&](unsigned k) {  // tile k into buffer k % NS
+                const int s = (int)(k % NS);
+                last_fill[s] = (long long)k;
+                if (A.load) {
+                    unsigned b, t, mid;
+                    int c4;
+                    tile_coords(k, b, t, mid, c4);
+                    unsigned char *buf = sm + (size_t)s * NV * TB;
+                    const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)A.nvec_io * TB);
+                    tma_load_5d(buf, &map0, &full[s], 0, c1, c2, 0, c4);
+                    if (A.nvec_io == 2)
+                        tma_load_5d(buf + TB, &map1, &full[s], 0, c1, c2, 0, c4);
+                } else {
+                    mbar_arrive(&full[s]);  // generating pass: the buffer is free
+                }
+            };
+            for (unsigned k = 0; k < (unsigned)NS && k < niter; k++)
+                fill(k);
+            for (unsigned k = 0; k < niter && ok; k++) {
+                const int s = (int)(k % NS);
+                if (!mbar_wait_bounded(&done[s], (k / NS) & 1u) || *reinterpret_cast<volatile int *>(&s_flag)) {
+                    ok = false;
+                    break;
+                }
+                if (A.write) {
+                    unsigned b, t, mid;
+                    int c4;
+                    tile_coords(k, b, t, mid, c4);
+                    unsigned char *buf = sm + (size_t)s * NV * TB;
+                    const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
+                    tma_store_5d(&map0, buf, 0, c1, c2, 0, c4);
+                    if (NV == 2)
+                        tma_store_5d(&map1, buf + TB, 0, c1, c2, 0, c4);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+                if (k + NS < niter) {
+                    if (A.write)  // the buffer is reloaded: its store must have read it
+                        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    fill(k + NS);
+                }
             }
-            const double2 csd = A.cs[(size_t)b * A.p + A.layer];
-            const double cb = csd.x, sb = A.sign_s * csd.y;
-            X.use_cot = fabs(sb) > fabs(cb);
-            X.tq = X.use_cot ? (R)(cb / sb) : (R)(sb / cb);
-            const double f = X.use_cot ? sb : cb;
-            double fj = 1.0, fn = 1.0;
-            for (int i = 0; i < A.n; i++) {
-                if (i < A.j0)
-                    fj *= f;
-                fn *= f;
-            }
-            X.f = (R)f;
-            X.fn = (R)fn;
-            X.fn2 = (R)(fn * fn);
-            X.scale0 = (R)fj;
-            cur_b = (int)b;
-            __syncthreads();
-        }
-        X.sv0 = reinterpret_cast<C *>(buf);
-        X.sv1 = reinterpret_cast<C *>(buf + TB);
-        X.fixed = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
-
-        if (A.load) {
-            if (!mbar_wait_bounded(&bars[s], (k / NS) & 1u))
-                atomicOr(&s_flag, 1);
-        } else if (tid == 0 && A.write) {
-            // the stage buffer is rewritten by this tile's threads: the store
-            // of tile k-NS from it must have finished reading (at most NS-1
-            // younger store groups may still be pending)
-            asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory");
-            static_assert(NS == 3, "wait_group immediate assumes three stages");
-        }
-        __syncthreads();
-        if (s_flag) {  // a tile never arrived: record, drain our own copies, stop
-            if (tid == 0) {
+            if (!ok) {
                 atomicExch(A.err, 1);
-                for (unsigned q = k; q < k + NS - 1 && q < niter; q++)
-                    mbar_wait_bounded(&bars[q % NS], (q / NS) & 1u);
-                asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+                s_flag = 1;
+                if (A.load)  // no TMA load may still be writing shared memory at exit
+                    for (int s = 0; s < NS; s++)
+                        if (last_fill[s] >= 0)
+                            mbar_wait_bounded(&full[s], (unsigned)((last_fill[s] / NS) & 1));
             }
-            return;
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
         }
-
-        C a[NR], l[NR];
+    } else {
+        // ------------------------------------------------------- compute
+        const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.j0, A.amp0};
+        double acc0 = 0.0, acc1 = 0.0;
+        int cur_b = -1;
+        StageCtx<R> X;
+        X.tab = tab;
+        X.cost_nbr = cost_nbr;
+        X.obs_nbr = obs_nbr;
+        X.obs_w = obs_w;
+        X.obs_k = A.obs.K;
+        X.s = A.s;
+        X.cb = cb;
+        X.tid = tid;
         X.first = true;
-        X.run = X.scale0;
-        if (P.is_low) {
-            run_stage<R, NV, 0>(P, X, a, l, acc0, acc1);
-            X.first = false;
-            __syncthreads();
-        }
-        run_stage<R, NV, 1>(P, X, a, l, acc0, acc1);
-        X.first = false;
-        __syncthreads();
-        // refill the buffer freed by tile k-1: its store was committed two
-        // register stages ago and has finished reading shared memory by now
-        if (tid == 0 && A.load && k + NS - 1 < niter) {
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-            issue_load(k + NS - 1);
-        }
-        run_stage<R, NV, 2>(P, X, a, l, acc0, acc1);
-        if (P.write) {
-            fence_proxy_async_smem();
-            __syncthreads();
+
+        auto flush = [&](int b) {  // this CTA's sums for point b -> partials
+            compute_sum2<NTHR>(acc0, acc1, red);
             if (tid == 0) {
-                const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
-                tma_store_5d(&map0, buf, 0, c1, c2, 0, c4);
-                if (NV == 2)
-                    tma_store_5d(&map1, buf + TB, 0, c1, c2, 0, c4);
-                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                A.partials[((size_t)0 * A.B + b) * grid + blockIdx.x] = acc0;
+                A.partials[((size_t)1 * A.B + b) * grid + blockIdx.x] = acc1;
             }
-        } else {
-            fence_proxy_async_smem();  // generic reads before the buffer's next TMA load
-            __syncthreads();
+            acc0 = acc1 = 0.0;
+        };
+
+        bool ok = true;
+        for (unsigned k = 0; k < niter; k++) {
+            unsigned b, t, mid;
+            int c4;
+            tile_coords(k, b, t, mid, c4);
+            const int s = (int)(k % NS);
+            unsigned char *buf = sm + (size_t)s * NV * TB;
+            if ((int)b != cur_b) {  // new parameter point: its phase table and mixer angle
+                if (cur_b >= 0 && reduce)
+                    flush(cur_b);
+                compute_sync<NTHR>();
+                if (A.pre_phase || (A.post & POST_PHASE_CONJ)) {
+                    const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.layer) * A.tab_len;
+                    for (int i = tid; i < A.tab_len; i += NTHR)
+                        tab[i] = src[i];
+                }
+                const double2 csd = A.cs[(size_t)b * A.p + A.layer];
+                const double cbv = csd.x, sbv = A.sign_s * csd.y;
+                X.use_cot = fabs(sbv) > fabs(cbv);
+                X.tq = X.use_cot ? (R)(cbv / sbv) : (R)(sbv / cbv);
+                const double f = X.use_cot ? sbv : cbv;
+                double fj = 1.0, fn = 1.0;
+                for (int i = 0; i < A.n; i++) {
+                    if (i < A.j0)
+                        fj *= f;
+                    fn *= f;
+                }
+                X.f = (R)f;
+                X.fn = (R)fn;
+                X.fn2 = (R)(fn * fn);
+                X.scale0 = (R)fj;
+                cur_b = (int)b;
+                compute_sync<NTHR>();
+            }
+            X.sv0 = reinterpret_cast<C *>(buf);
+            X.sv1 = reinterpret_cast<C *>(buf + TB);
+            X.fixed = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
+
+            if (!mbar_wait_bounded(&full[s], (k / NS) & 1u))
+                atomicOr(&s_flag, 1);
+            compute_sync<NTHR>();
+            if (s_flag) {  // a tile never arrived
+                if (tid == 0)
+                    atomicExch(A.err, 1);
+                ok = false;
+                break;
+            }
+
+            C a[NR], l[NR];
+            X.first = true;
+            X.run = X.scale0;
+            if (P.is_low) {
+                run_stage<R, NV, 0, OPS>(P, X, a, l, acc0, acc1);
+                X.first = false;
+                compute_sync<NTHR>();
+            }
+            run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1);
+            X.first = false;
+            compute_sync<NTHR>();
+            run_stage<R, NV, 2, OPS>(P, X, a, l, acc0, acc1);
+            // results (if any) are in the buffer: hand it to the producer
+            fence_proxy_async_smem();
+            mbar_arrive(&done[s]);
         }
-    }
-    if (tid == 0)
-        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    if (reduce) {
-        if (cur_b >= 0)
+        if (ok && reduce && cur_b >= 0)
             flush(cur_b);
-        pass_final_reduce<G::NTHR>(A, red, total);
     }
+    __syncthreads();
+    if (s_flag)
+        return;
+    if (reduce)
+        pass_final_reduce(A, red, total);
 }
 
 // ------------------------------------------------------ parameter tables
@@ -1335,19 +1424,29 @@ int launch_params(bool c128, int B, int p, int tab_len, int n, const double *d_g
     return (int)cudaGetLastError();
 }
 
-template <typename R, int NV>
-static int launch_pass_t(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid, cudaStream_t st)
+template <typename R, int NV, bool OPS>
+static int launch_pass_ops(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
+                           cudaStream_t st)
 {
     const size_t smem = pass_smem_total<R, NV>();
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_pass<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_pass<R, NV, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return (int)e;
         attr_done = true;
     }
-    k_pass<R, NV><<<grid, Geo<R, NV>::NTHR, smem, st>>>(m0, m1, a);
+    k_pass<R, NV, OPS><<<grid, Geo<R, NV>::NTHR + 32, smem, st>>>(m0, m1, a);
     return (int)cudaGetLastError();
+}
+
+// passes without a pre- or post-operation run the lean instantiation
+template <typename R, int NV>
+static int launch_pass_t(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid, cudaStream_t st)
+{
+    const bool ops = a.pre_phase || a.pre_lambda || a.post;
+    return ops ? launch_pass_ops<R, NV, true>(m0, m1, a, grid, st) : launch_pass_ops<R, NV, false>(m0, m1, a, grid, st);
 }
 
 int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
