@@ -338,7 +338,50 @@ def extras(dev, stream):
             del pl
             torch.cuda.empty_cache()
         out[name] = rec
+    out["batch"] = batch_extras(dev, stream)
     return out
+
+
+def batch_extras(dev, stream):
+    """The two batch shapes: a 4096-point landscape on the star S_19 (n = 20,
+    p = 1) in one call with the angles on the device, and 256 graphs of uneven
+    size (n in 12..22, p = 2) through the CUDA-graph batch call."""
+    import torch
+    from paper_2410_22247_gb300 import orbits as ORB
+    from paper_2410_22247_gb300 import workloads as W
+    from paper_2410_22247_gb300.api import MultiPlan, Plan
+
+    res = {}
+    n, e = W.star_graph(20)
+    gs, bs = W.angle_grid(64)
+    pl = Plan(n, e, 1, orbits=ORB.edge_orbits(n, e), precision="c64", batch=4096, with_grad=False,
+              stream=stream, device=dev)
+    dg, db = torch.tensor(gs, device=dev), torch.tensor(bs, device=dev)
+    o = torch.zeros(4096, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        ms = timed(lambda: pl.expect_device(dg, db, o, "red"), 3, stream)
+    res["landscape_star_S19_4096pts_p1_c64"] = {"ms_per_call": ms, "evals_per_s": 4096 / (ms / 1000.0),
+                                                 "launches_per_call": pl.launch_count()}
+    pl.close()
+    del pl
+    torch.cuda.empty_cache()
+
+    graphs = [(nn, ee, ORB.edge_orbits(nn, ee)) for _, nn, ee in W.mixed_graph_batch(256, 12, 22, 7)]
+    mp = MultiPlan(graphs, 2, precision="c64", stream=stream, device=dev)
+    rng = W.rng(11)
+    ga = rng.uniform(0, np.pi, size=(256, 2))
+    ba = rng.uniform(0, np.pi / 2, size=(256, 2))
+    mp.expect(ga, ba, "red")  # autotune + capture
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        mp.expect(ga, ba, "red")
+    dt = (time.perf_counter() - t0) / reps
+    info = mp.info()
+    res["uneven_256_graphs_n12to22_p2_c64"] = {"ms_per_call": dt * 1000.0, "evals_per_s": 256 / dt, **info,
+                                               "timing": "host wall clock per call, H2D angles + graph replay + D2H"}
+    mp.close()
+    return res
 
 
 def traffic_from_profiles():

@@ -240,6 +240,61 @@ int aaqaoa_aggregate_only(aaqaoa_plan *plan, int observable, int agg_mode, doubl
 int aaqaoa_expect_static(aaqaoa_plan *plan, const double *gamma, const double *beta, int observable,
                          double *energy);
 
+/*
+ * Uneven batches of graphs (many small instances of different n, one call).
+ *
+ * aaqaoa_graph_desc describes one graph exactly as the arguments of
+ * aaqaoa_prepare (edges, optional orbit representatives and weights).
+ * aaqaoa_prepare_multi validates every graph (same rules and errors as
+ * aaqaoa_prepare, the detail names the graph) and copies all host arrays.
+ * Graphs that fit one CTA (n <= 13 for C64, n <= 12 for C128) are evaluated
+ * together by one kernel launch; each larger graph runs the tiled passes.
+ * The first aaqaoa_expect_multi call for an observable times a few ways of
+ * spreading the large graphs over parallel CUDA streams (autotune; cached per
+ * device and batch shape for the process; AAQAOA_AUTOTUNE=0 in the
+ * environment skips the timing) and captures the whole evaluation into a
+ * CUDA graph, which later calls replay.
+ *
+ * aaqaoa_multi_workspace_bytes / aaqaoa_multi_set_workspace: one caller-owned
+ * device buffer (256-byte aligned) for the whole batch.
+ * aaqaoa_expect_multi: gamma, beta host, G*p doubles (graph-major); energy
+ * host, G doubles (fused aggregation). Synchronises the batch's stream.
+ * aaqaoa_multi_info: graphs, how many run in the small-graph kernel, the
+ * chosen number of parallel branches, kernel launches per evaluation.
+ */
+typedef struct aaqaoa_multi aaqaoa_multi;
+typedef struct {
+    int n;
+    int num_edges;
+    const int32_t *edges;
+    int num_orbits;
+    const int32_t *orbit_rep;
+    const int32_t *orbit_weight;
+} aaqaoa_graph_desc;
+
+int aaqaoa_prepare_multi(int G, const aaqaoa_graph_desc *graphs, int p, unsigned flags, void *stream,
+                         aaqaoa_multi **out);
+int aaqaoa_multi_workspace_bytes(const aaqaoa_multi *multi, size_t *bytes);
+int aaqaoa_multi_set_workspace(aaqaoa_multi *multi, void *device_ptr, size_t bytes);
+int aaqaoa_expect_multi(aaqaoa_multi *multi, const double *gamma, const double *beta, int observable,
+                        double *energy);
+int aaqaoa_multi_info(const aaqaoa_multi *multi, int *G, int *small_graphs, int *branches,
+                      int *launches_per_call);
+void aaqaoa_destroy_multi(aaqaoa_multi *multi);
+
+/*
+ * aaqaoa_inject_fault -- test hook for the failure path of the tiled passes.
+ * kind AAQAOA_FAULT_DROP_TILE: the next tiled pass that loads the statevector
+ * leaves the first tile of one CTA unloaded, so that CTA's bounded wait
+ * (about one second) runs out; the call returns AAQAOA_ERR_TIMEOUT, its
+ * results are invalid, and the plan keeps working for later calls. Nothing
+ * faults: the wait is the same bounded wait every pass uses. kind 0 clears a
+ * pending fault. Plans with n <= the tile size have no tiled pass
+ * (AAQAOA_ERR_UNSUPPORTED).
+ */
+#define AAQAOA_FAULT_DROP_TILE 1
+int aaqaoa_inject_fault(aaqaoa_plan *plan, int kind);
+
 /* Plan properties: qubits, layers, edges, orbits, precision flag. */
 int aaqaoa_plan_info(const aaqaoa_plan *plan, int *n, int *p, int *num_edges, int *num_orbits,
                      unsigned *flags);

@@ -20,11 +20,19 @@ AAQAOA_OBS_RED = 1
 AAQAOA_AGG_FUSED = 0
 AAQAOA_AGG_PERTERM = 1
 AAQAOA_AGG_SINGLEPASS = 2
+AAQAOA_FAULT_DROP_TILE = 1
 AAQAOA_OK = 0
 ERRORS = {
     -1: "AAQAOA_ERR_INVALID_ARG", -2: "AAQAOA_ERR_BAD_ORBITS", -3: "AAQAOA_ERR_WORKSPACE",
     -4: "AAQAOA_ERR_CUDA", -5: "AAQAOA_ERR_TIMEOUT", -6: "AAQAOA_ERR_UNSUPPORTED",
 }
+
+class GraphDesc(ctypes.Structure):
+    """aaqaoa_graph_desc"""
+    _fields_ = [("n", ctypes.c_int), ("num_edges", ctypes.c_int), ("edges", ctypes.POINTER(ctypes.c_int32)),
+                ("num_orbits", ctypes.c_int), ("orbit_rep", ctypes.POINTER(ctypes.c_int32)),
+                ("orbit_weight", ctypes.POINTER(ctypes.c_int32))]
+
 
 # (name, restype, argtypes)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -46,6 +54,15 @@ _PROTOS = [
     ("aaqaoa_statevector", ctypes.c_int, [_vp, _f64p, _f64p, _vp]),
     ("aaqaoa_aggregate_only", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _f64p]),
     ("aaqaoa_expect_static", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_int, _f64p]),
+    ("aaqaoa_prepare_multi", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(GraphDesc), ctypes.c_int, ctypes.c_uint,
+                                            _vp, ctypes.POINTER(_vp)]),
+    ("aaqaoa_multi_workspace_bytes", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    ("aaqaoa_multi_set_workspace", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    ("aaqaoa_expect_multi", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_int, _f64p]),
+    ("aaqaoa_multi_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("aaqaoa_destroy_multi", None, [_vp]),
+    ("aaqaoa_inject_fault", ctypes.c_int, [_vp, ctypes.c_int]),
     ("aaqaoa_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_uint)]),

@@ -155,6 +155,74 @@ class Plan:
             pass
 
 
+class MultiPlan:
+    """An uneven batch of graphs evaluated in one call (``aaqaoa_*_multi``).
+
+    ``graphs`` is a list of ``(n, edges, orbits)`` with ``orbits`` as for
+    :class:`Plan` (or None). Energies of all graphs come back from one
+    replay of a CUDA graph captured on the first call.
+    """
+
+    def __init__(self, graphs, p, precision="c64", stream=None, device=None):
+        import torch
+
+        self._lib = N.load()
+        self.p = int(p)
+        self.G = len(graphs)
+        self.precision = precision
+        self._keep = []
+        descs = (N.GraphDesc * self.G)()
+        for i, (n, edges, orbits) in enumerate(graphs):
+            e = _i32(edges)
+            rep = weight = None
+            if orbits is not None:
+                rep = _i32(orbits.rep if hasattr(orbits, "rep") else orbits[0])
+                weight = _i32(orbits.weight if hasattr(orbits, "weight") else orbits[1])
+            self._keep += [e, rep, weight]
+            descs[i].n = int(n)
+            descs[i].num_edges = len(e) // 2
+            descs[i].edges = _ptr(e, ctypes.c_int32)
+            descs[i].num_orbits = 0 if rep is None else len(rep)
+            descs[i].orbit_rep = _ptr(rep, ctypes.c_int32)
+            descs[i].orbit_weight = _ptr(weight, ctypes.c_int32)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        flags = N.AAQAOA_C128 if precision == "c128" else N.AAQAOA_C64
+        h = ctypes.c_void_p()
+        N.check(N.aaqaoa_prepare_multi(self.G, descs, self.p, flags, ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(h)), "aaqaoa_prepare_multi")
+        self.handle = h
+        size = ctypes.c_size_t()
+        N.check(N.aaqaoa_multi_workspace_bytes(self.handle, ctypes.byref(size)), "aaqaoa_multi_workspace_bytes")
+        self.workspace = torch.empty(int(size.value), dtype=torch.uint8, device=self.device)
+        N.check(N.aaqaoa_multi_set_workspace(self.handle, ctypes.c_void_p(self.workspace.data_ptr()), size.value),
+                "aaqaoa_multi_set_workspace")
+
+    def expect(self, gammas, betas, observable="full"):
+        g, b = _f64(gammas), _f64(betas)
+        out = np.zeros(self.G)
+        N.check(N.aaqaoa_expect_multi(self.handle, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                      OBSERVABLES[observable], _ptr(out, ctypes.c_double)), "aaqaoa_expect_multi")
+        return out
+
+    def info(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        N.check(N.aaqaoa_multi_info(self.handle, *[ctypes.byref(x) for x in v]), "aaqaoa_multi_info")
+        return dict(zip(("graphs", "small_graphs", "branches", "launches_per_call"), (x.value for x in v)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            N.aaqaoa_destroy_multi(self.handle)
+            self.handle = ctypes.c_void_p()
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _autograd_function():
     import torch
 

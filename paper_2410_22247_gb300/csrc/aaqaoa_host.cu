@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -112,6 +113,7 @@ struct aaqaoa_plan {
     std::vector<CUtensorMap> map_bphi, map_blam; // adjoint, per pass
     int launches = 0;
     bool state_valid = false;
+    int inject = 0;  // pending test fault (aaqaoa_inject_fault)
     // launch profiling
     bool prof = false;
     struct ProfRec {
@@ -130,7 +132,8 @@ struct aaqaoa_plan {
     int out_stride() const { return 1 + 2 * p; }
     bool small() const { return n <= T(); }
     int tiles() const { return small() ? 1 : 1 << (n - T()); }
-    int *d_err() const { return reinterpret_cast<int *>(ws + L.ctrl); }
+    int *err_shared = nullptr;  // set when the plan is part of a multi-graph batch
+    int *d_err() const { return err_shared ? err_shared : reinterpret_cast<int *>(ws + L.ctrl); }
     unsigned *d_counter_pass() const { return reinterpret_cast<unsigned *>(ws + L.ctrl + 8); }
     unsigned *d_counter_agg() const { return reinterpret_cast<unsigned *>(ws + L.ctrl + 16); }
     double *d_out() const { return reinterpret_cast<double *>(ws + L.out); }
@@ -316,12 +319,15 @@ enum FwdMode { FWD_ENERGY, FWD_GRAD, FWD_STATE };
 int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
 {
     const int np = (int)pl->passes.size();
-    const int grid = pass_grid((long long)pl->tiles() * B);
+    const long long total = (long long)pl->tiles() * B;
+    const int grid = pass_grid(total);
+    const int chunk = B > 1 ? (int)((total + grid - 1) / grid) : 0;
     for (int l = 0; l < pl->p; l++) {
         for (int k = 0; k < np; k++) {
             const Pass &ps = pl->passes[k];
             PassArgs a = base_args(pl, obs);
             a.B = B;
+            a.chunk = chunk;
             a.s = ps.s;
             a.cb = ps.cb;
             a.wide_rows = ps.wide;
@@ -342,6 +348,10 @@ int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
                 a.slot_idx[0] = 0;
                 a.slot_scale[0] = 1.0;
             }
+            if (pl->inject == AAQAOA_FAULT_DROP_TILE && a.load) {
+                a.drop_first_load = 1;
+                pl->inject = 0;
+            }
             const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
             ProfScope ps_(pl, PK_FWD, S * ((a.load ? 1 : 0) + (a.write ? 1 : 0)));
             CKL(launch_pass(pl->c128, 1, pl->map_phi[k], pl->map_phi[k], a, grid, pl->stream), "forward pass");
@@ -358,6 +368,7 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
     pass_geometry(pl->c128, 2, &T, &CB, &HB);
     const int tiles = 1 << (pl->n - T);
     const int grid = pass_grid((long long)tiles * B);
+    const int chunk = B > 1 ? (int)(((long long)tiles * B + grid - 1) / grid) : 0;
     const int np = (int)pl->bwd_passes.size();
     bool first = true;
     for (int l = pl->p - 1; l >= 0; l--) {
@@ -367,6 +378,7 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
             const bool last_of_layer = (kk == 0);
             PassArgs a = base_args(pl, obs);
             a.B = B;
+            a.chunk = chunk;
             a.tiles = tiles;
             a.s = ps.s;
             a.cb = ps.cb;
@@ -990,6 +1002,18 @@ int aaqaoa_aggregate_only(aaqaoa_plan *pl, int observable, int agg_mode, double 
     return AAQAOA_OK;
 }
 
+int aaqaoa_inject_fault(aaqaoa_plan *pl, int kind)
+{
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    if (kind != 0 && kind != AAQAOA_FAULT_DROP_TILE)
+        return fail(AAQAOA_ERR_INVALID_ARG, "fault kind %d unknown", kind);
+    if (kind == AAQAOA_FAULT_DROP_TILE && pl->small())
+        return fail(AAQAOA_ERR_UNSUPPORTED, "n=%d runs in one CTA: no tiled pass to drop a tile from", pl->n);
+    pl->inject = kind;
+    return AAQAOA_OK;
+}
+
 int aaqaoa_plan_info(const aaqaoa_plan *pl, int *n, int *p, int *num_edges, int *num_orbits, unsigned *flags)
 {
     if (!pl)
@@ -1225,3 +1249,377 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
         return fail(AAQAOA_ERR_TIMEOUT, "a bounded device wait expired (TMA tile never arrived)");
     return AAQAOA_OK;
 }
+
+// ============================================== uneven multi-graph batches
+// Graphs with n up to the tile size run together in one k_small_multi launch;
+// larger graphs each own a tiled sub-plan. One evaluation of the batch is
+// captured into a CUDA graph whose large-graph work is spread over `branches`
+// parallel streams; the branch count is chosen by timing (autotune) on the
+// first call for each observable and cached for the process.
+struct aaqaoa_multi {
+    int G = 0, p = 0;
+    bool c128 = false;
+    cudaStream_t stream = nullptr;  // the caller's stream: uploads, graph launch, downloads
+    cudaStream_t cap = nullptr;     // private stream the evaluation is captured on
+    std::vector<aaqaoa_plan *> plans;  // one per graph (validation + host tables)
+    std::vector<int> small_idx, large_idx;
+    std::vector<SmallGraph> desc;       // small graphs, in small_idx order
+    int small_max_n = 1, small_max_tab = 1;
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t off_params = 0, off_energy = 0, off_desc = 0, off_err = 0;
+    std::vector<size_t> sub_off, sub_bytes;
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int branches[2] = {0, 0};
+    int launches = 0;
+};
+
+namespace {
+
+constexpr int MULTI_MAX_BRANCHES = 16;
+
+size_t multi_layout(aaqaoa_multi *m)
+{
+    size_t off = 0;
+    m->off_err = off;
+    off += 256;
+    m->off_params = off;
+    off = align256(off + 2 * (size_t)m->G * m->p * sizeof(double));
+    m->off_energy = off;
+    off = align256(off + (size_t)m->G * sizeof(double));
+    m->off_desc = off;
+    off = align256(off + (m->desc.size() + 1) * sizeof(SmallGraph));
+    m->sub_off.clear();
+    m->sub_bytes.clear();
+    for (int gi : m->large_idx) {
+        size_t b = 0;
+        aaqaoa_workspace_bytes(m->plans[gi], 1, 0, &b);
+        m->sub_off.push_back(off);
+        m->sub_bytes.push_back(b);
+        off = align256(off + b);
+    }
+    return off;
+}
+
+// everything one evaluation enqueues, on `origin` (+ side streams)
+int multi_enqueue(aaqaoa_multi *m, int obs, int branches, cudaStream_t origin)
+{
+    double *d_par = reinterpret_cast<double *>(m->ws + m->off_params);
+    double *d_en = reinterpret_cast<double *>(m->ws + m->off_energy);
+    const size_t Gp = (size_t)m->G * m->p;
+    m->launches = 0;
+    CK(cudaEventRecord(m->fork, origin));
+    for (int b = 0; b < branches; b++)
+        CK(cudaStreamWaitEvent(m->side[b], m->fork, 0));
+    if (!m->small_idx.empty()) {
+        CKL(launch_small_multi(m->c128, reinterpret_cast<const SmallGraph *>(m->ws + m->off_desc),
+                               (int)m->small_idx.size(), m->p, obs, m->small_max_n, m->small_max_tab, d_par,
+                               d_par + Gp, d_en, origin),
+            "small-graph batch kernel");
+        m->launches++;
+    }
+    for (size_t j = 0; j < m->large_idx.size(); j++) {
+        const int gi = m->large_idx[j];
+        aaqaoa_plan *pl = m->plans[gi];
+        cudaStream_t st = branches > 0 ? m->side[j % branches] : origin;
+        pl->stream = st;
+        pl->launches = 0;
+        int r = enqueue_expect(pl, 1, d_par + (size_t)gi * m->p, d_par + Gp + (size_t)gi * m->p, obs,
+                               AAQAOA_AGG_FUSED);
+        if (r)
+            return r;
+        m->launches += pl->launches;
+        CK(cudaMemcpyAsync(d_en + gi, pl->d_out(), sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    for (int b = 0; b < branches; b++) {
+        CK(cudaEventRecord(m->join[b], m->side[b]));
+        CK(cudaStreamWaitEvent(origin, m->join[b], 0));
+    }
+    return AAQAOA_OK;
+}
+
+int multi_capture(aaqaoa_multi *m, int obs, int branches, cudaGraphExec_t *exec)
+{
+    CK(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal));
+    int r = multi_enqueue(m, obs, branches, m->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(m->cap, &graph);
+    if (r) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return r;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGraphInstantiate");
+    return AAQAOA_OK;
+}
+
+std::map<std::string, int> &autotune_cache()
+{
+    static std::map<std::string, int> c;
+    return c;
+}
+
+std::string multi_signature(const aaqaoa_multi *m, int obs)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    std::string sig = "?";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+        sig = prop.name;
+    char buf[64];
+    snprintf(buf, sizeof buf, "|%d|%d|%d|", m->c128 ? 128 : 64, m->p, obs);
+    sig += buf;
+    for (int gi : m->large_idx) {
+        snprintf(buf, sizeof buf, "%d,", m->plans[gi]->n);
+        sig += buf;
+    }
+    return sig;
+}
+
+// choose the branch count by timing each candidate graph (3 launches each)
+int multi_autotune(aaqaoa_multi *m, int obs)
+{
+    const int L = (int)m->large_idx.size();
+    const std::string sig = multi_signature(m, obs);
+    auto &cache = autotune_cache();
+    const char *env = getenv("AAQAOA_AUTOTUNE");
+    const bool tune = !(env && env[0] == '0');
+    int best = L > 0 ? (L < 4 ? L : 4) : 0;
+    if (cache.count(sig)) {
+        best = cache[sig];
+    } else if (tune && L > 1) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        float best_ms = 1e30f;
+        for (int br = 1; br <= MULTI_MAX_BRANCHES && br <= L; br *= 2) {
+            cudaGraphExec_t ex = nullptr;
+            int r = multi_capture(m, obs, br, &ex);
+            if (r) {
+                cudaEventDestroy(a);
+                cudaEventDestroy(b);
+                return r;
+            }
+            cudaGraphLaunch(ex, m->stream);
+            cudaEventRecord(a, m->stream);
+            for (int i = 0; i < 3; i++)
+                cudaGraphLaunch(ex, m->stream);
+            cudaEventRecord(b, m->stream);
+            cudaError_t e = cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            cudaGraphExecDestroy(ex);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(a);
+                cudaEventDestroy(b);
+                return cuda_fail(e, "autotune run");
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = br;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cache[sig] = best;
+    }
+    m->branches[obs] = best;
+    return multi_capture(m, obs, best, &m->exec[obs]);
+}
+
+}  // namespace
+
+extern "C" {
+
+int aaqaoa_prepare_multi(int G, const aaqaoa_graph_desc *graphs, int p, unsigned flags, void *stream,
+                         aaqaoa_multi **out)
+{
+    g_detail.clear();
+    if (!out)
+        return fail(AAQAOA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (G < 1 || !graphs)
+        return fail(AAQAOA_ERR_INVALID_ARG, "G=%d or graphs NULL", G);
+    aaqaoa_multi *m = new (std::nothrow) aaqaoa_multi();
+    if (!m)
+        return fail(AAQAOA_ERR_INVALID_ARG, "out of host memory");
+    m->G = G;
+    m->p = p;
+    m->c128 = flags == AAQAOA_C128;
+    m->stream = (cudaStream_t)stream;
+    for (int gi = 0; gi < G; gi++) {
+        const aaqaoa_graph_desc &d = graphs[gi];
+        aaqaoa_plan *pl = nullptr;
+        int r = aaqaoa_prepare(d.n, d.num_edges, d.edges, d.num_orbits, d.orbit_rep, d.orbit_weight, nullptr, p,
+                               flags, stream, &pl);
+        if (r) {
+            std::string why = g_detail;
+            aaqaoa_destroy_multi(m);
+            return fail(r, "graph %d: %s", gi, why.c_str());
+        }
+        m->plans.push_back(pl);
+        if (pl->small()) {
+            SmallGraph sg;
+            memset(&sg, 0, sizeof sg);
+            sg.gi = gi;
+            sg.n = pl->n;
+            sg.tab_len = pl->tab_len();
+            for (int o = 0; o < 2; o++) {
+                sg.K[o] = pl->obs[o].K;
+                for (int k = 0; k < MAXK; k++) {
+                    sg.w[o][k] = pl->obs[o].w[k];
+                    for (int u = 0; u < MAXN; u++)
+                        sg.obs[o][k][u] = pl->obs[o].nbr[k][u];
+                }
+            }
+            for (int u = 0; u < MAXN; u++)
+                sg.cost[u] = pl->cost.nbr[u];
+            m->desc.push_back(sg);
+            m->small_idx.push_back(gi);
+            m->small_max_n = std::max(m->small_max_n, pl->n);
+            m->small_max_tab = std::max(m->small_max_tab, pl->tab_len());
+        } else {
+            m->large_idx.push_back(gi);
+        }
+    }
+    const int nb = std::min<int>(MULTI_MAX_BRANCHES, std::max<int>(1, (int)m->large_idx.size()));
+    for (int b = 0; b < nb; b++) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            aaqaoa_destroy_multi(m);
+            return fail(AAQAOA_ERR_CUDA, "could not create the batch's side streams");
+        }
+        m->side.push_back(s);
+        m->join.push_back(e);
+    }
+    if (cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        aaqaoa_destroy_multi(m);
+        return fail(AAQAOA_ERR_CUDA, "could not create the batch's fork event");
+    }
+    *out = m;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_multi_workspace_bytes(const aaqaoa_multi *m, size_t *bytes)
+{
+    if (!m || !bytes)
+        return fail(AAQAOA_ERR_INVALID_ARG, "multi or bytes NULL");
+    *bytes = multi_layout(const_cast<aaqaoa_multi *>(m));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_multi_set_workspace(aaqaoa_multi *m, void *device_ptr, size_t bytes)
+{
+    if (!m)
+        return fail(AAQAOA_ERR_INVALID_ARG, "multi is NULL");
+    if (!device_ptr || ((uintptr_t)device_ptr & 255))
+        return fail(AAQAOA_ERR_WORKSPACE, "workspace pointer NULL or not 256-byte aligned");
+    const size_t need = multi_layout(m);
+    if (bytes < need)
+        return fail(AAQAOA_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", bytes, need);
+    m->ws = (unsigned char *)device_ptr;
+    m->ws_bytes = bytes;
+    for (int o = 0; o < 2; o++)
+        if (m->exec[o]) {
+            cudaGraphExecDestroy(m->exec[o]);
+            m->exec[o] = nullptr;
+        }
+    for (size_t j = 0; j < m->large_idx.size(); j++) {
+        aaqaoa_plan *pl = m->plans[m->large_idx[j]];
+        int r = aaqaoa_set_workspace(pl, m->ws + m->sub_off[j], m->sub_bytes[j], 1, 0);
+        if (r)
+            return r;
+        pl->err_shared = reinterpret_cast<int *>(m->ws + m->off_err);
+    }
+    CK(cudaMemsetAsync(m->ws, 0, 256, m->stream));
+    if (!m->desc.empty())
+        CK(cudaMemcpyAsync(m->ws + m->off_desc, m->desc.data(), m->desc.size() * sizeof(SmallGraph),
+                           cudaMemcpyHostToDevice, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_expect_multi(aaqaoa_multi *m, const double *gamma, const double *beta, int observable, double *energy)
+{
+    g_detail.clear();
+    if (!m || !gamma || !beta || !energy)
+        return fail(AAQAOA_ERR_INVALID_ARG, "multi, gamma, beta or energy NULL");
+    if (!m->ws)
+        return fail(AAQAOA_ERR_WORKSPACE, "no workspace set (aaqaoa_multi_set_workspace)");
+    if (observable != AAQAOA_OBS_FULL && observable != AAQAOA_OBS_RED)
+        return fail(AAQAOA_ERR_INVALID_ARG, "observable %d unknown", observable);
+    if (observable == AAQAOA_OBS_RED)
+        for (int gi = 0; gi < m->G; gi++)
+            if (m->plans[gi]->num_orbits == 0 && m->plans[gi]->m > 0)
+                return fail(AAQAOA_ERR_INVALID_ARG, "H_red requested but graph %d has no edge orbits", gi);
+    const size_t Gp = (size_t)m->G * m->p;
+    double *d_par = reinterpret_cast<double *>(m->ws + m->off_params);
+    CK(cudaMemcpyAsync(d_par, gamma, Gp * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemcpyAsync(d_par + Gp, beta, Gp * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    if (!m->exec[observable]) {
+        // one direct run first (sets kernel attributes outside any capture)
+        int r = multi_enqueue(m, observable, 0, m->stream);
+        if (r)
+            return r;
+        CK(cudaStreamSynchronize(m->stream));
+        if ((r = multi_autotune(m, observable)))
+            return r;
+    }
+    CK(cudaGraphLaunch(m->exec[observable], m->stream));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, m->ws + m->off_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaMemcpyAsync(energy, m->ws + m->off_energy, (size_t)m->G * sizeof(double), cudaMemcpyDeviceToHost,
+                       m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    if (err) {
+        cudaMemsetAsync(m->ws, 0, 256, m->stream);
+        cudaStreamSynchronize(m->stream);
+        return fail(AAQAOA_ERR_TIMEOUT, "a bounded device wait expired in the batch");
+    }
+    return AAQAOA_OK;
+}
+
+int aaqaoa_multi_info(const aaqaoa_multi *m, int *G, int *small_graphs, int *branches, int *launches_per_call)
+{
+    if (!m)
+        return fail(AAQAOA_ERR_INVALID_ARG, "multi is NULL");
+    if (G) *G = m->G;
+    if (small_graphs) *small_graphs = (int)m->small_idx.size();
+    if (branches) *branches = std::max(m->branches[0], m->branches[1]);
+    if (launches_per_call) *launches_per_call = m->launches;
+    return AAQAOA_OK;
+}
+
+void aaqaoa_destroy_multi(aaqaoa_multi *m)
+{
+    if (!m)
+        return;
+    for (int o = 0; o < 2; o++)
+        if (m->exec[o])
+            cudaGraphExecDestroy(m->exec[o]);
+    for (auto s : m->side)
+        cudaStreamDestroy(s);
+    for (auto e : m->join)
+        cudaEventDestroy(e);
+    if (m->fork)
+        cudaEventDestroy(m->fork);
+    if (m->cap)
+        cudaStreamDestroy(m->cap);
+    for (auto pl : m->plans)
+        aaqaoa_destroy(pl);
+    delete m;
+}
+
+}  // extern "C"

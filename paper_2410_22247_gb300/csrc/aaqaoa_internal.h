@@ -43,6 +43,7 @@ struct PassArgs {
     int hmask;        // which local high bits (bit j = local bit cb + j) get a butterfly
     int tiles;        // tiles per statevector = 2^(n - tile bits)
     int B;            // statevectors (parameter points) in this launch
+    int chunk;        // 0: CTAs interleave tiles; else each CTA takes `chunk` consecutive tiles
     int load;         // 1: TMA-load the tile(s); 0: generate |+>^n
     int pre_phase;    // multiply by the cost-layer phase before any butterfly
     int pre_lambda;   // adjoint: load phi only and form lambda = O(x) phi first
@@ -64,6 +65,7 @@ struct PassArgs {
     int slot_idx[2];  // output index (within a point's row) of slot 0 / 1, or -1
     double slot_scale[2];
     int *err;         // device error flag
+    int drop_first_load;  // test hook: CTA 0 never loads its first tile (bounded wait expires)
     CutFn obs;        // observable of the reduction / lambda
     CostFn cost;      // C(x) for the phase and dE/dgamma
 };
@@ -82,6 +84,18 @@ struct SmallArgs {
     void *state;       // [B][2^n] (optional)
     CutFn obs;
     CostFn cost;
+};
+
+// Device descriptor of one small graph in an uneven batch (whole circuit in
+// one CTA): cost masks, and the masks and weights of both observables
+// (index 0 = H_C, 1 = H_red).
+struct SmallGraph {
+    int gi;  // index of the graph in the batch: its (gamma, beta) row and energy slot
+    int n, tab_len;
+    int K[2];
+    int w[2][MAXK];
+    uint64_t cost[MAXN];
+    uint64_t obs[2][MAXK][MAXN];
 };
 
 // Aggregation over a stored statevector.
@@ -114,5 +128,8 @@ int small_max_qubits(bool c128, int mode);
 int launch_agg_fused(bool c128, const AggArgs &a, cudaStream_t st, int grid);
 int launch_agg_terms(bool c128, const AggArgs &a, cudaStream_t st, int grid);
 int agg_grid(bool c128);
+size_t small_multi_smem_bytes(bool c128, int max_n, int max_tab);
+int launch_small_multi(bool c128, const SmallGraph *d_graphs, int G, int p, int obs, int max_n, int max_tab,
+                       const double *d_gamma, const double *d_beta, double *d_energy, cudaStream_t st);
 
 }  // namespace aaq

@@ -452,7 +452,7 @@ __host__ __device__ constexpr size_t tile_bytes() { return ((size_t)1 << Geo<R, 
 template <typename R, int NV>
 __host__ __device__ constexpr size_t pass_smem_total()
 {
-    return (size_t)Geo<R, NV>::NSTAGE * NV * tile_bytes<R, NV>() + (size_t)MAXTAB * sizeof(R) * 2 +
+    return (size_t)Geo<R, NV>::NSTAGE * NV * tile_bytes<R, NV>() + 2 * (size_t)MAXTAB * sizeof(R) * 2 +
            (size_t)(MAXK + 1) * MAXN * 8 + 1024;
 }
 static_assert(pass_smem_total<float, 1>() <= 227 * 1024, "c64 pipeline smem");
@@ -750,18 +750,41 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Was any tile of point b processed by CTA c? (CTA c takes tiles c, c+G, ...)
-__device__ __forceinline__ bool cta_touches(unsigned c, unsigned b, unsigned tiles, unsigned grid, unsigned total)
+// Tiles of CTA c: interleaved (c, c+G, c+2G, ...) when chunk == 0, else the
+// contiguous range [c*chunk, (c+1)*chunk) -- used for batches so that a CTA
+// meets each parameter point once.
+__device__ __forceinline__ unsigned cta_tile(unsigned c, unsigned k, unsigned grid, unsigned chunk)
+{
+    return chunk ? c * chunk + k : c + k * grid;
+}
+
+__device__ __forceinline__ unsigned cta_tile_count(unsigned c, unsigned grid, unsigned chunk, unsigned total)
+{
+    if (chunk) {
+        const unsigned lo = c * chunk;
+        return lo < total ? (total - lo < chunk ? total - lo : chunk) : 0;
+    }
+    return c < total ? (total - c + grid - 1) / grid : 0;
+}
+
+// Was any tile of point b processed by CTA c?
+__device__ __forceinline__ bool cta_touches(unsigned c, unsigned b, unsigned tiles, unsigned grid, unsigned total,
+                                            unsigned chunk)
 {
     const unsigned lo = b * tiles, hi = lo + tiles;
+    if (chunk) {
+        const unsigned c0 = c * chunk, c1 = c0 + cta_tile_count(c, grid, chunk, total);
+        return c0 < hi && lo < c1;
+    }
     unsigned g0 = c;
     if (g0 < lo)
         g0 += ((lo - c + grid - 1) / grid) * grid;
     return g0 < hi && g0 < total;
 }
 
-// partials[slot][b][cta]; the last CTA to finish sums them in a fixed order
-__device__ void pass_final_reduce(const PassArgs &A, double (*red)[32], unsigned total)
+// partials[slot][b][cta]; the last CTA to finish sums them in a fixed order:
+// one warp per (slot, point), lanes over the CTAs, then a fixed shuffle tree
+__device__ void pass_final_reduce(const PassArgs &A, unsigned total)
 {
     __shared__ unsigned s_last;
     __syncthreads();
@@ -774,20 +797,23 @@ __device__ void pass_final_reduce(const PassArgs &A, double (*red)[32], unsigned
         return;
     __threadfence();
     const unsigned G = gridDim.x;
-    for (int slot = 0; slot < 2; slot++) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int job = w; job < 2 * A.B; job += nw) {
+        const int slot = job / A.B, b = job - slot * A.B;
         if (A.slot_idx[slot] < 0)
             continue;
-        for (int b = 0; b < A.B; b++) {
-            const double *src = A.partials + ((size_t)slot * A.B + b) * G;
-            double a = 0.0;
-            for (unsigned c = threadIdx.x; c < G; c += blockDim.x)
-                if (cta_touches(c, (unsigned)b, (unsigned)A.tiles, G, total))
-                    a += __ldcg(src + c);
-            a = block_sum_all(a, red);
-            if (threadIdx.x == 0)
-                A.out[(size_t)b * A.out_stride + A.slot_idx[slot]] += A.slot_scale[slot] * a;
-        }
+        const double *src = A.partials + ((size_t)slot * A.B + b) * G;
+        double a = 0.0;
+        for (unsigned c = lane; c < G; c += 32)
+            if (cta_touches(c, (unsigned)b, (unsigned)A.tiles, G, total, (unsigned)A.chunk))
+                a += __ldcg(src + c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0)
+            A.out[(size_t)b * A.out_stride + A.slot_idx[slot]] += A.slot_scale[slot] * a;
     }
+    __syncthreads();
     if (threadIdx.x == 0)
         *A.counter = 0u;
 }
@@ -814,17 +840,18 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[NS], done[NS];
     __shared__ double red[2][32];
+    __shared__ double pred[2][2][32];  // per-warp sums of a finished point, two buffers
     __shared__ int s_flag;
     __shared__ int obs_w[MAXK];
 
     const int tid = threadIdx.x;
     C *tab = reinterpret_cast<C *>(sm + (size_t)NS * NV * TB);
-    uint64_t *cost_nbr = reinterpret_cast<uint64_t *>(tab + MAXTAB);
+    uint64_t *cost_nbr = reinterpret_cast<uint64_t *>(tab + 2 * MAXTAB);  // two table slots
     uint64_t *obs_nbr = cost_nbr + MAXN;
 
     const unsigned total = (unsigned)A.tiles * (unsigned)A.B;
     const unsigned grid = gridDim.x;
-    const unsigned niter = blockIdx.x < total ? (total - blockIdx.x + grid - 1) / grid : 0;
+    const unsigned niter = cta_tile_count(blockIdx.x, grid, (unsigned)A.chunk, total);
     // tile = 2^cb contiguous amplitudes x 2^(T-cb) rows along qubits s..
     const int cb = A.cb, hb = G::T - A.cb;
     const int midbits = A.s - cb;
@@ -850,7 +877,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         return;
 
     auto tile_coords = [&](unsigned k, unsigned &b, unsigned &t, unsigned &mid, int &c4) {
-        const unsigned g = blockIdx.x + k * grid;
+        const unsigned g = cta_tile(blockIdx.x, k, grid, (unsigned)A.chunk);
         b = g / (unsigned)A.tiles;
         t = g - b * (unsigned)A.tiles;
         mid = t & ((1u << midbits) - 1u);
@@ -867,6 +894,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 last_fill[s] = -1;
             auto fill = [&](unsigned k) {  // tile k into buffer k % NS
                 const int s = (int)(k % NS);
+                if (A.drop_first_load && k == 0 && blockIdx.x == 0)
+                    return;  // test hook: this tile's load is never issued, its wait runs out
                 last_fill[s] = (long long)k;
                 if (A.load) {
                     unsigned b, t, mid;
@@ -933,13 +962,40 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         X.tid = tid;
         X.first = true;
 
-        auto flush = [&](int b) {  // this CTA's sums for point b -> partials
-            compute_sum2<NTHR>(acc0, acc1, red);
-            if (tid == 0) {
-                A.partials[((size_t)0 * A.B + b) * grid + blockIdx.x] = acc0;
-                A.partials[((size_t)1 * A.B + b) * grid + blockIdx.x] = acc1;
+        // A point change costs no extra barrier. The phase table has two
+        // slots (the one being replaced was last read before the previous
+        // barrier), and the finished point's sums are warp-reduced into
+        // pred[parity] and written out by thread 0 after the next barrier.
+        // pred alternates between two buffers, so a warp that stashes the
+        // following point cannot overwrite sums thread 0 has not read yet:
+        // that stash comes after a barrier thread 0 only reaches when done.
+        const int lane = tid & 31, warp = tid >> 5;
+        int pend_b = -1, tslot = 1, par = 1;
+        auto stash = [&](int b) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+            }
+            par ^= 1;
+            if (lane == 0) {
+                pred[par][0][warp] = acc0;
+                pred[par][1][warp] = acc1;
             }
             acc0 = acc1 = 0.0;
+            pend_b = b;
+        };
+        auto write_pending = [&]() {  // after a barrier
+            if (pend_b >= 0 && tid == 0) {
+                double s0 = 0.0, s1 = 0.0;
+                for (int w = 0; w < NTHR / 32; w++) {
+                    s0 += pred[par][0][w];
+                    s1 += pred[par][1][w];
+                }
+                A.partials[((size_t)0 * A.B + pend_b) * grid + blockIdx.x] = s0;
+                A.partials[((size_t)1 * A.B + pend_b) * grid + blockIdx.x] = s1;
+            }
+            pend_b = -1;
         };
 
         bool ok = true;
@@ -951,12 +1007,14 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             unsigned char *buf = sm + (size_t)s * NV * TB;
             if ((int)b != cur_b) {  // new parameter point: its phase table and mixer angle
                 if (cur_b >= 0 && reduce)
-                    flush(cur_b);
-                compute_sync<NTHR>();
+                    stash(cur_b);
+                tslot ^= 1;
+                X.tab = tab + tslot * MAXTAB;
                 if (A.pre_phase || (A.post & POST_PHASE_CONJ)) {
                     const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.layer) * A.tab_len;
+                    C *dst = tab + tslot * MAXTAB;
                     for (int i = tid; i < A.tab_len; i += NTHR)
-                        tab[i] = src[i];
+                        dst[i] = src[i];
                 }
                 const double2 csd = A.cs[(size_t)b * A.p + A.layer];
                 const double cbv = csd.x, sbv = A.sign_s * csd.y;
@@ -974,7 +1032,6 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 X.fn2 = (R)(fn * fn);
                 X.scale0 = (R)fj;
                 cur_b = (int)b;
-                compute_sync<NTHR>();
             }
             X.sv0 = reinterpret_cast<C *>(buf);
             X.sv1 = reinterpret_cast<C *>(buf + TB);
@@ -983,6 +1040,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             if (!mbar_wait_bounded(&full[s], (k / NS) & 1u))
                 atomicOr(&s_flag, 1);
             compute_sync<NTHR>();
+            write_pending();
             if (s_flag) {  // a tile never arrived
                 if (tid == 0)
                     atomicExch(A.err, 1);
@@ -1006,14 +1064,17 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             fence_proxy_async_smem();
             mbar_arrive(&done[s]);
         }
-        if (ok && reduce && cur_b >= 0)
-            flush(cur_b);
+        if (ok && reduce && cur_b >= 0) {
+            stash(cur_b);
+            compute_sync<NTHR>();
+            write_pending();
+        }
     }
     __syncthreads();
     if (s_flag)
         return;
     if (reduce)
-        pass_final_reduce(A, red, total);
+        pass_final_reduce(A, total);
 }
 
 // ------------------------------------------------------ parameter tables
@@ -1187,6 +1248,86 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallArgs
             A.out[(size_t)b * A.out_stride + 1 + A.p + l] = 2.0 * gb;
         }
     }
+}
+
+// ------------------------------------- uneven batch of small graphs
+// One CTA per graph (n <= 13 for complex64, <= 12 for complex128), the whole
+// p-layer circuit and the fused energy in shared memory. Each CTA reads its
+// graph's masks from a device descriptor and builds its own phase factors
+// exp(-i ((gamma_l c) mod 2 pi)) in FP64, so graphs of different n and |E|
+// share one launch.
+template <typename R>
+__global__ void __launch_bounds__(256) k_small_multi(const SmallGraph *__restrict__ graphs, int G, int p, int obs,
+                                                      const double *__restrict__ gamma,
+                                                      const double *__restrict__ beta, double *__restrict__ energy)
+{
+    using C = typename CT<R>::T;
+    constexpr int NT = 256;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2][32];
+    __shared__ uint64_t s_cost[MAXN], s_obs[MAXK * MAXN];
+    __shared__ int s_w[MAXK];
+    const int g = blockIdx.x, tid = threadIdx.x;
+    if (g >= G)
+        return;
+    const SmallGraph &D = graphs[g];
+    const int n = D.n, N = 1 << n, half = N >> 1, K = D.K[obs], tab_len = D.tab_len;
+    for (int i = tid; i < MAXN; i += NT)
+        s_cost[i] = D.cost[i];
+    for (int i = tid; i < K * MAXN; i += NT)
+        s_obs[i] = D.obs[obs][i / MAXN][i % MAXN];
+    if (tid < MAXK)
+        s_w[tid] = D.w[obs][tid];
+    C *phi = reinterpret_cast<C *>(smem_raw);
+    C *tab = phi + N;
+    const double TWO_PI = 6.283185307179586476925286766559;
+    const double amp0 = rsqrt((double)N);
+    for (int x = tid; x < N; x += NT)
+        phi[x] = mkc<C>((R)amp0, (R)0);
+    for (int l = 0; l < p; l++) {
+        __syncthreads();
+        const double gl = gamma[(size_t)D.gi * p + l];
+        for (int c = tid; c < tab_len; c += NT) {
+            double ang = fmod(gl * (double)c, TWO_PI);
+            if (ang < 0.0)
+                ang += TWO_PI;
+            double sn, cn;
+            sincos(ang, &sn, &cn);
+            tab[c] = mkc<C>((R)cn, (R)(-sn));
+        }
+        double sb, cbv;
+        sincos(beta[(size_t)D.gi * p + l], &sb, &cbv);
+        const R c = (R)cbv, s = (R)sb;
+        __syncthreads();
+        for (int x = tid; x < N; x += NT) {
+            int cv = 0;
+            for (int u = 0; u < n; u++)
+                cv += ((x >> u) & 1) ? __popcll(s_cost[u] & ~(uint64_t)x) : 0;
+            phi[x] = cmul(phi[x], tab[cv]);
+        }
+        for (int q = 0; q < n; q++) {
+            __syncthreads();
+            for (int j = tid; j < half; j += NT) {
+                const int x0 = ((j >> q) << (q + 1)) | (j & ((1 << q) - 1));
+                bfly(phi[x0], phi[x0 | (1 << q)], c, s);
+            }
+        }
+    }
+    __syncthreads();
+    double e = 0.0, dummy = 0.0;
+    for (int x = tid; x < N; x += NT) {
+        int v = 0;
+        for (int k = 0; k < K; k++) {
+            int cut = 0;
+            for (int u = 0; u < n; u++)
+                cut += ((x >> u) & 1) ? __popcll(s_obs[k * MAXN + u] & ~(uint64_t)x) : 0;
+            v += s_w[k] * cut;
+        }
+        e += (double)((phi[x].x * phi[x].x + phi[x].y * phi[x].y) * (R)v);
+    }
+    block_sum2<NT>(e, dummy, red);
+    if (tid == 0)
+        energy[D.gi] = e;
 }
 
 // -------------------------------------------- aggregation over a state
@@ -1488,6 +1629,30 @@ int launch_small(bool c128, const SmallArgs &a, int B, cudaStream_t st)
         if (e != cudaSuccess)
             return (int)e;
         k_small<float><<<B, 256, smem, st>>>(a);
+    }
+    return (int)cudaGetLastError();
+}
+
+size_t small_multi_smem_bytes(bool c128, int max_n, int max_tab)
+{
+    return (((size_t)1 << max_n) + (size_t)max_tab) * (c128 ? 16 : 8);
+}
+
+int launch_small_multi(bool c128, const SmallGraph *d_graphs, int G, int p, int obs, int max_n, int max_tab,
+                       const double *d_gamma, const double *d_beta, double *d_energy, cudaStream_t st)
+{
+    const size_t smem = small_multi_smem_bytes(c128, max_n, max_tab);
+    cudaError_t e;
+    if (c128) {
+        e = cudaFuncSetAttribute(k_small_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return (int)e;
+        k_small_multi<double><<<G, 256, smem, st>>>(d_graphs, G, p, obs, d_gamma, d_beta, d_energy);
+    } else {
+        e = cudaFuncSetAttribute(k_small_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return (int)e;
+        k_small_multi<float><<<G, 256, smem, st>>>(d_graphs, G, p, obs, d_gamma, d_beta, d_energy);
     }
     return (int)cudaGetLastError();
 }

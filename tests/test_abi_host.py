@@ -114,3 +114,18 @@ def test_workspace_size_grows_with_batch_and_gradient():
 def test_strerror_covers_codes():
     for c in [0, -1, -2, -3, -4, -5, -6]:
         assert N.aaqaoa_strerror(c)
+
+
+def test_prepare_multi_names_the_bad_graph():
+    good = np.ascontiguousarray(np.array([[0, 1], [1, 2]], dtype=np.int32).reshape(-1))
+    bad = np.ascontiguousarray(np.array([[0, 0]], dtype=np.int32).reshape(-1))
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    descs = (N.GraphDesc * 3)()
+    for i, (n, e) in enumerate([(3, good), (3, good), (2, bad)]):
+        descs[i].n = n
+        descs[i].num_edges = len(e) // 2
+        descs[i].edges = P(e)
+        descs[i].num_orbits = 0
+    h = ctypes.c_void_p()
+    assert N.aaqaoa_prepare_multi(3, descs, 1, 0, None, ctypes.byref(h)) == -1
+    assert b"graph 2" in N.aaqaoa_last_error_detail()
