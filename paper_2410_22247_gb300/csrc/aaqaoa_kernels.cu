@@ -285,62 +285,6 @@ __device__ __forceinline__ void eval_cut(const CutFn &f, int n, uint64_t x0, con
     finish_cut<RB>(base, d, W, v);
 }
 
-// Smem-resident copies of the cut functions: cost masks nbr[u]; observable
-// masks nbr[c * MAXN + u] with integer class weights w[c].
-template <int RB>
-__device__ __forceinline__ void eval_cost_s(const uint64_t *nbr, int n, uint64_t x0, const int (&gp)[RB],
-                                            int (&v)[1 << RB])
-{
-    int base = 0;
-    for (int u = 0; u < n; u++) {
-        const uint64_t nb = nbr[u];
-        base += ((x0 >> u) & 1ull) ? __popcll(nb & ~x0) : 0;
-    }
-    int d[RB], W[RB][RB];
-#pragma unroll
-    for (int k = 0; k < RB; k++) {
-        const uint64_t nb = nbr[gp[k]];
-        d[k] = __popcll(nb) - 2 * __popcll(nb & x0);
-#pragma unroll
-        for (int k2 = 0; k2 < RB; k2++)
-            W[k][k2] = (int)((nb >> gp[k2]) & 1ull);
-    }
-    finish_cut<RB>(base, d, W, v);
-}
-
-template <int RB>
-__device__ __forceinline__ void eval_cut_s(const uint64_t *nbr, const int *w, int K, int n, uint64_t x0,
-                                           const int (&gp)[RB], int (&v)[1 << RB])
-{
-    int base = 0, d[RB], W[RB][RB];
-#pragma unroll
-    for (int k = 0; k < RB; k++) {
-        d[k] = 0;
-#pragma unroll
-        for (int k2 = 0; k2 < RB; k2++)
-            W[k][k2] = 0;
-    }
-    for (int c = 0; c < K; c++) {
-        const int wc = w[c];
-        const uint64_t *nc = nbr + c * MAXN;
-        int bc = 0;
-        for (int u = 0; u < n; u++) {
-            const uint64_t nb = nc[u];
-            bc += ((x0 >> u) & 1ull) ? __popcll(nb & ~x0) : 0;
-        }
-        base += wc * bc;
-#pragma unroll
-        for (int k = 0; k < RB; k++) {
-            const uint64_t nb = nc[gp[k]];
-            d[k] += wc * (__popcll(nb) - 2 * __popcll(nb & x0));
-#pragma unroll
-            for (int k2 = 0; k2 < RB; k2++)
-                W[k][k2] += wc * (int)((nb >> gp[k2]) & 1ull);
-        }
-    }
-    finish_cut<RB>(base, d, W, v);
-}
-
 // ---------------------------------------------------------- tile geometry
 // A tile holds 2^T amplitudes per vector: local bits 0..CB-1 are one 128-byte
 // row of contiguous amplitudes, local bits CB..CB+HB-1 are HB consecutive
@@ -455,10 +399,20 @@ __host__ __device__ constexpr size_t pass_smem_total()
     return (size_t)Geo<R, NV>::NSTAGE * NV * tile_bytes<R, NV>() + 2 * (size_t)MAXTAB * sizeof(R) * 2 +
            (size_t)(MAXK + 1) * MAXN * 8 + 1024;
 }
-static_assert(pass_smem_total<float, 1>() <= 227 * 1024, "c64 pipeline smem");
-static_assert(pass_smem_total<float, 2>() <= 227 * 1024, "c64 adjoint pipeline smem");
-static_assert(pass_smem_total<double, 1>() <= 227 * 1024, "c128 pipeline smem");
-static_assert(pass_smem_total<double, 2>() <= 227 * 1024, "c128 adjoint pipeline smem");
+// static shared memory of the pass kernel (mbarriers, per-point sums, cut
+// constants) plus slack for the final reduction's flag
+template <typename R, int NV>
+__host__ __device__ constexpr size_t pass_static_smem()
+{
+    using G = Geo<R, NV>;
+    return 2 * G::NSTAGE * 8 + 2 * 2 * 32 * 8 + 4 + MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
+           2 * (G::RB + 1) * G::NTHR * 4 + 2 * 2 * 32 * 4 + 256;
+}
+static_assert(pass_smem_total<float, 1>() + pass_static_smem<float, 1>() <= 227 * 1024, "c64 pipeline smem");
+static_assert(pass_smem_total<float, 2>() + pass_static_smem<float, 2>() <= 227 * 1024, "c64 adjoint pipeline smem");
+static_assert(pass_smem_total<double, 1>() + pass_static_smem<double, 1>() <= 227 * 1024, "c128 pipeline smem");
+static_assert(pass_smem_total<double, 2>() + pass_static_smem<double, 2>() <= 227 * 1024,
+              "c128 adjoint pipeline smem");
 
 template <typename G>
 __host__ __device__ constexpr uint32_t reg_offset(int st, int m)
@@ -518,9 +472,10 @@ template <typename R>
 struct StageCtx {
     typename CT<R>::T *sv0, *sv1;
     const typename CT<R>::T *tab;
-    const uint64_t *cost_nbr, *obs_nbr;
-    const int *obs_w;
-    int obs_k;
+    const int *tc;     // this tile's constants [2][16] (function 0 = C, 1 = O)
+    const int *ptc;    // this thread's launch constants: ptc[(e * (RB + 1) + i) * NTHR]
+    const int *qr;     // [2][2^RB] register-pair terms
+    const float *qrf;  // the same as floats
     uint64_t fixed;
     int s, cb, tid;  // high qubit s and contiguous bits cb of this pass's tiles
     bool first;
@@ -531,6 +486,87 @@ struct StageCtx {
     R scale0;      // f^j0: butterflies of this layer applied by earlier passes
     R run;         // f^j for the current tile (advanced by every butterfly)
 };
+
+// ------------------------------------------------ cut values in a stage
+// A weighted cut function is quadratic in the bits: flipping vertex u from 0
+// to 1 changes it by h_u(x) = sum_c w_c (deg_c(u) - 2 |N_c(u) & x|), and two
+// flipped neighbours u, v interact by J_uv = -2 sum_c w_c [uv in E_c]. Write
+// a basis state of a tile as x = f | t | r: f the tile's fixed bits, t the
+// thread's bits of this stage, r its register bits. Then
+//   O(x) = O(f) + sum_{u in t} h_u(f) + sum_{u<v in t} J_uv        (base)
+//        + sum_{k in r} (h_k(f) + sum_{u in t} J_ku)             (d_k)
+//        + sum_{k<k' in r} J_kk'                                  (Qr[r]).
+// O(f) and h_u(f) for the T tile vertices depend on the tile only (the
+// producer warp computes them per tile), the t-only sums on the thread only
+// (computed once per launch), Qr on the stage only. What is left per thread
+// and tile is a subset sum over the 2^RB register states.
+template <typename G, int ST>
+__device__ __forceinline__ void cut_terms(const int *tc, const int *pt, int tid, int &base, int (&d)[G::RB])
+{
+    constexpr int NTB = G::T - G::RB;
+    base = tc[15] + pt[0];
+#pragma unroll
+    for (int j = 0; j < NTB; j++)
+        if ((tid >> j) & 1)
+            base += tc[G::thr(ST, j)];
+#pragma unroll
+    for (int k = 0; k < G::RB; k++)
+        d[k] = tc[G::reg(ST, k)] + pt[(1 + k) * G::NTHR];
+}
+
+// integer cut values (phase-table indices)
+template <typename G, int ST>
+__device__ __forceinline__ void cut_int(const int *tc, const int *pt, const int *qr, int tid, int (&v)[1 << G::RB])
+{
+    constexpr int RB = G::RB;
+    int base, d[RB];
+    cut_terms<G, ST>(tc, pt, tid, base, d);
+    v[0] = base;
+#pragma unroll
+    for (int m = 1; m < (1 << RB); m++) {
+        const int top = hibit(m);
+        v[m] = v[m ^ (1 << top)] + d[top];
+    }
+#pragma unroll
+    for (int m = 1; m < (1 << RB); m++)
+        v[m] += qr[m];
+}
+
+// cut values as multipliers of type R (exact: integers below 2^24)
+template <typename G, typename R, int ST>
+__device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int *qr, const float *qrf, int tid,
+                                         R (&v)[1 << G::RB])
+{
+    constexpr int RB = G::RB;
+    int base, d[RB];
+    cut_terms<G, ST>(tc, pt, tid, base, d);
+    if constexpr (std::is_same<R, float>::value) {
+        float df[RB];
+#pragma unroll
+        for (int k = 0; k < RB; k++)
+            df[k] = (float)d[k];
+        v[0] = (float)base;
+#pragma unroll
+        for (int m = 1; m < (1 << RB); m++) {
+            const int top = hibit(m);
+            v[m] = v[m ^ (1 << top)] + df[top];
+        }
+#pragma unroll
+        for (int m = 1; m < (1 << RB); m++)
+            v[m] += qrf[m];
+    } else {
+        int iv[1 << RB];
+        iv[0] = base;
+#pragma unroll
+        for (int m = 1; m < (1 << RB); m++) {
+            const int top = hibit(m);
+            iv[m] = iv[m ^ (1 << top)] + d[top];
+        }
+#pragma unroll
+        for (int m = 0; m < (1 << RB); m++)
+            v[m] = (R)(iv[m] + qr[m]);
+    }
+}
 
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
 template <typename R, int NV, int ST, bool OPS>
@@ -561,28 +597,24 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
                 load_regs<R, NV, ST>(X.sv1, sb, l);
     }
 
-    int gp[RB];
-#pragma unroll
-    for (int k = 0; k < RB; k++) {
-        const int L = G::reg(ST, k);
-        gp[k] = L < X.cb ? L : X.s + L - X.cb;
-    }
-    const uint64_t x0 = X.fixed | (uint64_t)(base & ((1u << X.cb) - 1u)) | ((uint64_t)(base >> X.cb) << X.s);
+    // cut-function constants: function 0 is C (cost), 1 the observable O
+    const int *tc0 = X.tc, *tc1 = X.tc + 16;
+    const int *pt0 = X.ptc + X.tid, *pt1 = X.ptc + (RB + 1) * G::NTHR + X.tid;
 
     if (OPS && ST == 0 && A.pre_phase) {
         int cv[NR];
-        eval_cost_s<RB>(X.cost_nbr, A.n, x0, gp, cv);
+        cut_int<G, ST>(tc0, pt0, X.qr, X.tid, cv);
 #pragma unroll
         for (int m = 0; m < NR; m++)
             a[m] = cmul(a[m], X.tab[cv[m]]);
     }
     if constexpr (NV == 2) {
         if (OPS && X.first && A.pre_lambda) {  // lambda = O phi, from the stored final state
-            int ov[NR];
-            eval_cut_s<RB>(X.obs_nbr, X.obs_w, X.obs_k, A.n, x0, gp, ov);
+            R ov[NR];
+            cut_real<G, R, ST>(tc1, pt1, X.qr + 32, X.qrf + 32, X.tid, ov);
 #pragma unroll
             for (int m = 0; m < NR; m++)
-                l[m] = mkc<C>(a[m].x * (R)ov[m], a[m].y * (R)ov[m]);
+                l[m] = mkc<C>(a[m].x * ov[m], a[m].y * ov[m]);
         }
     }
 
@@ -653,26 +685,28 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     }
 
     if (OPS && LAST && (A.post & POST_REDUCE)) {
-        int ov[NR];
-        eval_cut_s<RB>(X.obs_nbr, X.obs_w, X.obs_k, A.n, x0, gp, ov);
+        R ov[NR];
+        cut_real<G, R, ST>(tc1, pt1, X.qr + 32, X.qrf + 32, X.tid, ov);
         R e = 0;
 #pragma unroll
         for (int m = 0; m < NR; m++)
-            e += (a[m].x * a[m].x + a[m].y * a[m].y) * (R)ov[m];
+            e += (a[m].x * a[m].x + a[m].y * a[m].y) * ov[m];
         acc0 += (A.post & POST_RESCALE) ? (double)e : (double)e * (double)X.fn2;
     }
     if constexpr (NV == 2) {
         if (OPS && LAST && (A.post & (POST_GAMMA | POST_PHASE_CONJ))) {
-            int cv[NR];
-            eval_cost_s<RB>(X.cost_nbr, A.n, x0, gp, cv);
             if (A.post & POST_GAMMA) {
+                R cr[NR];
+                cut_real<G, R, ST>(tc0, pt0, X.qr, X.qrf, X.tid, cr);
                 R g = 0;
 #pragma unroll
                 for (int m = 0; m < NR; m++)
-                    g += (R)cv[m] * im_conj_mul(l[m], a[m]);
+                    g += cr[m] * im_conj_mul(l[m], a[m]);
                 acc1 += (double)g * (double)X.fn2;  // both vectors carry 1/f^n here
             }
             if (A.post & POST_PHASE_CONJ) {  // inverse cost layer, restoring f^n
+                int cv[NR];
+                cut_int<G, ST>(tc0, pt0, X.qr, X.tid, cv);
 #pragma unroll
                 for (int m = 0; m < NR; m++) {
                     const C t = X.tab[cv[m]];
@@ -839,10 +873,13 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     // shared array itself, so every tile access stays a shared-memory access
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[NS], done[NS];
-    __shared__ double red[2][32];
     __shared__ double pred[2][2][32];  // per-warp sums of a finished point, two buffers
     __shared__ int s_flag;
     __shared__ int obs_w[MAXK];
+    __shared__ int tcs[NS][2][16];                  // per buffer: O(f) and h_u(f) of its tile
+    __shared__ int ptc[2 * (G::RB + 1) * NTHR];     // per thread: t-only terms of each function
+    __shared__ int qr[2][32];                       // per function: register-pair terms
+    __shared__ float qrf[2][32];
 
     const int tid = threadIdx.x;
     C *tab = reinterpret_cast<C *>(sm + (size_t)NS * NV * TB);
@@ -876,6 +913,63 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     if (s_flag)
         return;
 
+    // The register stage that evaluates each cut function in this pass, or -1:
+    // C for the phase of a forward low pass (stage 0) and for the gradient and
+    // inverse phase of the last adjoint pass of a layer (last stage); O for
+    // lambda = O phi (first stage of the first adjoint pass) and for the
+    // energy (last stage of the last forward pass).
+    int est[2] = {-1, -1};
+    if (OPS) {
+        if (A.pre_phase)
+            est[0] = 0;
+        else if (NV == 2 && (A.post & (POST_GAMMA | POST_PHASE_CONJ)))
+            est[0] = G::NST - 1;
+        if (NV == 2 && A.pre_lambda)
+            est[1] = A.is_low ? 0 : 1;
+        else if (A.post & POST_REDUCE)
+            est[1] = G::NST - 1;
+    }
+    // vertex of local tile bit L, and the weight of edge (u, v) in function e
+    auto gq = [&](int L) { return L < A.cb ? L : A.s + L - A.cb; };
+    auto wgt = [&](int e, int u, int v) -> int {
+        if (e == 0)
+            return (int)((cost_nbr[u] >> v) & 1ull);
+        int w = 0;
+        for (int c = 0; c < A.obs.K; c++)
+            w += obs_w[c] * (int)((obs_nbr[c * MAXN + u] >> v) & 1ull);
+        return w;
+    };
+    if (tid < NTHR) {  // launch constants of the quadratic decomposition
+        constexpr int RB = G::RB, NTB = G::T - G::RB;
+        for (int e = 0; e < 2; e++) {
+            const int st = est[e];
+            if (st < 0)
+                continue;
+            int q = 0;
+            for (int j = 0; j < NTB; j++)
+                for (int j2 = 0; j2 < j; j2++)
+                    if (((tid >> j) & 1) && ((tid >> j2) & 1))
+                        q -= 2 * wgt(e, gq(G::thr(st, j)), gq(G::thr(st, j2)));
+            ptc[(e * (RB + 1)) * NTHR + tid] = q;
+            for (int kk = 0; kk < RB; kk++) {
+                int dk = 0;
+                for (int j = 0; j < NTB; j++)
+                    if ((tid >> j) & 1)
+                        dk -= 2 * wgt(e, gq(G::reg(st, kk)), gq(G::thr(st, j)));
+                ptc[(e * (RB + 1) + 1 + kk) * NTHR + tid] = dk;
+            }
+            if (tid < (1 << RB)) {
+                int qq = 0;
+                for (int kk = 0; kk < RB; kk++)
+                    for (int k2 = 0; k2 < kk; k2++)
+                        if (((tid >> kk) & 1) && ((tid >> k2) & 1))
+                            qq -= 2 * wgt(e, gq(G::reg(st, kk)), gq(G::reg(st, k2)));
+                qr[e][tid] = qq;
+                qrf[e][tid] = (float)qq;
+            }
+        }
+    }
+
     auto tile_coords = [&](unsigned k, unsigned &b, unsigned &t, unsigned &mid, int &c4) {
         const unsigned g = cta_tile(blockIdx.x, k, grid, (unsigned)A.chunk);
         b = g / (unsigned)A.tiles;
@@ -887,39 +981,77 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
 
     if (tid >= NTHR) {
         // ------------------------------------------------------ producer
-        if (tid == NTHR) {
-            bool ok = true;
-            long long last_fill[NS];  // newest tile loaded into each buffer
-            for (int s = 0; s < NS; s++)
-                last_fill[s] = -1;
-            auto fill = [&](unsigned k) {  // tile k into buffer k % NS
-                const int s = (int)(k % NS);
-                if (A.drop_first_load && k == 0 && blockIdx.x == 0)
-                    return;  // test hook: this tile's load is never issued, its wait runs out
-                last_fill[s] = (long long)k;
-                if (A.load) {
-                    unsigned b, t, mid;
-                    int c4;
-                    tile_coords(k, b, t, mid, c4);
-                    unsigned char *buf = sm + (size_t)s * NV * TB;
-                    const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
-                    mbar_arrive_expect_tx(&full[s], (uint32_t)A.nvec_io * TB);
-                    tma_load_5d(buf, &map0, &full[s], 0, c1, c2, 0, c4);
-                    if (A.nvec_io == 2)
-                        tma_load_5d(buf + TB, &map1, &full[s], 0, c1, c2, 0, c4);
-                } else {
-                    mbar_arrive(&full[s]);  // generating pass: the buffer is free
+        // Lane 0 issues the TMA copies and waits on the mbarriers; the whole
+        // warp computes each tile's cut constants O(f), h_u(f) before the
+        // tile's buffer is handed over (the arrive on full[s] releases them).
+        const int lane = tid - NTHR;
+        auto tile_consts = [&](unsigned k, int s) {
+            if (est[0] < 0 && est[1] < 0)
+                return;
+            unsigned b, t, mid;
+            int c4;
+            tile_coords(k, b, t, mid, c4);
+            const uint64_t f = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
+            for (int e = 0; e < 2; e++) {
+                if (est[e] < 0)
+                    continue;
+                const int K = e == 0 ? 1 : A.obs.K;
+                int hs = 0, os = 0;
+                for (int c = 0; c < K; c++) {
+                    const uint64_t *nb = e == 0 ? cost_nbr : obs_nbr + c * MAXN;
+                    const int w = e == 0 ? 1 : obs_w[c];
+                    if (lane < G::T) {
+                        const uint64_t m = nb[gq(lane)];
+                        hs += w * (__popcll(m) - 2 * __popcll(m & f));
+                    }
+                    for (int u = lane; u < A.n; u += 32)
+                        if ((f >> u) & 1ull)
+                            os += w * __popcll(nb[u] & ~f);
                 }
-            };
-            for (unsigned k = 0; k < (unsigned)NS && k < niter; k++)
-                fill(k);
-            for (unsigned k = 0; k < niter && ok; k++) {
-                const int s = (int)(k % NS);
-                if (!mbar_wait_bounded(&done[s], (k / NS) & 1u) || *reinterpret_cast<volatile int *>(&s_flag)) {
-                    ok = false;
-                    break;
-                }
-                if (A.write) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    os += __shfl_xor_sync(0xffffffffu, os, o);
+                if (lane < G::T)
+                    tcs[s][e][lane] = hs;
+                if (lane == 0)
+                    tcs[s][e][15] = os;
+            }
+        };
+        bool ok = true;
+        long long last_fill[NS];  // newest tile loaded into each buffer (lane 0)
+        for (int s = 0; s < NS; s++)
+            last_fill[s] = -1;
+        auto fill = [&](unsigned k) {  // tile k into buffer k % NS
+            const int s = (int)(k % NS);
+            tile_consts(k, s);
+            __syncwarp();
+            if (lane != 0)
+                return;
+            if (A.drop_first_load && k == 0 && blockIdx.x == 0)
+                return;  // test hook: this tile's load is never issued, its wait runs out
+            last_fill[s] = (long long)k;
+            if (A.load) {
+                unsigned b, t, mid;
+                int c4;
+                tile_coords(k, b, t, mid, c4);
+                unsigned char *buf = sm + (size_t)s * NV * TB;
+                const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
+                mbar_arrive_expect_tx(&full[s], (uint32_t)A.nvec_io * TB);
+                tma_load_5d(buf, &map0, &full[s], 0, c1, c2, 0, c4);
+                if (A.nvec_io == 2)
+                    tma_load_5d(buf + TB, &map1, &full[s], 0, c1, c2, 0, c4);
+            } else {
+                mbar_arrive(&full[s]);  // generating pass: the buffer is free
+            }
+        };
+        for (unsigned k = 0; k < (unsigned)NS && k < niter; k++)
+            fill(k);
+        for (unsigned k = 0; k < niter && ok; k++) {
+            const int s = (int)(k % NS);
+            int good = 1;
+            if (lane == 0) {
+                good = mbar_wait_bounded(&done[s], (k / NS) & 1u) && !*reinterpret_cast<volatile int *>(&s_flag);
+                if (good && A.write) {
                     unsigned b, t, mid;
                     int c4;
                     tile_coords(k, b, t, mid, c4);
@@ -929,13 +1061,19 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                     if (NV == 2)
                         tma_store_5d(&map1, buf + TB, 0, c1, c2, 0, c4);
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-                }
-                if (k + NS < niter) {
-                    if (A.write)  // the buffer is reloaded: its store must have read it
+                    if (k + NS < niter)  // the buffer is reloaded: its store must have read it
                         asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                    fill(k + NS);
                 }
             }
+            good = __shfl_sync(0xffffffffu, good, 0);
+            if (!good) {
+                ok = false;
+                break;
+            }
+            if (k + NS < niter)
+                fill(k + NS);
+        }
+        if (lane == 0) {
             if (!ok) {
                 atomicExch(A.err, 1);
                 s_flag = 1;
@@ -953,10 +1091,9 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         int cur_b = -1;
         StageCtx<R> X;
         X.tab = tab;
-        X.cost_nbr = cost_nbr;
-        X.obs_nbr = obs_nbr;
-        X.obs_w = obs_w;
-        X.obs_k = A.obs.K;
+        X.ptc = ptc;
+        X.qr = &qr[0][0];
+        X.qrf = &qrf[0][0];
         X.s = A.s;
         X.cb = cb;
         X.tid = tid;
@@ -1035,6 +1172,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             }
             X.sv0 = reinterpret_cast<C *>(buf);
             X.sv1 = reinterpret_cast<C *>(buf + TB);
+            X.tc = &tcs[s][0][0];
             X.fixed = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
 
             if (!mbar_wait_bounded(&full[s], (k / NS) & 1u))
