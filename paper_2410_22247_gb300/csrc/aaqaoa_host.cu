@@ -920,8 +920,12 @@ int aaqaoa_statevector(aaqaoa_plan *pl, const double *gamma, const double *beta,
         SmallArgs s = small_args(pl, AAQAOA_OBS_FULL, SMALL_ENERGY, 1);
         CKL(launch_small(pl->c128, s, 1, pl->stream), "whole-circuit kernel");
         pl->launches++;
-    } else if ((r = enqueue_forward(pl, 1, AAQAOA_OBS_FULL, FWD_STATE))) {
-        return r;
+    } else {
+        if ((r = enqueue_forward(pl, 1, AAQAOA_OBS_FULL, FWD_STATE)))
+            return r;
+        // the passes store the twisted, shifted-angle state: map it back
+        CKL(launch_untwist(pl->c128, pl->d_phi(), pl->n, pl->d_cs(), pl->p, pl->stream), "statevector export");
+        pl->launches++;
     }
     pl->state_valid = true;
     std::vector<double> rows;

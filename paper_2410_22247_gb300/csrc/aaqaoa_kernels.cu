@@ -79,28 +79,44 @@ __device__ __forceinline__ void bfly(C &a, C &b, R c, R s)
     b = b2;
 }
 
-// RX(2 beta) up to a real factor f, with one FMA per output component:
-//   |cos| >= |sin|: f = cos, t = tan:  (a, b) <- (a - i t b, b - i t a)
-//   |cos| <  |sin|: f = sin, u = cot:  (a, b) <- (u a - i b, u b - i a)
-// so c a - i s b = f * (new a). The caller rescales by f^k after k of them.
+// The tiled passes keep the statevector in the twisted frame
+//   psi~(x) = i^|x| psi(x)        (|x| = number of one bits of x).
+// There RX(2 beta) on the pair (x, x ^ e_q), x_q = 0, is the real rotation
+//   (a, b) <- (c a - s b, c b + s a)
+// applied to real and imaginary parts alike, so one packed two-lane FMA
+// updates a whole complex amplitude. Up to the real factor f it reads
+//   f = cos beta, t = tan beta:            (a, b) <- (a - t b, b + t a)
+// and for |sin| > |cos| the same form with f = sin beta, t = -cot beta is the
+// rotation by beta - pi/2, i.e. RX(2 beta) with the factor -i X dropped on
+// every qubit. (-i X)^n commutes with the phase and the observable (a cut
+// value is invariant when all bits flip), so energies and gradients are
+// unchanged; only the exported statevector is corrected for it.
 template <typename C, typename R>
-__device__ __forceinline__ void bfly_tan(C &a, C &b, R t)
+__device__ __forceinline__ void rot(C &a, C &b, R t)
 {
-    const C a0 = a, b0 = b;
-    a.x = fma(t, b0.y, a0.x);
-    a.y = fma(-t, b0.x, a0.y);
-    b.x = fma(t, a0.y, b0.x);
-    b.y = fma(-t, a0.x, b0.y);
+    if constexpr (std::is_same<R, float>::value) {
+        const float2 a0 = a;
+        a = __ffma2_rn(make_float2(-t, -t), b, a);
+        b = __ffma2_rn(make_float2(t, t), a0, b);
+    } else {
+        const C a0 = a;
+        a.x = fma(-t, b.x, a.x);
+        a.y = fma(-t, b.y, a.y);
+        b.x = fma(t, a0.x, b.x);
+        b.y = fma(t, a0.y, b.y);
+    }
 }
 
-template <typename C, typename R>
-__device__ __forceinline__ void bfly_cot(C &a, C &b, R u)
+// acc += (u.x v.x, u.y v.y): Re(conj(u) v) summed over the two lanes later
+template <typename C>
+__device__ __forceinline__ void dot_acc(C &acc, const C &u, const C &v)
 {
-    const C a0 = a, b0 = b;
-    a.x = fma(u, a0.x, b0.y);
-    a.y = fma(u, a0.y, -b0.x);
-    b.x = fma(u, b0.x, a0.y);
-    b.y = fma(u, b0.y, -a0.x);
+    if constexpr (std::is_same<C, float2>::value) {
+        acc = __ffma2_rn(u, v, acc);
+    } else {
+        acc.x = fma(u.x, v.x, acc.x);
+        acc.y = fma(u.y, v.y, acc.y);
+    }
 }
 
 // Im(conj(l) f)
@@ -479,8 +495,7 @@ struct StageCtx {
     uint64_t fixed;
     int s, cb, tid;  // high qubit s and contiguous bits cb of this pass's tiles
     bool first;
-    bool use_cot;  // which butterfly form (|sin beta| > |cos beta|)
-    R tq;          // tan beta or cot beta (the inverse mixer flips the sign)
+    R tq;          // t of the rotation: tan beta, or -cot beta when |sin| > |cos|
     R f;           // factor dropped by one butterfly: cos beta or sin beta
     R fn, fn2;     // f^n and f^(2n): one whole layer of butterflies
     R scale0;      // f^j0: butterflies of this layer applied by earlier passes
@@ -586,10 +601,14 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         base |= ((uint32_t(X.tid) >> j) & 1u) << G::thr(ST, j);
     const uint32_t sb = G::swz(base);
 
-    if (ST == 0 && !A.load) {
+    if (ST == 0 && !A.load) {  // |+>^n in the twisted frame: 2^(-n/2) i^|x|
+        const int c0 = (__popcll(X.fixed) + __popc(base)) & 3;
+        const R amp = (R)A.amp0;
 #pragma unroll
-        for (int m = 0; m < NR; m++)
-            a[m] = mkc<C>((R)A.amp0, (R)0);
+        for (int m = 0; m < NR; m++) {
+            const int e = (c0 + __popc(m)) & 3;
+            a[m] = mkc<C>(e == 0 ? amp : e == 2 ? -amp : (R)0, e == 1 ? amp : e == 3 ? -amp : (R)0);
+        }
     } else {
         load_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
@@ -618,10 +637,11 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         }
     }
 
-    // Butterflies in tan/cot form, no rescaling: after j butterflies of this
+    // Rotations (twisted frame), no rescaling: after j butterflies of this
     // layer the vectors carry 1/f^j (restored by the next phase table or the
     // last pass), so an inner product taken before butterfly j+1 is scaled
-    // by f^(2j). Four independent FMA chains per inner product.
+    // by f^(2j). In the twisted frame Im<lambda|X_q|phi> sums, over the pairs
+    // (x, x'), Re(conj(lambda_x') phi_x) - Re(conj(lambda_x) phi_x').
     R gb = 0, sc = X.run;
 #pragma unroll
     for (int k = 0; k < RB; k++) {
@@ -634,42 +654,25 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
             due = A.is_low;
         if (!due)
             continue;
-        R ip[4] = {0, 0, 0, 0};
-        if (X.use_cot) {
+        C ipp[2], ipn[2];
+        ipp[0] = ipp[1] = ipn[0] = ipn[1] = mkc<C>((R)0, (R)0);
 #pragma unroll
-            for (int m = 0; m < NR; m++) {
-                if (m & (1 << k))
-                    continue;
-                const int m1 = m | (1 << k);
-                if constexpr (NV == 2) {
-                    R &q = ip[(m >> (k == 0 ? 1 : 0)) & 3];
-                    q = fma(l[m].x, a[m1].y, q);
-                    q = fma(-l[m].y, a[m1].x, q);
-                    q = fma(l[m1].x, a[m].y, q);
-                    q = fma(-l[m1].y, a[m].x, q);
-                    bfly_cot(l[m], l[m1], X.tq);
-                }
-                bfly_cot(a[m], a[m1], X.tq);
+        for (int m = 0; m < NR; m++) {
+            if (m & (1 << k))
+                continue;
+            const int m1 = m | (1 << k);
+            if constexpr (NV == 2) {
+                const int c = (m >> (k == 0 ? 1 : 0)) & 1;
+                dot_acc(ipp[c], l[m1], a[m]);
+                dot_acc(ipn[c], l[m], a[m1]);
+                rot(l[m], l[m1], X.tq);
             }
-        } else {
-#pragma unroll
-            for (int m = 0; m < NR; m++) {
-                if (m & (1 << k))
-                    continue;
-                const int m1 = m | (1 << k);
-                if constexpr (NV == 2) {
-                    R &q = ip[(m >> (k == 0 ? 1 : 0)) & 3];
-                    q = fma(l[m].x, a[m1].y, q);
-                    q = fma(-l[m].y, a[m1].x, q);
-                    q = fma(l[m1].x, a[m].y, q);
-                    q = fma(-l[m1].y, a[m].x, q);
-                    bfly_tan(l[m], l[m1], X.tq);
-                }
-                bfly_tan(a[m], a[m1], X.tq);
-            }
+            rot(a[m], a[m1], X.tq);
         }
-        if constexpr (NV == 2)
-            gb = fma((ip[0] + ip[1]) + (ip[2] + ip[3]), sc * sc, gb);
+        if constexpr (NV == 2) {
+            const R q = ((ipp[0].x + ipp[0].y) + (ipp[1].x + ipp[1].y)) - ((ipn[0].x + ipn[0].y) + (ipn[1].x + ipn[1].y));
+            gb = fma(q, sc * sc, gb);
+        }
         sc *= X.f;
     }
     X.run = sc;
@@ -749,6 +752,23 @@ template <int NTHR>
 __device__ __forceinline__ void compute_sync()
 {
     asm volatile("bar.sync 1, %0;" ::"n"(NTHR) : "memory");
+}
+
+// Barrier over the compute threads that also returns, to every thread, the OR
+// of a per-thread flag: a decision all threads take alike.
+template <int NTHR>
+__device__ __forceinline__ bool compute_sync_or(bool flag)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred ip, op;\n\t"
+        "setp.ne.u32 ip, %1, 0;\n\t"
+        "barrier.cta.red.or.pred op, 1, %2, ip;\n\t"
+        "selp.u32 %0, 1, 0, op;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)flag), "n"(NTHR)
+        : "memory");
+    return r != 0;
 }
 
 // (a, b) summed over the NTHR compute threads; valid in thread 0.
@@ -1142,7 +1162,9 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             tile_coords(k, b, t, mid, c4);
             const int s = (int)(k % NS);
             unsigned char *buf = sm + (size_t)s * NV * TB;
+            bool sync_now = (k == 0);  // launch constants (qr) and the table need a barrier
             if ((int)b != cur_b) {  // new parameter point: its phase table and mixer angle
+                sync_now = true;
                 if (cur_b >= 0 && reduce)
                     stash(cur_b);
                 tslot ^= 1;
@@ -1155,9 +1177,9 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 }
                 const double2 csd = A.cs[(size_t)b * A.p + A.layer];
                 const double cbv = csd.x, sbv = A.sign_s * csd.y;
-                X.use_cot = fabs(sbv) > fabs(cbv);
-                X.tq = X.use_cot ? (R)(cbv / sbv) : (R)(sbv / cbv);
-                const double f = X.use_cot ? sbv : cbv;
+                const bool shifted = fabs(sbv) > fabs(cbv);  // rotate by beta - pi/2
+                X.tq = shifted ? (R)(-cbv / sbv) : (R)(sbv / cbv);
+                const double f = shifted ? sbv : cbv;
                 double fj = 1.0, fn = 1.0;
                 for (int i = 0; i < A.n; i++) {
                     if (i < A.j0)
@@ -1175,28 +1197,41 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             X.tc = &tcs[s][0][0];
             X.fixed = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
 
-            if (!mbar_wait_bounded(&full[s], (k / NS) & 1u))
-                atomicOr(&s_flag, 1);
-            compute_sync<NTHR>();
-            write_pending();
-            if (s_flag) {  // a tile never arrived
-                if (tid == 0)
-                    atomicExch(A.err, 1);
-                ok = false;
-                break;
+            // No barrier between tiles unless a point starts: a warp may begin
+            // this tile while others still store the previous one. The first
+            // barrier inside the tile decides a missed tile for all threads
+            // alike (stage work on an unfilled buffer only reads garbage).
+            const bool late = !mbar_wait_bounded(&full[s], (k / NS) & 1u);
+            if (sync_now) {
+                compute_sync<NTHR>();
+                write_pending();
             }
 
             C a[NR], l[NR];
             X.first = true;
             X.run = X.scale0;
+            bool bad;
             if (P.is_low) {
                 run_stage<R, NV, 0, OPS>(P, X, a, l, acc0, acc1);
                 X.first = false;
-                compute_sync<NTHR>();
+                bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
+                if (!bad) {
+                    run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1);
+                    compute_sync<NTHR>();
+                }
+            } else {
+                run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1);
+                X.first = false;
+                bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
             }
-            run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1);
-            X.first = false;
-            compute_sync<NTHR>();
+            if (bad) {  // a tile never arrived, or the producer gave up
+                if (tid == 0) {
+                    atomicExch(A.err, 1);
+                    s_flag = 1;
+                }
+                ok = false;
+                break;
+            }
             run_stage<R, NV, 2, OPS>(P, X, a, l, acc0, acc1);
             // results (if any) are in the buffer: hand it to the producer
             fence_proxy_async_smem();
@@ -1768,6 +1803,50 @@ int launch_small(bool c128, const SmallArgs &a, int B, cudaStream_t st)
             return (int)e;
         k_small<float><<<B, 256, smem, st>>>(a);
     }
+    return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------ exported statevector
+// The passes leave psi~(x) = i^|x| psi'(x) where psi' is the state of the
+// circuit with every mixer layer l whose |sin beta_l| > |cos beta_l| rotated
+// by beta_l - pi/2 instead of beta_l. With K such layers
+//   psi = (-i)^(n K) (X^n)^K psi',
+// so psi(x) = (-i)^(nK) i^(-|y|) psi~(y), y = x with all bits flipped when K
+// is odd, else y = x. In place; for odd K each thread handles a pair (x, ~x).
+template <typename R>
+__global__ void k_untwist(typename CT<R>::T *psi, int n, const double2 *cs, int p)
+{
+    using C = typename CT<R>::T;
+    int K = 0;
+    for (int l = 0; l < p; l++)
+        K += fabs(cs[l].y) > fabs(cs[l].x) ? 1 : 0;
+    const int ph = (4 - ((n * K) & 3)) & 3;  // (-i)^(nK) = i^ph
+    auto turn = [](C v, int e) -> C {          // v * i^e
+        e &= 3;
+        return e == 0 ? v : e == 1 ? mkc<C>(-v.y, v.x) : e == 2 ? mkc<C>(-v.x, -v.y) : mkc<C>(v.y, -v.x);
+    };
+    const uint64_t N = 1ull << n, full = N - 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (K & 1) {
+        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N / 2; x += stride) {
+            const uint64_t y = x ^ full;
+            const C vx = psi[x], vy = psi[y];
+            psi[x] = turn(vy, ph - __popcll(y));
+            psi[y] = turn(vx, ph - __popcll(x));
+        }
+    } else {
+        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += stride)
+            psi[x] = turn(psi[x], ph - __popcll(x));
+    }
+}
+
+int launch_untwist(bool c128, void *psi, int n, const double2 *cs, int p, cudaStream_t st)
+{
+    const int grid = 4 * device_sms();
+    if (c128)
+        k_untwist<double><<<grid, 256, 0, st>>>((double2 *)psi, n, cs, p);
+    else
+        k_untwist<float><<<grid, 256, 0, st>>>((float2 *)psi, n, cs, p);
     return (int)cudaGetLastError();
 }
 
