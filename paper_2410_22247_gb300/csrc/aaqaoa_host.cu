@@ -84,6 +84,8 @@ struct Pass {
     int is_low;  // contiguous tile whose low qubits are transformed
     int hmask;   // high local bits that receive a butterfly
     int wide;    // tensor-map form (rows of more than 128 bytes)
+    int skip_last = 0;  // low pass done after register stage 1
+    int qubits = 0;     // butterflies of this pass
 };
 
 struct Layout {
@@ -256,21 +258,40 @@ int make_map(CUtensorMap *map, void *base, int n, int s, int cb, int T, int cbmi
 }
 
 // Passes of one layer for tiles of T qubits: a low pass over qubits
-// 0..T-1 (contiguous tiles), then K = ceil((n-T)/hbmax) high passes that
-// share the remaining n-T qubits evenly. A high pass with h < hbmax row qubits
+// 0..L-1 (contiguous tiles), then K = ceil((n-T)/hbmax) high passes that
+// share the remaining n-L qubits evenly. A high pass with h < hbmax row qubits
 // spends the spare tile bits on longer contiguous rows (cb = T-h), which keeps
-// the strided passes close to streaming bandwidth.
-std::vector<Pass> make_passes(int n, int T, int cbmin, int hbmax)
+// the strided passes close to streaming bandwidth. L is T unless the K high
+// passes can take all but the L2 qubits of the low pass's first two register
+// stages; then L = L2 and the low pass skips its third stage.
+std::vector<Pass> make_passes(int n, int T, int cbmin, int hbmax, int L2)
 {
     std::vector<Pass> v;
     if (n <= T)
         return v;
-    v.push_back({cbmin, cbmin, 1, (1 << (T - cbmin)) - 1, 0});
-    const int r = n - T, K = (r + hbmax - 1) / hbmax;
-    int s = T;
+    const int K = (n - T + hbmax - 1) / hbmax;
+    int L = T;
+    if (L2 >= cbmin && L2 < T && n - L2 <= K * hbmax) {
+        bool fits = true;  // every high pass keeps its contiguous bits below its rows
+        for (int k = 0; k < K; k++) {
+            const int h = (n - L2) / K + (k < (n - L2) % K ? 1 : 0);
+            if (h < 1 || T - h > L2 || h > hbmax)
+                fits = false;
+        }
+        if (fits)
+            L = L2;
+    }
+    Pass low{cbmin, cbmin, 1, (1 << (L - cbmin)) - 1, 0};
+    low.skip_last = L < T ? 1 : 0;
+    low.qubits = L;
+    v.push_back(low);
+    const int r = n - L;
+    int s = L;
     for (int k = 0; k < K; k++) {
         const int h = r / K + (k < r % K ? 1 : 0);
-        v.push_back({s, T - h, 0, (1 << h) - 1, 0});
+        Pass hp{s, T - h, 0, (1 << h) - 1, 0};
+        hp.qubits = h;
+        v.push_back(hp);
         s += h;
     }
     return v;
@@ -280,9 +301,9 @@ void build_passes(aaqaoa_plan *pl)
 {
     int T, CB, HB;
     pass_geometry(pl->c128, 1, &T, &CB, &HB);
-    pl->passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB);
+    pl->passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB, low_two_stage_bits(pl->c128, 1));
     pass_geometry(pl->c128, 2, &T, &CB, &HB);
-    pl->bwd_passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB);
+    pl->bwd_passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB, low_two_stage_bits(pl->c128, 2));
 }
 
 // table `kind` (0 exact, 1 forward-scaled, 2 inverse) of a call with B points
@@ -333,6 +354,7 @@ int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
             a.wide_rows = ps.wide;
             a.is_low = ps.is_low;
             a.hmask = ps.hmask;
+            a.skip_last = ps.skip_last;
             a.layer = l;
             a.sign_s = 1.0;
             a.tab = tab_kind(pl, pl->d_tab(), B, 1);
@@ -371,11 +393,14 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
     const int chunk = B > 1 ? (int)(((long long)tiles * B + grid - 1) / grid) : 0;
     const int np = (int)pl->bwd_passes.size();
     bool first = true;
+    // Each layer runs its passes low pass first, so the cut-function work at
+    // the layer's end (dE/dgamma, inverse phase) falls in a high pass and the
+    // low pass can stop after two register stages.
     for (int l = pl->p - 1; l >= 0; l--) {
         int j0 = 0;  // qubits of this layer's inverse mixer done by earlier passes
-        for (int kk = np - 1; kk >= 0; kk--) {
+        for (int kk = 0; kk < np; kk++) {
             const Pass &ps = pl->bwd_passes[kk];
-            const bool last_of_layer = (kk == 0);
+            const bool last_of_layer = (kk == np - 1);
             PassArgs a = base_args(pl, obs);
             a.B = B;
             a.chunk = chunk;
@@ -385,11 +410,12 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
             a.wide_rows = ps.wide;
             a.is_low = ps.is_low;
             a.hmask = ps.hmask;
+            a.skip_last = ps.skip_last;
             a.layer = l;
             a.sign_s = -1.0;
             a.tab = tab_kind(pl, pl->d_tab(), B, 2);
             a.j0 = j0;
-            j0 += ps.is_low ? T : __builtin_popcount((unsigned)ps.hmask);
+            j0 += ps.qubits;
             a.load = 1;
             a.pre_phase = 0;
             a.pre_lambda = first ? 1 : 0;
@@ -1216,6 +1242,7 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
                 a.wide_rows = wide[k];
                 a.is_low = ps.is_low;
                 a.hmask = ps.hmask;
+                a.skip_last = ps.skip_last;
                 a.tiles = pl->tiles();
                 a.B = 1;
                 a.load = !(l == 0 && k == 0);

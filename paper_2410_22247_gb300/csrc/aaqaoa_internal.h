@@ -44,6 +44,7 @@ struct PassArgs {
     int tiles;        // tiles per statevector = 2^(n - tile bits)
     int B;            // statevectors (parameter points) in this launch
     int chunk;        // 0: CTAs interleave tiles; else each CTA takes `chunk` consecutive tiles
+    int skip_last;    // low pass whose qubits all lie in register stages 0 and 1 (no third stage)
     int load;         // 1: TMA-load the tile(s); 0: generate |+>^n
     int pre_phase;    // multiply by the cost-layer phase before any butterfly
     int pre_lambda;   // adjoint: load phi only and form lambda = O(x) phi first
@@ -116,6 +117,7 @@ struct AggArgs {
 // Launchers (aaqaoa_kernels.cu). They return a cudaError_t as int.
 int tile_bits(bool c128);
 void pass_geometry(bool c128, int nv, int *T, int *CB, int *HB);
+int low_two_stage_bits(bool c128, int nv);
 int device_sms();
 int pass_grid(long long total_tiles);
 int launch_params(bool c128, int B, int p, int tab_len, int n, const double *d_gamma, const double *d_beta,

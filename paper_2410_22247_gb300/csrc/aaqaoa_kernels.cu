@@ -480,7 +480,7 @@ __device__ __forceinline__ void store_regs(typename CT<R>::T *sv, uint32_t sb,
 // The pass's scalar controls, copied from the parameter space into registers
 // once per CTA.
 struct PassRegs {
-    int n, s, is_low, hmask, load, pre_phase, pre_lambda, write, post, j0;
+    int n, s, is_low, hmask, load, pre_phase, pre_lambda, write, post, j0, skip_last;
     double amp0;
 };
 
@@ -602,13 +602,19 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     const uint32_t sb = G::swz(base);
 
     if (ST == 0 && !A.load) {  // |+>^n in the twisted frame: 2^(-n/2) i^|x|
+        // the four values amp * i^((c0 + j) & 3) once, then a compile-time
+        // choice by the register index's own bit count
         const int c0 = (__popcll(X.fixed) + __popc(base)) & 3;
         const R amp = (R)A.amp0;
+        C zc[4];
 #pragma unroll
-        for (int m = 0; m < NR; m++) {
-            const int e = (c0 + __popc(m)) & 3;
-            a[m] = mkc<C>(e == 0 ? amp : e == 2 ? -amp : (R)0, e == 1 ? amp : e == 3 ? -amp : (R)0);
+        for (int j = 0; j < 4; j++) {
+            const int e = (c0 + j) & 3;
+            zc[j] = mkc<C>(e == 0 ? amp : e == 2 ? -amp : (R)0, e == 1 ? amp : e == 3 ? -amp : (R)0);
         }
+#pragma unroll
+        for (int m = 0; m < NR; m++)
+            a[m] = zc[__popc(m) & 3];
     } else {
         load_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
@@ -1106,7 +1112,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         }
     } else {
         // ------------------------------------------------------- compute
-        const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.j0, A.amp0};
+        const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.j0,
+                         A.skip_last, A.amp0};
         double acc0 = 0.0, acc1 = 0.0;
         int cur_b = -1;
         StageCtx<R> X;
@@ -1217,7 +1224,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
                 if (!bad) {
                     run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1);
-                    compute_sync<NTHR>();
+                    if (!P.skip_last)
+                        compute_sync<NTHR>();
                 }
             } else {
                 run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1);
@@ -1232,7 +1240,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 ok = false;
                 break;
             }
-            run_stage<R, NV, 2, OPS>(P, X, a, l, acc0, acc1);
+            if (!P.skip_last)  // a low pass over the qubits of stages 0 and 1 only ends here
+                run_stage<R, NV, 2, OPS>(P, X, a, l, acc0, acc1);
             // results (if any) are in the buffer: hand it to the producer
             fence_proxy_async_smem();
             mbar_arrive(&done[s]);
@@ -1692,6 +1701,29 @@ __global__ void __launch_bounds__(256) k_agg_terms(const __grid_constant__ AggAr
 
 // ------------------------------------------------------------- launchers
 int tile_bits(bool c128) { return c128 ? Geo<double, 1>::T : Geo<float, 1>::T; }
+
+// Low qubits 0..L-1 all transformed by register stages 0 and 1: a low pass
+// over at most L qubits needs no third stage.
+template <typename G>
+constexpr int two_stage_low_bits()
+{
+    uint32_t m = 0;
+    for (int st = 0; st < 2; st++)
+        for (int k = 0; k < G::RB; k++)
+            if ((G::own(st) >> k) & 1)
+                m |= 1u << G::reg(st, k);
+    int L = 0;
+    while (L < G::T && ((m >> L) & 1))
+        L++;
+    return L;
+}
+
+int low_two_stage_bits(bool c128, int nv)
+{
+    if (c128)
+        return nv == 2 ? two_stage_low_bits<Geo<double, 2>>() : two_stage_low_bits<Geo<double, 1>>();
+    return nv == 2 ? two_stage_low_bits<Geo<float, 2>>() : two_stage_low_bits<Geo<float, 1>>();
+}
 
 void pass_geometry(bool c128, int nv, int *T, int *CB, int *HB)
 {
