@@ -194,6 +194,23 @@ int aaqaoa_sync(aaqaoa_plan *plan);
 int aaqaoa_edge_zz(aaqaoa_plan *plan, const double *gamma, const double *beta, double *zz);
 
 /*
+ * aaqaoa_verify_orbits -- debug check of the orbit data behind H_red. The
+ * library cannot prove that the classes given to aaqaoa_prepare are orbits of
+ * Aut(G) (Sec. 4, Algorithm 1); by Eq. (A3) every member of a true orbit has
+ * the same <Z_u Z_v> as its representative at any angles. This call evaluates
+ * all edge terms at (gamma, beta) (host arrays of p doubles, preferably
+ * generic values) and compares each edge with the representative of its
+ * class. Equality is necessary, not sufficient: a class that passes at one
+ * angle set may still fail at another.
+ * tol: largest accepted |<ZZ>_e - <ZZ>_rep| (>= 0; about 1e-5 for C64,
+ *   1e-10 for C128). bad_orbit (host, 1 int): -1 on success, else the first
+ *   class that fails.
+ * Returns AAQAOA_ERR_BAD_ORBITS for a failing class, AAQAOA_ERR_INVALID_ARG
+ * if the plan was prepared without edge_orbit (membership unknown).
+ */
+int aaqaoa_verify_orbits(aaqaoa_plan *plan, const double *gamma, const double *beta, double tol, int *bad_orbit);
+
+/*
  * aaqaoa_statevector -- the final state psi_p itself, copied to host memory:
  * 2^n complex amplitudes in the plan's precision (interleaved re, im as float
  * for C64 or double for C128). host_out must hold 2^n * 8 (C64) or

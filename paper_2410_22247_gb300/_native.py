@@ -51,6 +51,7 @@ _PROTOS = [
     ("aaqaoa_grad_device", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     ("aaqaoa_sync", ctypes.c_int, [_vp]),
     ("aaqaoa_edge_zz", ctypes.c_int, [_vp, _f64p, _f64p, _f64p]),
+    ("aaqaoa_verify_orbits", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
     ("aaqaoa_statevector", ctypes.c_int, [_vp, _f64p, _f64p, _vp]),
     ("aaqaoa_aggregate_only", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _f64p]),
     ("aaqaoa_expect_static", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_int, _f64p]),

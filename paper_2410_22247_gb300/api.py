@@ -108,6 +108,16 @@ class Plan:
                 "aaqaoa_edge_zz")
         return out
 
+    def verify_orbits(self, gamma, beta, tol):
+        """Check that every edge has its class representative's <ZZ> at
+        (gamma, beta) (Eq. A3); returns -1, or raises AAQAOAError with code
+        AAQAOA_ERR_BAD_ORBITS naming the first failing class."""
+        g, b = _f64(gamma), _f64(beta)
+        bad = ctypes.c_int(-1)
+        N.check(N.aaqaoa_verify_orbits(self.handle, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                       float(tol), ctypes.byref(bad)), "aaqaoa_verify_orbits")
+        return bad.value
+
     def statevector(self, gamma, beta):
         g, b = _f64(gamma), _f64(beta)
         dt = np.complex128 if self.precision == "c128" else np.complex64

@@ -100,6 +100,7 @@ struct aaqaoa_plan {
     bool c128 = false;
     std::vector<int32_t> edges;  // normalised (u < v), caller's edge order
     std::vector<int32_t> orbit_rep, orbit_weight;
+    std::vector<int32_t> edge_orbit;  // class of every edge (empty when the caller gave none)
     CostFn cost{};
     CutFn obs[2]{};
     cudaStream_t stream = nullptr;
@@ -737,6 +738,8 @@ int aaqaoa_prepare(int n, int num_edges, const int32_t *edges, int num_orbits, c
     pl->edges = e;
     pl->orbit_rep.assign(orbit_rep, orbit_rep + num_orbits);
     pl->orbit_weight.assign(orbit_weight, orbit_weight + num_orbits);
+    if (edge_orbit)
+        pl->edge_orbit.assign(edge_orbit, edge_orbit + num_edges);
     pl->stream = (cudaStream_t)stream;
     for (int u = 0; u < n; u++)
         pl->cost.nbr[u] = adj[u];
@@ -1007,6 +1010,32 @@ int aaqaoa_edge_zz(aaqaoa_plan *pl, const double *gamma, const double *beta, dou
         return r;
     if (pl->m > 0)
         CK(cudaMemcpy(zz, pl->d_zz(), pl->m * sizeof(double), cudaMemcpyDeviceToHost));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_verify_orbits(aaqaoa_plan *pl, const double *gamma, const double *beta, double tol, int *bad_orbit)
+{
+    g_detail.clear();
+    if (!pl || !bad_orbit)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan or bad_orbit is NULL");
+    *bad_orbit = -1;
+    if (pl->num_orbits == 0 || pl->edge_orbit.empty())
+        return fail(AAQAOA_ERR_INVALID_ARG, "the plan was prepared without edge_orbit: class membership unknown");
+    if (!(tol >= 0.0))
+        return fail(AAQAOA_ERR_INVALID_ARG, "tolerance %g is not >= 0", tol);
+    std::vector<double> zz((size_t)pl->m);
+    int r = aaqaoa_edge_zz(pl, gamma, beta, zz.data());
+    if (r)
+        return r;
+    for (int e = 0; e < pl->m; e++) {
+        const int c = pl->edge_orbit[e], rep = pl->orbit_rep[c];
+        const double d = std::fabs(zz[e] - zz[rep]);
+        if (d > tol) {
+            *bad_orbit = c;
+            return fail(AAQAOA_ERR_BAD_ORBITS, "edge %d differs from the representative %d of orbit %d by %.3g in <ZZ>",
+                        e, rep, c, d);
+        }
+    }
     return AAQAOA_OK;
 }
 

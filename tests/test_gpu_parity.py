@@ -212,6 +212,31 @@ def test_errors_reported_not_raised_on_device():
         pl.aggregate_only("full", "singlepass")
 
 
+def test_verify_orbits_accepts_orbits_and_rejects_a_merged_class():
+    """Eq. (A3): members of one Aut(G) orbit share <ZZ>. The finder's orbits
+    pass at generic angles (small and tiled plans); a class that merges the
+    end edges of a path with its middle edge is rejected."""
+    from paper_2410_22247_gb300._native import AAQAOAError
+    from paper_2410_22247_gb300.api import Plan
+    g, b = W.random_angles(2, 5)
+    for n, e in (W.heap_binary_tree(15), W.star_graph(16), W.balanced_tree(3, 2)):
+        for prec, tol in (("c128", 1e-10), ("c64", 1e-5)):
+            pl, orb = plan_for(n, e, 2, prec, grad=False)
+            assert orb.num_orbits < len(e)
+            assert pl.verify_orbits(g, b, tol) == -1
+    e = np.array([[0, 1], [1, 2], [2, 3]], dtype=np.int32)
+    bad = Plan(4, e, 1, orbits=(np.array([0]), np.array([3]), np.array([0, 0, 0])), precision="c128",
+               with_grad=False)
+    with pytest.raises(AAQAOAError, match="BAD_ORBITS"):
+        bad.verify_orbits([0.7], [0.3], 1e-10)
+    ok = Plan(4, e, 1, orbits=(np.array([0, 1]), np.array([2, 1]), np.array([0, 1, 0])), precision="c128",
+              with_grad=False)
+    assert ok.verify_orbits([0.7], [0.3], 1e-10) == -1
+    no_members = Plan(4, e, 1, orbits=(np.array([0, 1]), np.array([2, 1])), precision="c128", with_grad=False)
+    with pytest.raises(AAQAOAError, match="INVALID_ARG"):
+        no_members.verify_orbits([0.7], [0.3], 1e-10)
+
+
 def test_autograd_function_matches_grad():
     torch = pytest.importorskip("torch")
     from paper_2410_22247_gb300.api import energy
