@@ -211,6 +211,31 @@ int aaqaoa_edge_zz(aaqaoa_plan *plan, const double *gamma, const double *beta, d
 int aaqaoa_verify_orbits(aaqaoa_plan *plan, const double *gamma, const double *beta, double tol, int *bad_orbit);
 
 /*
+ * aaqaoa_max_cut -- C_max = max over all 2^n basis states of the cut count
+ * C(x), the denominator of the approximation ratio F_p / C_max (Sec. 2), by
+ * exhaustion on the device: no statevector is read (the workspace is only
+ * needed for an 8-byte result). c_max (host, 1 int32); argmax (host, 1
+ * uint64): the smallest x that attains it (bit i = vertex i on side 1).
+ * Synchronises the plan's stream.
+ */
+int aaqaoa_max_cut(aaqaoa_plan *plan, int32_t *c_max, uint64_t *argmax);
+
+/*
+ * aaqaoa_sample -- K bitstrings drawn from the final-state distribution
+ * |psi_p(x)|^2 (the measurement the paper's pipeline ends with, Sec. 5.4).
+ * The uniform numbers are the caller's: u (host, K doubles in [0, 1)); sample
+ * k is the smallest x whose cumulative probability sum_{y <= x} |psi_y|^2,
+ * taken in index order and in FP64, exceeds u_k times the total. x_out (host,
+ * K uint64); cut_out (host, K int32, or NULL): C(x) of each sample.
+ * 1 <= K <= AAQAOA_SAMPLE_MAX per call. The state is left in the workspace
+ * (aaqaoa_aggregate_only may follow). Errors: INVALID_ARG for K or u out of
+ * range.
+ */
+#define AAQAOA_SAMPLE_MAX 65536
+int aaqaoa_sample(aaqaoa_plan *plan, const double *gamma, const double *beta, int K, const double *u,
+                  uint64_t *x_out, int32_t *cut_out);
+
+/*
  * aaqaoa_statevector -- the final state psi_p itself, copied to host memory:
  * 2^n complex amplitudes in the plan's precision (interleaved re, im as float
  * for C64 or double for C128). host_out must hold 2^n * 8 (C64) or

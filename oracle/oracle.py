@@ -63,6 +63,10 @@ def load_library(path):
     lib.oracle_energy_grad.restype = ctypes.c_double
     lib.oracle_energy_grad.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, f64p, f64p,
                                        ctypes.c_int, i32p, f64p, f64p, f64p, c128p, c128p]
+    lib.oracle_max_cut.restype = ctypes.c_int64
+    lib.oracle_max_cut.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_uint64)]
+    lib.oracle_sample.restype = ctypes.c_int
+    lib.oracle_sample.argtypes = [ctypes.c_int, c128p, ctypes.c_int, f64p, ctypes.POINTER(ctypes.c_uint64)]
     return lib
 
 
@@ -185,3 +189,23 @@ def finite_difference_grad(n, edges, gamma, beta, obs=None, h=1e-6):
             vec[i] = old
             out[i] = (ep - em) / (2 * h)
     return dg, db
+
+
+def max_cut(n, edges):
+    """(C_max, smallest maximising x) by exhaustion over 2^n states."""
+    e = _edges(edges)
+    arg = ctypes.c_uint64()
+    c = _load().oracle_max_cut(n, len(e), e, ctypes.byref(arg))
+    return int(c), int(arg.value)
+
+
+def sample(psi, u):
+    """Inverse-CDF samples of basis states from |psi|^2 for uniforms u in [0, 1)."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    n = int(round(np.log2(len(psi))))
+    u = _f64(u)
+    out = np.zeros(len(u), dtype=np.uint64)
+    r = _load().oracle_sample(n, psi, len(u), u, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    if r != 0:
+        raise MemoryError("oracle_sample: no memory for the cumulative sums")
+    return out

@@ -192,3 +192,53 @@ double oracle_energy_grad(int n, int m, const int32_t *edges, int p,
     }
     return energy;
 }
+
+/* Maximum cut C_max = max_x C(x) by exhaustion over all 2^n basis states, and
+ * the smallest x attaining it: the denominator of the approximation ratio
+ * F_p / C_max (Sec. 2). */
+int64_t oracle_max_cut(int n, int m, const int32_t *edges, uint64_t *argmax)
+{
+    int64_t best = -1;
+    uint64_t arg = 0;
+    for (uint64_t x = 0; x < ((uint64_t)1 << n); x++) {
+        int64_t c = oracle_cut_value(m, edges, x);
+        if (c > best) {
+            best = c;
+            arg = x;
+        }
+    }
+    *argmax = arg;
+    return best;
+}
+
+/* Inverse-CDF sampling of basis states from |psi|^2: with the cumulative sums
+ * S(x) = sum_{y <= x} |psi_y|^2 taken in index order, u_k in [0, 1) selects
+ * the smallest x with S(x) > u_k S(2^n - 1) (the last index if none). The
+ * uniform numbers are inputs, so no generator is needed here. */
+int oracle_sample(int n, const cplx *psi, int K, const double *u, uint64_t *x_out)
+{
+    const uint64_t N = (uint64_t)1 << n;
+    double *cdf = (double *)malloc(N * sizeof(double));
+    if (!cdf)
+        return -1;
+    double s = 0.0;
+    for (uint64_t x = 0; x < N; x++) {
+        double a = creal(psi[x]), b = cimag(psi[x]);
+        s += a * a + b * b;
+        cdf[x] = s;
+    }
+    for (int k = 0; k < K; k++) {
+        const double t = u[k] * s;
+        uint64_t lo = 0, hi = N;  /* first x in [lo, hi) with cdf[x] > t */
+        while (lo < hi) {
+            uint64_t mid = lo + (hi - lo) / 2;
+            if (cdf[mid] > t)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        x_out[k] = lo < N ? lo : N - 1;
+    }
+    free(cdf);
+    return 0;
+}

@@ -87,3 +87,20 @@ def energy_grad(model, gamma, beta):
 
 def energy(model, gamma, beta):
     return energy_grad(model, gamma, beta)[0]
+
+
+def cut_distribution(model, gamma, beta):
+    """{cut value: probability} of the final state, FP64. In the symmetric
+    basis each component is one normalised Dicke state (times a centre bit for
+    the star) whose basis states all share one cut value, so its probability
+    is |component|^2."""
+    c0, cost, hm = model
+    ex = _Expm(hm)
+    phi = c0.copy()
+    for l in range(len(np.atleast_1d(gamma))):
+        phi = np.exp(-1j * np.atleast_1d(gamma)[l] * cost) * phi
+        phi = ex(np.atleast_1d(beta)[l], phi)
+    out = {}
+    for c, a in zip(cost.astype(int), np.abs(phi) ** 2):
+        out[int(c)] = out.get(int(c), 0.0) + float(a)
+    return out

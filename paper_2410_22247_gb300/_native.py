@@ -52,6 +52,8 @@ _PROTOS = [
     ("aaqaoa_sync", ctypes.c_int, [_vp]),
     ("aaqaoa_edge_zz", ctypes.c_int, [_vp, _f64p, _f64p, _f64p]),
     ("aaqaoa_verify_orbits", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    ("aaqaoa_max_cut", ctypes.c_int, [_vp, _i32p, ctypes.POINTER(ctypes.c_uint64)]),
+    ("aaqaoa_sample", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_int, _f64p, ctypes.POINTER(ctypes.c_uint64), _i32p]),
     ("aaqaoa_statevector", ctypes.c_int, [_vp, _f64p, _f64p, _vp]),
     ("aaqaoa_aggregate_only", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _f64p]),
     ("aaqaoa_expect_static", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_int, _f64p]),

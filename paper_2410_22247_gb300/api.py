@@ -118,6 +118,30 @@ class Plan:
                                        float(tol), ctypes.byref(bad)), "aaqaoa_verify_orbits")
         return bad.value
 
+    def max_cut(self):
+        """(C_max, smallest maximising bitstring) by device exhaustion."""
+        c = np.zeros(1, dtype=np.int32)
+        x = ctypes.c_uint64()
+        N.check(N.aaqaoa_max_cut(self.handle, _ptr(c, ctypes.c_int32), ctypes.byref(x)), "aaqaoa_max_cut")
+        return int(c[0]), int(x.value)
+
+    def approximation_ratio(self, gamma, beta, observable="red"):
+        """F_p / C_max (Sec. 2) with F_p from the given observable."""
+        cmax, _ = self.max_cut()
+        return self.expect(gamma, beta, observable) / cmax
+
+    def sample(self, gamma, beta, u):
+        """Bitstrings drawn from |psi_p|^2 for the caller's uniforms u in [0, 1),
+        with their cut values: (x uint64 array, C(x) int32 array)."""
+        g, b = _f64(gamma), _f64(beta)
+        u = _f64(u)
+        x = np.zeros(len(u), dtype=np.uint64)
+        cut = np.zeros(len(u), dtype=np.int32)
+        N.check(N.aaqaoa_sample(self.handle, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double), len(u),
+                                _ptr(u, ctypes.c_double), x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                _ptr(cut, ctypes.c_int32)), "aaqaoa_sample")
+        return x, cut
+
     def statevector(self, gamma, beta):
         g, b = _f64(gamma), _f64(beta)
         dt = np.complex128 if self.precision == "c128" else np.complex64
@@ -270,3 +294,26 @@ def energy(gamma, beta, plan, observable="full"):
     if _FN is None:
         _FN = _autograd_function()
     return _FN.apply(gamma, beta, plan, observable)
+
+
+def maximize(plan, gamma0, beta0, steps=200, lr=0.05, observable="red", betas=(0.9, 0.999), eps=1e-8):
+    """Adam ascent of F_p(gamma, beta) driven by the adjoint gradient
+    (aaqaoa_grad). Returns (gamma, beta, history of F_p). The paper optimises
+    with gradient-free COBYLA (Sec. 6); this is the gradient-based form of the
+    same outer loop."""
+    g = np.array(gamma0, dtype=np.float64)
+    b = np.array(beta0, dtype=np.float64)
+    x = np.concatenate([g, b])
+    m = np.zeros_like(x)
+    v = np.zeros_like(x)
+    hist = []
+    for t in range(1, steps + 1):
+        E, dg, db = plan.grad(x[:plan.p], x[plan.p:], observable)
+        hist.append(E)
+        d = np.concatenate([dg, db])
+        m = betas[0] * m + (1 - betas[0]) * d
+        v = betas[1] * v + (1 - betas[1]) * d * d
+        mh = m / (1 - betas[0] ** t)
+        vh = v / (1 - betas[1] ** t)
+        x = x + lr * mh / (np.sqrt(vh) + eps)
+    return x[:plan.p], x[plan.p:], np.array(hist)

@@ -89,7 +89,7 @@ struct Pass {
 };
 
 struct Layout {
-    size_t ctrl, out, params, cs, tab, partials, zz, phi, lam, total;
+    size_t ctrl, out, params, cs, tab, partials, zz, samp, phi, lam, total;
     size_t partial_count;
 };
 
@@ -145,6 +145,13 @@ struct aaqaoa_plan {
     void *d_tab() const { return ws + L.tab; }
     double *d_partials() const { return reinterpret_cast<double *>(ws + L.partials); }
     double *d_zz() const { return reinterpret_cast<double *>(ws + L.zz); }
+    // sampling scratch: chunk masses | total | u[SMAX] | x[SMAX] | cut[SMAX]
+    double *d_samp_sums() const { return reinterpret_cast<double *>(ws + L.samp); }
+    double *d_samp_total() const { return d_samp_sums() + sample_chunk_count(n); }
+    double *d_samp_u() const { return d_samp_total() + 32; }
+    unsigned long long *d_samp_x() const { return reinterpret_cast<unsigned long long *>(d_samp_u() + AAQAOA_SAMPLE_MAX); }
+    int *d_samp_cut() const { return reinterpret_cast<int *>(d_samp_x() + AAQAOA_SAMPLE_MAX); }
+    unsigned long long *d_maxcut_key() const { return reinterpret_cast<unsigned long long *>(ws + L.ctrl + 32); }
     void *d_phi() const { return ws + L.phi; }
     void *d_lam() const { return ws + L.lam; }
 };
@@ -210,6 +217,9 @@ Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
     off = align256(off + L.partial_count * sizeof(double));
     L.zz = off;
     off = align256(off + (size_t)(pl->m > 0 ? pl->m : 1) * sizeof(double));
+    L.samp = off;
+    off = align256(off + (sample_chunk_count(pl->n) + 32 + 2 * (size_t)AAQAOA_SAMPLE_MAX) * sizeof(double) +
+                   (size_t)AAQAOA_SAMPLE_MAX * sizeof(int));
     L.phi = off;
     off = align256(off + B * ((size_t)1 << pl->n) * pl->amp());
     L.lam = off;
@@ -1036,6 +1046,66 @@ int aaqaoa_verify_orbits(aaqaoa_plan *pl, const double *gamma, const double *bet
                         e, rep, c, d);
         }
     }
+    return AAQAOA_OK;
+}
+
+int aaqaoa_max_cut(aaqaoa_plan *pl, int32_t *c_max, uint64_t *argmax)
+{
+    g_detail.clear();
+    if (!pl || !c_max || !argmax)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan, c_max or argmax is NULL");
+    if (!pl->ws)
+        return fail(AAQAOA_ERR_WORKSPACE, "no workspace set (aaqaoa_set_workspace)");
+    (void)cudaGetLastError();
+    CK(cudaMemsetAsync(pl->d_maxcut_key(), 0, sizeof(unsigned long long), pl->stream));
+    CKL(launch_maxcut(pl->cost, pl->n, pl->d_maxcut_key(), pl->stream), "maximum cut");
+    unsigned long long key = 0;
+    CK(cudaMemcpyAsync(&key, pl->d_maxcut_key(), sizeof key, cudaMemcpyDeviceToHost, pl->stream));
+    CK(cudaStreamSynchronize(pl->stream));
+    const unsigned long long low = (1ull << 35) - 1ull;
+    *c_max = (int32_t)(key >> 35);
+    *argmax = (uint64_t)(low - (key & low));
+    return AAQAOA_OK;
+}
+
+int aaqaoa_sample(aaqaoa_plan *pl, const double *gamma, const double *beta, int K, const double *u,
+                  uint64_t *x_out, int32_t *cut_out)
+{
+    g_detail.clear();
+    int r = check_ready(pl, AAQAOA_OBS_FULL, false, 1);
+    if (r)
+        return r;
+    if (K < 1 || K > AAQAOA_SAMPLE_MAX)
+        return fail(AAQAOA_ERR_INVALID_ARG, "K = %d outside [1, %d]", K, AAQAOA_SAMPLE_MAX);
+    if (!u || !x_out)
+        return fail(AAQAOA_ERR_INVALID_ARG, "u or x_out is NULL");
+    for (int k = 0; k < K; k++)
+        if (!(u[k] >= 0.0 && u[k] < 1.0))
+            return fail(AAQAOA_ERR_INVALID_ARG, "u[%d] = %g is not in [0, 1)", k, u[k]);
+    pl->launches = 0;
+    if ((r = upload_params(pl, 1, gamma, beta)))
+        return r;
+    if ((r = enqueue_params(pl, 1, pl->d_params(), pl->d_params() + pl->p)))
+        return r;
+    if (pl->small()) {
+        SmallArgs s = small_args(pl, AAQAOA_OBS_FULL, SMALL_ENERGY, 1);
+        CKL(launch_small(pl->c128, s, 1, pl->stream), "whole-circuit kernel");
+        pl->launches++;
+    } else if ((r = enqueue_forward(pl, 1, AAQAOA_OBS_FULL, FWD_STATE))) {
+        return r;
+    }
+    pl->state_valid = true;
+    CK(cudaMemcpyAsync(pl->d_samp_u(), u, (size_t)K * sizeof(double), cudaMemcpyHostToDevice, pl->stream));
+    CKL(launch_sample(pl->c128, pl->d_phi(), pl->n, pl->d_samp_sums(), pl->d_samp_total(), K, pl->d_samp_u(),
+                      pl->d_samp_x(), cut_out ? pl->d_samp_cut() : nullptr, pl->cost, pl->stream),
+        "sampling");
+    pl->launches += 3;
+    std::vector<double> rows;
+    if ((r = fetch_out(pl, 1, rows)))
+        return r;
+    CK(cudaMemcpy(x_out, pl->d_samp_x(), (size_t)K * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (cut_out)
+        CK(cudaMemcpy(cut_out, pl->d_samp_cut(), (size_t)K * sizeof(int32_t), cudaMemcpyDeviceToHost));
     return AAQAOA_OK;
 }
 

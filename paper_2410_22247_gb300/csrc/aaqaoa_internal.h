@@ -132,6 +132,10 @@ int launch_agg_terms(bool c128, const AggArgs &a, cudaStream_t st, int grid);
 int agg_grid(bool c128);
 size_t small_multi_smem_bytes(bool c128, int max_n, int max_tab);
 int launch_untwist(bool c128, void *psi, int n, const double2 *cs, int p, cudaStream_t st);
+int launch_maxcut(const CostFn &cost, int n, unsigned long long *d_key, cudaStream_t st);
+size_t sample_chunk_count(int n);
+int launch_sample(bool c128, const void *psi, int n, double *d_sums, double *d_total, int K, const double *d_u,
+                  unsigned long long *d_x, int *d_cut, const CostFn &cost, cudaStream_t st);
 int launch_small_multi(bool c128, const SmallGraph *d_graphs, int G, int p, int obs, int max_n, int max_tab,
                        const double *d_gamma, const double *d_beta, double *d_energy, cudaStream_t st);
 

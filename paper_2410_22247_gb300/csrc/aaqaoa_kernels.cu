@@ -1872,6 +1872,209 @@ __global__ void k_untwist(typename CT<R>::T *psi, int n, const double2 *cs, int 
     }
 }
 
+// ------------------------------------------------------- maximum cut
+// C_max = max_x C(x) by exhaustion with no memory traffic: each thread takes
+// blocks of 32 states x0 | r (r over qubits 0..4) and evaluates them with the
+// base-plus-deltas form of eval_cost. Only x with the top bit clear are
+// visited (C(x) = C(~x), and the smallest maximiser has that bit clear). The
+// result is packed as (value << 35) | (2^35 - 1 - x), so one atomicMax keeps
+// the largest value and, among equal values, the smallest x, in any order.
+__global__ void __launch_bounds__(256) k_maxcut(const __grid_constant__ CostFn cost, int n,
+                                                unsigned long long *key)
+{
+    const int nb = n - 1;
+    auto pack = [](int v, uint64_t x) { return ((unsigned long long)v << 35) | ((1ull << 35) - 1ull - x); };
+    unsigned long long best = 0;
+    if (nb < 5) {
+        if (blockIdx.x == 0 && threadIdx.x < (1u << nb)) {
+            const uint64_t x = threadIdx.x;
+            int c = 0;
+            for (int u = 0; u < n; u++)
+                c += ((x >> u) & 1ull) ? __popcll(cost.nbr[u] & ~x) : 0;
+            best = pack(c, x);
+        }
+    } else {
+        const uint64_t blocks = 1ull << (nb - 5);
+        const int gp[5] = {0, 1, 2, 3, 4};
+        for (uint64_t blk = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; blk < blocks;
+             blk += (uint64_t)gridDim.x * blockDim.x) {
+            const uint64_t x0 = blk << 5;
+            int v[32];
+            eval_cost<5>(cost, n, x0, gp, v);
+#pragma unroll
+            for (int m = 0; m < 32; m++) {
+                const unsigned long long q = pack(v[m], x0 | (uint64_t)m);
+                best = q > best ? q : best;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long q = __shfl_xor_sync(0xffffffffu, best, o);
+        best = q > best ? q : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best)
+        atomicMax(key, best);
+}
+
+int launch_maxcut(const CostFn &cost, int n, unsigned long long *d_key, cudaStream_t st)
+{
+    k_maxcut<<<4 * device_sms(), 256, 0, st>>>(cost, n, d_key);
+    return (int)cudaGetLastError();
+}
+
+// ----------------------------------------------------------- sampling
+// Inverse-CDF sampling from |psi(x)|^2 (the twisted frame has the same
+// moduli). Chunk c holds amplitudes [c 2^SB, (c+1) 2^SB). sums[c] is the FP64
+// chunk total (fixed-order block reduction); an exclusive scan turns it into
+// the cumulative mass before the chunk; then one warp per sample finds the
+// chunk by binary search and the amplitude inside it by a lane scan. Sample k
+// is the smallest x whose cumulative mass exceeds u_k * total (the last index
+// if rounding leaves none).
+constexpr int SAMPLE_BITS = 12;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_sample_chunks(const typename CT<R>::T *psi, int n, double *sums)
+{
+    __shared__ double red[2][32];
+    const int cb = n < SAMPLE_BITS ? n : SAMPLE_BITS;
+    const uint64_t nchunks = 1ull << (n - cb), len = 1ull << cb;
+    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        double s = 0.0;
+        for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) {
+            const typename CT<R>::T a = psi[c * len + i];
+            s += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+        }
+        double z = 0.0;
+        block_sum2<256>(s, z, red);
+        if (threadIdx.x == 0)
+            sums[c] = s;
+        __syncthreads();
+    }
+}
+
+// exclusive scan of `count` doubles in place, one block of 1024 threads,
+// each thread a contiguous segment; writes the grand total to *total
+__global__ void __launch_bounds__(1024) k_sample_scan(double *v, uint64_t count, double *total)
+{
+    __shared__ double seg[1024];
+    const uint64_t per = (count + 1023) / 1024;
+    const uint64_t lo = threadIdx.x * per, hi = lo + per < count ? lo + per : count;
+    double s = 0.0;
+    for (uint64_t i = lo; i < hi; i++)
+        s += v[i];
+    seg[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double run = 0.0;
+        for (int t = 0; t < 1024; t++) {
+            const double c = seg[t];
+            seg[t] = run;
+            run += c;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    double run = seg[threadIdx.x];
+    for (uint64_t i = lo; i < hi; i++) {
+        const double c = v[i];
+        v[i] = run;
+        run += c;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_sample_draw(const typename CT<R>::T *psi, int n, const double *prefix,
+                                                     const double *total, int K, const double *u,
+                                                     unsigned long long *x_out, int *cut_out,
+                                                     const __grid_constant__ CostFn cost)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int cb = n < SAMPLE_BITS ? n : SAMPLE_BITS;
+    const uint64_t nchunks = 1ull << (n - cb), len = 1ull << cb, N = 1ull << n;
+    const uint64_t per = len >= 32 ? len / 32 : 1;  // amplitudes per lane
+    for (int k = warp; k < K; k += nwarps) {
+        const double t = u[k] * *total;
+        uint64_t lo = 0, hi = nchunks;  // last chunk with prefix <= t
+        while (hi - lo > 1) {
+            const uint64_t mid = lo + (hi - lo) / 2;
+            if (prefix[mid] <= t)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const uint64_t c = lo;
+        const double rem = t - prefix[c];
+        // lane sums, then an inclusive warp scan in lane order
+        const uint64_t base = c * len + (uint64_t)lane * per;
+        double s = 0.0;
+        if ((uint64_t)lane * per < len)
+            for (uint64_t i = 0; i < per; i++) {
+                const typename CT<R>::T a = psi[base + i];
+                s += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+            }
+        double inc = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o)
+                inc += y;
+        }
+        const unsigned over = __ballot_sync(0xffffffffu, inc > rem && (uint64_t)lane * per < len);
+        uint64_t x;
+        if (over) {
+            const int L = __ffs(over) - 1;
+            const double before = __shfl_sync(0xffffffffu, inc - s, L);
+            x = c * len + (uint64_t)L * per + per - 1;  // fallback: the lane's last amplitude
+            if (lane == L) {
+                double run = before;
+                for (uint64_t i = 0; i < per; i++) {
+                    const typename CT<R>::T a = psi[base + i];
+                    run += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+                    if (run > rem) {
+                        x = base + i;
+                        break;
+                    }
+                }
+            }
+            x = __shfl_sync(0xffffffffu, x, L);
+        } else {
+            x = c + 1 < nchunks ? (c + 1) * len - 1 : N - 1;  // rounding left the target past the chunk
+        }
+        if (lane == 0) {
+            x_out[k] = x;
+            if (cut_out) {
+                int v = 0;
+                for (int q = 0; q < n; q++)
+                    v += ((x >> q) & 1ull) ? __popcll(cost.nbr[q] & ~x) : 0;
+                cut_out[k] = v;
+            }
+        }
+    }
+}
+
+size_t sample_chunk_count(int n) { return (size_t)1 << (n < SAMPLE_BITS ? 0 : n - SAMPLE_BITS); }
+
+int launch_sample(bool c128, const void *psi, int n, double *d_sums, double *d_total, int K, const double *d_u,
+                  unsigned long long *d_x, int *d_cut, const CostFn &cost, cudaStream_t st)
+{
+    const uint64_t nchunks = sample_chunk_count(n);
+    const int g1 = (int)(nchunks < (uint64_t)(8 * device_sms()) ? nchunks : (uint64_t)(8 * device_sms()));
+    const int g3 = (K + 7) / 8 < 4 * device_sms() ? (K + 7) / 8 : 4 * device_sms();
+    if (c128)
+        k_sample_chunks<double><<<g1, 256, 0, st>>>((const double2 *)psi, n, d_sums);
+    else
+        k_sample_chunks<float><<<g1, 256, 0, st>>>((const float2 *)psi, n, d_sums);
+    k_sample_scan<<<1, 1024, 0, st>>>(d_sums, nchunks, d_total);
+    if (c128)
+        k_sample_draw<double><<<g3, 256, 0, st>>>((const double2 *)psi, n, d_sums, d_total, K, d_u, d_x, d_cut, cost);
+    else
+        k_sample_draw<float><<<g3, 256, 0, st>>>((const float2 *)psi, n, d_sums, d_total, K, d_u, d_x, d_cut, cost);
+    return (int)cudaGetLastError();
+}
+
 int launch_untwist(bool c128, void *psi, int n, const double2 *cs, int p, cudaStream_t st)
 {
     const int grid = 4 * device_sms();

@@ -1,0 +1,133 @@
+"""Beyond the evaluation itself, through the C ABI against the oracle:
+maximum cut and approximation ratio, sampling of the final state, and a
+gradient-driven optimisation loop."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import symmetric as SYM
+from oracle import closed_form as CF
+from paper_2410_22247_gb300 import workloads as W
+from paper_2410_22247_gb300 import orbits as ORB
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_22247_gb300 import _native
+    _native.load()
+
+
+def plan(n, e, p, precision="c64", grad=False):
+    from paper_2410_22247_gb300.api import Plan
+    return Plan(n, e, p, orbits=ORB.edge_orbits(n, e), precision=precision, with_grad=grad)
+
+
+@pytest.mark.parametrize("graph", ["K12", "prufer16", "reg3_18", "petersen", "cycle15", "star20", "reg3_24",
+                                   "path5", "k4"])
+def test_max_cut_matches_exhaustion(graph):
+    g = {"K12": W.complete_graph(12), "prufer16": W.prufer_tree(16, 2), "reg3_18": W.random_regular(18, 3, 1),
+         "petersen": W.generalized_petersen(5, 2), "cycle15": W.cycle_graph(15), "star20": W.star_graph(20),
+         "reg3_24": W.random_regular(24, 3, 4), "path5": (5, W.canonical_edges([(i, i + 1) for i in range(4)])),
+         "k4": W.complete_graph(4)}[graph]
+    n, e = g
+    for prec in ("c64", "c128"):
+        c, x = plan(n, e, 1, prec).max_cut()
+        assert (c, x) == O.max_cut(n, e)
+
+
+def test_max_cut_full_size_closed_forms():
+    # bipartite graphs cut every edge; the smallest maximiser is the colour
+    # class that avoids the top vertex
+    n, e = W.star_graph(30)
+    assert plan(n, e, 1).max_cut() == (29, 1)
+    n, e = W.heap_binary_tree(34)
+    depth = [int(np.floor(np.log2(v + 1))) for v in range(n)]
+    even = sum(1 << v for v in range(n) if depth[v] % 2 == 0)
+    odd = sum(1 << v for v in range(n) if depth[v] % 2 == 1)
+    assert plan(n, e, 1).max_cut() == (33, min(even, odd))
+    n, e = W.complete_graph(16)
+    c, x = plan(n, e, 1).max_cut()
+    assert c == 64 and x == 0xFF and O.cut_value(e, x) == 64
+
+
+def test_approximation_ratio_reduced_equals_full():
+    n, e = W.heap_binary_tree(20)
+    pl = plan(n, e, 2, "c128")
+    g, b = W.random_angles(2, 6)
+    r_full = pl.approximation_ratio(g, b, "full")
+    r_red = pl.approximation_ratio(g, b, "red")
+    assert abs(r_full - r_red) < 1e-12 and abs(r_full - O.energy(n, e, g, b) / len(e)) < 1e-10
+
+
+def _away_from_boundaries(cdf, u, margin):
+    d = np.min(np.abs(cdf[None, :] - u[:, None]), axis=1)
+    return u[d > margin]
+
+
+@pytest.mark.parametrize("n,family", [(10, "prufer"), (13, "reg3"), (16, "star"), (19, "prufer")])
+def test_samples_match_oracle_inverse_cdf(n, family):
+    """complex128: the same x as the oracle's inverse CDF for every uniform
+    farther than 1e-11 from a CDF step. complex64: every sample lies in its
+    uniform's CDF bracket up to 2e-6 (the FP32 state's probability error)."""
+    if family == "prufer":
+        n, e = W.prufer_tree(n, 7)
+    elif family == "reg3":
+        n, e = W.random_regular(n + (n % 2), 3, 2)
+    else:
+        n, e = W.star_graph(n)
+    g, b = W.random_angles(2, 11)
+    psi = O.qaoa_state(n, e, g, b)
+    cdf = np.cumsum(np.abs(psi) ** 2)
+    cdf = cdf / cdf[-1]
+    u_all = W.rng(5).uniform(0, 1, 2000)
+    u = _away_from_boundaries(cdf, u_all, 1e-11)
+    x, cut = plan(n, e, 2, "c128").sample(g, b, u)
+    assert len(u) > 1900 and np.array_equal(x, O.sample(psi, u))
+    assert all(cut[i] == O.cut_value(e, int(x[i])) for i in range(0, len(u), 97))
+    x, cut = plan(n, e, 2, "c64").sample(g, b, u_all)
+    xi = x.astype(np.int64)
+    lo = np.where(xi > 0, cdf[np.maximum(xi - 1, 0)], 0.0)
+    assert np.all(lo - 2e-6 <= u_all) and np.all(u_all < cdf[xi] + 2e-6)
+
+
+def test_samples_full_size_star_follow_cut_distribution():
+    # S_29 (n = 30): the cut value of each sample follows the exact FP64
+    # distribution of the symmetric-subspace model (seeded uniforms, 5 sigma)
+    n, e = W.star_graph(30)
+    g, b = W.random_angles(2, 12)
+    K = 65536
+    u = W.rng(13).uniform(0, 1, K)
+    x, cut = plan(n, e, 2).sample(g, b, u)
+    dist = SYM.cut_distribution(SYM.star_model(n), g, b)
+    counts = np.bincount(cut, minlength=30)
+    for c, pr in dist.items():
+        assert abs(counts[c] - K * pr) <= 5 * np.sqrt(K * pr * (1 - pr)) + 1
+    assert all(O.cut_value(e, int(x[i])) == cut[i] for i in range(0, K, 1031))
+    assert abs(cut.mean() - SYM.energy(SYM.star_model(n), g, b)) < 5 * cut.std() / np.sqrt(K)
+
+
+def test_sampling_rejects_bad_uniforms():
+    from paper_2410_22247_gb300._native import AAQAOAError
+    n, e = W.cycle_graph(12)
+    pl = plan(n, e, 1)
+    with pytest.raises(AAQAOAError, match="INVALID_ARG"):
+        pl.sample([0.1], [0.2], [0.5, 1.0])
+    with pytest.raises(AAQAOAError, match="INVALID_ARG"):
+        pl.sample([0.1], [0.2], [-0.1])
+
+
+def test_adam_reaches_ring_p1_optimum():
+    # p = 1 on a triangle-free 2-regular graph: F_1/|E| = 1/2 + sin(4 beta) sin(2 gamma) / 4,
+    # maximum 3/4 (closed form)
+    from paper_2410_22247_gb300.api import maximize
+    n, e = W.cycle_graph(16)
+    pl = plan(n, e, 1, "c128", grad=True)
+    gam, bet, hist = maximize(pl, [0.3], [0.2], steps=300, lr=0.03)
+    assert abs(hist[-1] / len(e) - 0.75) < 1e-4
+    assert abs(CF.energy_p1(n, e, gam[0], bet[0]) / len(e) - 0.75) < 1e-4
+    assert hist[10] > hist[0]
