@@ -211,6 +211,7 @@ def run_native(args, rank, world, local):
     stream = torch.cuda.Stream(device=dev)
     n, e, orb = graph()
     plan = Plan(n, e, P_LAYERS, orbits=orb, precision="c64", with_grad=True, stream=stream, device=dev)
+    pass_plan = plan.autotune()  # qubits per pass, timed on this GPU before the warm-up
     K, Wm = args.steps, args.warmup
     gs, bs = angle_sets(K + Wm, 1000 * (rank + 1))
     d_g = torch.tensor(gs, dtype=torch.float64, device=dev)
@@ -273,7 +274,7 @@ def run_native(args, rank, world, local):
     result = {
         "ms": ms_max, "evals_per_s": world * K / (ms_max / 1000.0), "prof": prof, "launches": launches,
         "clocks": clk.summary(), "e2e_evals_per_s": world * k_e2e / t_e2e,
-        "E0": float(res[0, 0]),
+        "E0": float(res[0, 0]), "pass_plan": pass_plan,
     }
     extra = {}
     if rank == 0 and not args.quick:
@@ -339,7 +340,47 @@ def extras(dev, stream):
             torch.cuda.empty_cache()
         out[name] = rec
     out["batch"] = batch_extras(dev, stream)
+    out["next"] = next_extras(dev, stream)
     return out
+
+
+def next_extras(dev, stream):
+    """Maximum cut by exhaustion (no memory traffic) on the 3-regular n = 30
+    control, and 65536 samples of the S_29 final state (forward pass that
+    stores the state + one read for the chunk masses + the draws)."""
+    import torch
+    from paper_2410_22247_gb300 import orbits as ORB
+    from paper_2410_22247_gb300 import workloads as W
+    from paper_2410_22247_gb300.api import Plan
+
+    res = {}
+    n, e = W.random_regular(30, 3, 0)
+    pl = Plan(n, e, 1, orbits=ORB.edge_orbits(n, e), precision="c64", with_grad=False, stream=stream, device=dev)
+    pl.max_cut()
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        c, x = pl.max_cut()
+    dt = (time.perf_counter() - t0) / reps
+    res["max_cut_regular3_n30"] = {"c_max": c, "ms_per_call": dt * 1000.0, "states_per_s": 2.0 ** 29 / dt,
+                                   "timing": "host wall clock per call incl. sync; 2^29 states (top bit fixed)"}
+    pl.close()
+    del pl
+    torch.cuda.empty_cache()
+    n, e = W.star_graph(30)
+    pl = Plan(n, e, P_LAYERS, orbits=ORB.edge_orbits(n, e), precision="c64", with_grad=False, stream=stream,
+              device=dev)
+    g, b = W.random_angles(P_LAYERS, 5)
+    u = W.rng(9).uniform(0, 1, 65536)
+    pl.sample(g, b, u)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        x, cut = pl.sample(g, b, u)
+    dt = (time.perf_counter() - t0) / 3
+    res["sample_star_S29_65536"] = {"ms_per_call": dt * 1000.0, "mean_cut": float(cut.mean()),
+                                    "timing": "host wall clock per call: forward (state stored) + sampling"}
+    pl.close()
+    return res
 
 
 def batch_extras(dev, stream):
@@ -455,7 +496,11 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_QUBITS, "p": P_LAYERS, "graph": "star S_29", "observable": "H_red",
                    "precision": "complex64", "l2": "statevector 8.6 GB >> 129 MB L2; no flush needed",
-                   "parallelism": f"independent evaluations per GPU x{world}"},
+                   "parallelism": f"independent evaluations per GPU x{world}",
+                   "pass_plan": {"forward_low_qubits": result["pass_plan"][0],
+                                 "forward_high_passes": result["pass_plan"][1],
+                                 "adjoint_low_qubits": result["pass_plan"][2],
+                                 "adjoint_high_passes": result["pass_plan"][3], "chosen_by": "autotune"}},
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": traffic_from_profiles(),

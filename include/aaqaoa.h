@@ -337,6 +337,29 @@ void aaqaoa_destroy_multi(aaqaoa_multi *multi);
 #define AAQAOA_FAULT_DROP_TILE 1
 int aaqaoa_inject_fault(aaqaoa_plan *plan, int kind);
 
+/*
+ * Qubits per pass (the "fusion depth" of the tiled mixer, Sec. 2's H_M applied
+ * as one butterfly per qubit): a layer is a low pass over qubits 0..L-1 plus K
+ * high passes sharing the other n - L qubits. plan4 = {L, K} of the forward
+ * passes and {L, K} of the two-vector adjoint passes (all 0 for plans small
+ * enough for the whole-circuit kernel).
+ *
+ * aaqaoa_get_pass_plan: plan4 (host, 4 ints) receives the current plan.
+ * aaqaoa_set_pass_plan: 0 keeps the default for that entry (the fewest high
+ *   passes; a two-register-stage low pass when they can take the rest).
+ *   INVALID_ARG if an (L, K) does not tile n with rows of >= 128 bytes.
+ *   Rebuilds the workspace's tensor maps; the stored state becomes invalid.
+ * aaqaoa_autotune: times each candidate (the fewest and one more high pass,
+ *   each with the full and the two-stage low pass) on the plan's workspace
+ *   and stream and keeps the fastest forward and adjoint plans; the choice is
+ *   cached per process by (device, precision, n, batch, gradient). Leaves
+ *   garbage in the workspace's vectors. AAQAOA_AUTOTUNE=0 in the environment
+ *   keeps the default plan. plan4 (host, 4 ints, or NULL) receives the result.
+ */
+int aaqaoa_get_pass_plan(aaqaoa_plan *plan, int *plan4);
+int aaqaoa_set_pass_plan(aaqaoa_plan *plan, int fwd_low, int fwd_high, int bwd_low, int bwd_high);
+int aaqaoa_autotune(aaqaoa_plan *plan, int *plan4);
+
 /* Plan properties: qubits, layers, edges, orbits, precision flag. */
 int aaqaoa_plan_info(const aaqaoa_plan *plan, int *n, int *p, int *num_edges, int *num_orbits,
                      unsigned *flags);

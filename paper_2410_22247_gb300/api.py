@@ -118,6 +118,22 @@ class Plan:
                                        float(tol), ctypes.byref(bad)), "aaqaoa_verify_orbits")
         return bad.value
 
+    def pass_plan(self):
+        """[L, K] of the forward and [L, K] of the adjoint passes per layer."""
+        out = np.zeros(4, dtype=np.int32)
+        N.check(N.aaqaoa_get_pass_plan(self.handle, _ptr(out, ctypes.c_int32)), "aaqaoa_get_pass_plan")
+        return out.tolist()
+
+    def set_pass_plan(self, fwd_low=0, fwd_high=0, bwd_low=0, bwd_high=0):
+        N.check(N.aaqaoa_set_pass_plan(self.handle, int(fwd_low), int(fwd_high), int(bwd_low), int(bwd_high)),
+                "aaqaoa_set_pass_plan")
+
+    def autotune(self):
+        """Time the candidate pass plans and keep the fastest; returns pass_plan()."""
+        out = np.zeros(4, dtype=np.int32)
+        N.check(N.aaqaoa_autotune(self.handle, _ptr(out, ctypes.c_int32)), "aaqaoa_autotune")
+        return out.tolist()
+
     def max_cut(self):
         """(C_max, smallest maximising bitstring) by device exhaustion."""
         c = np.zeros(1, dtype=np.int32)

@@ -13,6 +13,10 @@
 // memory.
 #include <cudaTypedefs.h>
 
+#include <array>
+#include <functional>
+#include <tuple>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -77,6 +81,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     }
     return fn;
 }
+
+constexpr int MAX_PASSES = 8;  // passes per layer (tensor maps kept per pass)
 
 struct Pass {
     int s;       // first qubit of the tile rows
@@ -268,53 +274,57 @@ int make_map(CUtensorMap *map, void *base, int n, int s, int cb, int T, int cbmi
     return AAQAOA_OK;
 }
 
-// Passes of one layer for tiles of T qubits: a low pass over qubits
-// 0..L-1 (contiguous tiles), then K = ceil((n-T)/hbmax) high passes that
-// share the remaining n-L qubits evenly. A high pass with h < hbmax row qubits
-// spends the spare tile bits on longer contiguous rows (cb = T-h), which keeps
-// the strided passes close to streaming bandwidth. L is T unless the K high
-// passes can take all but the L2 qubits of the low pass's first two register
-// stages; then L = L2 and the low pass skips its third stage.
-std::vector<Pass> make_passes(int n, int T, int cbmin, int hbmax, int L2)
+// Passes of one layer for tiles of T qubits: a low pass over qubits 0..L-1
+// (contiguous tiles), then K high passes that share the remaining n-L qubits
+// evenly. A high pass with h < hbmax row qubits spends the spare tile bits on
+// longer contiguous rows (cb = T-h), which keeps the strided passes close to
+// streaming bandwidth. Returns false when (L, K) does not give valid tiles.
+bool layer_passes(int n, int T, int cbmin, int hbmax, int L2, int L, int K, std::vector<Pass> &v)
 {
-    std::vector<Pass> v;
-    if (n <= T)
-        return v;
-    const int K = (n - T + hbmax - 1) / hbmax;
-    int L = T;
-    if (L2 >= cbmin && L2 < T && n - L2 <= K * hbmax) {
-        bool fits = true;  // every high pass keeps its contiguous bits below its rows
-        for (int k = 0; k < K; k++) {
-            const int h = (n - L2) / K + (k < (n - L2) % K ? 1 : 0);
-            if (h < 1 || T - h > L2 || h > hbmax)
-                fits = false;
-        }
-        if (fits)
-            L = L2;
-    }
+    v.clear();
+    if (n <= T || L < cbmin || L > T || K < 1 || n - L < K || n - L > K * hbmax || K + 1 > MAX_PASSES)
+        return false;
     Pass low{cbmin, cbmin, 1, (1 << (L - cbmin)) - 1, 0};
-    low.skip_last = L < T ? 1 : 0;
+    low.skip_last = L <= L2 && L < T ? 1 : 0;
     low.qubits = L;
     v.push_back(low);
     const int r = n - L;
     int s = L;
     for (int k = 0; k < K; k++) {
         const int h = r / K + (k < r % K ? 1 : 0);
+        if (h > hbmax || T - h > s || T - h < cbmin)  // contiguous bits stay below the rows
+            return false;
         Pass hp{s, T - h, 0, (1 << h) - 1, 0};
         hp.qubits = h;
         v.push_back(hp);
         s += h;
     }
-    return v;
+    return true;
+}
+
+// The default plan: the fewest high passes, K = ceil((n-T)/hbmax); the low
+// pass covers T qubits unless those K passes can take all but the L2 qubits
+// of its first two register stages, in which case it skips its third stage.
+void default_layer(int n, int T, int cbmin, int hbmax, int L2, int *L, int *K)
+{
+    *K = (n - T + hbmax - 1) / hbmax;
+    std::vector<Pass> v;
+    *L = (L2 < T && layer_passes(n, T, cbmin, hbmax, L2, L2, *K, v)) ? L2 : T;
 }
 
 void build_passes(aaqaoa_plan *pl)
 {
-    int T, CB, HB;
-    pass_geometry(pl->c128, 1, &T, &CB, &HB);
-    pl->passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB, low_two_stage_bits(pl->c128, 1));
-    pass_geometry(pl->c128, 2, &T, &CB, &HB);
-    pl->bwd_passes = pl->small() ? std::vector<Pass>() : make_passes(pl->n, T, CB, HB, low_two_stage_bits(pl->c128, 2));
+    pl->passes.clear();
+    pl->bwd_passes.clear();
+    if (pl->small())
+        return;
+    for (int nv = 1; nv <= 2; nv++) {
+        int T, CB, HB, L, K;
+        pass_geometry(pl->c128, nv, &T, &CB, &HB);
+        const int L2 = low_two_stage_bits(pl->c128, nv);
+        default_layer(pl->n, T, CB, HB, L2, &L, &K);
+        layer_passes(pl->n, T, CB, HB, L2, L, K, nv == 1 ? pl->passes : pl->bwd_passes);
+    }
 }
 
 // table `kind` (0 exact, 1 forward-scaled, 2 inverse) of a call with B points
@@ -775,6 +785,37 @@ int aaqaoa_workspace_bytes(const aaqaoa_plan *plan, int batch, int with_grad, si
     return AAQAOA_OK;
 }
 
+// TMA tensor maps of the current pass plans over the workspace's vectors
+int build_maps(aaqaoa_plan *pl)
+{
+    pl->map_phi.assign(pl->passes.size(), CUtensorMap{});
+    pl->map_bphi.assign(pl->bwd_passes.size(), CUtensorMap{});
+    pl->map_blam.assign(pl->bwd_passes.size(), CUtensorMap{});
+    if (!pl->ws)
+        return AAQAOA_OK;
+    int T, CB, HB;
+    pass_geometry(pl->c128, 1, &T, &CB, &HB);
+    for (size_t k = 0; k < pl->passes.size(); k++) {
+        Pass &ps = pl->passes[k];
+        int r = make_map(&pl->map_phi[k], pl->d_phi(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), pl->cap, &ps.wide);
+        if (r)
+            return r;
+    }
+    if (pl->ws_grad) {
+        pass_geometry(pl->c128, 2, &T, &CB, &HB);
+        for (size_t k = 0; k < pl->bwd_passes.size(); k++) {
+            Pass &ps = pl->bwd_passes[k];
+            int r = make_map(&pl->map_bphi[k], pl->d_phi(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), pl->cap, &ps.wide);
+            if (r)
+                return r;
+            r = make_map(&pl->map_blam[k], pl->d_lam(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), pl->cap, &ps.wide);
+            if (r)
+                return r;
+        }
+    }
+    return AAQAOA_OK;
+}
+
 int aaqaoa_set_workspace(aaqaoa_plan *pl, void *device_ptr, size_t bytes, int batch, int with_grad)
 {
     if (!pl || batch < 1)
@@ -790,32 +831,186 @@ int aaqaoa_set_workspace(aaqaoa_plan *pl, void *device_ptr, size_t bytes, int ba
     pl->ws_grad = with_grad != 0;
     pl->L = L;
     pl->state_valid = false;
-    pl->map_phi.assign(pl->passes.size(), CUtensorMap{});
-    pl->map_bphi.assign(pl->bwd_passes.size(), CUtensorMap{});
-    pl->map_blam.assign(pl->bwd_passes.size(), CUtensorMap{});
-    int T, CB, HB;
-    pass_geometry(pl->c128, 1, &T, &CB, &HB);
-    for (size_t k = 0; k < pl->passes.size(); k++) {
-        Pass &ps = pl->passes[k];
-        int r = make_map(&pl->map_phi[k], pl->d_phi(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), batch, &ps.wide);
-        if (r)
-            return r;
-    }
-    if (with_grad) {
-        pass_geometry(pl->c128, 2, &T, &CB, &HB);
-        for (size_t k = 0; k < pl->bwd_passes.size(); k++) {
-            Pass &ps = pl->bwd_passes[k];
-            int r = make_map(&pl->map_bphi[k], pl->d_phi(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), batch, &ps.wide);
-            if (r)
-                return r;
-            r = make_map(&pl->map_blam[k], pl->d_lam(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), batch, &ps.wide);
-            if (r)
-                return r;
-        }
-    }
+    int r = build_maps(pl);
+    if (r)
+        return r;
     CK(cudaMemsetAsync(pl->ws + L.ctrl, 0, 256, pl->stream));
     CK(cudaStreamSynchronize(pl->stream));
     return AAQAOA_OK;
+}
+
+// ------------------------------------------------- pass plans, autotune
+// A layer's qubits per pass (the low pass's qubit count L and the number K of
+// high passes) for the forward (nv = 1) and the two-vector adjoint (nv = 2)
+// passes. 0 selects the default of build_passes().
+static int set_layers(aaqaoa_plan *pl, const int plan4[4])
+{
+    if (pl->small())
+        return AAQAOA_OK;
+    std::vector<Pass> v[2];
+    for (int nv = 1; nv <= 2; nv++) {
+        int T, CB, HB, L, K;
+        pass_geometry(pl->c128, nv, &T, &CB, &HB);
+        const int L2 = low_two_stage_bits(pl->c128, nv);
+        default_layer(pl->n, T, CB, HB, L2, &L, &K);
+        if (plan4[2 * (nv - 1)] > 0)
+            L = plan4[2 * (nv - 1)];
+        if (plan4[2 * (nv - 1) + 1] > 0)
+            K = plan4[2 * (nv - 1) + 1];
+        if (!layer_passes(pl->n, T, CB, HB, L2, L, K, v[nv - 1]))
+            return fail(AAQAOA_ERR_INVALID_ARG, "%s plan: low pass of %d qubits + %d high passes does not tile n=%d",
+                        nv == 1 ? "forward" : "adjoint", L, K, pl->n);
+    }
+    pl->passes = v[0];
+    pl->bwd_passes = v[1];
+    pl->state_valid = false;
+    return build_maps(pl);
+}
+
+int aaqaoa_get_pass_plan(aaqaoa_plan *pl, int *plan4)
+{
+    if (!pl || !plan4)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan or plan4 is NULL");
+    plan4[0] = pl->passes.empty() ? 0 : pl->passes[0].qubits;
+    plan4[1] = pl->passes.empty() ? 0 : (int)pl->passes.size() - 1;
+    plan4[2] = pl->bwd_passes.empty() ? 0 : pl->bwd_passes[0].qubits;
+    plan4[3] = pl->bwd_passes.empty() ? 0 : (int)pl->bwd_passes.size() - 1;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_set_pass_plan(aaqaoa_plan *pl, int fwd_low, int fwd_high, int bwd_low, int bwd_high)
+{
+    g_detail.clear();
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    if (fwd_low < 0 || fwd_high < 0 || bwd_low < 0 || bwd_high < 0)
+        return fail(AAQAOA_ERR_INVALID_ARG, "negative pass-plan entry");
+    const int plan4[4] = {fwd_low, fwd_high, bwd_low, bwd_high};
+    return set_layers(pl, plan4);
+}
+
+namespace {
+struct TuneKey {
+    int dev, c128, n, cap, grad;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(dev, c128, n, cap, grad) < std::tie(o.dev, o.c128, o.n, o.cap, o.grad);
+    }
+};
+std::map<TuneKey, std::array<int, 4>> &plan_tune_cache()
+{
+    static std::map<TuneKey, std::array<int, 4>> cache;
+    return cache;
+}
+
+// candidate (L, K) of one pass kind: the fewest and one more high pass, each
+// with the full low pass and with the two-stage one
+std::vector<std::array<int, 2>> layer_candidates(const aaqaoa_plan *pl, int nv)
+{
+    int T, CB, HB, L, K;
+    pass_geometry(pl->c128, nv, &T, &CB, &HB);
+    const int L2 = low_two_stage_bits(pl->c128, nv);
+    default_layer(pl->n, T, CB, HB, L2, &L, &K);
+    std::vector<std::array<int, 2>> c;
+    for (int k = K; k <= K + 1; k++)
+        for (int l : {T, L2}) {
+            std::vector<Pass> v;
+            if (layer_passes(pl->n, T, CB, HB, L2, l, k, v) &&
+                std::find(c.begin(), c.end(), std::array<int, 2>{l, k}) == c.end())
+                c.push_back({l, k});
+        }
+    return c;
+}
+
+float time_ms(cudaStream_t st, const std::function<int()> &work, int reps)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    int r = 0;
+    for (int i = 0; i < reps && !r; i++)
+        r = work();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return r ? 1e30f : ms / reps;
+}
+}  // namespace
+
+int aaqaoa_autotune(aaqaoa_plan *pl, int *plan4)
+{
+    g_detail.clear();
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    if (!pl->ws)
+        return fail(AAQAOA_ERR_WORKSPACE, "no workspace set (aaqaoa_set_workspace)");
+    int r = AAQAOA_OK;
+    const char *env = std::getenv("AAQAOA_AUTOTUNE");
+    if (!pl->small() && !(env && env[0] == '0')) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const TuneKey key{dev, pl->c128 ? 1 : 0, pl->n, pl->cap, pl->ws_grad ? 1 : 0};
+        auto it = plan_tune_cache().find(key);
+        if (it != plan_tune_cache().end()) {
+            r = set_layers(pl, it->second.data());
+        } else {
+            std::vector<double> g(pl->p), b(pl->p);
+            for (int l = 0; l < pl->p; l++) {
+                g[l] = 0.3 + 0.1 * l;
+                b[l] = 0.2 + 0.05 * l;
+            }
+            if ((r = upload_params(pl, 1, g.data(), b.data())) ||
+                (r = enqueue_params(pl, 1, pl->d_params(), pl->d_params() + pl->p)))
+                return r;
+            const FwdMode fm = pl->ws_grad ? FWD_GRAD : FWD_ENERGY;
+            std::array<int, 4> best{0, 0, 0, 0};
+            float best_ms = 1e30f;
+            for (auto &c : layer_candidates(pl, 1)) {
+                const int cand[4] = {c[0], c[1], 0, 0};
+                if ((r = set_layers(pl, cand)))
+                    return r;
+                auto run = [&]() { return enqueue_forward(pl, 1, AAQAOA_OBS_FULL, fm); };
+                time_ms(pl->stream, run, 1);
+                const float ms = time_ms(pl->stream, run, 2);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best[0] = c[0];
+                    best[1] = c[1];
+                }
+            }
+            if (pl->ws_grad) {
+                best_ms = 1e30f;
+                for (auto &c : layer_candidates(pl, 2)) {
+                    const int cand[4] = {best[0], best[1], c[0], c[1]};
+                    if ((r = set_layers(pl, cand)))
+                        return r;
+                    if ((r = enqueue_forward(pl, 1, AAQAOA_OBS_FULL, FWD_GRAD)))
+                        return r;
+                    auto run = [&]() { return enqueue_backward(pl, 1, AAQAOA_OBS_FULL); };
+                    time_ms(pl->stream, run, 1);
+                    const float ms = time_ms(pl->stream, run, 2);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best[2] = c[0];
+                        best[3] = c[1];
+                    }
+                }
+            }
+            if ((r = set_layers(pl, best.data())))
+                return r;
+            std::vector<double> rows;
+            if ((r = fetch_out(pl, 1, rows)))  // a device timeout during tuning surfaces here
+                return r;
+            plan_tune_cache()[key] = best;
+        }
+    }
+    if (!r && plan4)
+        r = aaqaoa_get_pass_plan(pl, plan4);
+    return r;
 }
 
 int aaqaoa_set_stream(aaqaoa_plan *pl, void *stream)

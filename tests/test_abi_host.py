@@ -129,3 +129,38 @@ def test_prepare_multi_names_the_bad_graph():
     h = ctypes.c_void_p()
     assert N.aaqaoa_prepare_multi(3, descs, 1, 0, None, ctypes.byref(h)) == -1
     assert b"graph 2" in N.aaqaoa_last_error_detail()
+
+
+def _handle(n, edges, p):
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    h = ctypes.c_void_p()
+    assert N.aaqaoa_prepare(n, len(e) // 2, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0, None, None, None,
+                            p, 0, None, ctypes.byref(h)) == 0
+    return h
+
+
+def test_pass_plans_default_and_validation():
+    """Default qubits per pass and the rejection of plans that do not tile n
+    (host-side only: no workspace, so no tensor maps are built)."""
+    h = _handle(*W.star_graph(30), p=2)
+    try:
+        out = np.zeros(4, dtype=np.int32)
+        assert N.aaqaoa_get_pass_plan(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))) == 0
+        assert out.tolist() == [13, 2, 8, 3]   # forward 13 + 9 + 8, adjoint 8 + 8 + 7 + 7
+        assert N.aaqaoa_set_pass_plan(h, 9, 3, 12, 3) == 0
+        assert N.aaqaoa_get_pass_plan(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))) == 0
+        assert out.tolist() == [9, 3, 12, 3]
+        assert N.aaqaoa_set_pass_plan(h, 13, 1, 0, 0) == -1   # 17 qubits in one high pass
+        assert N.aaqaoa_set_pass_plan(h, 3, 2, 0, 0) == -1    # low pass below one row
+        assert N.aaqaoa_set_pass_plan(h, 0, 0, 0, 0) == 0
+        assert N.aaqaoa_get_pass_plan(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))) == 0
+        assert out.tolist() == [13, 2, 8, 3]
+    finally:
+        N.aaqaoa_destroy(h)
+    h = _handle(*W.cycle_graph(10), p=1)
+    try:
+        out = np.ones(4, dtype=np.int32)
+        assert N.aaqaoa_get_pass_plan(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))) == 0
+        assert out.tolist() == [0, 0, 0, 0]
+    finally:
+        N.aaqaoa_destroy(h)

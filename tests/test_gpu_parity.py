@@ -291,8 +291,16 @@ def test_full_size_k16_p1():
     assert e_rel(SYM.energy(SYM.complete_graph_model(16), g, b), Ec) < 1e-12
 
 
+def _release_cached_device_memory(torch):
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
 def test_full_size_binary_tree_n34_p1_c64():
     torch = pytest.importorskip("torch")
+    _release_cached_device_memory(torch)
     free, _ = torch.cuda.mem_get_info()
     if free < 150e9:
         pytest.skip("needs ~140 GB of free device memory")
@@ -309,6 +317,7 @@ def test_full_size_binary_tree_n34_p1_c64():
 
 def test_full_size_prufer_n32_p4_c64_sampled_edges():
     torch = pytest.importorskip("torch")
+    _release_cached_device_memory(torch)
     free, _ = torch.cuda.mem_get_info()
     if free < 80e9:
         pytest.skip("needs ~70 GB of free device memory")
@@ -333,3 +342,40 @@ def test_full_size_prufer_n32_p4_c64_sampled_edges():
     assert e_rel(float(np.sum(0.5 * (1 - zz))), E) < 1e-5
     pl.close()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,prec", [(22, "c64"), (21, "c128"), (26, "c64")])
+def test_every_candidate_pass_plan_matches_oracle(n, prec):
+    """Each (low-pass qubits, number of high passes) the autotuner may choose
+    gives the oracle's energy and gradient; autotune then keeps one of them."""
+    from paper_2410_22247_gb300.api import Plan
+    if n == 26:
+        nn, e = W.star_graph(n)
+        Er, dgr, dbr = SYM.energy_grad(SYM.star_model(n), *W.random_angles(2, 21))
+    else:
+        nn, e = W.prufer_tree(n, 21)
+        Er, dgr, dbr = O.energy_grad(nn, e, *W.random_angles(2, 21))
+    g, b = W.random_angles(2, 21)
+    pl, _ = plan_for(nn, e, 2, prec)
+    T = {"c64": (13, 9, 12, 8), "c128": (12, 8, 11, 7)}[prec]
+    fwd = [(L, K) for K in (1, 2, 3) for L in (T[0], T[1])]
+    bwd = [(L, K) for K in (1, 2, 3, 4) for L in (T[2], T[3])]
+    tried = set()
+    for (lf, kf) in fwd:
+        for (lb, kb) in bwd:
+            try:
+                pl.set_pass_plan(lf, kf, lb, kb)
+            except Exception:
+                continue
+            tried.add(tuple(pl.pass_plan()))
+            E, dg, db = pl.grad(g, b, "red")
+            tol = TOL[prec]
+            assert e_rel(E, Er) < tol, (lf, kf, lb, kb)
+            scale = max(abs(Er), 1.0) if prec == "c64" else 1e-3 * abs(Er)
+            for x, r in zip(np.concatenate([dg, db]), np.concatenate([dgr, dbr])):
+                assert abs(x - r) <= tol * max(abs(r), scale), (lf, kf, lb, kb)
+    assert len(tried) >= 4
+    choice = tuple(pl.autotune())
+    assert choice in tried
+    E, dg, db = pl.grad(g, b, "red")
+    assert e_rel(E, Er) < TOL[prec]
