@@ -1,6 +1,6 @@
 """Build the CUDA library ``libaaqaoa.so`` in-tree for sm_103a.
 
-Two translation units (kernels, host ABI) are compiled in parallel with nvcc
+The translation units (kernels, host ABI, host orbit finder) are compiled in parallel with nvcc
 and linked into ``paper_2410_22247_gb300/_lib/libaaqaoa.so``. The build is
 skipped when the library is newer than every source.
 """
@@ -28,7 +28,7 @@ def nvcc() -> str:
 
 
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def _stale() -> bool:
@@ -45,7 +45,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(OUT_DIR, exist_ok=True)
     objs, procs = [], []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src).replace(".cu", f".{os.getpid()}.o"))
+        obj = os.path.join(OUT_DIR, os.path.splitext(os.path.basename(src))[0] + f".{os.getpid()}.o")
         cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
         if ptxas_info:
             cmd += ["-Xptxas", "-v"]

@@ -31,7 +31,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["EdgeOrbits", "automorphism_generators", "edge_orbits", "is_automorphism"]
+__all__ = ["EdgeOrbits", "automorphism_generators", "edge_orbits", "edge_orbits_native", "is_automorphism"]
 
 
 def _adjacency(n, edges):
@@ -216,3 +216,22 @@ def edge_orbits(n, edges, generators=None) -> EdgeOrbits:
         weights.append(size)
     return EdgeOrbits(cls.astype(np.int32), np.asarray(reps, dtype=np.int32),
                       np.asarray(weights, dtype=np.int32), generators)
+
+
+def edge_orbits_native(n, edges) -> EdgeOrbits:
+    """The same classes from the library's C++ implementation
+    (``aaqaoa_edge_orbits``: same refinement, search order and closure).
+    Generators are not returned (``generators`` is empty)."""
+    import ctypes
+
+    from . import _native as N
+
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    m = len(e) // 2
+    eo = np.zeros(max(m, 1), dtype=np.int32)
+    rep = np.zeros(max(m, 1), dtype=np.int32)
+    w = np.zeros(max(m, 1), dtype=np.int32)
+    k = ctypes.c_int32()
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    N.check(N.aaqaoa_edge_orbits(int(n), m, P(e), P(eo), ctypes.byref(k), P(rep), P(w)), "aaqaoa_edge_orbits")
+    return EdgeOrbits(eo[:m].copy(), rep[:k.value].copy(), w[:k.value].copy(), [])

@@ -82,3 +82,46 @@ def test_group_order_matches_networkx():
         g.add_edges_from(map(tuple, e))
         count = sum(1 for _ in GraphMatcher(g, g).isomorphisms_iter())
         assert count == len(AUT.automorphism_group(n, e))
+
+
+@pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: "native-" + r[5])
+def test_native_orbit_counts_match_paper(row):
+    """The library's C++ finder (aaqaoa_edge_orbits, no GPU) on the printed counts."""
+    fam, prm, n, m, orbits, cite = row
+    nn, e = _graph(fam, prm)
+    res = ORB.edge_orbits_native(nn, e)
+    assert res.num_orbits == orbits, cite
+    assert int(res.weight.sum()) == m
+
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+def test_native_orbits_match_brute_force(k):
+    n, e = SMALL[k]
+    res = ORB.edge_orbits_native(n, e)
+    canon = [tuple(map(int, x)) for x in e]
+    mine = {frozenset(canon[i] for i in range(len(canon)) if res.edge_orbit[i] == c) for c in range(res.num_orbits)}
+    ref, _ = AUT.edge_orbit_partition(n, e)
+    assert mine == ref
+
+
+def test_native_and_python_finders_agree():
+    graphs = [W.heap_binary_tree(34), W.complete_graph(16), W.star_graph(30), W.random_regular(30, 3, 0),
+              W.generalized_petersen(5, 2), W.prufer_tree(32, 0), W.circulant_graph(12, (1, 3))]
+    graphs += [(n, e) for _, n, e in W.mixed_graph_batch(40, 12, 22, 7)]
+    for n, e in graphs:
+        a, b = ORB.edge_orbits(n, e), ORB.edge_orbits_native(n, e)
+        assert np.array_equal(a.edge_orbit, b.edge_orbit) and np.array_equal(a.rep, b.rep)
+        assert np.array_equal(a.weight, b.weight)
+
+
+def test_native_finder_rejects_bad_edges():
+    import ctypes
+    from paper_2410_22247_gb300 import _native as N
+    out = np.zeros(4, dtype=np.int32)
+    k = ctypes.c_int32()
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    for bad in ([0, 0, 1, 2], [0, 1, 1, 0], [0, 5, 1, 2]):
+        e = np.array(bad, dtype=np.int32)
+        assert N.aaqaoa_edge_orbits(4, 2, P(e), P(out), ctypes.byref(k), P(out), P(out)) == -1
+    e = np.array([0, 1], dtype=np.int32)
+    assert N.aaqaoa_edge_orbits(65, 1, P(e), P(out), ctypes.byref(k), P(out), P(out)) == -1
