@@ -114,6 +114,22 @@ int aaqaoa_prepare(int n, int num_edges, const int32_t *edges,
                    aaqaoa_plan **out);
 
 /*
+ * aaqaoa_prepare_weighted -- aaqaoa_prepare for weighted MaxCut with integer
+ * edge weights w_e >= 1: H_C = 1/2 sum_e w_e (1 - Z_u Z_v), so the phase uses
+ * the weighted cut C(x) = sum_e w_e [x_u != x_v] and H_red keeps one
+ * representative per class at weight |S~_m| * w_rep (Sec. 5 with the edge
+ * weights carried along; orbits must come from weight-preserving
+ * automorphisms). edge_weight: num_edges int32, or NULL for all 1 (then this
+ * is aaqaoa_prepare). The total weight must not exceed 561 (the phase table
+ * holds one entry per cut value): AAQAOA_ERR_UNSUPPORTED otherwise.
+ * AAQAOA_ERR_BAD_ORBITS if edge_orbit puts edges of different weight in one
+ * class. Plans with weights are not accepted by aaqaoa_prepare_multi.
+ */
+int aaqaoa_prepare_weighted(int n, int num_edges, const int32_t *edges, const int32_t *edge_weight, int num_orbits,
+                            const int32_t *orbit_rep, const int32_t *orbit_weight, const int32_t *edge_orbit, int p,
+                            unsigned flags, void *stream, aaqaoa_plan **out);
+
+/*
  * aaqaoa_workspace_bytes -- device bytes needed for a workspace able to hold
  * `batch` statevectors (batch >= 1), with room for the adjoint gradient's
  * second statevector when with_grad != 0. Writes *bytes.

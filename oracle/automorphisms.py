@@ -13,19 +13,23 @@ from itertools import permutations
 import numpy as np
 
 
-def automorphism_group(n, edges):
-    es = {(min(int(u), int(v)), max(int(u), int(v))) for u, v in np.asarray(edges).reshape(-1, 2)}
+def automorphism_group(n, edges, weights=None):
+    """All vertex permutations mapping edges to edges (of equal weight when
+    integer edge weights are given)."""
+    e = np.asarray(edges).reshape(-1, 2)
+    w = [1] * len(e) if weights is None else [int(x) for x in np.asarray(weights).reshape(-1)]
+    es = {(min(int(u), int(v)), max(int(u), int(v))): wi for (u, v), wi in zip(e, w)}
     group = []
     for perm in permutations(range(n)):
-        if all((min(perm[u], perm[v]), max(perm[u], perm[v])) in es for u, v in es):
+        if all(es.get((min(perm[u], perm[v]), max(perm[u], perm[v]))) == wi for (u, v), wi in es.items()):
             group.append(perm)
     return group
 
 
-def edge_orbit_partition(n, edges):
+def edge_orbit_partition(n, edges, weights=None):
     """The set of edge orbits, each a frozenset of (u, v) tuples."""
     es = sorted({(min(int(u), int(v)), max(int(u), int(v))) for u, v in np.asarray(edges).reshape(-1, 2)})
-    group = automorphism_group(n, edges)
+    group = automorphism_group(n, edges, weights)
     seen, orbits = set(), []
     for e in es:
         if e in seen:

@@ -209,3 +209,34 @@ def sample(psi, u):
     if r != 0:
         raise MemoryError("oracle_sample: no memory for the cumulative sums")
     return out
+
+
+# ------------------------------------------------ integer edge weights
+# Weighted MaxCut, H_C = 1/2 sum_e w_e (1 - Z_u Z_v) with integer w_e >= 1: the
+# weighted cut sum_e w_e [x_u != x_v] is the plain cut of the edge list in
+# which edge e appears w_e times, so the C routines above serve unchanged with
+# that list as the cost and (edges, w) as the observable.
+
+def weighted_cost_edges(edges, weights):
+    e = _edges(edges)
+    w = np.asarray(weights, dtype=np.int64).reshape(-1)
+    return _edges(np.repeat(e, w, axis=0))
+
+
+def full_observable_w(edges, weights):
+    return _edges(edges), _f64(weights)
+
+
+def qaoa_state_w(n, edges, weights, gamma, beta):
+    return qaoa_state(n, weighted_cost_edges(edges, weights), gamma, beta)
+
+
+def energy_grad_w(n, edges, weights, gamma, beta, obs=None):
+    """(E, dE/dgamma, dE/dbeta) of weighted MaxCut; obs defaults to the weighted H_C."""
+    if obs is None:
+        obs = full_observable_w(edges, weights)
+    return energy_grad(n, weighted_cost_edges(edges, weights), gamma, beta, obs)
+
+
+def max_cut_w(n, edges, weights):
+    return max_cut(n, weighted_cost_edges(edges, weights))

@@ -41,6 +41,8 @@ _vp = ctypes.c_void_p
 _PROTOS = [
     ("aaqaoa_prepare", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int, _i32p, _i32p, _i32p,
                                       ctypes.c_int, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
+    ("aaqaoa_prepare_weighted", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
+                                               _i32p, ctypes.c_int, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
     ("aaqaoa_workspace_bytes", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("aaqaoa_set_workspace", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
     ("aaqaoa_set_stream", ctypes.c_int, [_vp, _vp]),

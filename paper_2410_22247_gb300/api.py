@@ -37,7 +37,7 @@ class Plan:
     """
 
     def __init__(self, n, edges, p, orbits=None, precision="c64", batch=1, with_grad=True,
-                 stream=None, device=None):
+                 stream=None, device=None, weights=None):
         import torch
 
         self._lib = N.load()
@@ -59,10 +59,13 @@ class Plan:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         handle = ctypes.c_void_p()
-        N.check(N.aaqaoa_prepare(self.n, len(self.edges), _ptr(e, ctypes.c_int32), self.num_orbits,
-                                 _ptr(rep, ctypes.c_int32), _ptr(weight, ctypes.c_int32), _ptr(eo, ctypes.c_int32),
-                                 self.p, flags, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)),
-                "aaqaoa_prepare")
+        self.weights = None if weights is None else _i32(weights)
+        N.check(N.aaqaoa_prepare_weighted(self.n, len(self.edges), _ptr(e, ctypes.c_int32),
+                                          _ptr(self.weights, ctypes.c_int32), self.num_orbits,
+                                          _ptr(rep, ctypes.c_int32), _ptr(weight, ctypes.c_int32),
+                                          _ptr(eo, ctypes.c_int32), self.p, flags,
+                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)),
+                "aaqaoa_prepare_weighted")
         self.handle = handle
         self.batch = int(batch)
         self.with_grad = bool(with_grad)

@@ -107,6 +107,8 @@ struct aaqaoa_plan {
     std::vector<int32_t> edges;  // normalised (u < v), caller's edge order
     std::vector<int32_t> orbit_rep, orbit_weight;
     std::vector<int32_t> edge_orbit;  // class of every edge (empty when the caller gave none)
+    std::vector<int32_t> edge_w;      // integer edge weights (all 1 for MaxCut)
+    int wsum = 0;                     // sum of the edge weights: the largest cut value
     CostFn cost{};
     CutFn obs[2]{};
     cudaStream_t stream = nullptr;
@@ -137,7 +139,7 @@ struct aaqaoa_plan {
     int CB() const { int t, c, h; pass_geometry(c128, 1, &t, &c, &h); return c; }
     int HB() const { int t, c, h; pass_geometry(c128, 1, &t, &c, &h); return h; }
     size_t amp() const { return c128 ? 16 : 8; }
-    int tab_len() const { return m + 1; }
+    int tab_len() const { return wsum + 1; }  // cut values 0..sum of edge weights
     int out_stride() const { return 1 + 2 * p; }
     bool small() const { return n <= T(); }
     int tiles() const { return small() ? 1 : 1 << (n - T()); }
@@ -536,7 +538,7 @@ int enqueue_aggregate(aaqaoa_plan *pl, int obs, int agg)
         a.num_terms = 1;
         a.term_u[0] = pl->edges[2 * e];
         a.term_v[0] = pl->edges[2 * e + 1];
-        a.term_w[0] = obs == AAQAOA_OBS_FULL ? 1.0 : (double)pl->orbit_weight[t];
+        a.term_w[0] = obs == AAQAOA_OBS_FULL ? (double)pl->edge_w[e] : (double)pl->orbit_weight[t] * pl->edge_w[e];
         ProfScope ps_(pl, PK_AGG, S);
         CKL(launch_agg_terms(c128, a, pl->stream, grid), "per-term aggregation");
         pl->launches++;
@@ -674,6 +676,14 @@ int aaqaoa_prepare(int n, int num_edges, const int32_t *edges, int num_orbits, c
                    const int32_t *orbit_weight, const int32_t *edge_orbit, int p, unsigned flags, void *stream,
                    aaqaoa_plan **out)
 {
+    return aaqaoa_prepare_weighted(n, num_edges, edges, nullptr, num_orbits, orbit_rep, orbit_weight, edge_orbit, p,
+                                   flags, stream, out);
+}
+
+int aaqaoa_prepare_weighted(int n, int num_edges, const int32_t *edges, const int32_t *edge_weight, int num_orbits,
+                            const int32_t *orbit_rep, const int32_t *orbit_weight, const int32_t *edge_orbit, int p,
+                            unsigned flags, void *stream, aaqaoa_plan **out)
+{
     g_detail.clear();
     if (!out)
         return fail(AAQAOA_ERR_INVALID_ARG, "out is NULL");
@@ -705,6 +715,19 @@ int aaqaoa_prepare(int n, int num_edges, const int32_t *edges, int num_orbits, c
         e[2 * i] = u;
         e[2 * i + 1] = v;
     }
+    std::vector<int32_t> w(num_edges, 1);
+    long long wsum = 0;
+    for (int i = 0; i < num_edges; i++) {
+        if (edge_weight) {
+            if (edge_weight[i] < 1)
+                return fail(AAQAOA_ERR_INVALID_ARG, "edge %d has weight %d < 1", i, edge_weight[i]);
+            w[i] = edge_weight[i];
+        }
+        wsum += w[i];
+    }
+    if (wsum > MAXTAB - 1)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "total edge weight %lld exceeds the phase-table limit %d", wsum,
+                    MAXTAB - 1);
     if (num_orbits < 0)
         return fail(AAQAOA_ERR_BAD_ORBITS, "num_orbits=%d < 0", num_orbits);
     if (num_orbits > 0) {
@@ -742,6 +765,10 @@ int aaqaoa_prepare(int n, int num_edges, const int32_t *edges, int num_orbits, c
                     return fail(AAQAOA_ERR_BAD_ORBITS, "orbit %d has %d edges but weight %d", c, count[c],
                                 orbit_weight[c]);
             }
+            for (int i = 0; i < num_edges; i++)  // automorphisms of a weighted graph keep edge weights
+                if (w[i] != w[orbit_rep[edge_orbit[i]]])
+                    return fail(AAQAOA_ERR_BAD_ORBITS, "orbit %d mixes edge weights %d and %d", edge_orbit[i], w[i],
+                                w[orbit_rep[edge_orbit[i]]]);
         }
     } else if (edge_orbit) {
         return fail(AAQAOA_ERR_BAD_ORBITS, "edge_orbit given without orbits");
@@ -761,15 +788,16 @@ int aaqaoa_prepare(int n, int num_edges, const int32_t *edges, int num_orbits, c
     if (edge_orbit)
         pl->edge_orbit.assign(edge_orbit, edge_orbit + num_edges);
     pl->stream = (cudaStream_t)stream;
-    for (int u = 0; u < n; u++)
-        pl->cost.nbr[u] = adj[u];
+    pl->edge_w = w;
+    pl->wsum = (int)wsum;
     std::vector<std::pair<std::pair<int, int>, int>> full, red;
     for (int i = 0; i < num_edges; i++)
-        full.push_back({{e[2 * i], e[2 * i + 1]}, 1});
+        full.push_back({{e[2 * i], e[2 * i + 1]}, w[i]});
     for (int c = 0; c < num_orbits; c++) {
         const int i = orbit_rep[c];
-        red.push_back({{e[2 * i], e[2 * i + 1]}, orbit_weight[c]});
+        red.push_back({{e[2 * i], e[2 * i + 1]}, orbit_weight[c] * w[i]});
     }
+    pl->cost = make_cutfn(n, full);
     pl->obs[AAQAOA_OBS_FULL] = make_cutfn(n, full);
     pl->obs[AAQAOA_OBS_RED] = make_cutfn(n, red);
     build_passes(pl);
@@ -1807,7 +1835,7 @@ int aaqaoa_prepare_multi(int G, const aaqaoa_graph_desc *graphs, int p, unsigned
                 }
             }
             for (int u = 0; u < MAXN; u++)
-                sg.cost[u] = pl->cost.nbr[u];
+                sg.cost[u] = pl->cost.nbr[0][u];
             m->desc.push_back(sg);
             m->small_idx.push_back(gi);
             m->small_max_n = std::max(m->small_max_n, pl->n);

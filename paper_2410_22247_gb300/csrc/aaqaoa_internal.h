@@ -21,10 +21,9 @@ struct CutFn {
     uint64_t nbr[MAXK][MAXN];
 };
 
-// The cost function C(x) of the ansatz: one class, unit weight.
-struct CostFn {
-    uint64_t nbr[MAXN];
-};
+// The cost function C(x) of the ansatz: one class at weight 1 for MaxCut;
+// integer edge weights grouped into classes for weighted MaxCut.
+using CostFn = CutFn;
 
 // Operations of one tiled pass over the statevector(s).
 enum PostOp : int {

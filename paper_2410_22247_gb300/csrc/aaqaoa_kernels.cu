@@ -250,27 +250,6 @@ __device__ __forceinline__ void finish_cut(int base, const int (&d)[RB], const i
 }
 
 template <int RB>
-__device__ __forceinline__ void eval_cost(const CostFn &f, int n, uint64_t x0, const int (&gp)[RB],
-                                          int (&v)[1 << RB])
-{
-    int base = 0;
-    for (int u = 0; u < n; u++) {
-        const uint64_t nb = f.nbr[u];
-        base += ((x0 >> u) & 1ull) ? __popcll(nb & ~x0) : 0;
-    }
-    int d[RB], W[RB][RB];
-#pragma unroll
-    for (int k = 0; k < RB; k++) {
-        const uint64_t nb = f.nbr[gp[k]];
-        d[k] = __popcll(nb) - 2 * __popcll(nb & x0);
-#pragma unroll
-        for (int k2 = 0; k2 < RB; k2++)
-            W[k][k2] = (int)((nb >> gp[k2]) & 1ull);
-    }
-    finish_cut<RB>(base, d, W, v);
-}
-
-template <int RB>
 __device__ __forceinline__ void eval_cut(const CutFn &f, int n, uint64_t x0, const int (&gp)[RB], int (&v)[1 << RB])
 {
     int base = 0, d[RB], W[RB][RB];
@@ -413,7 +392,7 @@ template <typename R, int NV>
 __host__ __device__ constexpr size_t pass_smem_total()
 {
     return (size_t)Geo<R, NV>::NSTAGE * NV * tile_bytes<R, NV>() + 2 * (size_t)MAXTAB * sizeof(R) * 2 +
-           (size_t)(MAXK + 1) * MAXN * 8 + 1024;
+           (size_t)(2 * MAXK) * MAXN * 8 + 1024;
 }
 // static shared memory of the pass kernel (mbarriers, per-point sums, cut
 // constants) plus slack for the final reduction's flag
@@ -421,7 +400,7 @@ template <typename R, int NV>
 __host__ __device__ constexpr size_t pass_static_smem()
 {
     using G = Geo<R, NV>;
-    return 2 * G::NSTAGE * 8 + 2 * 2 * 32 * 8 + 4 + MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
+    return 2 * G::NSTAGE * 8 + 2 * 2 * 32 * 8 + 4 + 2 * MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
            2 * (G::RB + 1) * G::NTHR * 4 + 2 * 2 * 32 * 4 + 256;
 }
 static_assert(pass_smem_total<float, 1>() + pass_static_smem<float, 1>() <= 227 * 1024, "c64 pipeline smem");
@@ -901,7 +880,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     __shared__ __align__(8) uint64_t full[NS], done[NS];
     __shared__ double pred[2][2][32];  // per-warp sums of a finished point, two buffers
     __shared__ int s_flag;
-    __shared__ int obs_w[MAXK];
+    __shared__ int obs_w[MAXK], cost_w[MAXK];
     __shared__ int tcs[NS][2][16];                  // per buffer: O(f) and h_u(f) of its tile
     __shared__ int ptc[2 * (G::RB + 1) * NTHR];     // per thread: t-only terms of each function
     __shared__ int qr[2][32];                       // per function: register-pair terms
@@ -910,7 +889,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     const int tid = threadIdx.x;
     C *tab = reinterpret_cast<C *>(sm + (size_t)NS * NV * TB);
     uint64_t *cost_nbr = reinterpret_cast<uint64_t *>(tab + 2 * MAXTAB);  // two table slots
-    uint64_t *obs_nbr = cost_nbr + MAXN;
+    uint64_t *obs_nbr = cost_nbr + MAXK * MAXN;
 
     const unsigned total = (unsigned)A.tiles * (unsigned)A.B;
     const unsigned grid = gridDim.x;
@@ -929,12 +908,14 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         }
         fence_barrier_init();
     }
-    for (int i = tid; i < MAXN; i += blockDim.x)
-        cost_nbr[i] = A.cost.nbr[i];
+    for (int i = tid; i < A.cost.K * MAXN; i += blockDim.x)
+        cost_nbr[i] = A.cost.nbr[i / MAXN][i % MAXN];
     for (int i = tid; i < A.obs.K * MAXN; i += blockDim.x)
         obs_nbr[i] = A.obs.nbr[i / MAXN][i % MAXN];
-    if (tid < MAXK)
+    if (tid < MAXK) {
         obs_w[tid] = A.obs.w[tid];
+        cost_w[tid] = A.cost.w[tid];
+    }
     __syncthreads();
     if (s_flag)
         return;
@@ -958,11 +939,12 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     // vertex of local tile bit L, and the weight of edge (u, v) in function e
     auto gq = [&](int L) { return L < A.cb ? L : A.s + L - A.cb; };
     auto wgt = [&](int e, int u, int v) -> int {
-        if (e == 0)
-            return (int)((cost_nbr[u] >> v) & 1ull);
+        const uint64_t *nb = e == 0 ? cost_nbr : obs_nbr;
+        const int *ww = e == 0 ? cost_w : obs_w;
+        const int K = e == 0 ? A.cost.K : A.obs.K;
         int w = 0;
-        for (int c = 0; c < A.obs.K; c++)
-            w += obs_w[c] * (int)((obs_nbr[c * MAXN + u] >> v) & 1ull);
+        for (int c = 0; c < K; c++)
+            w += ww[c] * (int)((nb[c * MAXN + u] >> v) & 1ull);
         return w;
     };
     if (tid < NTHR) {  // launch constants of the quadratic decomposition
@@ -1021,11 +1003,11 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             for (int e = 0; e < 2; e++) {
                 if (est[e] < 0)
                     continue;
-                const int K = e == 0 ? 1 : A.obs.K;
+                const int K = e == 0 ? A.cost.K : A.obs.K;
                 int hs = 0, os = 0;
                 for (int c = 0; c < K; c++) {
-                    const uint64_t *nb = e == 0 ? cost_nbr : obs_nbr + c * MAXN;
-                    const int w = e == 0 ? 1 : obs_w[c];
+                    const uint64_t *nb = (e == 0 ? cost_nbr : obs_nbr) + c * MAXN;
+                    const int w = e == 0 ? cost_w[c] : obs_w[c];
                     if (lane < G::T) {
                         const uint64_t m = nb[gq(lane)];
                         hs += w * (__popcll(m) - 2 * __popcll(m & f));
@@ -1323,14 +1305,6 @@ __global__ void k_params(int B, int p, int tab_len, int n, const double *__restr
 }
 
 // --------------------------------------------- whole circuit in one CTA
-__device__ __forceinline__ int cost_direct(const CostFn &f, int n, uint32_t x)
-{
-    int c = 0;
-    for (int u = 0; u < n; u++)
-        c += ((x >> u) & 1u) ? __popcll(f.nbr[u] & ~(uint64_t)x) : 0;
-    return c;
-}
-
 __device__ __forceinline__ int cut_direct(const CutFn &f, int n, uint32_t x)
 {
     int v = 0;
@@ -1366,7 +1340,7 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallArgs
         const R c = (R)cs.x, s = (R)cs.y;
         __syncthreads();
         for (int x = tid; x < N; x += NT)
-            phi[x] = cmul(phi[x], tab[cost_direct(A.cost, n, (uint32_t)x)]);
+            phi[x] = cmul(phi[x], tab[cut_direct(A.cost, n, (uint32_t)x)]);
         for (int q = 0; q < n; q++) {
             __syncthreads();
             for (int j = tid; j < half; j += NT) {
@@ -1416,7 +1390,7 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallArgs
         }
         __syncthreads();
         for (int x = tid; x < N; x += NT) {
-            const int cv = cost_direct(A.cost, n, (uint32_t)x);
+            const int cv = cut_direct(A.cost, n, (uint32_t)x);
             gg += (double)((R)cv * im_conj_mul(lam[x], phi[x]));
             if (l > 0) {
                 const C t = tab[cv];
@@ -1875,7 +1849,7 @@ __global__ void k_untwist(typename CT<R>::T *psi, int n, const double2 *cs, int 
 // ------------------------------------------------------- maximum cut
 // C_max = max_x C(x) by exhaustion with no memory traffic: each thread takes
 // blocks of 32 states x0 | r (r over qubits 0..4) and evaluates them with the
-// base-plus-deltas form of eval_cost. Only x with the top bit clear are
+// base-plus-deltas form of eval_cut. Only x with the top bit clear are
 // visited (C(x) = C(~x), and the smallest maximiser has that bit clear). The
 // result is packed as (value << 35) | (2^35 - 1 - x), so one atomicMax keeps
 // the largest value and, among equal values, the smallest x, in any order.
@@ -1889,8 +1863,12 @@ __global__ void __launch_bounds__(256) k_maxcut(const __grid_constant__ CostFn c
         if (blockIdx.x == 0 && threadIdx.x < (1u << nb)) {
             const uint64_t x = threadIdx.x;
             int c = 0;
-            for (int u = 0; u < n; u++)
-                c += ((x >> u) & 1ull) ? __popcll(cost.nbr[u] & ~x) : 0;
+            for (int cl = 0; cl < cost.K; cl++) {
+                int s = 0;
+                for (int u = 0; u < n; u++)
+                    s += ((x >> u) & 1ull) ? __popcll(cost.nbr[cl][u] & ~x) : 0;
+                c += cost.w[cl] * s;
+            }
             best = pack(c, x);
         }
     } else {
@@ -1900,7 +1878,7 @@ __global__ void __launch_bounds__(256) k_maxcut(const __grid_constant__ CostFn c
              blk += (uint64_t)gridDim.x * blockDim.x) {
             const uint64_t x0 = blk << 5;
             int v[32];
-            eval_cost<5>(cost, n, x0, gp, v);
+            eval_cut<5>(cost, n, x0, gp, v);
 #pragma unroll
             for (int m = 0; m < 32; m++) {
                 const unsigned long long q = pack(v[m], x0 | (uint64_t)m);
@@ -2047,8 +2025,12 @@ __global__ void __launch_bounds__(256) k_sample_draw(const typename CT<R>::T *ps
             x_out[k] = x;
             if (cut_out) {
                 int v = 0;
-                for (int q = 0; q < n; q++)
-                    v += ((x >> q) & 1ull) ? __popcll(cost.nbr[q] & ~x) : 0;
+                for (int cl = 0; cl < cost.K; cl++) {
+                    int s = 0;
+                    for (int q = 0; q < n; q++)
+                        s += ((x >> q) & 1ull) ? __popcll(cost.nbr[cl][q] & ~x) : 0;
+                    v += cost.w[cl] * s;
+                }
                 cut_out[k] = v;
             }
         }

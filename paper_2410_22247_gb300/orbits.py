@@ -47,11 +47,15 @@ def _rank(keys):
     return [order[k] for k in keys]
 
 
-def _refine(adj, col):
-    """Colour refinement to the coarsest equitable partition refining ``col``."""
+def _refine(adj, col, wadj=None):
+    """Colour refinement to the coarsest equitable partition refining ``col``
+    (with edge weights, a neighbour counts with the weight of its edge)."""
     ncells = len(set(col))
     while True:
-        sig = [(col[v], tuple(sorted(col[u] for u in adj[v]))) for v in range(len(col))]
+        if wadj is None:
+            sig = [(col[v], tuple(sorted(col[u] for u in adj[v]))) for v in range(len(col))]
+        else:
+            sig = [(col[v], tuple(sorted((col[u], w) for u, w in wadj[v]))) for v in range(len(col))]
         new = _rank(sig)
         k = len(set(new))
         if k == ncells:
@@ -59,9 +63,9 @@ def _refine(adj, col):
         col, ncells = new, k
 
 
-def _individualise(adj, col, v):
+def _individualise(adj, col, v, wadj=None):
     keys = [(col[u], 0 if u == v else 1) for u in range(len(col))]
-    return _refine(adj, _rank(keys))
+    return _refine(adj, _rank(keys), wadj)
 
 
 def _target_cell(col):
@@ -82,10 +86,15 @@ def _cell_sizes(col):
 
 
 def is_automorphism(perm, edge_set) -> bool:
-    """True when the vertex permutation maps the edge set onto itself."""
+    """True when the vertex permutation maps the edge set onto itself (and,
+    when ``edge_set`` maps edges to weights, every edge to one of equal weight)."""
+    weighted = isinstance(edge_set, dict)
     for u, v in edge_set:
         a, b = perm[u], perm[v]
-        if (min(a, b), max(a, b)) not in edge_set:
+        img = (min(a, b), max(a, b))
+        if img not in edge_set:
+            return False
+        if weighted and edge_set[img] != edge_set[(u, v)]:
             return False
     return True
 
@@ -107,21 +116,31 @@ def _orbit_ids(n, gens):
     return [find(a) for a in range(n)]
 
 
-def automorphism_generators(n, edges):
-    """A generating set of Aut(G) as a list of permutations (lists of length n)."""
+def automorphism_generators(n, edges, weights=None):
+    """A generating set of Aut(G) as a list of permutations (lists of length n);
+    with integer edge weights, of the weight-preserving automorphisms."""
     edges = [tuple(map(int, e)) for e in np.asarray(edges).reshape(-1, 2)]
-    edge_set = {(min(u, v), max(u, v)) for u, v in edges}
+    if weights is None:
+        edge_set = {(min(u, v), max(u, v)) for u, v in edges}
+        wadj = None
+    else:
+        wl = [int(w) for w in np.asarray(weights).reshape(-1)]
+        edge_set = {(min(u, v), max(u, v)): w for (u, v), w in zip(edges, wl)}
+        wadj = [[] for _ in range(n)]
+        for (u, v), w in zip(edges, wl):
+            wadj[u].append((v, w))
+            wadj[v].append((u, w))
     adj = _adjacency(n, edges)
     if n == 0:
         return []
-    col = _refine(adj, [0] * n)
+    col = _refine(adj, [0] * n, wadj)
     path = []
     while True:
         cell = _target_cell(col)
         if cell is None:
             break
         path.append((col, cell, cell[0]))
-        col = _individualise(adj, col, cell[0])
+        col = _individualise(adj, col, cell[0], wadj)
     leaf0 = col
     inv0 = [0] * n
     for v, c in enumerate(leaf0):
@@ -144,7 +163,7 @@ def automorphism_generators(n, edges):
             g = leaf_map(col)
             return g if is_automorphism(g, edge_set) else None
         for x in cell:
-            r = search(_individualise(adj, col, x), depth + 1)
+            r = search(_individualise(adj, col, x, wadj), depth + 1)
             if r is not None:
                 return r
         return None
@@ -158,7 +177,7 @@ def automorphism_generators(n, edges):
             orb = _orbit_ids(n, gens)
             if orb[w] == orb[v_k]:
                 continue
-            g = search(_individualise(adj, col_k, w), level + 1)
+            g = search(_individualise(adj, col_k, w, wadj), level + 1)
             if g is not None:
                 assert is_automorphism(g, edge_set)
                 gens.append(g)
@@ -183,15 +202,16 @@ class EdgeOrbits:
         return len(self.rep)
 
 
-def edge_orbits(n, edges, generators=None) -> EdgeOrbits:
-    """Algorithm 1: breadth-first closure of the edges under the generators."""
+def edge_orbits(n, edges, generators=None, weights=None) -> EdgeOrbits:
+    """Algorithm 1: breadth-first closure of the edges under the generators
+    (of the weight-preserving automorphisms when integer edge weights are given)."""
     edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
     canon = [(int(min(u, v)), int(max(u, v))) for u, v in edges]
     if canon != sorted(canon):
         raise ValueError("edges must be in canonical sorted order (u < v, lexicographic)")
     index = {e: i for i, e in enumerate(canon)}
     if generators is None:
-        generators = automorphism_generators(n, edges)
+        generators = automorphism_generators(n, edges, weights)
     m = len(canon)
     cls = np.full(m, -1, dtype=np.int64)
     reps, weights = [], []

@@ -47,13 +47,15 @@ def _op_on(n, q, a):
     return m
 
 
-def dense_state(n, edges, gamma, beta):
+def dense_state(n, edges, gamma, beta, weights=None):
     X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
     Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
     dim = 1 << n
     HC = np.zeros((dim, dim), dtype=np.complex128)
-    for u, v in np.asarray(edges).reshape(-1, 2):
-        HC += 0.5 * (np.eye(dim) - _op_on(n, int(u), Z) @ _op_on(n, int(v), Z))
+    e = np.asarray(edges).reshape(-1, 2)
+    w = np.ones(len(e)) if weights is None else np.asarray(weights, dtype=np.float64)
+    for (u, v), we in zip(e, w):
+        HC += 0.5 * we * (np.eye(dim) - _op_on(n, int(u), Z) @ _op_on(n, int(v), Z))
     HM = sum(_op_on(n, q, X) for q in range(n))
     psi = np.ones(dim, dtype=np.complex128) / math.sqrt(dim)
     for g, b in zip(gamma, beta):
@@ -186,3 +188,19 @@ ALL_CHECKS = {
     "finite_difference": check_finite_difference,
     "invariants": check_invariants,
 }
+
+
+def check_weighted():
+    """Integer edge weights: the oracle's state against dense exponentials of
+    the weighted H_C, and the scaling E_{c w}(gamma, beta) = c E_w(c gamma, beta)
+    for a uniform factor c (the phase sees c*gamma, the observable c)."""
+    worst = 0.0
+    for k, (n, e) in enumerate(small_graphs()):
+        w = W.rng(200 + k).integers(1, 5, size=len(e))
+        g, b = W.random_angles(2, 300 + k)
+        ref = dense_state(n, e, g, b, w)
+        worst = max(worst, float(np.max(np.abs(O.qaoa_state_w(n, e, w, g, b) - ref))))
+        E1 = O.energy_grad_w(n, e, w, g, b)[0]
+        E3 = O.energy_grad_w(n, e, 3 * w, np.asarray(g) / 3.0, b)[0]
+        worst = max(worst, abs(E3 - 3.0 * E1) / max(abs(E1), 1.0))
+    return worst

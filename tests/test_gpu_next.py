@@ -131,3 +131,77 @@ def test_adam_reaches_ring_p1_optimum():
     assert abs(hist[-1] / len(e) - 0.75) < 1e-4
     assert abs(CF.energy_p1(n, e, gam[0], bet[0]) / len(e) - 0.75) < 1e-4
     assert hist[10] > hist[0]
+
+
+def wplan(n, e, w, p, precision, orbits=True, grad=True):
+    from paper_2410_22247_gb300.api import Plan
+    orb = ORB.edge_orbits(n, e, weights=w) if orbits else None
+    return Plan(n, e, p, orbits=orb, precision=precision, with_grad=grad, weights=w)
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("case", ["prufer14_rand", "reg3_20_rand", "star22_orbit", "tree24_depth", "k8_rand"])
+def test_weighted_maxcut_energy_and_gradient(prec, case):
+    """Weighted MaxCut (integer weights): energy and adjoint gradient against the
+    weighted oracle, with H_C and with H_red from weight-preserving orbits."""
+    if case == "prufer14_rand":
+        n, e = W.prufer_tree(14, 5)
+        w = W.rng(1).integers(1, 5, size=len(e))
+    elif case == "reg3_20_rand":
+        n, e = W.random_regular(20, 3, 6)
+        w = W.rng(2).integers(1, 4, size=len(e))
+    elif case == "star22_orbit":
+        n, e = W.star_graph(22)
+        w = np.full(len(e), 3)
+    elif case == "tree24_depth":
+        n, e = W.heap_binary_tree(24)
+        w = np.array([1 + int(np.floor(np.log2(int(v) + 1))) % 3 for _, v in e])
+    else:
+        n, e = W.complete_graph(8)
+        w = W.rng(3).integers(1, 6, size=len(e))
+    g, b = W.random_angles(2, 17)
+    pl = wplan(n, e, w, 2, prec)
+    if case == "star22_orbit":
+        # uniform weight 3: E_w(gamma, beta) = 3 E(3 gamma, beta) (pinned on the
+        # CPU), with E from the exact symmetric-subspace model. The plain C
+        # oracle's sequential sums over 2^22 terms carry ~2^n eps relative error
+        # on this case's large gradient components, more than 1e-10.
+        E1, dg1, db1 = SYM.energy_grad(SYM.star_model(n), 3 * np.asarray(g), b)
+        Er, dgr, dbr = 3 * E1, 9 * dg1, 3 * db1
+    else:
+        Er, dgr, dbr = O.energy_grad_w(n, e, w, g, b)
+    tol = {"c64": 1e-5, "c128": 1e-10}[prec]
+    scale = max(abs(Er), 1.0) if prec == "c64" else 1e-3 * abs(Er)
+    for obs in ("full", "red"):
+        E, dg, db = pl.grad(g, b, obs)
+        assert abs(E - Er) <= tol * max(abs(Er), 1.0), obs
+        for x, r in zip(np.concatenate([dg, db]), np.concatenate([dgr, dbr])):
+            assert abs(x - r) <= tol * max(abs(r), scale), obs
+        assert abs(pl.expect(g, b, obs) - Er) <= tol * max(abs(Er), 1.0)
+    for mode in ("singlepass", "perterm"):
+        pl.expect(g, b, "full", "singlepass")
+        assert abs(pl.aggregate_only("red", mode) - Er) <= tol * max(abs(Er), 1.0)
+
+
+def test_weighted_max_cut_and_samples():
+    n, e = W.random_regular(18, 3, 7)
+    w = W.rng(4).integers(1, 5, size=len(e))
+    pl = wplan(n, e, w, 1, "c128", grad=False)
+    assert pl.max_cut() == O.max_cut_w(n, e, w)
+    g, b = [0.4], [0.3]
+    x, cut = pl.sample(g, b, W.rng(6).uniform(0, 1, 500))
+    we = O.weighted_cost_edges(e, w)
+    assert all(cut[i] == O.cut_value(we, int(x[i])) for i in range(500))
+
+
+def test_weighted_prepare_errors():
+    from paper_2410_22247_gb300._native import AAQAOAError
+    from paper_2410_22247_gb300.api import Plan
+    n, e = W.cycle_graph(6)
+    with pytest.raises(AAQAOAError, match="INVALID_ARG"):
+        Plan(n, e, 1, weights=[1, 1, 0, 1, 1, 1], with_grad=False)
+    with pytest.raises(AAQAOAError, match="UNSUPPORTED"):
+        Plan(n, e, 1, weights=[100] * 6, with_grad=False)
+    orb = ORB.edge_orbits(n, e)  # one orbit of the unweighted cycle
+    with pytest.raises(AAQAOAError, match="BAD_ORBITS"):
+        Plan(n, e, 1, orbits=orb, weights=[1, 2, 1, 2, 1, 2], with_grad=False)

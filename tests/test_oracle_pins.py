@@ -97,3 +97,19 @@ def test_inverse_cdf_sampler(oracle_lib):
     x = O.sample(psi, (np.arange(K) + 0.5) / K)
     counts = np.bincount(x.astype(np.int64), minlength=1 << n)
     assert np.all(np.abs(counts - K * p) <= 1.0 + 1e-9)
+
+
+def test_weighted_oracle_matches_dense_and_scaling(oracle_lib):
+    assert P.check_weighted() < 1e-11
+
+
+def test_weighted_max_cut_pins(oracle_lib):
+    # uniform weight c scales every cut by c; a path with weights (1, 5, 1)
+    # cuts all three edges (bipartite)
+    n, e = W.cycle_graph(7)
+    assert O.max_cut_w(n, e, [3] * 7)[0] == 3 * O.max_cut(n, e)[0]
+    path = W.canonical_edges([(0, 1), (1, 2), (2, 3)])
+    assert O.max_cut_w(4, path, [1, 5, 1])[0] == 7
+    # triangle with weights (1, 2, 3): the best cut leaves out the lightest edge
+    tri = W.canonical_edges([(0, 1), (0, 2), (1, 2)])
+    assert O.max_cut_w(3, tri, [1, 2, 3])[0] == 5

@@ -125,3 +125,27 @@ def test_native_finder_rejects_bad_edges():
         assert N.aaqaoa_edge_orbits(4, 2, P(e), P(out), ctypes.byref(k), P(out), P(out)) == -1
     e = np.array([0, 1], dtype=np.int32)
     assert N.aaqaoa_edge_orbits(65, 1, P(e), P(out), ctypes.byref(k), P(out), P(out)) == -1
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_weighted_orbits_match_brute_force(k):
+    """Weight-preserving automorphisms (weighted MaxCut): the finder's classes
+    against brute force over all permutations, for seeded integer weights and
+    for weights constant on the unweighted orbits (where nothing splits)."""
+    n, e = SMALL[k]
+    for mode in ("random", "orbit"):
+        if mode == "random":
+            w = W.rng(40 + k).integers(1, 3, size=len(e))
+        else:
+            base = ORB.edge_orbits(n, e)
+            w = (base.edge_orbit % 3 + 1).astype(np.int64)
+        res = ORB.edge_orbits(n, e, weights=w)
+        canon = [tuple(map(int, x)) for x in e]
+        mine = {frozenset(canon[i] for i in range(len(canon)) if res.edge_orbit[i] == c)
+                for c in range(res.num_orbits)}
+        ref, _ = AUT.edge_orbit_partition(n, e, w)
+        assert mine == ref, mode
+        for c in range(res.num_orbits):  # one weight per class
+            assert len({int(w[i]) for i in range(len(e)) if res.edge_orbit[i] == c}) == 1
+        if mode == "orbit":
+            assert res.num_orbits == ORB.edge_orbits(n, e).num_orbits
