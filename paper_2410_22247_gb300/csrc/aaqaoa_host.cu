@@ -144,6 +144,7 @@ struct aaqaoa_plan {
     bool small() const { return n <= T(); }
     int tiles() const { return small() ? 1 : 1 << (n - T()); }
     int *err_shared = nullptr;  // set when the plan is part of a multi-graph batch
+    const GraphFns *pt_dev = nullptr;  // set for a group of same-n graphs: point b is graph b
     int *d_err() const { return err_shared ? err_shared : reinterpret_cast<int *>(ws + L.ctrl); }
     unsigned *d_counter_pass() const { return reinterpret_cast<unsigned *>(ws + L.ctrl + 8); }
     unsigned *d_counter_agg() const { return reinterpret_cast<unsigned *>(ws + L.ctrl + 16); }
@@ -355,6 +356,8 @@ PassArgs base_args(const aaqaoa_plan *pl, int obs)
     a.err = pl->d_err();
     a.obs = pl->obs[obs];
     a.cost = pl->cost;
+    a.pt = pl->pt_dev;
+    a.pt_obs = obs;
     return a;
 }
 
@@ -1616,12 +1619,23 @@ struct aaqaoa_multi {
     cudaStream_t cap = nullptr;     // private stream the evaluation is captured on
     std::vector<aaqaoa_plan *> plans;  // one per graph (validation + host tables)
     std::vector<int> small_idx, large_idx;
+    // Graphs too large for one CTA run in groups of equal n: one batched pass
+    // sequence per group, point b of the group being its b-th graph. Rows of
+    // the parameter and energy arrays follow `order` (small graphs first,
+    // then each group's members), so a group's rows are contiguous.
+    struct Group {
+        int n = 0, row0 = 0;
+        std::vector<int> members;
+        aaqaoa_plan *pl = nullptr;
+        size_t off_fns = 0, off_ws = 0, ws_bytes = 0;
+    };
+    std::vector<Group> groups;
+    std::vector<int> order;  // graph index of each row
     std::vector<SmallGraph> desc;       // small graphs, in small_idx order
     int small_max_n = 1, small_max_tab = 1;
     unsigned char *ws = nullptr;
     size_t ws_bytes = 0;
     size_t off_params = 0, off_energy = 0, off_desc = 0, off_err = 0;
-    std::vector<size_t> sub_off, sub_bytes;
     std::vector<cudaStream_t> side;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
@@ -1645,13 +1659,13 @@ size_t multi_layout(aaqaoa_multi *m)
     off = align256(off + (size_t)m->G * sizeof(double));
     m->off_desc = off;
     off = align256(off + (m->desc.size() + 1) * sizeof(SmallGraph));
-    m->sub_off.clear();
-    m->sub_bytes.clear();
-    for (int gi : m->large_idx) {
+    for (auto &g : m->groups) {
+        g.off_fns = off;
+        off = align256(off + g.members.size() * sizeof(GraphFns));
         size_t b = 0;
-        aaqaoa_workspace_bytes(m->plans[gi], 1, 0, &b);
-        m->sub_off.push_back(off);
-        m->sub_bytes.push_back(b);
+        aaqaoa_workspace_bytes(g.pl, (int)g.members.size(), 0, &b);
+        g.off_ws = off;
+        g.ws_bytes = b;
         off = align256(off + b);
     }
     return off;
@@ -1660,6 +1674,8 @@ size_t multi_layout(aaqaoa_multi *m)
 // everything one evaluation enqueues, on `origin` (+ side streams)
 int multi_enqueue(aaqaoa_multi *m, int obs, int branches, cudaStream_t origin)
 {
+    if (branches > (int)m->side.size())
+        branches = (int)m->side.size();
     double *d_par = reinterpret_cast<double *>(m->ws + m->off_params);
     double *d_en = reinterpret_cast<double *>(m->ws + m->off_energy);
     const size_t Gp = (size_t)m->G * m->p;
@@ -1674,18 +1690,21 @@ int multi_enqueue(aaqaoa_multi *m, int obs, int branches, cudaStream_t origin)
             "small-graph batch kernel");
         m->launches++;
     }
-    for (size_t j = 0; j < m->large_idx.size(); j++) {
-        const int gi = m->large_idx[j];
-        aaqaoa_plan *pl = m->plans[gi];
+    for (size_t j = 0; j < m->groups.size(); j++) {
+        auto &g = m->groups[j];
+        aaqaoa_plan *pl = g.pl;
+        const int B = (int)g.members.size();
         cudaStream_t st = branches > 0 ? m->side[j % branches] : origin;
         pl->stream = st;
         pl->launches = 0;
-        int r = enqueue_expect(pl, 1, d_par + (size_t)gi * m->p, d_par + Gp + (size_t)gi * m->p, obs,
+        int r = enqueue_expect(pl, B, d_par + (size_t)g.row0 * m->p, d_par + Gp + (size_t)g.row0 * m->p, obs,
                                AAQAOA_AGG_FUSED);
         if (r)
             return r;
         m->launches += pl->launches;
-        CK(cudaMemcpyAsync(d_en + gi, pl->d_out(), sizeof(double), cudaMemcpyDeviceToDevice, st));
+        // energies: column 0 of the group's [B][1+2p] output rows
+        CK(cudaMemcpy2DAsync(d_en + g.row0, sizeof(double), pl->d_out(), pl->out_stride() * sizeof(double),
+                             sizeof(double), B, cudaMemcpyDeviceToDevice, st));
     }
     for (int b = 0; b < branches; b++) {
         CK(cudaEventRecord(m->join[b], m->side[b]));
@@ -1731,8 +1750,8 @@ std::string multi_signature(const aaqaoa_multi *m, int obs)
     char buf[64];
     snprintf(buf, sizeof buf, "|%d|%d|%d|", m->c128 ? 128 : 64, m->p, obs);
     sig += buf;
-    for (int gi : m->large_idx) {
-        snprintf(buf, sizeof buf, "%d,", m->plans[gi]->n);
+    for (auto &g : m->groups) {
+        snprintf(buf, sizeof buf, "%dx%d,", g.n, (int)g.members.size());
         sig += buf;
     }
     return sig;
@@ -1741,7 +1760,7 @@ std::string multi_signature(const aaqaoa_multi *m, int obs)
 // choose the branch count by timing each candidate graph (3 launches each)
 int multi_autotune(aaqaoa_multi *m, int obs)
 {
-    const int L = (int)m->large_idx.size();
+    const int L = (int)m->groups.size();  // independent branches: one per group, at most one side stream each
     const std::string sig = multi_signature(m, obs);
     auto &cache = autotune_cache();
     const char *env = getenv("AAQAOA_AUTOTUNE");
@@ -1754,7 +1773,7 @@ int multi_autotune(aaqaoa_multi *m, int obs)
         CK(cudaEventCreate(&a));
         CK(cudaEventCreate(&b));
         float best_ms = 1e30f;
-        for (int br = 1; br <= MULTI_MAX_BRANCHES && br <= L; br *= 2) {
+        for (int br = 1; br <= (int)m->side.size() && br <= L; br *= 2) {
             cudaGraphExec_t ex = nullptr;
             int r = multi_capture(m, obs, br, &ex);
             if (r) {
@@ -1823,7 +1842,7 @@ int aaqaoa_prepare_multi(int G, const aaqaoa_graph_desc *graphs, int p, unsigned
         if (pl->small()) {
             SmallGraph sg;
             memset(&sg, 0, sizeof sg);
-            sg.gi = gi;
+            sg.gi = (int)m->small_idx.size();  // its row: small graphs come first
             sg.n = pl->n;
             sg.tab_len = pl->tab_len();
             for (int o = 0; o < 2; o++) {
@@ -1844,7 +1863,29 @@ int aaqaoa_prepare_multi(int G, const aaqaoa_graph_desc *graphs, int p, unsigned
             m->large_idx.push_back(gi);
         }
     }
-    const int nb = std::min<int>(MULTI_MAX_BRANCHES, std::max<int>(1, (int)m->large_idx.size()));
+    // rows: small graphs, then the large ones grouped by n (ascending)
+    m->order = m->small_idx;
+    std::map<int, std::vector<int>> by_n;
+    for (int gi : m->large_idx)
+        by_n[m->plans[gi]->n].push_back(gi);
+    for (auto &kv : by_n) {
+        aaqaoa_multi::Group g;
+        g.n = kv.first;
+        g.row0 = (int)m->order.size();
+        g.members = kv.second;
+        const aaqaoa_graph_desc &d = graphs[g.members[0]];
+        int r = aaqaoa_prepare(d.n, d.num_edges, d.edges, d.num_orbits, d.orbit_rep, d.orbit_weight, nullptr, p,
+                               flags, stream, &g.pl);
+        if (r) {
+            aaqaoa_destroy_multi(m);
+            return r;
+        }
+        for (int gi : g.members)  // tables long enough for every member's cut values
+            g.pl->wsum = std::max(g.pl->wsum, m->plans[gi]->wsum);
+        m->order.insert(m->order.end(), g.members.begin(), g.members.end());
+        m->groups.push_back(std::move(g));
+    }
+    const int nb = std::min<int>(MULTI_MAX_BRANCHES, std::max<int>(1, (int)m->groups.size()));
     for (int b = 0; b < nb; b++) {
         cudaStream_t s = nullptr;
         cudaEvent_t e = nullptr;
@@ -1889,12 +1930,22 @@ int aaqaoa_multi_set_workspace(aaqaoa_multi *m, void *device_ptr, size_t bytes)
             cudaGraphExecDestroy(m->exec[o]);
             m->exec[o] = nullptr;
         }
-    for (size_t j = 0; j < m->large_idx.size(); j++) {
-        aaqaoa_plan *pl = m->plans[m->large_idx[j]];
-        int r = aaqaoa_set_workspace(pl, m->ws + m->sub_off[j], m->sub_bytes[j], 1, 0);
+    for (auto &g : m->groups) {
+        int r = aaqaoa_set_workspace(g.pl, m->ws + g.off_ws, g.ws_bytes, (int)g.members.size(), 0);
         if (r)
             return r;
-        pl->err_shared = reinterpret_cast<int *>(m->ws + m->off_err);
+        g.pl->err_shared = reinterpret_cast<int *>(m->ws + m->off_err);
+        std::vector<GraphFns> fns(g.members.size());
+        for (size_t b = 0; b < g.members.size(); b++) {
+            const aaqaoa_plan *q = m->plans[g.members[b]];
+            fns[b].cost = q->cost;
+            fns[b].obs[0] = q->obs[0];
+            fns[b].obs[1] = q->obs[1];
+        }
+        CK(cudaMemcpyAsync(m->ws + g.off_fns, fns.data(), fns.size() * sizeof(GraphFns), cudaMemcpyHostToDevice,
+                           m->stream));
+        CK(cudaStreamSynchronize(m->stream));  // `fns` is a host temporary
+        g.pl->pt_dev = reinterpret_cast<const GraphFns *>(m->ws + g.off_fns);
     }
     CK(cudaMemsetAsync(m->ws, 0, 256, m->stream));
     if (!m->desc.empty())
@@ -1919,8 +1970,13 @@ int aaqaoa_expect_multi(aaqaoa_multi *m, const double *gamma, const double *beta
                 return fail(AAQAOA_ERR_INVALID_ARG, "H_red requested but graph %d has no edge orbits", gi);
     const size_t Gp = (size_t)m->G * m->p;
     double *d_par = reinterpret_cast<double *>(m->ws + m->off_params);
-    CK(cudaMemcpyAsync(d_par, gamma, Gp * sizeof(double), cudaMemcpyHostToDevice, m->stream));
-    CK(cudaMemcpyAsync(d_par + Gp, beta, Gp * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+    std::vector<double> rows(2 * Gp), en((size_t)m->G);
+    for (int r = 0; r < m->G; r++)
+        for (int l = 0; l < m->p; l++) {
+            rows[(size_t)r * m->p + l] = gamma[(size_t)m->order[r] * m->p + l];
+            rows[Gp + (size_t)r * m->p + l] = beta[(size_t)m->order[r] * m->p + l];
+        }
+    CK(cudaMemcpyAsync(d_par, rows.data(), 2 * Gp * sizeof(double), cudaMemcpyHostToDevice, m->stream));
     if (!m->exec[observable]) {
         // one direct run first (sets kernel attributes outside any capture)
         int r = multi_enqueue(m, observable, 0, m->stream);
@@ -1933,9 +1989,11 @@ int aaqaoa_expect_multi(aaqaoa_multi *m, const double *gamma, const double *beta
     CK(cudaGraphLaunch(m->exec[observable], m->stream));
     int err = 0;
     CK(cudaMemcpyAsync(&err, m->ws + m->off_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(energy, m->ws + m->off_energy, (size_t)m->G * sizeof(double), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(en.data(), m->ws + m->off_energy, (size_t)m->G * sizeof(double), cudaMemcpyDeviceToHost,
                        m->stream));
     CK(cudaStreamSynchronize(m->stream));
+    for (int r = 0; r < m->G; r++)
+        energy[m->order[r]] = en[r];
     if (err) {
         cudaMemsetAsync(m->ws, 0, 256, m->stream);
         cudaStreamSynchronize(m->stream);
@@ -1972,6 +2030,8 @@ void aaqaoa_destroy_multi(aaqaoa_multi *m)
         cudaStreamDestroy(m->cap);
     for (auto pl : m->plans)
         aaqaoa_destroy(pl);
+    for (auto &g : m->groups)
+        aaqaoa_destroy(g.pl);
     delete m;
 }
 

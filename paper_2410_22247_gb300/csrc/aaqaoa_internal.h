@@ -25,6 +25,13 @@ struct CutFn {
 // integer edge weights grouped into classes for weighted MaxCut.
 using CostFn = CutFn;
 
+// Cut functions of one graph of a batch of graphs with the same n: the cost
+// C(x) and the two observables (0 = H_C, 1 = H_red).
+struct GraphFns {
+    CutFn cost;
+    CutFn obs[2];
+};
+
 // Operations of one tiled pass over the statevector(s).
 enum PostOp : int {
     POST_REDUCE = 1,      // acc0 += |phi|^2 O(x)                 (energy)
@@ -68,6 +75,8 @@ struct PassArgs {
     int drop_first_load;  // test hook: CTA 0 never loads its first tile (bounded wait expires)
     CutFn obs;        // observable of the reduction / lambda
     CostFn cost;      // C(x) for the phase and dE/dgamma
+    const GraphFns *pt;  // non-null: point b is its own graph, pt[b] (obs and cost above unused)
+    int pt_obs;          // which observable of pt[b]
 };
 
 // Whole-circuit kernel for states that fit one CTA's shared memory.

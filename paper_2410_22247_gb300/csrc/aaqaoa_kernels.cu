@@ -401,7 +401,7 @@ __host__ __device__ constexpr size_t pass_static_smem()
 {
     using G = Geo<R, NV>;
     return 2 * G::NSTAGE * 8 + 2 * 2 * 32 * 8 + 4 + 2 * MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
-           2 * (G::RB + 1) * G::NTHR * 4 + 2 * 2 * 32 * 4 + 256;
+           2 * (G::RB + 1) * G::NTHR * 4 + 2 * 2 * 2 * 32 * 4 + 256;
 }
 static_assert(pass_smem_total<float, 1>() + pass_static_smem<float, 1>() <= 227 * 1024, "c64 pipeline smem");
 static_assert(pass_smem_total<float, 2>() + pass_static_smem<float, 2>() <= 227 * 1024, "c64 adjoint pipeline smem");
@@ -455,6 +455,13 @@ __device__ __forceinline__ void store_regs(typename CT<R>::T *sv, uint32_t sb,
             sv[sb ^ G::swz(reg_offset<G>(ST, m))] = a[m];
     }
 }
+
+// A cut function as neighbour masks nbr[c * MAXN + u] with class weights w[c].
+struct CutView {
+    const uint64_t *nbr;
+    const int *w;
+    int K;
+};
 
 // The pass's scalar controls, copied from the parameter space into registers
 // once per CTA.
@@ -864,11 +871,14 @@ __device__ void pass_final_reduce(const PassArgs &A, unsigned total)
 // the register stages. Per stage buffer s two mbarriers hand the buffer over:
 // full[s] (producer -> compute: tile loaded, or buffer free in a generating
 // pass) and done[s] (compute -> producer: results in shared memory).
-template <typename R, int NV, bool OPS>
+// MODE 0: mixer only; 1: with cut-function work on one graph; 2: the same
+// with point b of the batch being its own graph (A.pt[b]).
+template <typename R, int NV, int MODE>
 __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     k_pass(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
            const __grid_constant__ PassArgs A)
 {
+    constexpr bool OPS = MODE != 0, MG = MODE == 2;
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
     constexpr int NR = 1 << G::RB, NS = G::NSTAGE, NTHR = G::NTHR;
@@ -883,8 +893,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     __shared__ int obs_w[MAXK], cost_w[MAXK];
     __shared__ int tcs[NS][2][16];                  // per buffer: O(f) and h_u(f) of its tile
     __shared__ int ptc[2 * (G::RB + 1) * NTHR];     // per thread: t-only terms of each function
-    __shared__ int qr[2][32];                       // per function: register-pair terms
-    __shared__ float qrf[2][32];
+    __shared__ int qr[2][2][32];                    // [slot][function]: register-pair terms
+    __shared__ float qrf[2][2][32];
 
     const int tid = threadIdx.x;
     C *tab = reinterpret_cast<C *>(sm + (size_t)NS * NV * TB);
@@ -936,19 +946,41 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         else if (A.post & POST_REDUCE)
             est[1] = G::NST - 1;
     }
-    // vertex of local tile bit L, and the weight of edge (u, v) in function e
+    // vertex of local tile bit L; the two cut functions of point b (shared
+    // memory copies for a single graph, the batch's global array otherwise);
+    // the weight of edge (u, v) in a function
     auto gq = [&](int L) { return L < A.cb ? L : A.s + L - A.cb; };
+    auto views = [&](unsigned b, CutView (&v)[2]) {
+        if constexpr (MG) {
+            const GraphFns &gf = A.pt[b];
+            v[0] = CutView{&gf.cost.nbr[0][0], gf.cost.w, gf.cost.K};
+            v[1] = CutView{&gf.obs[A.pt_obs].nbr[0][0], gf.obs[A.pt_obs].w, gf.obs[A.pt_obs].K};
+        } else {
+            v[0] = CutView{cost_nbr, cost_w, A.cost.K};
+            v[1] = CutView{obs_nbr, obs_w, A.obs.K};
+        }
+    };
+    CutView curv[2];  // per-point graphs: the current point's functions
     auto wgt = [&](int e, int u, int v) -> int {
-        const uint64_t *nb = e == 0 ? cost_nbr : obs_nbr;
-        const int *ww = e == 0 ? cost_w : obs_w;
-        const int K = e == 0 ? A.cost.K : A.obs.K;
         int w = 0;
-        for (int c = 0; c < K; c++)
-            w += ww[c] * (int)((nb[c * MAXN + u] >> v) & 1ull);
+        if constexpr (MG) {
+            const CutView &f = curv[e];
+            for (int c = 0; c < f.K; c++)
+                w += f.w[c] * (int)((f.nbr[c * MAXN + u] >> v) & 1ull);
+        } else {  // the shared-memory copies of the launch's one graph
+            const uint64_t *nb = e == 0 ? cost_nbr : obs_nbr;
+            const int *ww = e == 0 ? cost_w : obs_w;
+            const int K = e == 0 ? A.cost.K : A.obs.K;
+            for (int c = 0; c < K; c++)
+                w += ww[c] * (int)((nb[c * MAXN + u] >> v) & 1ull);
+        }
         return w;
     };
-    if (tid < NTHR) {  // launch constants of the quadratic decomposition
+    // launch constants of the quadratic decomposition, into qr slot `qs`
+    // (each thread writes its own ptc entries)
+    auto launch_consts = [&](int qs) {
         constexpr int RB = G::RB, NTB = G::T - G::RB;
+#pragma unroll
         for (int e = 0; e < 2; e++) {
             const int st = est[e];
             if (st < 0)
@@ -972,11 +1004,13 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                     for (int k2 = 0; k2 < kk; k2++)
                         if (((tid >> kk) & 1) && ((tid >> k2) & 1))
                             qq -= 2 * wgt(e, gq(G::reg(st, kk)), gq(G::reg(st, k2)));
-                qr[e][tid] = qq;
-                qrf[e][tid] = (float)qq;
+                qr[qs][e][tid] = qq;
+                qrf[qs][e][tid] = (float)qq;
             }
         }
-    }
+    };
+    if (tid < NTHR && !MG && (est[0] >= 0 || est[1] >= 0))
+        launch_consts(0);
 
     auto tile_coords = [&](unsigned k, unsigned &b, unsigned &t, unsigned &mid, int &c4) {
         const unsigned g = cta_tile(blockIdx.x, k, grid, (unsigned)A.chunk);
@@ -1000,14 +1034,18 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             int c4;
             tile_coords(k, b, t, mid, c4);
             const uint64_t f = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
+            CutView v[2];
+            if constexpr (MG)
+                views(b, v);
+#pragma unroll
             for (int e = 0; e < 2; e++) {
                 if (est[e] < 0)
                     continue;
-                const int K = e == 0 ? A.cost.K : A.obs.K;
+                const int K = MG ? v[e].K : (e == 0 ? A.cost.K : A.obs.K);
                 int hs = 0, os = 0;
                 for (int c = 0; c < K; c++) {
-                    const uint64_t *nb = (e == 0 ? cost_nbr : obs_nbr) + c * MAXN;
-                    const int w = e == 0 ? cost_w[c] : obs_w[c];
+                    const uint64_t *nb = MG ? v[e].nbr + c * MAXN : (e == 0 ? cost_nbr : obs_nbr) + c * MAXN;
+                    const int w = MG ? v[e].w[c] : (e == 0 ? cost_w[c] : obs_w[c]);
                     if (lane < G::T) {
                         const uint64_t m = nb[gq(lane)];
                         hs += w * (__popcll(m) - 2 * __popcll(m & f));
@@ -1101,8 +1139,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         StageCtx<R> X;
         X.tab = tab;
         X.ptc = ptc;
-        X.qr = &qr[0][0];
-        X.qrf = &qrf[0][0];
+        X.qr = &qr[0][0][0];
+        X.qrf = &qrf[0][0][0];
         X.s = A.s;
         X.cb = cb;
         X.tid = tid;
@@ -1158,6 +1196,14 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                     stash(cur_b);
                 tslot ^= 1;
                 X.tab = tab + tslot * MAXTAB;
+                if constexpr (MG) {  // this point's own graph
+                    if (est[0] >= 0 || est[1] >= 0) {
+                        views(b, curv);
+                        launch_consts(tslot);
+                        X.qr = &qr[tslot][0][0];
+                        X.qrf = &qrf[tslot][0][0];
+                    }
+                }
                 if (A.pre_phase || (A.post & POST_PHASE_CONJ)) {
                     const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.layer) * A.tab_len;
                     C *dst = tab + tslot * MAXTAB;
@@ -1744,7 +1790,7 @@ int launch_params(bool c128, int B, int p, int tab_len, int n, const double *d_g
     return (int)cudaGetLastError();
 }
 
-template <typename R, int NV, bool OPS>
+template <typename R, int NV, int MODE>
 static int launch_pass_ops(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
                            cudaStream_t st)
 {
@@ -1752,21 +1798,24 @@ static int launch_pass_ops(const CUtensorMap &m0, const CUtensorMap &m1, const P
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_pass<R, NV, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_pass<R, NV, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return (int)e;
         attr_done = true;
     }
-    k_pass<R, NV, OPS><<<grid, Geo<R, NV>::NTHR + 32, smem, st>>>(m0, m1, a);
+    k_pass<R, NV, MODE><<<grid, Geo<R, NV>::NTHR + 32, smem, st>>>(m0, m1, a);
     return (int)cudaGetLastError();
 }
 
-// passes without a pre- or post-operation run the lean instantiation
+// passes without a pre- or post-operation run the lean instantiation; a batch
+// of different graphs the per-point one
 template <typename R, int NV>
 static int launch_pass_t(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid, cudaStream_t st)
 {
     const bool ops = a.pre_phase || a.pre_lambda || a.post;
-    return ops ? launch_pass_ops<R, NV, true>(m0, m1, a, grid, st) : launch_pass_ops<R, NV, false>(m0, m1, a, grid, st);
+    if (!ops)
+        return launch_pass_ops<R, NV, 0>(m0, m1, a, grid, st);
+    return a.pt ? launch_pass_ops<R, NV, 2>(m0, m1, a, grid, st) : launch_pass_ops<R, NV, 1>(m0, m1, a, grid, st);
 }
 
 int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
