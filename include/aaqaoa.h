@@ -383,14 +383,16 @@ int aaqaoa_autotune(aaqaoa_plan *plan, int *plan4);
  * closure of every unclassified edge, in the given edge order, under them.
  * No GPU is used.
  * n: 1..64 vertices. edges: 2*num_edges int32, unordered pairs, no loops or
- * repeats. Outputs (host, caller-owned): edge_orbit[num_edges] class of each
+ * repeats. edge_weight: num_edges int32 >= 1 (weighted MaxCut: only
+ * automorphisms that keep every edge's weight count), or NULL for unweighted.
+ * Outputs (host, caller-owned): edge_orbit[num_edges] class of each
  * edge; *num_orbits; orbit_rep[<= num_edges] the seed (lowest-index) edge of
  * each class; orbit_weight[<= num_edges] class sizes |S~_m|. These are
  * exactly the orbit arguments of aaqaoa_prepare.
  * Returns AAQAOA_ERR_INVALID_ARG for bad sizes, pointers or edges.
  */
-int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, int32_t *edge_orbit, int32_t *num_orbits,
-                       int32_t *orbit_rep, int32_t *orbit_weight);
+int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, const int32_t *edge_weight, int32_t *edge_orbit,
+                       int32_t *num_orbits, int32_t *orbit_rep, int32_t *orbit_weight);
 
 /* Plan properties: qubits, layers, edges, orbits, precision flag. */
 int aaqaoa_plan_info(const aaqaoa_plan *plan, int *n, int *p, int *num_edges, int *num_orbits,

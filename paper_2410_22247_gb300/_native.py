@@ -68,7 +68,7 @@ _PROTOS = [
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("aaqaoa_destroy_multi", None, [_vp]),
     ("aaqaoa_inject_fault", ctypes.c_int, [_vp, ctypes.c_int]),
-    ("aaqaoa_edge_orbits", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    ("aaqaoa_edge_orbits", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
     ("aaqaoa_get_pass_plan", ctypes.c_int, [_vp, _i32p]),
     ("aaqaoa_set_pass_plan", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("aaqaoa_autotune", ctypes.c_int, [_vp, _i32p]),

@@ -16,7 +16,9 @@
 // Algorithm 1 then seeds a class with every unclassified edge, in the caller's
 // edge order, and adds the images of dequeued edges under every generator
 // (normalised to (min, max)) that are unclassified edges. The seed is the
-// class representative and the class size its weight.
+// class representative and the class size its weight. With integer edge
+// weights (weighted MaxCut) refinement counts neighbours per edge weight and
+// only weight-preserving automorphisms are accepted.
 #include <algorithm>
 #include <cstdint>
 #include <deque>
@@ -33,7 +35,10 @@ using Col = std::vector<int>;
 struct G {
     int n;
     std::vector<std::vector<int>> adj;
-    std::vector<uint64_t> nb;  // neighbour masks (n <= 64)
+    std::vector<std::vector<int>> wt;  // weight of each adjacency entry (all 1 when unweighted)
+    std::vector<uint64_t> nb;          // neighbour masks (n <= 64)
+    bool weighted = false;
+    std::map<std::pair<int, int>, int> w;  // edge (u < v) -> weight
 };
 
 Col rank_keys(const std::vector<std::vector<int>> &keys)
@@ -60,10 +65,21 @@ Col refine(const G &g, Col col)
         std::vector<std::vector<int>> sig(g.n);
         for (int v = 0; v < g.n; v++) {
             std::vector<int> s;
-            s.reserve(g.adj[v].size() + 1);
-            for (int u : g.adj[v])
-                s.push_back(col[u]);
-            std::sort(s.begin(), s.end());
+            if (!g.weighted) {
+                s.reserve(g.adj[v].size() + 1);
+                for (int u : g.adj[v])
+                    s.push_back(col[u]);
+                std::sort(s.begin(), s.end());
+            } else {  // neighbours as (colour, edge weight) pairs, sorted
+                std::vector<std::pair<int, int>> pr;
+                for (size_t i = 0; i < g.adj[v].size(); i++)
+                    pr.push_back({col[g.adj[v][i]], g.wt[v][i]});
+                std::sort(pr.begin(), pr.end());
+                for (auto &q : pr) {
+                    s.push_back(q.first);
+                    s.push_back(q.second);
+                }
+            }
             s.insert(s.begin(), col[v]);
             sig[v] = std::move(s);
         }
@@ -111,6 +127,12 @@ bool is_automorphism(const G &g, const std::vector<int> &perm)
         for (int v : g.adj[u])
             if (!((g.nb[perm[u]] >> perm[v]) & 1ull))
                 return false;
+    if (g.weighted)
+        for (auto &kv : g.w) {
+            const int a = perm[kv.first.first], b = perm[kv.first.second];
+            if (g.w.at({std::min(a, b), std::max(a, b)}) != kv.second)
+                return false;
+        }
     return true;
 }
 
@@ -213,8 +235,8 @@ std::vector<std::vector<int>> generators(const G &g)
 
 }  // namespace
 
-extern "C" int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, int32_t *edge_orbit,
-                                  int32_t *num_orbits, int32_t *orbit_rep, int32_t *orbit_weight)
+extern "C" int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, const int32_t *edge_weight,
+                                  int32_t *edge_orbit, int32_t *num_orbits, int32_t *orbit_rep, int32_t *orbit_weight)
 {
     if (n < 1 || n > 64 || num_edges < 0 || (num_edges > 0 && !edges) || !num_orbits ||
         (num_edges > 0 && (!edge_orbit || !orbit_rep || !orbit_weight)))
@@ -222,7 +244,9 @@ extern "C" int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, in
     G g;
     g.n = n;
     g.adj.assign(n, {});
+    g.wt.assign(n, {});
     g.nb.assign(n, 0);
+    g.weighted = edge_weight != nullptr;
     std::map<std::pair<int, int>, int> index;
     for (int i = 0; i < num_edges; i++) {
         int u = edges[2 * i], v = edges[2 * i + 1];
@@ -232,8 +256,14 @@ extern "C" int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, in
             std::swap(u, v);
         if (!index.emplace(std::make_pair(u, v), i).second)
             return AAQAOA_ERR_INVALID_ARG;  // repeated edge
+        const int wi = edge_weight ? edge_weight[i] : 1;
+        if (wi < 1)
+            return AAQAOA_ERR_INVALID_ARG;
+        g.w[{u, v}] = wi;
         g.adj[u].push_back(v);
         g.adj[v].push_back(u);
+        g.wt[u].push_back(wi);
+        g.wt[v].push_back(wi);
         g.nb[u] |= 1ull << v;
         g.nb[v] |= 1ull << u;
     }

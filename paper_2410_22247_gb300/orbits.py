@@ -238,7 +238,7 @@ def edge_orbits(n, edges, generators=None, weights=None) -> EdgeOrbits:
                       np.asarray(weights, dtype=np.int32), generators)
 
 
-def edge_orbits_native(n, edges) -> EdgeOrbits:
+def edge_orbits_native(n, edges, weights=None) -> EdgeOrbits:
     """The same classes from the library's C++ implementation
     (``aaqaoa_edge_orbits``: same refinement, search order and closure).
     Generators are not returned (``generators`` is empty)."""
@@ -253,5 +253,7 @@ def edge_orbits_native(n, edges) -> EdgeOrbits:
     w = np.zeros(max(m, 1), dtype=np.int32)
     k = ctypes.c_int32()
     P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-    N.check(N.aaqaoa_edge_orbits(int(n), m, P(e), P(eo), ctypes.byref(k), P(rep), P(w)), "aaqaoa_edge_orbits")
+    wt = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.int32).reshape(-1))
+    N.check(N.aaqaoa_edge_orbits(int(n), m, P(e), P(wt) if wt is not None else None, P(eo), ctypes.byref(k), P(rep),
+                                 P(w)), "aaqaoa_edge_orbits")
     return EdgeOrbits(eo[:m].copy(), rep[:k.value].copy(), w[:k.value].copy(), [])

@@ -122,9 +122,11 @@ def test_native_finder_rejects_bad_edges():
     P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     for bad in ([0, 0, 1, 2], [0, 1, 1, 0], [0, 5, 1, 2]):
         e = np.array(bad, dtype=np.int32)
-        assert N.aaqaoa_edge_orbits(4, 2, P(e), P(out), ctypes.byref(k), P(out), P(out)) == -1
+        assert N.aaqaoa_edge_orbits(4, 2, P(e), None, P(out), ctypes.byref(k), P(out), P(out)) == -1
     e = np.array([0, 1], dtype=np.int32)
-    assert N.aaqaoa_edge_orbits(65, 1, P(e), P(out), ctypes.byref(k), P(out), P(out)) == -1
+    assert N.aaqaoa_edge_orbits(65, 1, P(e), None, P(out), ctypes.byref(k), P(out), P(out)) == -1
+    w0 = np.array([0], dtype=np.int32)
+    assert N.aaqaoa_edge_orbits(4, 1, P(e), P(w0), P(out), ctypes.byref(k), P(out), P(out)) == -1
 
 
 @pytest.mark.parametrize("k", range(8))
@@ -149,3 +151,15 @@ def test_weighted_orbits_match_brute_force(k):
             assert len({int(w[i]) for i in range(len(e)) if res.edge_orbit[i] == c}) == 1
         if mode == "orbit":
             assert res.num_orbits == ORB.edge_orbits(n, e).num_orbits
+
+
+
+def test_native_weighted_orbits_match_python_and_brute_force():
+    for k_, (n, e) in enumerate(SMALL[:8]):
+        w = W.rng(60 + k_).integers(1, 3, size=len(e))
+        a, b = ORB.edge_orbits(n, e, weights=w), ORB.edge_orbits_native(n, e, weights=w)
+        assert np.array_equal(a.edge_orbit, b.edge_orbit) and np.array_equal(a.weight, b.weight)
+    n, e = W.heap_binary_tree(31)
+    w = np.array([1 + int(np.floor(np.log2(int(v) + 1))) % 3 for _, v in e])
+    a, b = ORB.edge_orbits(n, e, weights=w), ORB.edge_orbits_native(n, e, weights=w)
+    assert np.array_equal(a.edge_orbit, b.edge_orbit) and a.num_orbits == ORB.edge_orbits(n, e).num_orbits
