@@ -31,7 +31,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["EdgeOrbits", "automorphism_generators", "edge_orbits", "edge_orbits_native", "is_automorphism"]
+__all__ = ["EdgeOrbits", "automorphism_generators", "edge_orbits", "edge_orbits_native", "eta", "eta_mean",
+           "is_automorphism"]
 
 
 def _adjacency(n, edges):
@@ -257,3 +258,68 @@ def edge_orbits_native(n, edges, weights=None) -> EdgeOrbits:
     N.check(N.aaqaoa_edge_orbits(int(n), m, P(e), P(wt) if wt is not None else None, P(eo), ctypes.byref(k), P(rep),
                                  P(w)), "aaqaoa_edge_orbits")
     return EdgeOrbits(eo[:m].copy(), rep[:k.value].copy(), w[:k.value].copy(), [])
+
+
+# ------------------------------------------------ structural descriptor eta_p
+# Eq. (eta): eta_p = 1 - |union over representatives e of RCC_p(e)| / |E|, the
+# fraction of edges outside the combined reverse causal cone of the orbit
+# representatives at depth p (Sec. 5.1). Reading of RCC_p(e) as an edge set:
+# the ZZ gates that can reach <Z_i Z_j> through p layers, i.e. the edges with
+# an endpoint within graph distance p - 1 of {i, j} (on trees the same as the
+# edges with both endpoints within distance p). Tables 1-2 print means over a
+# random representative per orbit; eta_mean is that expectation, exactly.
+
+def _adj_lists(n, edges):
+    adj = [[] for _ in range(n)]
+    for u, v in edges:
+        adj[u].append(v)
+        adj[v].append(u)
+    return adj
+
+
+def _rcc_edges(adj, edges, i, j, p):
+    dist = {i: 0, j: 0}
+    frontier = [i, j]
+    for d in range(p - 1):
+        nxt = []
+        for u in frontier:
+            for v in adj[u]:
+                if v not in dist:
+                    dist[v] = d + 1
+                    nxt.append(v)
+        frontier = nxt
+    return {k for k, (u, v) in enumerate(edges) if u in dist or v in dist}
+
+
+def eta(n, edges, p, reps):
+    """eta_p for one choice of representative edges (indices into ``edges``)."""
+    e = [tuple(map(int, x)) for x in np.asarray(edges).reshape(-1, 2)]
+    if not e:
+        return 0.0
+    adj = _adj_lists(n, e)
+    covered = set()
+    for r in reps:
+        covered |= _rcc_edges(adj, e, e[int(r)][0], e[int(r)][1], p)
+    return 1.0 - len(covered) / len(e)
+
+
+def eta_mean(n, edges, p, orbits=None):
+    """Expected eta_p when each orbit's representative is drawn uniformly and
+    independently: 1 - (1/|E|) sum_f P(f covered), P(f covered) =
+    1 - prod_m (1 - |{e in S~_m : f in RCC_p(e)}| / |S~_m|)."""
+    e = [tuple(map(int, x)) for x in np.asarray(edges).reshape(-1, 2)]
+    if not e:
+        return 0.0
+    if orbits is None:
+        orbits = edge_orbits(n, np.asarray(e))
+    adj = _adj_lists(n, e)
+    rcc = [_rcc_edges(adj, e, u, v, p) for u, v in e]
+    miss = np.ones(len(e))
+    for c in range(orbits.num_orbits):
+        members = [k for k in range(len(e)) if orbits.edge_orbit[k] == c]
+        hit = np.zeros(len(e))
+        for k in members:
+            for f in rcc[k]:
+                hit[f] += 1
+        miss *= 1.0 - hit / len(members)
+    return float(1.0 - np.sum(1.0 - miss) / len(e))

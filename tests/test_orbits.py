@@ -163,3 +163,48 @@ def test_native_weighted_orbits_match_python_and_brute_force():
     w = np.array([1 + int(np.floor(np.log2(int(v) + 1))) % 3 for _, v in e])
     a, b = ORB.edge_orbits(n, e, weights=w), ORB.edge_orbits_native(n, e, weights=w)
     assert np.array_equal(a.edge_orbit, b.edge_orbit) and a.num_orbits == ORB.edge_orbits(n, e).num_orbits
+
+
+ETA_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_eta_values.txt")
+
+
+def _eta_rows():
+    rows = []
+    for line in open(ETA_GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        fam, params, n, m, e1, e2, *cite = line.split()
+        prm = dict(kv.split("=") for kv in params.split(";"))
+        rows.append((fam, prm, int(n), int(m), float(e1), float(e2), " ".join(cite)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _eta_rows(), ids=lambda r: r[6])
+def test_eta_matches_paper_tables(row):
+    """The exact expectation over random representatives against the printed
+    means (two decimals of a sampled mean: within 0.011)."""
+    fam, prm, n, m, e1, e2, cite = row
+    nn, e = _graph(fam, prm)
+    assert (nn, len(e)) == (n, m)
+    assert abs(ORB.eta_mean(nn, e, 1) - e1) <= 0.011, cite
+    assert abs(ORB.eta_mean(nn, e, 2) - e2) <= 0.011, cite
+
+
+def test_eta_mean_is_the_enumerated_mean_and_bounds():
+    import itertools
+    for n, e in (W.balanced_tree(2, 3), W.heap_binary_tree(20), W.cycle_graph(9), W.generalized_petersen(5, 2)):
+        orb = ORB.edge_orbits(n, e)
+        classes = [[k for k in range(len(e)) if orb.edge_orbit[k] == c] for c in range(orb.num_orbits)]
+        for p in (1, 2):
+            vals = [ORB.eta(n, e, p, reps) for reps in itertools.product(*classes)]
+            assert abs(np.mean(vals) - ORB.eta_mean(n, e, p, orb)) < 1e-12
+            assert all(0.0 <= v <= 1.0 for v in vals)
+        assert ORB.eta_mean(n, e, 2, orb) <= ORB.eta_mean(n, e, 1, orb) + 1e-12
+    # closed forms: K_n, one representative touching 2n-3 edges at p = 1; the
+    # star's centre makes every cone span all edges; a cycle's cone has 3 edges
+    for n in (5, 8, 12):
+        nn, e = W.complete_graph(n)
+        assert abs(ORB.eta_mean(nn, e, 1) - (1 - (2 * n - 3) / (n * (n - 1) / 2))) < 1e-12
+        assert ORB.eta_mean(*W.star_graph(n), 1) == 0.0
+        assert abs(ORB.eta_mean(*W.cycle_graph(n), 1) - (1 - 3 / n)) < 1e-12
