@@ -5,7 +5,8 @@
  *   |psi_p(gamma, beta)> = prod_{l=1..p} exp(-i beta_l H_M) exp(-i gamma_l H_C) |+>^n
  * (Eq. (1); layer 1 acts first on |+>^n, as Eq. (A2) writes the product out),
  * with the unweighted MaxCut cost H_C = 1/2 sum_{(i,j) in E} (1 - Z_i Z_j)
- * (Eq. for H_P with w_ij in {0, 1}) and the mixer H_M = sum_i X_i, followed by
+ * (Eq. for H_P with w_ij in {0, 1}; integer edge weights through
+ * aaqaoa_prepare_weighted) and the mixer H_M = sum_i X_i, followed by
  * the cost expectation (F_p, Eq. (2)) aggregated over all 2^n amplitudes
  * with one of two observables:
  *   AAQAOA_OBS_FULL  H_C itself;

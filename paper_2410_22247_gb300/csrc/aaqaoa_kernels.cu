@@ -946,19 +946,14 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         else if (A.post & POST_REDUCE)
             est[1] = G::NST - 1;
     }
-    // vertex of local tile bit L; the two cut functions of point b (shared
-    // memory copies for a single graph, the batch's global array otherwise);
-    // the weight of edge (u, v) in a function
+    // vertex of local tile bit L; for a batch of graphs (MG) the two cut
+    // functions of point b, read from the batch's global array (a single
+    // graph uses the shared-memory copies above directly)
     auto gq = [&](int L) { return L < A.cb ? L : A.s + L - A.cb; };
     auto views = [&](unsigned b, CutView (&v)[2]) {
-        if constexpr (MG) {
-            const GraphFns &gf = A.pt[b];
-            v[0] = CutView{&gf.cost.nbr[0][0], gf.cost.w, gf.cost.K};
-            v[1] = CutView{&gf.obs[A.pt_obs].nbr[0][0], gf.obs[A.pt_obs].w, gf.obs[A.pt_obs].K};
-        } else {
-            v[0] = CutView{cost_nbr, cost_w, A.cost.K};
-            v[1] = CutView{obs_nbr, obs_w, A.obs.K};
-        }
+        const GraphFns &gf = A.pt[b];
+        v[0] = CutView{&gf.cost.nbr[0][0], gf.cost.w, gf.cost.K};
+        v[1] = CutView{&gf.obs[A.pt_obs].nbr[0][0], gf.obs[A.pt_obs].w, gf.obs[A.pt_obs].K};
     };
     CutView curv[2];  // per-point graphs: the current point's functions
     auto wgt = [&](int e, int u, int v) -> int {
