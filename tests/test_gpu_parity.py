@@ -379,3 +379,44 @@ def test_every_candidate_pass_plan_matches_oracle(n, prec):
     assert choice in tried
     E, dg, db = pl.grad(g, b, "red")
     assert e_rel(E, Er) < TOL[prec]
+
+
+BOUNDARY_ANGLES = [
+    ([0.0, 0.7], [0.3, 0.0]),                        # gamma = 0 and beta = 0 layers
+    ([0.9, 1.3], [np.pi / 4, -np.pi / 4]),           # |sin beta| = |cos beta|: either butterfly form
+    ([2 * np.pi, -0.4], [np.pi / 2, 1e-9]),          # full turn of gamma; beta = pi/2 (cos = 0)
+    ([40.0, -17.3], [2.3, -1.9]),                    # large |gamma| (mod 2 pi reduction), |beta| > pi/2
+]
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("case", ["cycle5", "reg16", "prufer22"])
+def test_boundary_angles_match_oracle(case, precision):
+    """Angles at the edges of the parameter domain: zero layers, the tie and
+    the pole of the tan/cot choice (shifted layers, cos beta = 0), a full turn
+    and large arguments of the phase."""
+    n, e = dict(CASES)[case]()
+    pl, orb = plan_for(n, e, 2, precision)
+    for g, b in BOUNDARY_ANGLES:
+        Er, dgr, dbr = O.energy_grad(n, e, g, b)
+        E, dg, db = pl.grad(g, b, "red")
+        assert e_rel(E, Er) < TOL[precision], (g, b, E, Er)
+        assert g_rel(dg, dgr, Er, precision) < TOL[precision], (g, b, dg, dgr)
+        assert g_rel(db, dbr, Er, precision) < TOL[precision], (g, b, db, dbr)
+        psi = pl.statevector(g, b)
+        ref = O.qaoa_state(n, e, g, b)
+        err = np.max(np.abs(psi.astype(np.complex128) - ref)) / np.max(np.abs(ref))
+        assert err < TOL[precision], (g, b, err)
+
+
+def test_large_p_matches_oracle():
+    n, e = W.prufer_tree(16, 4)
+    p = 12
+    g, b = W.random_angles(p, 41)
+    for precision in ("c64", "c128"):
+        pl, orb = plan_for(n, e, p, precision)
+        Er, dgr, dbr = O.energy_grad(n, e, g, b)
+        E, dg, db = pl.grad(g, b, "red")
+        assert e_rel(E, Er) < TOL[precision]
+        assert g_rel(dg, dgr, Er, precision) < TOL[precision]
+        assert g_rel(db, dbr, Er, precision) < TOL[precision]
