@@ -369,13 +369,41 @@ int aaqaoa_inject_fault(aaqaoa_plan *plan, int kind);
  * aaqaoa_autotune: times each candidate (the fewest and one more high pass,
  *   each with the full and the two-stage low pass) on the plan's workspace
  *   and stream and keeps the fastest forward and adjoint plans; the choice is
- *   cached per process by (device, precision, n, batch, gradient). Leaves
+ *   cached per process by (device, precision, n, p, batch, gradient, layer
+ *   fusion). Leaves
  *   garbage in the workspace's vectors. AAQAOA_AUTOTUNE=0 in the environment
  *   keeps the default plan. plan4 (host, 4 ints, or NULL) receives the result.
  */
 int aaqaoa_get_pass_plan(aaqaoa_plan *plan, int *plan4);
 int aaqaoa_set_pass_plan(aaqaoa_plan *plan, int fwd_low, int fwd_high, int bwd_low, int bwd_high);
 int aaqaoa_autotune(aaqaoa_plan *plan, int *plan4);
+
+/*
+ * Layer-boundary fusion (Eq. (1): consecutive layers U_M(beta_l) U_C(gamma_{l+1})
+ * meet at a diagonal step). With p >= 2 and at least two high passes per
+ * layer, the pass that ends layer l also applies the next layer's cost phase
+ * (the inverse phase in the adjoint) and its mixer on the same qubits, so the
+ * statevector is read and written once less per layer boundary. Results are
+ * the same up to rounding order. enable: 1 (the default) or 0.
+ * aaqaoa_get_layer_fusion writes the setting to *enable (host int).
+ * INVALID_ARG for a NULL plan/pointer or enable not 0/1. The stored state
+ * becomes invalid.
+ */
+int aaqaoa_set_layer_fusion(aaqaoa_plan *plan, int enable);
+int aaqaoa_get_layer_fusion(aaqaoa_plan *plan, int *enable);
+
+/*
+ * aaqaoa_get_schedule -- the tiled passes one forward (adjoint = 0) or adjoint
+ * (adjoint = 1) sweep launches, in order, as 5 ints each (host, row-major
+ * [cap][5]): the pass's first qubit s, its qubit count, the layer l whose
+ * mixer it applies there, the second layer of a fused pass or -1, and the
+ * number of layer l's qubits mixed by earlier passes. The forward sweep runs
+ * layers 0..p-1, the adjoint p-1..0. *count (host int) receives the number of
+ * passes; at most cap rows are written. Needs no device. Plans small enough
+ * for the whole-circuit kernel have no tiled passes (*count = 0).
+ * INVALID_ARG for NULL plan/count, cap < 0 or steps NULL with cap > 0.
+ */
+int aaqaoa_get_schedule(aaqaoa_plan *plan, int adjoint, int32_t *steps, int cap, int *count);
 
 /*
  * aaqaoa_edge_orbits -- the edge classes behind H_red, computed on the host

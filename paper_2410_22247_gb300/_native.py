@@ -72,6 +72,9 @@ _PROTOS = [
     ("aaqaoa_get_pass_plan", ctypes.c_int, [_vp, _i32p]),
     ("aaqaoa_set_pass_plan", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("aaqaoa_autotune", ctypes.c_int, [_vp, _i32p]),
+    ("aaqaoa_set_layer_fusion", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("aaqaoa_get_layer_fusion", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    ("aaqaoa_get_schedule", ctypes.c_int, [_vp, ctypes.c_int, _i32p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("aaqaoa_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_uint)]),

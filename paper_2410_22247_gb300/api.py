@@ -131,6 +131,27 @@ class Plan:
         N.check(N.aaqaoa_set_pass_plan(self.handle, int(fwd_low), int(fwd_high), int(bwd_low), int(bwd_high)),
                 "aaqaoa_set_pass_plan")
 
+    def layer_fusion(self):
+        """True when layer boundaries are fused into one pass (the default)."""
+        v = ctypes.c_int()
+        N.check(N.aaqaoa_get_layer_fusion(self.handle, ctypes.byref(v)), "aaqaoa_get_layer_fusion")
+        return bool(v.value)
+
+    def set_layer_fusion(self, enable):
+        N.check(N.aaqaoa_set_layer_fusion(self.handle, 1 if enable else 0), "aaqaoa_set_layer_fusion")
+
+    def schedule(self, adjoint=False):
+        """The tiled passes of one forward (or adjoint) sweep, in launch order:
+        a list of (first qubit, qubits, layer, fused second layer or -1,
+        qubits of the layer mixed before this pass)."""
+        cnt = ctypes.c_int()
+        N.check(N.aaqaoa_get_schedule(self.handle, int(bool(adjoint)), None, 0, ctypes.byref(cnt)),
+                "aaqaoa_get_schedule")
+        out = np.zeros((max(cnt.value, 1), 5), dtype=np.int32)
+        N.check(N.aaqaoa_get_schedule(self.handle, int(bool(adjoint)), _ptr(out, ctypes.c_int32), cnt.value,
+                                      ctypes.byref(cnt)), "aaqaoa_get_schedule")
+        return [tuple(int(v) for v in r) for r in out[:cnt.value]]
+
     def autotune(self):
         """Time the candidate pass plans and keep the fastest; returns pass_plan()."""
         out = np.zeros(4, dtype=np.int32)

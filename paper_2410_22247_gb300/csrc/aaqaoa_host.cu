@@ -143,6 +143,7 @@ struct aaqaoa_plan {
     int out_stride() const { return 1 + 2 * p; }
     bool small() const { return n <= T(); }
     int tiles() const { return small() ? 1 : 1 << (n - T()); }
+    bool fuse = true;  // fuse layer boundaries into one pass where the plan allows
     int *err_shared = nullptr;  // set when the plan is part of a multi-graph batch
     const GraphFns *pt_dev = nullptr;  // set for a group of same-n graphs: point b is graph b
     int *d_err() const { return err_shared ? err_shared : reinterpret_cast<int *>(ws + L.ctrl); }
@@ -219,7 +220,7 @@ Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
     off = align256(off + B * pl->p * sizeof(double2));
     L.tab = off;  // three tables: exact, forward-scaled, inverse layer
     off = align256(off + 3 * B * pl->p * pl->tab_len() * pl->amp());
-    const size_t pass_partials = pl->small() ? 0 : 2 * B * (size_t)device_sms();
+    const size_t pass_partials = pl->small() ? 0 : 3 * B * (size_t)device_sms();
     const size_t agg_partials = 64 * (size_t)agg_grid(pl->c128);
     L.partial_count = pass_partials > agg_partials ? pass_partials : agg_partials;
     L.partials = off;
@@ -352,7 +353,7 @@ PassArgs base_args(const aaqaoa_plan *pl, int obs)
     a.counter = pl->d_counter_pass();
     a.out = pl->d_out();
     a.out_stride = pl->out_stride();
-    a.slot_idx[0] = a.slot_idx[1] = -1;
+    a.slot_idx[0] = a.slot_idx[1] = a.slot_idx[2] = -1;
     a.err = pl->d_err();
     a.obs = pl->obs[obs];
     a.cost = pl->cost;
@@ -361,50 +362,107 @@ PassArgs base_args(const aaqaoa_plan *pl, int obs)
     return a;
 }
 
+// One launch of a layer sequence: pass k of the layer plan applied for
+// `layer`; layer2 >= 0 marks a fused pass that also applies layer2's mixer to
+// the same qubits (the boundary between two consecutive layers). j0 counts
+// the layer's butterflies done by its earlier passes.
+struct Step {
+    int k, layer, layer2, j0;
+    bool first_of_layer;  // first pass with this layer's own operations
+    bool last_of_layer;   // the layer's mixer is complete after this pass
+};
+
+// Every layer runs its low pass first, then its high passes in order. With
+// fusion (at least two high passes and two layers) the last pass of a layer
+// also starts the next layer in the direction of travel on the same qubits,
+// and the next layer skips that group and ends on another high group, so
+// consecutive boundaries alternate between the last two high groups.
+std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fuse, bool reverse)
+{
+    const int np = (int)passes.size();
+    fuse = fuse && np >= 3 && p >= 2;
+    std::vector<Step> out;
+    int skip = -1;   // group already applied for this layer by the previous fused pass
+    int done0 = 0;   // its qubits
+    for (int i = 0; i < p; i++) {
+        const int l = reverse ? p - 1 - i : i;
+        const bool more = i + 1 < p;
+        const int next = reverse ? l - 1 : l + 1;
+        std::vector<int> order;
+        for (int k = 0; k < np; k++)
+            if (k != skip)
+                order.push_back(k);
+        int j0 = done0;
+        for (size_t o = 0; o < order.size(); o++) {
+            const int k = order[o];
+            const bool last = o + 1 == order.size();
+            Step st{k, l, (fuse && more && last) ? next : -1, j0, o == 0 && skip < 0, last};
+            j0 += passes[k].qubits;
+            out.push_back(st);
+        }
+        if (fuse && more) {
+            skip = order.back();
+            done0 = passes[skip].qubits;
+        }
+    }
+    return out;
+}
+
+bool plan_fuses(const aaqaoa_plan *pl) { return pl->fuse && !pl->pt_dev; }
+
 enum FwdMode { FWD_ENERGY, FWD_GRAD, FWD_STATE };
 
 int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
 {
-    const int np = (int)pl->passes.size();
     const long long total = (long long)pl->tiles() * B;
     const int grid = pass_grid(total);
     const int chunk = B > 1 ? (int)((total + grid - 1) / grid) : 0;
-    for (int l = 0; l < pl->p; l++) {
-        for (int k = 0; k < np; k++) {
-            const Pass &ps = pl->passes[k];
-            PassArgs a = base_args(pl, obs);
-            a.B = B;
-            a.chunk = chunk;
-            a.s = ps.s;
-            a.cb = ps.cb;
-            a.wide_rows = ps.wide;
-            a.is_low = ps.is_low;
-            a.hmask = ps.hmask;
-            a.skip_last = ps.skip_last;
-            a.layer = l;
-            a.sign_s = 1.0;
-            a.tab = tab_kind(pl, pl->d_tab(), B, 1);
-            a.load = !(l == 0 && k == 0);
-            a.pre_phase = (k == 0);
-            a.nvec_io = 1;
-            const bool last = (l == pl->p - 1 && k == np - 1);
-            a.write = !(last && mode == FWD_ENERGY);
-            a.post = (last && mode != FWD_STATE) ? POST_REDUCE : 0;
-            if (last && a.write)
-                a.post |= POST_RESCALE;
-            if (last && mode != FWD_STATE) {
-                a.slot_idx[0] = 0;
-                a.slot_scale[0] = 1.0;
-            }
-            if (pl->inject == AAQAOA_FAULT_DROP_TILE && a.load) {
-                a.drop_first_load = 1;
-                pl->inject = 0;
-            }
-            const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
-            ProfScope ps_(pl, PK_FWD, S * ((a.load ? 1 : 0) + (a.write ? 1 : 0)));
-            CKL(launch_pass(pl->c128, 1, pl->map_phi[k], pl->map_phi[k], a, grid, pl->stream), "forward pass");
-            pl->launches++;
+    const std::vector<Step> sched = layer_schedule(pl->p, pl->passes, plan_fuses(pl), false);
+    for (size_t i = 0; i < sched.size(); i++) {
+        const Step &sp = sched[i];
+        const Pass &ps = pl->passes[sp.k];
+        const int l = sp.layer;
+        PassArgs a = base_args(pl, obs);
+        a.B = B;
+        a.chunk = chunk;
+        a.s = ps.s;
+        a.cb = ps.cb;
+        a.wide_rows = ps.wide;
+        a.is_low = ps.is_low;
+        a.hmask = ps.hmask;
+        a.skip_last = ps.skip_last;
+        a.layer = l;
+        a.tab_layer = l;
+        a.sign_s = 1.0;
+        a.tab = tab_kind(pl, pl->d_tab(), B, 1);
+        a.load = i > 0;
+        // a layer's phase comes with its first pass, or at the end of the
+        // fused pass that starts it
+        a.pre_phase = sp.first_of_layer ? 1 : 0;
+        a.nvec_io = 1;
+        const bool last = i + 1 == sched.size();
+        a.write = !(last && mode == FWD_ENERGY);
+        a.post = (last && mode != FWD_STATE) ? POST_REDUCE : 0;
+        if (last && a.write)
+            a.post |= POST_RESCALE;
+        if (last && mode != FWD_STATE) {
+            a.slot_idx[0] = 0;
+            a.slot_scale[0] = 1.0;
         }
+        if (sp.layer2 >= 0) {
+            a.fuse = 1;
+            a.layer2 = sp.layer2;
+            a.tab_layer = sp.layer2;
+            a.post |= POST_PHASE;
+        }
+        if (pl->inject == AAQAOA_FAULT_DROP_TILE && a.load) {
+            a.drop_first_load = 1;
+            pl->inject = 0;
+        }
+        const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
+        ProfScope ps_(pl, PK_FWD, S * ((a.load ? 1 : 0) + (a.write ? 1 : 0)));
+        CKL(launch_pass(pl->c128, 1, pl->map_phi[sp.k], pl->map_phi[sp.k], a, grid, pl->stream), "forward pass");
+        pl->launches++;
     }
     return AAQAOA_OK;
 }
@@ -417,49 +475,52 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
     const int tiles = 1 << (pl->n - T);
     const int grid = pass_grid((long long)tiles * B);
     const int chunk = B > 1 ? (int)(((long long)tiles * B + grid - 1) / grid) : 0;
-    const int np = (int)pl->bwd_passes.size();
-    bool first = true;
     // Each layer runs its passes low pass first, so the cut-function work at
     // the layer's end (dE/dgamma, inverse phase) falls in a high pass and the
     // low pass can stop after two register stages.
-    for (int l = pl->p - 1; l >= 0; l--) {
-        int j0 = 0;  // qubits of this layer's inverse mixer done by earlier passes
-        for (int kk = 0; kk < np; kk++) {
-            const Pass &ps = pl->bwd_passes[kk];
-            const bool last_of_layer = (kk == np - 1);
-            PassArgs a = base_args(pl, obs);
-            a.B = B;
-            a.chunk = chunk;
-            a.tiles = tiles;
-            a.s = ps.s;
-            a.cb = ps.cb;
-            a.wide_rows = ps.wide;
-            a.is_low = ps.is_low;
-            a.hmask = ps.hmask;
-            a.skip_last = ps.skip_last;
-            a.layer = l;
-            a.sign_s = -1.0;
-            a.tab = tab_kind(pl, pl->d_tab(), B, 2);
-            a.j0 = j0;
-            j0 += ps.qubits;
-            a.load = 1;
-            a.pre_phase = 0;
-            a.pre_lambda = first ? 1 : 0;
-            a.nvec_io = first ? 1 : 2;
-            a.post = last_of_layer ? (POST_GAMMA | (l > 0 ? POST_PHASE_CONJ : 0)) : 0;
-            a.write = !(last_of_layer && l == 0);
-            a.slot_idx[0] = 1 + pl->p + l;
-            a.slot_scale[0] = 2.0;
-            if (last_of_layer) {
-                a.slot_idx[1] = 1 + l;
-                a.slot_scale[1] = 2.0;
-            }
-            const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
-            ProfScope ps_(pl, PK_ADJ, S * (a.nvec_io + (a.write ? 2 : 0)));
-            CKL(launch_pass(pl->c128, 2, pl->map_bphi[kk], pl->map_blam[kk], a, grid, pl->stream), "adjoint pass");
-            pl->launches++;
-            first = false;
+    const std::vector<Step> sched = layer_schedule(pl->p, pl->bwd_passes, plan_fuses(pl), true);
+    for (size_t i = 0; i < sched.size(); i++) {
+        const Step &sp = sched[i];
+        const Pass &ps = pl->bwd_passes[sp.k];
+        const int l = sp.layer;
+        const bool first = i == 0;
+        PassArgs a = base_args(pl, obs);
+        a.B = B;
+        a.chunk = chunk;
+        a.tiles = tiles;
+        a.s = ps.s;
+        a.cb = ps.cb;
+        a.wide_rows = ps.wide;
+        a.is_low = ps.is_low;
+        a.hmask = ps.hmask;
+        a.skip_last = ps.skip_last;
+        a.layer = l;
+        a.tab_layer = l;
+        a.sign_s = -1.0;
+        a.tab = tab_kind(pl, pl->d_tab(), B, 2);
+        a.j0 = sp.j0;
+        a.load = 1;
+        a.pre_phase = 0;
+        a.pre_lambda = first ? 1 : 0;
+        a.nvec_io = first ? 1 : 2;
+        a.post = sp.last_of_layer ? (POST_GAMMA | (l > 0 ? POST_PHASE_CONJ : 0)) : 0;
+        a.write = !(sp.last_of_layer && l == 0);
+        a.slot_idx[0] = 1 + pl->p + l;
+        a.slot_scale[0] = 2.0;
+        if (sp.last_of_layer) {
+            a.slot_idx[1] = 1 + l;
+            a.slot_scale[1] = 2.0;
         }
+        if (sp.layer2 >= 0) {  // the next layer (l - 1) starts on the same qubits
+            a.fuse = 1;
+            a.layer2 = sp.layer2;
+            a.slot_idx[2] = 1 + pl->p + sp.layer2;
+            a.slot_scale[2] = 2.0;
+        }
+        const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
+        ProfScope ps_(pl, PK_ADJ, S * (a.nvec_io + (a.write ? 2 : 0)));
+        CKL(launch_pass(pl->c128, 2, pl->map_bphi[sp.k], pl->map_blam[sp.k], a, grid, pl->stream), "adjoint pass");
+        pl->launches++;
     }
     return AAQAOA_OK;
 }
@@ -920,12 +981,50 @@ int aaqaoa_set_pass_plan(aaqaoa_plan *pl, int fwd_low, int fwd_high, int bwd_low
     return set_layers(pl, plan4);
 }
 
+int aaqaoa_set_layer_fusion(aaqaoa_plan *pl, int enable)
+{
+    g_detail.clear();
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    if (enable != 0 && enable != 1)
+        return fail(AAQAOA_ERR_INVALID_ARG, "enable must be 0 or 1 (got %d)", enable);
+    pl->fuse = enable != 0;
+    pl->state_valid = false;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_get_layer_fusion(aaqaoa_plan *pl, int *enable)
+{
+    if (!pl || !enable)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan or enable is NULL");
+    *enable = pl->fuse ? 1 : 0;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_get_schedule(aaqaoa_plan *pl, int adjoint, int32_t *steps, int cap, int *count)
+{
+    if (!pl || !count || cap < 0 || (cap > 0 && !steps))
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan/count is NULL, cap < 0 or steps is NULL");
+    const std::vector<Pass> &passes = adjoint ? pl->bwd_passes : pl->passes;
+    const std::vector<Step> sched = layer_schedule(pl->p, passes, plan_fuses(pl), adjoint != 0);
+    *count = (int)sched.size();
+    for (int i = 0; i < cap && i < (int)sched.size(); i++) {
+        const Pass &ps = passes[sched[i].k];
+        steps[5 * i + 0] = ps.is_low ? 0 : ps.s;
+        steps[5 * i + 1] = ps.qubits;
+        steps[5 * i + 2] = sched[i].layer;
+        steps[5 * i + 3] = sched[i].layer2;
+        steps[5 * i + 4] = sched[i].j0;
+    }
+    return AAQAOA_OK;
+}
+
 namespace {
 struct TuneKey {
-    int dev, c128, n, cap, grad;
+    int dev, c128, n, p, cap, grad, fuse;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(dev, c128, n, cap, grad) < std::tie(o.dev, o.c128, o.n, o.cap, o.grad);
+        return std::tie(dev, c128, n, p, cap, grad, fuse) < std::tie(o.dev, o.c128, o.n, o.p, o.cap, o.grad, o.fuse);
     }
 };
 std::map<TuneKey, std::array<int, 4>> &plan_tune_cache()
@@ -984,7 +1083,7 @@ int aaqaoa_autotune(aaqaoa_plan *pl, int *plan4)
     if (!pl->small() && !(env && env[0] == '0')) {
         int dev = 0;
         cudaGetDevice(&dev);
-        const TuneKey key{dev, pl->c128 ? 1 : 0, pl->n, pl->cap, pl->ws_grad ? 1 : 0};
+        const TuneKey key{dev, pl->c128 ? 1 : 0, pl->n, pl->p, pl->cap, pl->ws_grad ? 1 : 0, plan_fuses(pl) ? 1 : 0};
         auto it = plan_tune_cache().find(key);
         if (it != plan_tune_cache().end()) {
             r = set_layers(pl, it->second.data());
@@ -1512,7 +1611,7 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
     void *d_tab = base + off;  // exact, forward-scaled and inverse tables
     off = align256(off + 3 * (size_t)p * pl->tab_len() * pl->amp());
     double *d_part = reinterpret_cast<double *>(base + off);
-    off = align256(off + 2 * (size_t)device_sms() * sizeof(double));
+    off = align256(off + 3 * (size_t)device_sms() * sizeof(double));
     if (off > STATIC_FIXED_BYTES)
         return fail(AAQAOA_ERR_UNSUPPORTED, "tables for p = %d and |E| = %d exceed the static scratch", p, pl->m);
     int *d_err = reinterpret_cast<int *>(base);
@@ -1556,45 +1655,53 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
                               1, &wide[k])))
                 return r;
         const int grid = pass_grid(pl->tiles());
-        for (int l = 0; l < p; l++) {
-            for (int k = 0; k < np; k++) {
-                const Pass &ps = pl->passes[k];
-                PassArgs a;
-                memset(&a, 0, sizeof a);
-                a.n = pl->n;
-                a.s = ps.s;
-                a.cb = ps.cb;
-                a.wide_rows = wide[k];
-                a.is_low = ps.is_low;
-                a.hmask = ps.hmask;
-                a.skip_last = ps.skip_last;
-                a.tiles = pl->tiles();
-                a.B = 1;
-                a.load = !(l == 0 && k == 0);
-                a.pre_phase = (k == 0);
-                const bool last = (l == p - 1 && k == np - 1);
-                a.write = !last;
-                a.post = last ? POST_REDUCE : 0;
-                a.nvec_io = 1;
-                a.layer = l;
-                a.p = p;
-                a.tab_len = pl->tab_len();
-                a.sign_s = 1.0;
-                a.amp0 = std::pow(2.0, -0.5 * pl->n);
-                a.tab = tab_kind(pl, d_tab, 1, 1);
-                a.cs = d_cs;
-                a.partials = d_part;
-                a.counter = d_counter;
-                a.out = d_out;
-                a.out_stride = pl->out_stride();
-                a.slot_idx[0] = last ? 0 : -1;
-                a.slot_idx[1] = -1;
-                a.slot_scale[0] = 1.0;
-                a.err = d_err;
-                a.obs = pl->obs[observable];
-                a.cost = pl->cost;
-                CKL(launch_pass(pl->c128, 1, maps[k], maps[k], a, grid, st), "forward pass");
+        const std::vector<Step> sched = layer_schedule(p, pl->passes, plan_fuses(pl), false);
+        for (size_t i = 0; i < sched.size(); i++) {
+            const Step &sp = sched[i];
+            const int k = sp.k, l = sp.layer;
+            const Pass &ps = pl->passes[k];
+            PassArgs a;
+            memset(&a, 0, sizeof a);
+            a.n = pl->n;
+            a.s = ps.s;
+            a.cb = ps.cb;
+            a.wide_rows = wide[k];
+            a.is_low = ps.is_low;
+            a.hmask = ps.hmask;
+            a.skip_last = ps.skip_last;
+            a.tiles = pl->tiles();
+            a.B = 1;
+            a.load = i > 0;
+            a.pre_phase = sp.first_of_layer ? 1 : 0;
+            const bool last = i + 1 == sched.size();
+            a.write = !last;
+            a.post = last ? POST_REDUCE : 0;
+            a.nvec_io = 1;
+            a.layer = l;
+            a.tab_layer = l;
+            a.p = p;
+            a.tab_len = pl->tab_len();
+            a.sign_s = 1.0;
+            a.amp0 = std::pow(2.0, -0.5 * pl->n);
+            a.tab = tab_kind(pl, d_tab, 1, 1);
+            a.cs = d_cs;
+            a.partials = d_part;
+            a.counter = d_counter;
+            a.out = d_out;
+            a.out_stride = pl->out_stride();
+            a.slot_idx[0] = last ? 0 : -1;
+            a.slot_idx[1] = a.slot_idx[2] = -1;
+            a.slot_scale[0] = 1.0;
+            if (sp.layer2 >= 0) {
+                a.fuse = 1;
+                a.layer2 = sp.layer2;
+                a.tab_layer = sp.layer2;
+                a.post |= POST_PHASE;
             }
+            a.err = d_err;
+            a.obs = pl->obs[observable];
+            a.cost = pl->cost;
+            CKL(launch_pass(pl->c128, 1, maps[k], maps[k], a, grid, st), "forward pass");
         }
     }
     int err = 0;

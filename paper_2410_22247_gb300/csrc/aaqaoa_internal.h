@@ -38,6 +38,7 @@ enum PostOp : int {
     POST_RESCALE = 2,     // multiply by f^n: the stored final state is exact
     POST_GAMMA = 4,       // acc1 += C(x) Im(conj(lambda) phi)     (dE/dgamma)
     POST_PHASE_CONJ = 8,  // phi, lambda *= inverse-layer table    (undo cost layer)
+    POST_PHASE = 16,      // phi *= forward table of layer tab_layer (next cost layer)
 };
 
 struct PassArgs {
@@ -58,6 +59,10 @@ struct PassArgs {
     int post;         // PostOp flags
     int nvec_io;      // vectors loaded (1 or 2)
     int layer;        // layer l (0-based): selects the phase table and (cos, sin)
+    int tab_layer;    // layer whose phase table the pass applies (the next one when fused)
+    int fuse;         // 1: after the last stage's operations, apply layer `layer2`'s mixer
+                      //    to the same qubits (a layer boundary inside one pass)
+    int layer2;       // the second layer of a fused pass
     int j0;           // butterflies of this layer applied by earlier passes (adjoint)
     int p;            // number of layers
     int tab_len;      // |E| + 1
@@ -65,12 +70,12 @@ struct PassArgs {
     double amp0;      // 2^(-n/2) for the generated |+>^n
     const void *tab;  // this pass's phase tables [B][p][tab_len]: forward-scaled or inverse
     const double2 *cs;  // [B][p] (cos beta_l, sin beta_l)
-    double *partials; // [2][B][grid]
+    double *partials; // [3][B][grid]
     unsigned *counter;  // last-block counter (zero between launches)
     double *out;      // [B][out_stride]
     int out_stride;
-    int slot_idx[2];  // output index (within a point's row) of slot 0 / 1, or -1
-    double slot_scale[2];
+    int slot_idx[3];  // output index (within a point's row) of slot 0 / 1 / 2, or -1
+    double slot_scale[3];  // slot 0: acc0 (energy or dE/dbeta_layer), 1: dE/dgamma, 2: dE/dbeta_layer2
     int *err;         // device error flag
     int drop_first_load;  // test hook: CTA 0 never loads its first tile (bounded wait expires)
     CutFn obs;        // observable of the reduction / lambda

@@ -400,7 +400,7 @@ template <typename R, int NV>
 __host__ __device__ constexpr size_t pass_static_smem()
 {
     using G = Geo<R, NV>;
-    return 2 * G::NSTAGE * 8 + 2 * 2 * 32 * 8 + 4 + 2 * MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
+    return 2 * G::NSTAGE * 8 + 2 * 3 * 32 * 8 + 4 + 2 * MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
            2 * (G::RB + 1) * G::NTHR * 4 + 2 * 2 * 2 * 32 * 4 + 256;
 }
 static_assert(pass_smem_total<float, 1>() + pass_static_smem<float, 1>() <= 227 * 1024, "c64 pipeline smem");
@@ -486,6 +486,8 @@ struct StageCtx {
     R fn, fn2;     // f^n and f^(2n): one whole layer of butterflies
     R scale0;      // f^j0: butterflies of this layer applied by earlier passes
     R run;         // f^j for the current tile (advanced by every butterfly)
+    R tq2, f2;     // fused pass: rotation of the second layer
+    R run2;        // its f^j (the second layer starts on exact vectors: j = 0)
 };
 
 // ------------------------------------------------ cut values in a stage
@@ -569,12 +571,67 @@ __device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int
     }
 }
 
+// The butterflies of stage ST due in this pass, with rotation t = tq and
+// dropped factor f; run is f^j on entry (j butterflies of the layer already
+// applied) and is advanced. Rotations (twisted frame), no rescaling: after j
+// butterflies of a layer the vectors carry 1/f^j (restored by the next phase
+// table or the last pass), so an inner product taken before butterfly j+1 is
+// scaled by f^(2j). In the twisted frame Im<lambda|X_q|phi> sums, over the
+// pairs (x, x'), Re(conj(lambda_x') phi_x) - Re(conj(lambda_x) phi_x').
+template <typename R, int NV, int ST>
+__device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R &run,
+                                         typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
+                                         typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc)
+{
+    using G = Geo<R, NV>;
+    using C = typename CT<R>::T;
+    constexpr int RB = G::RB, NR = 1 << RB;
+    R gb = 0, sc = run;
+#pragma unroll
+    for (int k = 0; k < RB; k++) {
+        if (!((G::own(ST) >> k) & 1))
+            continue;
+        bool due = true;
+        if (G::reg(ST, k) >= cb)
+            due = (A.hmask >> (G::reg(ST, k) - cb)) & 1;
+        else
+            due = A.is_low;
+        if (!due)
+            continue;
+        C ipp[2], ipn[2];
+        ipp[0] = ipp[1] = ipn[0] = ipn[1] = mkc<C>((R)0, (R)0);
+#pragma unroll
+        for (int m = 0; m < NR; m++) {
+            if (m & (1 << k))
+                continue;
+            const int m1 = m | (1 << k);
+            if constexpr (NV == 2) {
+                const int c = (m >> (k == 0 ? 1 : 0)) & 1;
+                dot_acc(ipp[c], l[m1], a[m]);
+                dot_acc(ipn[c], l[m], a[m1]);
+                rot(l[m], l[m1], tq);
+            }
+            rot(a[m], a[m1], tq);
+        }
+        if constexpr (NV == 2) {
+            const R q = ((ipp[0].x + ipp[0].y) + (ipp[1].x + ipp[1].y)) - ((ipn[0].x + ipn[0].y) + (ipn[1].x + ipn[1].y));
+            gb = fma(q, sc * sc, gb);
+        }
+        sc *= f;
+    }
+    run = sc;
+    if constexpr (NV == 2)
+        acc += (double)gb;
+}
+
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
-template <typename R, int NV, int ST, bool OPS>
+// FUSE (last stage of a fused pass): after this layer's operations the second
+// layer's butterflies of the same stage follow, their dE/dbeta into acc2.
+template <typename R, int NV, int ST, bool OPS, bool FUSE = false>
 __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                           typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc0,
-                                          double &acc1)
+                                          double &acc1, double &acc2)
 {
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
@@ -629,47 +686,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         }
     }
 
-    // Rotations (twisted frame), no rescaling: after j butterflies of this
-    // layer the vectors carry 1/f^j (restored by the next phase table or the
-    // last pass), so an inner product taken before butterfly j+1 is scaled
-    // by f^(2j). In the twisted frame Im<lambda|X_q|phi> sums, over the pairs
-    // (x, x'), Re(conj(lambda_x') phi_x) - Re(conj(lambda_x) phi_x').
-    R gb = 0, sc = X.run;
-#pragma unroll
-    for (int k = 0; k < RB; k++) {
-        if (!((G::own(ST) >> k) & 1))
-            continue;
-        bool due = true;
-        if (G::reg(ST, k) >= X.cb)
-            due = (A.hmask >> (G::reg(ST, k) - X.cb)) & 1;
-        else
-            due = A.is_low;
-        if (!due)
-            continue;
-        C ipp[2], ipn[2];
-        ipp[0] = ipp[1] = ipn[0] = ipn[1] = mkc<C>((R)0, (R)0);
-#pragma unroll
-        for (int m = 0; m < NR; m++) {
-            if (m & (1 << k))
-                continue;
-            const int m1 = m | (1 << k);
-            if constexpr (NV == 2) {
-                const int c = (m >> (k == 0 ? 1 : 0)) & 1;
-                dot_acc(ipp[c], l[m1], a[m]);
-                dot_acc(ipn[c], l[m], a[m1]);
-                rot(l[m], l[m1], X.tq);
-            }
-            rot(a[m], a[m1], X.tq);
-        }
-        if constexpr (NV == 2) {
-            const R q = ((ipp[0].x + ipp[0].y) + (ipp[1].x + ipp[1].y)) - ((ipn[0].x + ipn[0].y) + (ipn[1].x + ipn[1].y));
-            gb = fma(q, sc * sc, gb);
-        }
-        sc *= X.f;
-    }
-    X.run = sc;
-    if constexpr (NV == 2)
-        acc0 += (double)gb;
+    mix_regs<R, NV, ST>(A, X.cb, X.tq, X.f, X.run, a, l, acc0);
 
     if (OPS && LAST && (A.post & POST_RESCALE)) {  // the stored state is the exact one
 #pragma unroll
@@ -711,11 +728,44 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
             }
         }
     }
+    if constexpr (NV == 1) {
+        if (OPS && LAST && (A.post & POST_PHASE)) {  // the next layer's cost phase
+            int cv[NR];
+            cut_int<G, ST>(tc0, pt0, X.qr, X.tid, cv);
+#pragma unroll
+            for (int m = 0; m < NR; m++)
+                a[m] = cmul(a[m], X.tab[cv[m]]);
+        }
+    }
+    if constexpr (FUSE && LAST)
+        mix_regs<R, NV, ST>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2);
     if (!LAST || A.write) {
         store_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
             store_regs<R, NV, ST>(X.sv1, sb, l);
     }
+}
+
+// A stage of the second layer of a fused pass: load, its butterflies, store.
+template <typename R, int NV, int ST>
+__device__ __forceinline__ void mix_stage(const PassRegs &A, StageCtx<R> &X,
+                                          typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
+                                          typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc2)
+{
+    using G = Geo<R, NV>;
+    constexpr int NTB = G::T - G::RB;
+    uint32_t base = 0;
+#pragma unroll
+    for (int j = 0; j < NTB; j++)
+        base |= ((uint32_t(X.tid) >> j) & 1u) << G::thr(ST, j);
+    const uint32_t sb = G::swz(base);
+    load_regs<R, NV, ST>(X.sv0, sb, a);
+    if constexpr (NV == 2)
+        load_regs<R, NV, ST>(X.sv1, sb, l);
+    mix_regs<R, NV, ST>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2);
+    store_regs<R, NV, ST>(X.sv0, sb, a);
+    if constexpr (NV == 2)
+        store_regs<R, NV, ST>(X.sv1, sb, l);
 }
 
 // Sums over all threads of the block (any multiple of 32 threads).
@@ -844,7 +894,7 @@ __device__ void pass_final_reduce(const PassArgs &A, unsigned total)
     __threadfence();
     const unsigned G = gridDim.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int job = w; job < 2 * A.B; job += nw) {
+    for (int job = w; job < 3 * A.B; job += nw) {
         const int slot = job / A.B, b = job - slot * A.B;
         if (A.slot_idx[slot] < 0)
             continue;
@@ -872,13 +922,15 @@ __device__ void pass_final_reduce(const PassArgs &A, unsigned total)
 // full[s] (producer -> compute: tile loaded, or buffer free in a generating
 // pass) and done[s] (compute -> producer: results in shared memory).
 // MODE 0: mixer only; 1: with cut-function work on one graph; 2: the same
-// with point b of the batch being its own graph (A.pt[b]).
+// with point b of the batch being its own graph (A.pt[b]); 3: as 1, and the
+// pass is fused (A.fuse): after the last stage's operations the mixer of
+// layer A.layer2 is applied to the same qubits, last stage first.
 template <typename R, int NV, int MODE>
 __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     k_pass(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
            const __grid_constant__ PassArgs A)
 {
-    constexpr bool OPS = MODE != 0, MG = MODE == 2;
+    constexpr bool OPS = MODE != 0, MG = MODE == 2, FUSE = MODE == 3;
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
     constexpr int NR = 1 << G::RB, NS = G::NSTAGE, NTHR = G::NTHR;
@@ -888,7 +940,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     // shared array itself, so every tile access stays a shared-memory access
     unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[NS], done[NS];
-    __shared__ double pred[2][2][32];  // per-warp sums of a finished point, two buffers
+    __shared__ double pred[2][3][32];  // per-warp sums of a finished point, two buffers
     __shared__ int s_flag;
     __shared__ int obs_w[MAXK], cost_w[MAXK];
     __shared__ int tcs[NS][2][16];                  // per buffer: O(f) and h_u(f) of its tile
@@ -908,7 +960,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     const int cb = A.cb, hb = G::T - A.cb;
     const int midbits = A.s - cb;
     const unsigned tiles_per_hi = (unsigned)A.tiles >> midbits;  // 2^(n - s - hb)
-    const bool reduce = A.slot_idx[0] >= 0 || A.slot_idx[1] >= 0;
+    const bool reduce = A.slot_idx[0] >= 0 || A.slot_idx[1] >= 0 || A.slot_idx[2] >= 0;
 
     if (tid == 0) {
         s_flag = *reinterpret_cast<volatile int *>(A.err) ? 1 : 0;
@@ -931,8 +983,9 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         return;
 
     // The register stage that evaluates each cut function in this pass, or -1:
-    // C for the phase of a forward low pass (stage 0) and for the gradient and
-    // inverse phase of the last adjoint pass of a layer (last stage); O for
+    // C for the phase of a forward low pass (stage 0), for the next layer's
+    // phase in a fused forward pass and for the gradient and inverse phase of
+    // the last adjoint pass of a layer (last stage); O for
     // lambda = O phi (first stage of the first adjoint pass) and for the
     // energy (last stage of the last forward pass).
     int est[2] = {-1, -1};
@@ -940,6 +993,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         if (A.pre_phase)
             est[0] = 0;
         else if (NV == 2 && (A.post & (POST_GAMMA | POST_PHASE_CONJ)))
+            est[0] = G::NST - 1;
+        else if (NV == 1 && (A.post & POST_PHASE))
             est[0] = G::NST - 1;
         if (NV == 2 && A.pre_lambda)
             est[1] = A.is_low ? 0 : 1;
@@ -1129,7 +1184,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         // ------------------------------------------------------- compute
         const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.j0,
                          A.skip_last, A.amp0};
-        double acc0 = 0.0, acc1 = 0.0;
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
         int cur_b = -1;
         StageCtx<R> X;
         X.tab = tab;
@@ -1155,24 +1210,30 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             for (int o = 16; o > 0; o >>= 1) {
                 acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
                 acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+                if constexpr (FUSE)
+                    acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
             }
             par ^= 1;
             if (lane == 0) {
                 pred[par][0][warp] = acc0;
                 pred[par][1][warp] = acc1;
+                pred[par][2][warp] = acc2;
             }
-            acc0 = acc1 = 0.0;
+            acc0 = acc1 = acc2 = 0.0;
             pend_b = b;
         };
         auto write_pending = [&]() {  // after a barrier
             if (pend_b >= 0 && tid == 0) {
-                double s0 = 0.0, s1 = 0.0;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0;
                 for (int w = 0; w < NTHR / 32; w++) {
                     s0 += pred[par][0][w];
                     s1 += pred[par][1][w];
+                    s2 += pred[par][2][w];
                 }
                 A.partials[((size_t)0 * A.B + pend_b) * grid + blockIdx.x] = s0;
                 A.partials[((size_t)1 * A.B + pend_b) * grid + blockIdx.x] = s1;
+                if (FUSE)
+                    A.partials[((size_t)2 * A.B + pend_b) * grid + blockIdx.x] = s2;
             }
             pend_b = -1;
         };
@@ -1199,8 +1260,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                         X.qrf = &qrf[tslot][0][0];
                     }
                 }
-                if (A.pre_phase || (A.post & POST_PHASE_CONJ)) {
-                    const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.layer) * A.tab_len;
+                if (A.pre_phase || (A.post & (POST_PHASE_CONJ | POST_PHASE))) {
+                    const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.tab_layer) * A.tab_len;
                     C *dst = tab + tslot * MAXTAB;
                     for (int i = tid; i < A.tab_len; i += NTHR)
                         dst[i] = src[i];
@@ -1220,6 +1281,13 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 X.fn = (R)fn;
                 X.fn2 = (R)(fn * fn);
                 X.scale0 = (R)fj;
+                if constexpr (FUSE) {  // the second layer's rotation
+                    const double2 cs2 = A.cs[(size_t)b * A.p + A.layer2];
+                    const double c2 = cs2.x, s2 = A.sign_s * cs2.y;
+                    const bool sh2 = fabs(s2) > fabs(c2);
+                    X.tq2 = sh2 ? (R)(-c2 / s2) : (R)(s2 / c2);
+                    X.f2 = (R)(sh2 ? s2 : c2);
+                }
                 cur_b = (int)b;
             }
             X.sv0 = reinterpret_cast<C *>(buf);
@@ -1241,17 +1309,18 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             X.first = true;
             X.run = X.scale0;
             bool bad;
-            if (P.is_low) {
-                run_stage<R, NV, 0, OPS>(P, X, a, l, acc0, acc1);
+            X.run2 = (R)1;
+            if (!FUSE && P.is_low) {
+                run_stage<R, NV, 0, OPS>(P, X, a, l, acc0, acc1, acc2);
                 X.first = false;
                 bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
                 if (!bad) {
-                    run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1);
+                    run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1, acc2);
                     if (!P.skip_last)
                         compute_sync<NTHR>();
                 }
-            } else {
-                run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1);
+            } else {  // a high pass (every fused pass is one)
+                run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1, acc2);
                 X.first = false;
                 bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
             }
@@ -1263,8 +1332,13 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 ok = false;
                 break;
             }
-            if (!P.skip_last)  // a low pass over the qubits of stages 0 and 1 only ends here
-                run_stage<R, NV, 2, OPS>(P, X, a, l, acc0, acc1);
+            if (FUSE) {  // layer `layer` ends in stage 2, layer2 starts there and ends in stage 1
+                run_stage<R, NV, 2, OPS, true>(P, X, a, l, acc0, acc1, acc2);
+                compute_sync<NTHR>();
+                mix_stage<R, NV, 1>(P, X, a, l, acc2);
+            } else if (!P.skip_last) {  // a low pass over the qubits of stages 0 and 1 only ends here
+                run_stage<R, NV, 2, OPS>(P, X, a, l, acc0, acc1, acc2);
+            }
             // results (if any) are in the buffer: hand it to the producer
             fence_proxy_async_smem();
             mbar_arrive(&done[s]);
@@ -1803,13 +1877,16 @@ static int launch_pass_ops(const CUtensorMap &m0, const CUtensorMap &m1, const P
 }
 
 // passes without a pre- or post-operation run the lean instantiation; a batch
-// of different graphs the per-point one
+// of different graphs the per-point one; a fused pass (one graph, high qubits
+// only) its own
 template <typename R, int NV>
 static int launch_pass_t(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid, cudaStream_t st)
 {
-    const bool ops = a.pre_phase || a.pre_lambda || a.post;
+    const bool ops = a.pre_phase || a.pre_lambda || a.post || a.fuse;
     if (!ops)
         return launch_pass_ops<R, NV, 0>(m0, m1, a, grid, st);
+    if (a.fuse)
+        return a.pt || a.is_low ? (int)cudaErrorInvalidValue : launch_pass_ops<R, NV, 3>(m0, m1, a, grid, st);
     return a.pt ? launch_pass_ops<R, NV, 2>(m0, m1, a, grid, st) : launch_pass_ops<R, NV, 1>(m0, m1, a, grid, st);
 }
 

@@ -164,3 +164,87 @@ def test_pass_plans_default_and_validation():
         assert out.tolist() == [0, 0, 0, 0]
     finally:
         N.aaqaoa_destroy(h)
+
+
+def _schedule(h, adjoint):
+    cnt = ctypes.c_int()
+    assert N.aaqaoa_get_schedule(h, adjoint, None, 0, ctypes.byref(cnt)) == 0
+    out = np.zeros((max(cnt.value, 1), 5), dtype=np.int32)
+    assert N.aaqaoa_get_schedule(h, adjoint, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cnt.value,
+                                 ctypes.byref(cnt)) == 0
+    return [tuple(int(v) for v in r) for r in out[:cnt.value]]
+
+
+def _check_schedule(steps, n, p, adjoint, fused):
+    """The launches realise Eq. (1) layer by layer: flattened into (layer,
+    qubit group) mixer steps (a fused launch is two steps with the next
+    layer's diagonal step between them) the layers come in order, each layer
+    mixes every qubit exactly once, j0 counts the layer's qubits mixed
+    before, and the sweep's last launch is a high pass (it carries the
+    last-stage work: energy, or dE/dgamma of layer 0)."""
+    order = list(range(p - 1, -1, -1)) if adjoint else list(range(p))
+    flat = []
+    for s, q, l, l2, j0 in steps:
+        done = sum(qq for (ll, ss, qq) in flat if ll == l)
+        assert j0 == done
+        flat.append((l, s, q))
+        if l2 >= 0:
+            assert s > 0, "fused launches are high passes"
+            assert order.index(l2) == order.index(l) + 1
+            assert all(ll != l2 for (ll, _, _) in flat), "the fused half starts its layer"
+            flat.append((l2, s, q))
+    pos = [order.index(l) for (l, _, _) in flat]
+    assert pos == sorted(pos)
+    for l in range(p):
+        covered = sorted(b for (ll, s, q) in flat if ll == l for b in range(s, s + q))
+        assert covered == list(range(n)), l
+    assert steps[-1][0] > 0 and steps[-1][3] == -1
+    assert steps[0][0] == 0, "each sweep starts with the low pass"
+    nf = sum(1 for st in steps if st[3] >= 0)
+    assert nf == (p - 1 if fused else 0)
+
+
+@pytest.mark.parametrize("n,p,plan4", [(30, 2, (0, 0, 0, 0)), (30, 4, (0, 0, 0, 0)), (30, 5, (9, 3, 12, 3)),
+                                       (22, 3, (13, 2, 8, 3)), (26, 6, (9, 2, 8, 3)), (32, 3, (0, 0, 0, 0))])
+def test_fused_schedule_realises_the_layers_in_order(n, p, plan4):
+    h = _handle(*W.star_graph(n), p=p)
+    try:
+        assert N.aaqaoa_set_pass_plan(h, *plan4) == 0
+        plan = np.zeros(4, dtype=np.int32)
+        assert N.aaqaoa_get_pass_plan(h, plan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))) == 0
+        en = ctypes.c_int()
+        assert N.aaqaoa_get_layer_fusion(h, ctypes.byref(en)) == 0 and en.value == 1
+        for adjoint in (0, 1):
+            K = int(plan[2 * adjoint + 1])
+            steps = _schedule(h, adjoint)
+            _check_schedule(steps, n, p, adjoint, fused=K >= 2)
+            assert len(steps) == p * (K + 1) - (p - 1 if K >= 2 else 0)
+        assert N.aaqaoa_set_layer_fusion(h, 0) == 0
+        for adjoint in (0, 1):
+            K = int(plan[2 * adjoint + 1])
+            steps = _schedule(h, adjoint)
+            _check_schedule(steps, n, p, adjoint, fused=False)
+            assert len(steps) == p * (K + 1)
+    finally:
+        N.aaqaoa_destroy(h)
+
+
+def test_schedule_without_fusion_cases():
+    # one high pass per layer, or one layer: nothing to fuse
+    for n, p, plan4 in ((20, 3, (13, 1, 12, 1)), (30, 1, (0, 0, 0, 0))):
+        h = _handle(*W.star_graph(n), p=p)
+        try:
+            assert N.aaqaoa_set_pass_plan(h, *plan4) == 0
+            for adjoint in (0, 1):
+                steps = _schedule(h, adjoint)
+                assert all(st[3] == -1 for st in steps)
+                _check_schedule(steps, n, p, adjoint, fused=False)
+        finally:
+            N.aaqaoa_destroy(h)
+    h = _handle(*W.cycle_graph(10), p=3)  # whole-circuit kernel: no tiled passes
+    try:
+        assert _schedule(h, 0) == [] and _schedule(h, 1) == []
+        assert N.aaqaoa_set_layer_fusion(h, 2) == -1
+        assert N.aaqaoa_get_schedule(h, 0, None, -1, ctypes.byref(ctypes.c_int())) == -1
+    finally:
+        N.aaqaoa_destroy(h)
