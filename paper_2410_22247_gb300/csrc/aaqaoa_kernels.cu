@@ -456,6 +456,67 @@ __device__ __forceinline__ void store_regs(typename CT<R>::T *sv, uint32_t sb,
     }
 }
 
+// The local index bits a thread's index gives in stage ST, as runs of
+// consecutive thread bits that move by one shift: base = OR of
+// (tid & mask) << shift (a right shift for negative shifts).
+struct BitRuns {
+    int n;
+    uint32_t mask[16];
+    int shift[16];
+};
+template <typename G, int ST>
+__host__ __device__ constexpr BitRuns stage_runs()
+{
+    BitRuns r{0, {}, {}};
+    constexpr int NTB = G::T - G::RB;
+    int j = 0;
+    while (j < NTB) {
+        const int d = G::thr(ST, j) - j;
+        int e = j + 1;
+        while (e < NTB && G::thr(ST, e) - e == d)
+            e++;
+        r.mask[r.n] = ((1u << e) - 1u) & ~((1u << j) - 1u);
+        r.shift[r.n] = d;
+        r.n++;
+        j = e;
+    }
+    return r;
+}
+template <typename G, int ST>
+__device__ __forceinline__ uint32_t stage_base(uint32_t tid)
+{
+    constexpr BitRuns R = stage_runs<G, ST>();
+    uint32_t base = 0;
+#pragma unroll
+    for (int i = 0; i < R.n; i++)
+        base |= R.shift[i] >= 0 ? (tid & R.mask[i]) << R.shift[i] : (tid & R.mask[i]) >> -R.shift[i];
+    return base;
+}
+template <typename G, int ST>
+constexpr bool stage_runs_ok()
+{  // the runs reproduce the bit-by-bit map for every thread index
+    constexpr int NTB = G::T - G::RB;
+    constexpr BitRuns R = stage_runs<G, ST>();
+    for (uint32_t tid = 0; tid < (1u << NTB); tid++) {
+        uint32_t a = 0, b = 0;
+        for (int j = 0; j < NTB; j++)
+            a |= ((tid >> j) & 1u) << G::thr(ST, j);
+        for (int i = 0; i < R.n; i++)
+            b |= R.shift[i] >= 0 ? (tid & R.mask[i]) << R.shift[i] : (tid & R.mask[i]) >> -R.shift[i];
+        if (a != b)
+            return false;
+    }
+    return true;
+}
+static_assert(stage_runs_ok<Geo<float, 1>, 0>() && stage_runs_ok<Geo<float, 1>, 1>() &&
+                  stage_runs_ok<Geo<float, 1>, 2>(), "c64 thread-bit runs");
+static_assert(stage_runs_ok<Geo<float, 2>, 0>() && stage_runs_ok<Geo<float, 2>, 1>() &&
+                  stage_runs_ok<Geo<float, 2>, 2>(), "c64 two-vector thread-bit runs");
+static_assert(stage_runs_ok<Geo<double, 1>, 0>() && stage_runs_ok<Geo<double, 1>, 1>() &&
+                  stage_runs_ok<Geo<double, 1>, 2>(), "c128 thread-bit runs");
+static_assert(stage_runs_ok<Geo<double, 2>, 0>() && stage_runs_ok<Geo<double, 2>, 1>() &&
+                  stage_runs_ok<Geo<double, 2>, 2>(), "c128 two-vector thread-bit runs");
+
 // A cut function as neighbour masks nbr[c * MAXN + u] with class weights w[c].
 struct CutView {
     const uint64_t *nbr;
@@ -486,6 +547,7 @@ struct StageCtx {
     R fn, fn2;     // f^n and f^(2n): one whole layer of butterflies
     R scale0;      // f^j0: butterflies of this layer applied by earlier passes
     R run;         // f^j for the current tile (advanced by every butterfly)
+    R amp0;        // 2^(-n/2), the amplitude of the generated |+>^n
     R tq2, f2;     // fused pass: rotation of the second layer
     R run2;        // its f^j (the second layer starts on exact vectors: j = 0)
 };
@@ -571,6 +633,30 @@ __device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int
     }
 }
 
+// A thread's running sum over its tiles. complex64: a pair (hi, lo) of floats
+// updated by Knuth's TwoSum, so that hi + lo is the exact sum of the added
+// floats up to about 2^-47 relative, with the work on the FP32 pipes (FP64
+// instructions are slow on this part). complex128: a double.
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+    double v;
+    __device__ __forceinline__ void zero() { v = 0.0; }
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double get() const { return v; }
+};
+template <> struct Acc<float> {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = lo = 0.f; }
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = hi + x;
+        const float bp = t - hi;
+        lo += (hi - (t - bp)) + (x - bp);
+        hi = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+
 // The butterflies of stage ST due in this pass, with rotation t = tq and
 // dropped factor f; run is f^j on entry (j butterflies of the layer already
 // applied) and is advanced. Rotations (twisted frame), no rescaling: after j
@@ -581,7 +667,7 @@ __device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int
 template <typename R, int NV, int ST>
 __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R &run,
                                          typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
-                                         typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc)
+                                         typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc)
 {
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
@@ -621,7 +707,7 @@ __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R
     }
     run = sc;
     if constexpr (NV == 2)
-        acc += (double)gb;
+        acc.add(gb);
 }
 
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
@@ -630,25 +716,22 @@ __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R
 template <typename R, int NV, int ST, bool OPS, bool FUSE = false>
 __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
-                                          typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc0,
-                                          double &acc1, double &acc2)
+                                          typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc0,
+                                          Acc<R> &acc1, Acc<R> &acc2)
 {
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
     constexpr int RB = G::RB, NR = 1 << RB, NTB = G::T - RB;
     constexpr bool LAST = (ST == G::NST - 1);
 
-    uint32_t base = 0;
-#pragma unroll
-    for (int j = 0; j < NTB; j++)
-        base |= ((uint32_t(X.tid) >> j) & 1u) << G::thr(ST, j);
+    const uint32_t base = stage_base<G, ST>((uint32_t)X.tid);
     const uint32_t sb = G::swz(base);
 
     if (ST == 0 && !A.load) {  // |+>^n in the twisted frame: 2^(-n/2) i^|x|
         // the four values amp * i^((c0 + j) & 3) once, then a compile-time
         // choice by the register index's own bit count
         const int c0 = (__popcll(X.fixed) + __popc(base)) & 3;
-        const R amp = (R)A.amp0;
+        const R amp = X.amp0;
         C zc[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
@@ -703,7 +786,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
 #pragma unroll
         for (int m = 0; m < NR; m++)
             e += (a[m].x * a[m].x + a[m].y * a[m].y) * ov[m];
-        acc0 += (A.post & POST_RESCALE) ? (double)e : (double)e * (double)X.fn2;
+        acc0.add((A.post & POST_RESCALE) ? e : e * X.fn2);
     }
     if constexpr (NV == 2) {
         if (OPS && LAST && (A.post & (POST_GAMMA | POST_PHASE_CONJ))) {
@@ -714,7 +797,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
 #pragma unroll
                 for (int m = 0; m < NR; m++)
                     g += cr[m] * im_conj_mul(l[m], a[m]);
-                acc1 += (double)g * (double)X.fn2;  // both vectors carry 1/f^n here
+                acc1.add(g * X.fn2);  // both vectors carry 1/f^n here
             }
             if (A.post & POST_PHASE_CONJ) {  // inverse cost layer, restoring f^n
                 int cv[NR];
@@ -750,14 +833,11 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
 template <typename R, int NV, int ST>
 __device__ __forceinline__ void mix_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
-                                          typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], double &acc2)
+                                          typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc2)
 {
     using G = Geo<R, NV>;
     constexpr int NTB = G::T - G::RB;
-    uint32_t base = 0;
-#pragma unroll
-    for (int j = 0; j < NTB; j++)
-        base |= ((uint32_t(X.tid) >> j) & 1u) << G::thr(ST, j);
+    const uint32_t base = stage_base<G, ST>((uint32_t)X.tid);
     const uint32_t sb = G::swz(base);
     load_regs<R, NV, ST>(X.sv0, sb, a);
     if constexpr (NV == 2)
@@ -1062,10 +1142,11 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     if (tid < NTHR && !MG && (est[0] >= 0 || est[1] >= 0))
         launch_consts(0);
 
+    const int tiles_log2 = __ffs(A.tiles) - 1;  // tiles per state: a power of two
     auto tile_coords = [&](unsigned k, unsigned &b, unsigned &t, unsigned &mid, int &c4) {
         const unsigned g = cta_tile(blockIdx.x, k, grid, (unsigned)A.chunk);
-        b = g / (unsigned)A.tiles;
-        t = g - b * (unsigned)A.tiles;
+        b = g >> tiles_log2;
+        t = g & ((unsigned)A.tiles - 1u);
         mid = t & ((1u << midbits) - 1u);
         const unsigned hi = t >> midbits;
         c4 = (int)(hi + b * tiles_per_hi);
@@ -1184,7 +1265,10 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         // ------------------------------------------------------- compute
         const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.j0,
                          A.skip_last, A.amp0};
-        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+        Acc<R> acc0, acc1, acc2;
+        acc0.zero();
+        acc1.zero();
+        acc2.zero();
         int cur_b = -1;
         StageCtx<R> X;
         X.tab = tab;
@@ -1194,6 +1278,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         X.s = A.s;
         X.cb = cb;
         X.tid = tid;
+        X.amp0 = (R)A.amp0;
         X.first = true;
 
         // A point change costs no extra barrier. The phase table has two
@@ -1207,19 +1292,22 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         int pend_b = -1, tslot = 1, par = 1;
         auto stash = [&](int b) {
 #pragma unroll
+            double s0 = acc0.get(), s1 = acc1.get(), s2 = acc2.get();
             for (int o = 16; o > 0; o >>= 1) {
-                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
-                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
                 if constexpr (FUSE)
-                    acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             }
             par ^= 1;
             if (lane == 0) {
-                pred[par][0][warp] = acc0;
-                pred[par][1][warp] = acc1;
-                pred[par][2][warp] = acc2;
+                pred[par][0][warp] = s0;
+                pred[par][1][warp] = s1;
+                pred[par][2][warp] = s2;
             }
-            acc0 = acc1 = acc2 = 0.0;
+            acc0.zero();
+            acc1.zero();
+            acc2.zero();
             pend_b = b;
         };
         auto write_pending = [&]() {  // after a barrier
@@ -1882,6 +1970,8 @@ static int launch_pass_ops(const CUtensorMap &m0, const CUtensorMap &m1, const P
 template <typename R, int NV>
 static int launch_pass_t(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid, cudaStream_t st)
 {
+    if (a.tiles < 1 || (a.tiles & (a.tiles - 1)))  // the kernel splits tile indices with shifts
+        return (int)cudaErrorInvalidValue;
     const bool ops = a.pre_phase || a.pre_lambda || a.post || a.fuse;
     if (!ops)
         return launch_pass_ops<R, NV, 0>(m0, m1, a, grid, st);
