@@ -449,14 +449,14 @@ def traffic_from_profiles():
     return None
 
 
-def profile_case(n):
-    """Two energy+gradient evaluations (p = 2, complex64, H_red) of the star on n qubits."""
+def profile_case(n, precision="c64"):
+    """Two energy+gradient evaluations (p = 2, H_red) of the star on n qubits."""
     import torch
     from paper_2410_22247_gb300 import orbits as ORB
     from paper_2410_22247_gb300 import workloads as W
     from paper_2410_22247_gb300.api import Plan
     nn, e = W.star_graph(n)
-    pl = Plan(nn, e, P_LAYERS, orbits=ORB.edge_orbits(nn, e), precision="c64", with_grad=True)
+    pl = Plan(nn, e, P_LAYERS, orbits=ORB.edge_orbits(nn, e), precision=precision, with_grad=True)
     g, b = W.random_angles(P_LAYERS, 3)
     for _ in range(2):
         E, dg, db = pl.grad(g, b, "red")
@@ -473,9 +473,11 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side-by-side extras")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="run two energy+gradient evaluations of the star on N qubits (a small case for ncu) and exit")
+    ap.add_argument("--profile-precision", default="c64", choices=["c64", "c128"],
+                    help="precision of the --profile-case evaluations")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case)
+        profile_case(args.profile_case, args.profile_precision)
         return
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
