@@ -622,6 +622,7 @@ int enqueue_expect(aaqaoa_plan *pl, int B, const double *d_gamma, const double *
         CKL(launch_small(pl->c128, s, B, pl->stream), "whole-circuit kernel");
         pl->launches++;
     } else {
+        pl->state_valid = false;  // the passes overwrite the stored state
         r = enqueue_forward(pl, B, obs, materialise ? FWD_STATE : FWD_ENERGY);
         if (r)
             return r;

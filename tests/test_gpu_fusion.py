@@ -156,3 +156,20 @@ def test_fused_static_scratch_energy(precision):
             assert abs(E.value - Er) <= TOL[precision] * max(abs(Er), 1.0), (fused, E.value, Er)
     finally:
         N.aaqaoa_destroy(h)
+
+
+def test_aggregate_only_refuses_a_state_overwritten_by_a_fused_energy():
+    """A fused energy call streams the state through the passes without
+    storing the final state, so the stored state is gone afterwards."""
+    from paper_2410_22247_gb300._native import AAQAOAError
+    n, e = W.prufer_tree(22, 9)
+    p = 2
+    g, b = W.random_angles(p, 91)
+    pl = _plan(n, e, p, "c64", grad=False)
+    E1 = pl.expect(g, b, "red", "singlepass")  # stores the final state
+    assert abs(pl.aggregate_only("red") - E1) <= 1e-5 * max(abs(E1), 1.0)
+    pl.expect(*W.random_angles(p, 92), "red")  # fused: the passes overwrite it
+    with pytest.raises(AAQAOAError, match="INVALID_ARG"):
+        pl.aggregate_only("red")
+    pl.statevector(g, b)  # stored again
+    assert abs(pl.aggregate_only("red") - E1) <= 1e-5 * max(abs(E1), 1.0)
