@@ -189,12 +189,6 @@ __device__ __forceinline__ void tma_store_5d(const CUtensorMap *map, const void 
         : "memory");
 }
 
-__device__ __forceinline__ void tma_store_commit_and_wait_read()
-{
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -848,26 +842,6 @@ __device__ __forceinline__ void mix_stage(const PassRegs &A, StageCtx<R> &X,
         store_regs<R, NV, ST>(X.sv1, sb, l);
 }
 
-// Sums over all threads of the block (any multiple of 32 threads).
-__device__ __forceinline__ double block_sum_all(double a, double (*red)[32])
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-        red[0][w] = a;
-    __syncthreads();
-    if (w == 0) {
-        a = lane < nw ? red[0][lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-    }
-    return a;
-}
-
 // Named barrier 1 spans the NTHR compute threads only (the producer warp
 // never takes part).
 template <int NTHR>
@@ -891,34 +865,6 @@ __device__ __forceinline__ bool compute_sync_or(bool flag)
         : "r"((uint32_t)flag), "n"(NTHR)
         : "memory");
     return r != 0;
-}
-
-// (a, b) summed over the NTHR compute threads; valid in thread 0.
-template <int NTHR>
-__device__ __forceinline__ void compute_sum2(double &a, double &b, double (*red)[32])
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    compute_sync<NTHR>();
-    if (lane == 0) {
-        red[0][w] = a;
-        red[1][w] = b;
-    }
-    compute_sync<NTHR>();
-    if (w == 0) {
-        constexpr int NW = NTHR / 32;
-        a = lane < NW ? red[0][lane] : 0.0;
-        b = lane < NW ? red[1][lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-    }
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -1291,8 +1237,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         const int lane = tid & 31, warp = tid >> 5;
         int pend_b = -1, tslot = 1, par = 1;
         auto stash = [&](int b) {
-#pragma unroll
             double s0 = acc0.get(), s1 = acc1.get(), s2 = acc2.get();
+#pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 s0 += __shfl_xor_sync(0xffffffffu, s0, o);
                 s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -1622,7 +1568,7 @@ __global__ void __launch_bounds__(256) k_small_multi(const SmallGraph *__restric
 {
     using C = typename CT<R>::T;
     constexpr int NT = 256;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_multi[];
     __shared__ double red[2][32];
     __shared__ uint64_t s_cost[MAXN], s_obs[MAXK * MAXN];
     __shared__ int s_w[MAXK];
@@ -1637,7 +1583,7 @@ __global__ void __launch_bounds__(256) k_small_multi(const SmallGraph *__restric
         s_obs[i] = D.obs[obs][i / MAXN][i % MAXN];
     if (tid < MAXK)
         s_w[tid] = D.w[obs][tid];
-    C *phi = reinterpret_cast<C *>(smem_raw);
+    C *phi = reinterpret_cast<C *>(smem_multi);
     C *tab = phi + N;
     const double TWO_PI = 6.283185307179586476925286766559;
     const double amp0 = rsqrt((double)N);

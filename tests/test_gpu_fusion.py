@@ -173,3 +173,24 @@ def test_aggregate_only_refuses_a_state_overwritten_by_a_fused_energy():
         pl.aggregate_only("red")
     pl.statevector(g, b)  # stored again
     assert abs(pl.aggregate_only("red") - E1) <= 1e-5 * max(abs(E1), 1.0)
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_fused_weighted_maxcut_matches_oracle(precision):
+    """Weighted MaxCut (integer weights 1..3) through fused boundaries: the
+    next layer's phase table is indexed by the weighted cut value."""
+    from paper_2410_22247_gb300.api import Plan
+    n, e = W.prufer_tree(22, 9)
+    w = [1 + (k % 3) for k in range(len(e))]
+    p = 3
+    g, b = W.random_angles(p, 95)
+    Er, dgr, dbr = O.energy_grad_w(n, e, w, g, b)
+    pl = Plan(n, e, p, orbits=ORB.edge_orbits(n, e, weights=w), precision=precision, with_grad=True, weights=w)
+    pl.set_pass_plan(*PLANS[precision][0])
+    assert pl.layer_fusion()
+    tol = TOL[precision]
+    gscale = max(abs(Er), 1.0) if precision == "c64" else 1e-3 * max(abs(Er), 1.0)
+    for obs in ("red", "full"):
+        E, dg, db = pl.grad(g, b, obs)
+        assert abs(E - Er) <= tol * max(abs(Er), 1.0), (obs, E, Er)
+        assert _rel(dg, dgr, gscale) < tol and _rel(db, dbr, gscale) < tol, obs
