@@ -286,7 +286,8 @@ def run_native(args, rank, world, local):
     result = {
         "ms": ms_max, "evals_per_s": whole_job_rate(world, K, ms_max / 1000.0), "prof": prof, "launches": launches,
         "clocks": clk.summary(), "e2e_evals_per_s": whole_job_rate(world, k_e2e, t_e2e),
-        "E0": float(res[0, 0]), "pass_plan": pass_plan,
+        "E0": float(res[0, 0]), "pass_plan": pass_plan, "layer_fusion": plan.layer_fusion(),
+        "launches_per_sweep": [len(plan.schedule(False)), len(plan.schedule(True))],
     }
     extra = {}
     if rank == 0 and not args.quick:
@@ -514,7 +515,9 @@ def main():
                    "pass_plan": {"forward_low_qubits": result["pass_plan"][0],
                                  "forward_high_passes": result["pass_plan"][1],
                                  "adjoint_low_qubits": result["pass_plan"][2],
-                                 "adjoint_high_passes": result["pass_plan"][3], "chosen_by": "autotune"}},
+                                 "adjoint_high_passes": result["pass_plan"][3], "chosen_by": "autotune",
+                                 "layer_fusion": result["layer_fusion"],
+                                 "passes_forward_adjoint": result["launches_per_sweep"]}},
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": traffic_from_profiles(),
