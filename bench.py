@@ -465,6 +465,23 @@ def profile_case(n, precision="c64"):
     print(json.dumps({"profile_case": n, "E": E, "dgamma": list(dg), "dbeta": list(db)}))
 
 
+def profile_landscape(points):
+    """Two calls of the p = 1 landscape on the star S_19 (n = 20) over the
+    first `points` points of the 64 x 64 grid (a small case for ncu)."""
+    import torch
+    from paper_2410_22247_gb300 import orbits as ORB
+    from paper_2410_22247_gb300 import workloads as W
+    from paper_2410_22247_gb300.api import Plan
+    n, e = W.star_graph(20)
+    gs, bs = W.angle_grid(64)
+    gs, bs = gs[:points], bs[:points]
+    pl = Plan(n, e, 1, orbits=ORB.edge_orbits(n, e), precision="c64", batch=points, with_grad=False)
+    for _ in range(2):
+        E = pl.expect_batch(gs, bs, "red")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_landscape": points, "E_first": float(E[0]), "E_last": float(E[-1])}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -476,9 +493,14 @@ def main():
                     help="run two energy+gradient evaluations of the star on N qubits (a small case for ncu) and exit")
     ap.add_argument("--profile-precision", default="c64", choices=["c64", "c128"],
                     help="precision of the --profile-case evaluations")
+    ap.add_argument("--profile-landscape", type=int, default=0, metavar="B",
+                    help="run two calls of the S_19 landscape over B points (a small case for ncu) and exit")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_case, args.profile_precision)
+        return
+    if args.profile_landscape:
+        profile_landscape(args.profile_landscape)
         return
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
