@@ -412,23 +412,72 @@ __host__ __device__ constexpr uint32_t reg_offset(int st, int m)
     return off;
 }
 
+// Shared-memory index of register m in stage ST: sb ^ K_m, sb = swz(thread
+// bits), K_m = swz(register bits of m). Only the bits in LOW (those sb and
+// some K_m can both have: the swizzle's target bits) need the XOR; the rest
+// add. So sb ^ K_m = (sb & ~LOW) + (K_m & ~LOW) + ((sb & LOW) ^ (K_m & LOW)):
+// at most 2^|LOW| distinct bases per stage, each access a compile-time
+// offset from one of them (checked below for every thread and register).
+template <typename G, int ST>
+__host__ __device__ constexpr uint32_t split_low()
+{
+    uint32_t sbits = 0, kbits = 0;
+    for (int j = 0; j < G::T - G::RB; j++)
+        sbits |= G::swz(1u << G::thr(ST, j));
+    for (int k = 0; k < G::RB; k++)
+        kbits |= G::swz(1u << G::reg(ST, k));
+    return sbits & kbits;
+}
+template <typename G, int ST>
+__device__ __forceinline__ uint32_t smem_index(uint32_t sbh, uint32_t sbl, int m)
+{
+    constexpr uint32_t LOW = split_low<G, ST>();
+    const uint32_t K = G::swz(reg_offset<G>(ST, m));
+    return (sbh + (sbl ^ (K & LOW))) + (K & ~LOW);
+}
+template <typename G, int ST>
+constexpr bool split_ok()
+{
+    constexpr int NTB = G::T - G::RB;
+    constexpr uint32_t LOW = split_low<G, ST>();
+    for (uint32_t tid = 0; tid < (1u << NTB); tid++) {
+        uint32_t base = 0;
+        for (int j = 0; j < NTB; j++)
+            base |= ((tid >> j) & 1u) << G::thr(ST, j);
+        const uint32_t sb = G::swz(base);
+        for (int m = 0; m < (1 << G::RB); m++) {
+            const uint32_t K = G::swz(reg_offset<G>(ST, m));
+            if ((sb ^ K) != (sb & ~LOW) + (K & ~LOW) + ((sb & LOW) ^ (K & LOW)))
+                return false;
+        }
+    }
+    return true;
+}
+static_assert(split_ok<Geo<float, 1>, 0>() && split_ok<Geo<float, 1>, 1>() && split_ok<Geo<float, 1>, 2>() &&
+                  split_ok<Geo<float, 2>, 0>() && split_ok<Geo<float, 2>, 1>() && split_ok<Geo<float, 2>, 2>() &&
+                  split_ok<Geo<double, 1>, 0>() && split_ok<Geo<double, 1>, 1>() && split_ok<Geo<double, 1>, 2>() &&
+                  split_ok<Geo<double, 2>, 0>() && split_ok<Geo<double, 2>, 1>() && split_ok<Geo<double, 2>, 2>(),
+              "shared-memory index split");
+
 template <typename R, int NV, int ST>
 __device__ __forceinline__ void load_regs(const typename CT<R>::T *sv, uint32_t sb,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB])
 {
     using G = Geo<R, NV>;
     constexpr int NR = 1 << G::RB;
+    constexpr uint32_t LOW = split_low<G, ST>();
+    const uint32_t sbh = sb & ~LOW, sbl = sb & LOW;
     if constexpr (std::is_same<R, float>::value && G::reg(ST, 0) == 0) {
 #pragma unroll
         for (int m = 0; m < NR; m += 2) {
-            const float4 v = *reinterpret_cast<const float4 *>(&sv[sb ^ G::swz(reg_offset<G>(ST, m))]);
+            const float4 v = *reinterpret_cast<const float4 *>(&sv[smem_index<G, ST>(sbh, sbl, m)]);
             a[m] = make_float2(v.x, v.y);
             a[m + 1] = make_float2(v.z, v.w);
         }
     } else {
 #pragma unroll
         for (int m = 0; m < NR; m++)
-            a[m] = sv[sb ^ G::swz(reg_offset<G>(ST, m))];
+            a[m] = sv[smem_index<G, ST>(sbh, sbl, m)];
     }
 }
 
@@ -438,15 +487,17 @@ __device__ __forceinline__ void store_regs(typename CT<R>::T *sv, uint32_t sb,
 {
     using G = Geo<R, NV>;
     constexpr int NR = 1 << G::RB;
+    constexpr uint32_t LOW = split_low<G, ST>();
+    const uint32_t sbh = sb & ~LOW, sbl = sb & LOW;
     if constexpr (std::is_same<R, float>::value && G::reg(ST, 0) == 0) {
 #pragma unroll
         for (int m = 0; m < NR; m += 2)
-            *reinterpret_cast<float4 *>(&sv[sb ^ G::swz(reg_offset<G>(ST, m))]) =
+            *reinterpret_cast<float4 *>(&sv[smem_index<G, ST>(sbh, sbl, m)]) =
                 make_float4(a[m].x, a[m].y, a[m + 1].x, a[m + 1].y);
     } else {
 #pragma unroll
         for (int m = 0; m < NR; m++)
-            sv[sb ^ G::swz(reg_offset<G>(ST, m))] = a[m];
+            sv[smem_index<G, ST>(sbh, sbl, m)] = a[m];
     }
 }
 
