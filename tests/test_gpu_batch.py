@@ -106,3 +106,28 @@ def test_expired_wait_is_reported_and_the_plan_recovers():
     assert abs(pl.expect(g, b) - ref) < 1e-5 * ref
     small = Plan(*W.cycle_graph(6), 1, with_grad=False)
     assert N.aaqaoa_inject_fault(small.handle, N.AAQAOA_FAULT_DROP_TILE) == -6
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_uneven_batch_with_graphs_beyond_one_high_pass(precision):
+    """Graphs large enough for two high passes per layer (n = 23, 24) in an
+    uneven batch: each group of equal n runs the per-point-graph passes
+    (a graph per point) with the multi-pass plan, against the exact
+    symmetric-subspace energy of stars."""
+    from paper_2410_22247_gb300.api import MultiPlan
+    sizes = [23, 24, 23, 24, 14]
+    graphs = []
+    for n in sizes:
+        nn, e = W.star_graph(n)
+        graphs.append((nn, e, ORB.edge_orbits(nn, e)))
+    p = 2
+    mp = MultiPlan(graphs, p, precision=precision)
+    rng = W.rng(31)
+    gs = rng.uniform(0, np.pi, size=(len(graphs), p))
+    bs = rng.uniform(0, np.pi / 2, size=(len(graphs), p))
+    for obs in ("red", "full"):
+        E = mp.expect(gs, bs, obs)
+        for k, n in enumerate(sizes):
+            ref = SYM.energy(SYM.star_model(n), gs[k], bs[k])
+            assert abs(E[k] - ref) <= TOL[precision] * max(abs(ref), 1.0), (k, n, obs, E[k], ref)
+    mp.close()

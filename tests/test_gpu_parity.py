@@ -420,3 +420,24 @@ def test_large_p_matches_oracle():
         assert e_rel(E, Er) < TOL[precision]
         assert g_rel(dg, dgr, Er, precision) < TOL[precision]
         assert g_rel(db, dbr, Er, precision) < TOL[precision]
+
+
+def test_full_size_star_n34_p1_gradient_c64():
+    """The largest state the library takes (n = 34) through the two-vector
+    adjoint: 2 x 137 GB of workspace, against the exact symmetric-subspace
+    oracle of the star."""
+    torch = pytest.importorskip("torch")
+    _release_cached_device_memory(torch)
+    free, _ = torch.cuda.mem_get_info()
+    if free < 281e9:
+        pytest.skip("needs ~276 GB of free device memory")
+    n, e = W.star_graph(34)
+    g, b = [0.41], [0.27]
+    Er, dgr, dbr = SYM.energy_grad(SYM.star_model(34), g, b)
+    pl, orb = plan_for(n, e, 1, "c64", grad=True)
+    assert orb.num_orbits == 1
+    E, dg, db = pl.grad(g, b, "red")
+    assert e_rel(E, Er) < 1e-5
+    assert g_rel(dg, dgr, Er, "c64") < 1e-5 and g_rel(db, dbr, Er, "c64") < 1e-5
+    pl.close()
+    _release_cached_device_memory(torch)
