@@ -412,6 +412,46 @@ bool plan_fuses(const aaqaoa_plan *pl) { return pl->fuse && !pl->pt_dev; }
 
 enum FwdMode { FWD_ENERGY, FWD_GRAD, FWD_STATE };
 
+// Arguments of launch i (of n) of a forward sweep: pass sp of the schedule
+// over B points. The workspace pointers are the plan's (base_args).
+PassArgs forward_args(const aaqaoa_plan *pl, int obs, int B, const Step &sp, size_t i, size_t n, FwdMode mode)
+{
+    const Pass &ps = pl->passes[sp.k];
+    PassArgs a = base_args(pl, obs);
+    a.B = B;
+    a.s = ps.s;
+    a.cb = ps.cb;
+    a.wide_rows = ps.wide;
+    a.is_low = ps.is_low;
+    a.hmask = ps.hmask;
+    a.skip_last = ps.skip_last;
+    a.layer = sp.layer;
+    a.tab_layer = sp.layer;
+    a.sign_s = 1.0;
+    a.tab = pl->ws ? tab_kind(pl, pl->d_tab(), B, 1) : nullptr;  // the static path sets its own
+    a.load = i > 0;
+    // a layer's phase comes with its first pass, or at the end of the fused
+    // pass that starts it
+    a.pre_phase = sp.first_of_layer ? 1 : 0;
+    a.nvec_io = 1;
+    const bool last = i + 1 == n;
+    a.write = !(last && mode == FWD_ENERGY);
+    a.post = (last && mode != FWD_STATE) ? POST_REDUCE : 0;
+    if (last && a.write)
+        a.post |= POST_RESCALE;
+    if (last && mode != FWD_STATE) {
+        a.slot_idx[0] = 0;
+        a.slot_scale[0] = 1.0;
+    }
+    if (sp.layer2 >= 0) {
+        a.fuse = 1;
+        a.layer2 = sp.layer2;
+        a.tab_layer = sp.layer2;
+        a.post |= POST_PHASE;
+    }
+    return a;
+}
+
 int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
 {
     const long long total = (long long)pl->tiles() * B;
@@ -420,41 +460,8 @@ int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
     const std::vector<Step> sched = layer_schedule(pl->p, pl->passes, plan_fuses(pl), false);
     for (size_t i = 0; i < sched.size(); i++) {
         const Step &sp = sched[i];
-        const Pass &ps = pl->passes[sp.k];
-        const int l = sp.layer;
-        PassArgs a = base_args(pl, obs);
-        a.B = B;
+        PassArgs a = forward_args(pl, obs, B, sp, i, sched.size(), mode);
         a.chunk = chunk;
-        a.s = ps.s;
-        a.cb = ps.cb;
-        a.wide_rows = ps.wide;
-        a.is_low = ps.is_low;
-        a.hmask = ps.hmask;
-        a.skip_last = ps.skip_last;
-        a.layer = l;
-        a.tab_layer = l;
-        a.sign_s = 1.0;
-        a.tab = tab_kind(pl, pl->d_tab(), B, 1);
-        a.load = i > 0;
-        // a layer's phase comes with its first pass, or at the end of the
-        // fused pass that starts it
-        a.pre_phase = sp.first_of_layer ? 1 : 0;
-        a.nvec_io = 1;
-        const bool last = i + 1 == sched.size();
-        a.write = !(last && mode == FWD_ENERGY);
-        a.post = (last && mode != FWD_STATE) ? POST_REDUCE : 0;
-        if (last && a.write)
-            a.post |= POST_RESCALE;
-        if (last && mode != FWD_STATE) {
-            a.slot_idx[0] = 0;
-            a.slot_scale[0] = 1.0;
-        }
-        if (sp.layer2 >= 0) {
-            a.fuse = 1;
-            a.layer2 = sp.layer2;
-            a.tab_layer = sp.layer2;
-            a.post |= POST_PHASE;
-        }
         if (pl->inject == AAQAOA_FAULT_DROP_TILE && a.load) {
             a.drop_first_load = 1;
             pl->inject = 0;
@@ -1658,50 +1665,17 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
         const int grid = pass_grid(pl->tiles());
         const std::vector<Step> sched = layer_schedule(p, pl->passes, plan_fuses(pl), false);
         for (size_t i = 0; i < sched.size(); i++) {
-            const Step &sp = sched[i];
-            const int k = sp.k, l = sp.layer;
-            const Pass &ps = pl->passes[k];
-            PassArgs a;
-            memset(&a, 0, sizeof a);
-            a.n = pl->n;
-            a.s = ps.s;
-            a.cb = ps.cb;
+            const int k = sched[i].k;
+            // the plan's own pass arguments, pointed at the static scratch
+            PassArgs a = forward_args(pl, observable, 1, sched[i], i, sched.size(), FWD_ENERGY);
             a.wide_rows = wide[k];
-            a.is_low = ps.is_low;
-            a.hmask = ps.hmask;
-            a.skip_last = ps.skip_last;
-            a.tiles = pl->tiles();
-            a.B = 1;
-            a.load = i > 0;
-            a.pre_phase = sp.first_of_layer ? 1 : 0;
-            const bool last = i + 1 == sched.size();
-            a.write = !last;
-            a.post = last ? POST_REDUCE : 0;
-            a.nvec_io = 1;
-            a.layer = l;
-            a.tab_layer = l;
-            a.p = p;
-            a.tab_len = pl->tab_len();
-            a.sign_s = 1.0;
-            a.amp0 = std::pow(2.0, -0.5 * pl->n);
             a.tab = tab_kind(pl, d_tab, 1, 1);
             a.cs = d_cs;
             a.partials = d_part;
             a.counter = d_counter;
             a.out = d_out;
-            a.out_stride = pl->out_stride();
-            a.slot_idx[0] = last ? 0 : -1;
-            a.slot_idx[1] = a.slot_idx[2] = -1;
-            a.slot_scale[0] = 1.0;
-            if (sp.layer2 >= 0) {
-                a.fuse = 1;
-                a.layer2 = sp.layer2;
-                a.tab_layer = sp.layer2;
-                a.post |= POST_PHASE;
-            }
             a.err = d_err;
-            a.obs = pl->obs[observable];
-            a.cost = pl->cost;
+            a.pt = nullptr;
             CKL(launch_pass(pl->c128, 1, maps[k], maps[k], a, grid, st), "forward pass");
         }
     }
