@@ -76,7 +76,7 @@ typedef struct aaqaoa_plan aaqaoa_plan; /* opaque, owned by the library */
 #define AAQAOA_ERR_WORKSPACE    (-3) /* no workspace, or one too small/misaligned */
 #define AAQAOA_ERR_CUDA         (-4) /* a CUDA call failed (detail recorded)      */
 #define AAQAOA_ERR_TIMEOUT      (-5) /* a bounded device wait expired             */
-#define AAQAOA_ERR_UNSUPPORTED  (-6) /* valid request this build does not serve   */
+#define AAQAOA_ERR_UNSUPPORTED  (-6) /* valid request the library does not serve */
 
 #define AAQAOA_MAX_QUBITS 34
 
