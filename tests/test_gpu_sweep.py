@@ -76,3 +76,43 @@ def test_random_case_matches_oracle(seed):
     assert np.all(gerr <= tol * np.maximum(np.abs(np.concatenate([dgr, dbr])), floor)), where
     assert abs(pl.expect(g, b, obs) - Er) <= tol * max(abs(Er), 1.0), where
     pl.close()
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_maximum_layer_count_through_fused_boundaries(precision):
+    """p = 64, the largest layer count the library takes: 63 fused
+    boundaries in each sweep (plan with two high passes per layer)."""
+    from paper_2410_22247_gb300.api import Plan
+    n, e = W.prufer_tree(16, 3)
+    p = 64
+    rng = np.random.default_rng(64)
+    g = rng.uniform(-0.4, 0.4, size=p)
+    b = rng.uniform(-0.4, 0.4, size=p)
+    pl = Plan(n, e, p, orbits=ORB.edge_orbits(n, e), precision=precision, with_grad=True)
+    pl.set_pass_plan(9, 2, 8, 2) if precision == "c64" else pl.set_pass_plan(8, 2, 7, 2)
+    assert sum(1 for st in pl.schedule(False) if st[3] >= 0) == p - 1
+    Er, dgr, dbr = O.energy_grad(n, e, g, b)
+    E, dg, db = pl.grad(g, b, "red")
+    tol = TOL[precision]
+    floor = (1.0 if precision == "c64" else 1e-3) * max(abs(Er), 1.0)
+    assert abs(E - Er) <= tol * max(abs(Er), 1.0)
+    gerr = np.abs(np.concatenate([dg, db]) - np.concatenate([dgr, dbr]))
+    assert np.all(gerr <= tol * np.maximum(np.abs(np.concatenate([dgr, dbr])), floor))
+
+
+def test_isolated_qubits():
+    """Vertices without edges (a 12-vertex tree inside n = 18): their qubits
+    still go through the mixer, and the oracle sees the same register."""
+    from paper_2410_22247_gb300.api import Plan
+    _, e = W.prufer_tree(12, 8)
+    n = 18
+    g, b = W.random_angles(3, 12)
+    Er, dgr, dbr = O.energy_grad(n, e, g, b)
+    for precision in ("c64", "c128"):
+        pl = Plan(n, e, 3, orbits=ORB.edge_orbits(n, e), precision=precision, with_grad=True)
+        E, dg, db = pl.grad(g, b, "full")
+        tol = TOL[precision]
+        assert abs(E - Er) <= tol * max(abs(Er), 1.0)
+        floor = (1.0 if precision == "c64" else 1e-3) * max(abs(Er), 1.0)
+        gerr = np.abs(np.concatenate([dg, db]) - np.concatenate([dgr, dbr]))
+        assert np.all(gerr <= tol * np.maximum(np.abs(np.concatenate([dgr, dbr])), floor))
