@@ -259,6 +259,20 @@ def run_native(args, rank, world, local):
                 "profile read")
         if c.value:
             prof[nm] = {"ms": t.value, "launches": c.value, "bytes": by.value}
+    # the tiled passes by class: mixer only, with cut-function work, fused boundary
+    classes = {}
+    for r in plan.profile_launches():
+        if r["kind"] not in (0, 1):
+            continue
+        cls = ("forward" if r["kind"] == 0 else "adjoint") + (
+            "_fused" if r["fused"] else "_cut_work" if r["cut_work"] else "_mixer_only")
+        c = classes.setdefault(cls, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+        c["launches"] += 1
+        c["ms"] += r["ms"]
+        c["bytes"] += r["bytes"]
+    for c in classes.values():
+        c["ms_per_launch"] = c["ms"] / c["launches"]
+        c["GBps"] = c["bytes"] / (c["ms"] / 1000.0) / 1e9
     N.check(N.aaqaoa_profile_enable(plan.handle, 0), "profile")
     plan.sync()
     # results of the timed steps are finite
@@ -285,7 +299,7 @@ def run_native(args, rank, world, local):
 
     result = {
         "ms": ms_max, "evals_per_s": whole_job_rate(world, K, ms_max / 1000.0), "prof": prof, "launches": launches,
-        "clocks": clk.summary(), "e2e_evals_per_s": whole_job_rate(world, k_e2e, t_e2e),
+        "clocks": clk.summary(), "e2e_evals_per_s": whole_job_rate(world, k_e2e, t_e2e), "pass_classes": classes,
         "E0": float(res[0, 0]), "pass_plan": pass_plan, "layer_fusion": plan.layer_fusion(),
         "launches_per_sweep": [len(plan.schedule(False)), len(plan.schedule(True))],
     }
@@ -547,6 +561,7 @@ def main():
         "step_algorithmic": {"bytes": B_alg, "formula": "(6p+1)*2^n*8",
                              "GBps": B_alg / (result["ms"] / args.steps / 1000.0) / 1e9},
         "kernels": prof,
+        "pass_classes": result["pass_classes"],
         "cpu_baseline": cpu,
         "e2e": {"value": result["e2e_evals_per_s"], "unit": "evals/s", "h2d_bytes_per_step": 2 * P_LAYERS * 8,
                 "d2h_bytes_per_step": 4 + (1 + 2 * P_LAYERS) * 8},

@@ -446,6 +446,19 @@ int aaqaoa_launch_count(const aaqaoa_plan *plan, int *launches);
 int aaqaoa_profile_enable(aaqaoa_plan *plan, int enable);
 int aaqaoa_profile_read(aaqaoa_plan *plan, int kind, double *ms_total, int *launches, double *bytes);
 
+/*
+ * aaqaoa_profile_launches -- the recorded launches one by one, in launch
+ * order: per launch its kind (as above), flags (bit 0: the pass carries
+ * cut-function work -- phase, lambda = O phi, energy, dE/dgamma, inverse
+ * phase; bit 1: a fused layer boundary), event duration (ms) and bytes to
+ * move. kind, flags, ms, bytes: host arrays of at least max entries, each may
+ * be NULL. *count (host int) receives the number of records, also when it
+ * exceeds max. Synchronises the plan's stream. INVALID_ARG for a NULL plan
+ * or count, or max < 0.
+ */
+int aaqaoa_profile_launches(aaqaoa_plan *plan, int max, int *count, int *kind, int *flags, double *ms,
+                            double *bytes);
+
 /* Release a plan (not the workspace, which the caller owns). NULL is a no-op. */
 void aaqaoa_destroy(aaqaoa_plan *plan);
 

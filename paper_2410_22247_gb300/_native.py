@@ -81,6 +81,8 @@ _PROTOS = [
     ("aaqaoa_launch_count", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     ("aaqaoa_profile_enable", ctypes.c_int, [_vp, ctypes.c_int]),
     ("aaqaoa_profile_read", ctypes.c_int, [_vp, ctypes.c_int, _f64p, ctypes.POINTER(ctypes.c_int), _f64p]),
+    ("aaqaoa_profile_launches", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i32p, _i32p, _f64p,
+                                               _f64p]),
     ("aaqaoa_destroy", None, [_vp]),
     ("aaqaoa_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("aaqaoa_last_error_detail", ctypes.c_char_p, []),

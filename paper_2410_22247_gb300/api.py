@@ -152,6 +152,25 @@ class Plan:
                                       ctypes.byref(cnt)), "aaqaoa_get_schedule")
         return [tuple(int(v) for v in r) for r in out[:cnt.value]]
 
+    def profile_launches(self):
+        """The launches recorded since profiling was enabled
+        (aaqaoa_profile_enable), in order: dicts of kind (0 forward pass,
+        1 adjoint pass, 2 whole circuit, 3 aggregation, 4 parameter tables),
+        cut_work, fused, ms and bytes."""
+        cnt = ctypes.c_int()
+        N.check(N.aaqaoa_profile_launches(self.handle, 0, ctypes.byref(cnt), None, None, None, None),
+                "aaqaoa_profile_launches")
+        n = cnt.value
+        kind = np.zeros(max(n, 1), dtype=np.int32)
+        flags = np.zeros(max(n, 1), dtype=np.int32)
+        ms = np.zeros(max(n, 1))
+        by = np.zeros(max(n, 1))
+        N.check(N.aaqaoa_profile_launches(self.handle, n, ctypes.byref(cnt), _ptr(kind, ctypes.c_int32),
+                                          _ptr(flags, ctypes.c_int32), _ptr(ms, ctypes.c_double),
+                                          _ptr(by, ctypes.c_double)), "aaqaoa_profile_launches")
+        return [{"kind": int(kind[i]), "cut_work": bool(flags[i] & 1), "fused": bool(flags[i] & 2),
+                 "ms": float(ms[i]), "bytes": float(by[i])} for i in range(n)]
+
     def autotune(self):
         """Time the candidate pass plans and keep the fastest; returns pass_plan()."""
         out = np.zeros(4, dtype=np.int32)

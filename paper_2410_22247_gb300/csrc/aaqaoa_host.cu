@@ -129,6 +129,7 @@ struct aaqaoa_plan {
     bool prof = false;
     struct ProfRec {
         int kind;
+        int flags;  // bit 0: cut-function work, bit 1: fused layer boundary
         double bytes;
         cudaEvent_t a, b;
     };
@@ -187,8 +188,9 @@ struct ProfScope {
     aaqaoa_plan *pl;
     int kind;
     double bytes;
+    int flags;
     cudaEvent_t a = nullptr;
-    ProfScope(aaqaoa_plan *p, int k, double by) : pl(p), kind(k), bytes(by)
+    ProfScope(aaqaoa_plan *p, int k, double by, int fl = 0) : pl(p), kind(k), bytes(by), flags(fl)
     {
         if (pl->prof) {
             a = prof_event(pl);
@@ -200,10 +202,16 @@ struct ProfScope {
         if (pl->prof) {
             cudaEvent_t b = prof_event(pl);
             cudaEventRecord(b, pl->stream);
-            pl->prof_recs.push_back({kind, bytes, a, b});
+            pl->prof_recs.push_back({kind, flags, bytes, a, b});
         }
     }
 };
+
+// profile flags of a tiled pass
+int pass_flags(const PassArgs &a)
+{
+    return ((a.pre_phase || a.pre_lambda || a.post) ? 1 : 0) | (a.fuse ? 2 : 0);
+}
 
 Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
 {
@@ -467,7 +475,7 @@ int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
             pl->inject = 0;
         }
         const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
-        ProfScope ps_(pl, PK_FWD, S * ((a.load ? 1 : 0) + (a.write ? 1 : 0)));
+        ProfScope ps_(pl, PK_FWD, S * ((a.load ? 1 : 0) + (a.write ? 1 : 0)), pass_flags(a));
         CKL(launch_pass(pl->c128, 1, pl->map_phi[sp.k], pl->map_phi[sp.k], a, grid, pl->stream), "forward pass");
         pl->launches++;
     }
@@ -525,7 +533,7 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
             a.slot_scale[2] = 2.0;
         }
         const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
-        ProfScope ps_(pl, PK_ADJ, S * (a.nvec_io + (a.write ? 2 : 0)));
+        ProfScope ps_(pl, PK_ADJ, S * (a.nvec_io + (a.write ? 2 : 0)), pass_flags(a));
         CKL(launch_pass(pl->c128, 2, pl->map_bphi[sp.k], pl->map_blam[sp.k], a, grid, pl->stream), "adjoint pass");
         pl->launches++;
     }
@@ -1528,6 +1536,24 @@ int aaqaoa_profile_read(aaqaoa_plan *pl, int kind, double *ms_total, int *launch
     if (ms_total) *ms_total = ms;
     if (launches) *launches = cnt;
     if (bytes) *bytes = by;
+    return AAQAOA_OK;
+}
+
+int aaqaoa_profile_launches(aaqaoa_plan *pl, int max, int *count, int *kind, int *flags, double *ms, double *bytes)
+{
+    if (!pl || !count || max < 0)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan or count NULL, or max < 0");
+    CK(cudaStreamSynchronize(pl->stream));
+    *count = (int)pl->prof_recs.size();
+    for (int i = 0; i < max && i < (int)pl->prof_recs.size(); i++) {
+        const auto &r = pl->prof_recs[i];
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, r.a, r.b));
+        if (kind) kind[i] = r.kind;
+        if (flags) flags[i] = r.flags;
+        if (ms) ms[i] = t;
+        if (bytes) bytes[i] = r.bytes;
+    }
     return AAQAOA_OK;
 }
 

@@ -194,3 +194,29 @@ def test_fused_weighted_maxcut_matches_oracle(precision):
         E, dg, db = pl.grad(g, b, obs)
         assert abs(E - Er) <= tol * max(abs(Er), 1.0), (obs, E, Er)
         assert _rel(dg, dgr, gscale) < tol and _rel(db, dbr, gscale) < tol, obs
+
+
+def test_profile_records_each_launch_of_the_schedule():
+    """aaqaoa_profile_launches lists the launches of a gradient call in
+    order: the parameter tables, the forward sweep, the adjoint sweep, with
+    the fused boundaries flagged where the schedule has them."""
+    from paper_2410_22247_gb300 import _native as N
+    n, e = W.prufer_tree(22, 9)
+    p = 3
+    g, b = W.random_angles(p, 97)
+    pl = _plan(n, e, p, "c64")
+    pl.set_pass_plan(*PLANS["c64"][0])
+    fwd, adj = pl.schedule(False), pl.schedule(True)
+    N.check(N.aaqaoa_profile_enable(pl.handle, 1), "profile")
+    pl.grad(g, b, "red")
+    recs = pl.profile_launches()
+    N.check(N.aaqaoa_profile_enable(pl.handle, 0), "profile")
+    kinds = [r["kind"] for r in recs]
+    assert kinds == [4] + [0] * len(fwd) + [1] * len(adj)
+    fused = [r["fused"] for r in recs[1:]]
+    assert fused == [st[3] >= 0 for st in fwd] + [st[3] >= 0 for st in adj]
+    assert sum(fused) == 2 * (p - 1)
+    assert recs[1]["cut_work"] and recs[len(fwd)]["cut_work"]  # phase first, energy last
+    assert all(r["ms"] > 0 for r in recs[1:])
+    S = (1 << n) * 8
+    assert recs[1]["bytes"] == S and recs[len(fwd) + 1]["bytes"] == 3 * S  # |+> store; phi in, phi and lambda out
