@@ -434,6 +434,26 @@ def batch_extras(dev, stream):
     del pl
     torch.cuda.empty_cache()
 
+    # batched energy + gradient (multi-start optimisation): 16 points of the
+    # n = 22 tree per call against 16 one-point calls
+    n3, e3 = W.prufer_tree(22, 9)
+    B3, p3 = 16, 2
+    rng3 = W.rng(5)
+    g3 = torch.tensor(rng3.uniform(0, np.pi, size=(B3, p3)), device=dev)
+    b3 = torch.tensor(rng3.uniform(0, np.pi / 2, size=(B3, p3)), device=dev)
+    o3 = torch.zeros((B3, 1 + 2 * p3), dtype=torch.float64, device=dev)
+    pl3 = Plan(n3, e3, p3, orbits=ORB.edge_orbits(n3, e3), precision="c64", batch=B3, with_grad=True,
+               stream=stream, device=dev)
+    with torch.cuda.stream(stream):
+        t_batch = timed(lambda: pl3.grad_batch_device(g3, b3, o3, "red"), 5, stream)
+        t_single = timed(lambda: [pl3.grad_device(g3[k], b3[k], o3[k], "red") for k in range(B3)], 2, stream)
+    res["grad_batch_prufer_n22_p2_16pts_c64"] = {"ms_per_call": t_batch, "evals_per_s": B3 / (t_batch / 1000.0),
+                                                  "one_point_calls_evals_per_s": B3 / (t_single / 1000.0),
+                                                  "launches_per_call": pl3.launch_count()}
+    pl3.close()
+    del pl3
+    torch.cuda.empty_cache()
+
     graphs = [(nn, ee, ORB.edge_orbits(nn, ee)) for _, nn, ee in W.mixed_graph_batch(256, 12, 22, 7)]
     mp = MultiPlan(graphs, 2, precision="c64", stream=stream, device=dev)
     rng = W.rng(11)

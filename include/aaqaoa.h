@@ -185,6 +185,19 @@ int aaqaoa_expect_batch(aaqaoa_plan *plan, int B, const double *gamma, const dou
                         int observable, double *energy);
 
 /*
+ * aaqaoa_grad_batch -- energy and adjoint gradient of B parameter points on
+ * the plan's graph (multi-start optimisation, gradient landscapes), the
+ * points of one wave sharing every launch. gamma, beta: host, B*p doubles
+ * (point-major); energy: host, B doubles; dgamma, dbeta: host, B*p doubles
+ * (point-major). Points are processed in waves of the workspace's batch
+ * capacity, which must have been set with with_grad != 0 (two statevectors
+ * per point). Synchronises the plan's stream.
+ * Errors: INVALID_ARG (NULL pointer, B < 1), WORKSPACE, CUDA, TIMEOUT.
+ */
+int aaqaoa_grad_batch(aaqaoa_plan *plan, int B, const double *gamma, const double *beta, int observable,
+                      double *energy, double *dgamma, double *dbeta);
+
+/*
  * Device-pointer forms: the same computations with every argument already in
  * device memory. They only enqueue work on the plan's stream and return; the
  * results are valid once that stream has reached them. A device-side timeout
@@ -199,6 +212,11 @@ int aaqaoa_expect_device(aaqaoa_plan *plan, int B, const double *d_gamma, const 
                          int observable, double *d_energy);
 int aaqaoa_grad_device(aaqaoa_plan *plan, const double *d_gamma, const double *d_beta,
                        int observable, double *d_out);
+/* aaqaoa_grad_batch_device: d_gamma, d_beta: B*p doubles (point-major); d_out:
+ *   B rows of 1 + 2p doubles, [E, dE/dgamma_1..p, dE/dbeta_1..p] per point
+ *   (B <= the workspace's batch capacity; gradient workspace). */
+int aaqaoa_grad_batch_device(aaqaoa_plan *plan, int B, const double *d_gamma, const double *d_beta,
+                             int observable, double *d_out);
 
 /* aaqaoa_sync -- wait for the plan's stream and report any device-side error. */
 int aaqaoa_sync(aaqaoa_plan *plan);

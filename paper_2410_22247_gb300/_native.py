@@ -51,6 +51,8 @@ _PROTOS = [
     ("aaqaoa_expect_batch", ctypes.c_int, [_vp, ctypes.c_int, _f64p, _f64p, ctypes.c_int, _f64p]),
     ("aaqaoa_expect_device", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]),
     ("aaqaoa_grad_device", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    ("aaqaoa_grad_batch", ctypes.c_int, [_vp, ctypes.c_int, _f64p, _f64p, ctypes.c_int, _f64p, _f64p, _f64p]),
+    ("aaqaoa_grad_batch_device", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]),
     ("aaqaoa_sync", ctypes.c_int, [_vp]),
     ("aaqaoa_edge_zz", ctypes.c_int, [_vp, _f64p, _f64p, _f64p]),
     ("aaqaoa_verify_orbits", ctypes.c_int, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),

@@ -103,6 +103,20 @@ class Plan:
                                       OBSERVABLES[observable], _ptr(out, ctypes.c_double)), "aaqaoa_expect_batch")
         return out
 
+    def grad_batch(self, gammas, betas, observable="full"):
+        """(E[B], dE/dgamma[B, p], dE/dbeta[B, p]) of B points (rows of
+        gammas, betas), in waves of the workspace's batch size."""
+        g = _f64(gammas)
+        b = _f64(betas)
+        B = len(g) // self.p
+        E = np.zeros(B)
+        dg = np.zeros(B * self.p)
+        db = np.zeros(B * self.p)
+        N.check(N.aaqaoa_grad_batch(self.handle, B, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
+                                    OBSERVABLES[observable], _ptr(E, ctypes.c_double), _ptr(dg, ctypes.c_double),
+                                    _ptr(db, ctypes.c_double)), "aaqaoa_grad_batch")
+        return E, dg.reshape(B, self.p), db.reshape(B, self.p)
+
     def edge_zz(self, gamma, beta):
         g, b = _f64(gamma), _f64(beta)
         out = np.zeros(len(self.edges))
@@ -226,6 +240,13 @@ class Plan:
         N.check(N.aaqaoa_grad_device(self.handle, ctypes.c_void_p(d_gamma.data_ptr()),
                                      ctypes.c_void_p(d_beta.data_ptr()), OBSERVABLES[observable],
                                      ctypes.c_void_p(d_out.data_ptr())), "aaqaoa_grad_device")
+
+    def grad_batch_device(self, d_gamma, d_beta, d_out, observable="full"):
+        """d_gamma, d_beta: B*p doubles on the device; d_out: B rows of 1 + 2p."""
+        B = d_gamma.numel() // self.p
+        N.check(N.aaqaoa_grad_batch_device(self.handle, B, ctypes.c_void_p(d_gamma.data_ptr()),
+                                           ctypes.c_void_p(d_beta.data_ptr()), OBSERVABLES[observable],
+                                           ctypes.c_void_p(d_out.data_ptr())), "aaqaoa_grad_batch_device")
 
     def sync(self):
         N.check(N.aaqaoa_sync(self.handle), "aaqaoa_sync")

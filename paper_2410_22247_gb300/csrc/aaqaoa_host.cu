@@ -649,23 +649,24 @@ int enqueue_expect(aaqaoa_plan *pl, int B, const double *d_gamma, const double *
     return AAQAOA_OK;
 }
 
-int enqueue_grad(aaqaoa_plan *pl, const double *d_gamma, const double *d_beta, int obs)
+// energy and gradient of B points (rows of d_out)
+int enqueue_grad(aaqaoa_plan *pl, const double *d_gamma, const double *d_beta, int obs, int B = 1)
 {
-    int r = enqueue_params(pl, 1, d_gamma, d_beta);
+    int r = enqueue_params(pl, B, d_gamma, d_beta);
     if (r)
         return r;
     if (pl->small()) {
         SmallArgs s = small_args(pl, obs, SMALL_GRAD, 0);
         ProfScope ps_(pl, PK_SMALL, 0.0);
-        CKL(launch_small(pl->c128, s, 1, pl->stream), "whole-circuit kernel");
+        CKL(launch_small(pl->c128, s, B, pl->stream), "whole-circuit kernel");
         pl->launches++;
         return AAQAOA_OK;
     }
-    r = enqueue_forward(pl, 1, obs, FWD_GRAD);
+    r = enqueue_forward(pl, B, obs, FWD_GRAD);
     if (r)
         return r;
     pl->state_valid = false;
-    return enqueue_backward(pl, 1, obs);
+    return enqueue_backward(pl, B, obs);
 }
 
 // copy [err | pad | out rows] back and check the device error flag
@@ -1240,6 +1241,57 @@ int aaqaoa_expect_batch(aaqaoa_plan *pl, int B, const double *gamma, const doubl
         for (int b = 0; b < Bw; b++)
             energy[b0 + b] = rows[(size_t)b * pl->out_stride()];
     }
+    return AAQAOA_OK;
+}
+
+int aaqaoa_grad_batch(aaqaoa_plan *pl, int B, const double *gamma, const double *beta, int observable,
+                      double *energy, double *dgamma, double *dbeta)
+{
+    g_detail.clear();
+    if (!pl)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan is NULL");
+    if (B < 1 || !energy || !dgamma || !dbeta)
+        return fail(AAQAOA_ERR_INVALID_ARG, "B < 1 or an output pointer is NULL");
+    int r = check_ready(pl, observable, true, 1);
+    if (r)
+        return r;
+    pl->launches = 0;
+    const int p = pl->p;
+    std::vector<double> rows;
+    for (int b0 = 0; b0 < B; b0 += pl->cap) {  // waves of at most the workspace's batch size
+        const int Bw = B - b0 < pl->cap ? B - b0 : pl->cap;
+        if ((r = upload_params(pl, Bw, gamma + (size_t)b0 * p, beta + (size_t)b0 * p)))
+            return r;
+        if ((r = enqueue_grad(pl, pl->d_params(), pl->d_params() + (size_t)Bw * p, observable, Bw)))
+            return r;
+        if ((r = fetch_out(pl, Bw, rows)))
+            return r;
+        for (int b = 0; b < Bw; b++) {
+            const double *row = &rows[(size_t)b * pl->out_stride()];
+            energy[b0 + b] = row[0];
+            for (int l = 0; l < p; l++) {
+                dgamma[(size_t)(b0 + b) * p + l] = row[1 + l];
+                dbeta[(size_t)(b0 + b) * p + l] = row[1 + p + l];
+            }
+        }
+    }
+    return AAQAOA_OK;
+}
+
+int aaqaoa_grad_batch_device(aaqaoa_plan *pl, int B, const double *d_gamma, const double *d_beta, int observable,
+                             double *d_out)
+{
+    g_detail.clear();
+    int r = check_ready(pl, observable, true, B);
+    if (r)
+        return r;
+    if (!d_gamma || !d_beta || !d_out)
+        return fail(AAQAOA_ERR_INVALID_ARG, "device pointer is NULL");
+    pl->launches = 0;
+    if ((r = enqueue_grad(pl, d_gamma, d_beta, observable, B)))
+        return r;
+    CK(cudaMemcpyAsync(d_out, pl->d_out(), (size_t)B * pl->out_stride() * sizeof(double), cudaMemcpyDeviceToDevice,
+                       pl->stream));
     return AAQAOA_OK;
 }
 

@@ -131,3 +131,35 @@ def test_uneven_batch_with_graphs_beyond_one_high_pass(precision):
             ref = SYM.energy(SYM.star_model(n), gs[k], bs[k])
             assert abs(E[k] - ref) <= TOL[precision] * max(abs(ref), 1.0), (k, n, obs, E[k], ref)
     mp.close()
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("n_case", ["small12", "tiled18", "fused22"])
+def test_gradient_batch_matches_oracle_and_single_calls(n_case, precision):
+    """aaqaoa_grad_batch: B points through the whole-circuit kernel (n = 12),
+    the tiled passes (n = 18) and fused layer boundaries (n = 22), in two
+    waves of the workspace's batch size, against the oracle and against
+    one-point calls."""
+    from paper_2410_22247_gb300.api import Plan
+    n = {"small12": 12, "tiled18": 18, "fused22": 22}[n_case]
+    nn, e = W.prufer_tree(n, 6)
+    p, B = 3, 5
+    rng = W.rng(40 + n)
+    gs = rng.uniform(0, np.pi, size=(B, p))
+    bs = rng.uniform(-np.pi / 2, np.pi / 2, size=(B, p))
+    pl = Plan(nn, e, p, orbits=ORB.edge_orbits(nn, e), precision=precision, batch=3, with_grad=True)
+    if n_case == "fused22":
+        pl.set_pass_plan(*((13, 2, 12, 2) if precision == "c64" else (12, 2, 11, 2)))
+    E, dg, db = pl.grad_batch(gs, bs, "red")
+    tol = TOL[precision]
+    floor = (1.0 if precision == "c64" else 1e-3)
+    for k in range(B):
+        Er, dgr, dbr = O.energy_grad(nn, e, gs[k], bs[k])
+        s = max(abs(Er), 1.0)
+        assert abs(E[k] - Er) <= tol * s, (k, E[k], Er)
+        ref = np.concatenate([dgr, dbr])
+        got = np.concatenate([dg[k], db[k]])
+        assert np.all(np.abs(got - ref) <= tol * np.maximum(np.abs(ref), floor * s)), k
+        E1, dg1, db1 = pl.grad(gs[k], bs[k], "red")
+        assert abs(E1 - E[k]) <= tol * s
+        assert np.max(np.abs(np.concatenate([dg1, db1]) - got)) <= tol * s
