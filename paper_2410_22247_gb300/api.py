@@ -397,3 +397,28 @@ def maximize(plan, gamma0, beta0, steps=200, lr=0.05, observable="red", betas=(0
         vh = v / (1 - betas[1] ** t)
         x = x + lr * mh / (np.sqrt(vh) + eps)
     return x[:plan.p], x[plan.p:], np.array(hist)
+
+
+def maximize_multistart(plan, gammas0, betas0, steps=200, lr=0.05, observable="red", betas=(0.9, 0.999),
+                        eps=1e-8):
+    """Adam ascent from B starting points at once, each step one batched
+    energy + gradient call (aaqaoa_grad_batch) for all of them. gammas0,
+    betas0: arrays of shape (B, p). Returns (gamma, beta) of shape (B, p), the
+    history of F_p of shape (steps, B), and the index of the best final point."""
+    g = np.array(gammas0, dtype=np.float64).reshape(-1, plan.p)
+    b = np.array(betas0, dtype=np.float64).reshape(-1, plan.p)
+    x = np.concatenate([g, b], axis=1)
+    m = np.zeros_like(x)
+    v = np.zeros_like(x)
+    hist = []
+    for t in range(1, steps + 1):
+        E, dg, db = plan.grad_batch(x[:, :plan.p], x[:, plan.p:], observable)
+        hist.append(E)
+        d = np.concatenate([dg, db], axis=1)
+        m = betas[0] * m + (1 - betas[0]) * d
+        v = betas[1] * v + (1 - betas[1]) * d * d
+        mh = m / (1 - betas[0] ** t)
+        vh = v / (1 - betas[1] ** t)
+        x = x + lr * mh / (np.sqrt(vh) + eps)
+    hist = np.array(hist)
+    return x[:, :plan.p], x[:, plan.p:], hist, int(np.argmax(hist[-1]))

@@ -133,6 +133,24 @@ def test_adam_reaches_ring_p1_optimum():
     assert hist[10] > hist[0]
 
 
+def test_multistart_adam_matches_single_runs_and_finds_ring_optimum():
+    """maximize_multistart steps 4 starting points together through the
+    batched gradient; each trajectory equals the one-point run from the same
+    start, and the best reaches the closed-form ring optimum F_1/|E| = 3/4."""
+    from paper_2410_22247_gb300.api import Plan, maximize, maximize_multistart
+    n, e = W.cycle_graph(16)
+    pl = Plan(n, e, 1, orbits=ORB.edge_orbits(n, e), precision="c128", batch=4, with_grad=True)
+    g0 = np.array([[0.3], [1.2], [2.0], [-0.4]])
+    b0 = np.array([[0.2], [0.5], [-0.3], [0.9]])
+    gam, bet, hist, best = maximize_multistart(pl, g0, b0, steps=200, lr=0.03)
+    assert hist.shape == (200, 4)
+    for k in range(4):
+        g1, b1, h1 = maximize(pl, g0[k], b0[k], steps=200, lr=0.03)
+        assert np.max(np.abs(h1 - hist[:, k])) < 1e-9
+        assert abs(g1[0] - gam[k, 0]) < 1e-9 and abs(b1[0] - bet[k, 0]) < 1e-9
+    assert abs(hist[-1, best] / len(e) - 0.75) < 1e-3
+
+
 def wplan(n, e, w, p, precision, orbits=True, grad=True):
     from paper_2410_22247_gb300.api import Plan
     orb = ORB.edge_orbits(n, e, weights=w) if orbits else None
