@@ -29,6 +29,7 @@ from oracle import oracle as O
 from oracle import closed_form as CF
 from oracle import symmetric as SYM
 from oracle import automorphisms as AUT
+from oracle import lightcone as LC
 from paper_2410_22247_gb300 import workloads as W
 
 
@@ -204,3 +205,93 @@ def check_weighted():
         E3 = O.energy_grad_w(n, e, 3 * w, np.asarray(g) / 3.0, b)[0]
         worst = max(worst, abs(E3 - 3.0 * E1) / max(abs(E1), 1.0))
     return worst
+
+
+# ------------------------------------------------------------ light cones
+def path_graph(n):
+    return n, W.canonical_edges([(i, i + 1) for i in range(n - 1)])
+
+
+def caterpillar_graph():
+    """Spine 0..6 with one leg per spine vertex (7..13): a tree of 14 vertices
+    whose vertices have degrees 1..3 and whose balls differ in shape."""
+    spine = [(i, i + 1) for i in range(6)]
+    legs = [(i, 7 + i) for i in range(7)]
+    return 14, W.canonical_edges(spine + legs)
+
+
+def lightcone_cases():
+    """(graph, depths): every radius-p ball is strictly smaller than the graph,
+    except for the star, whose ball is the whole graph (a control)."""
+    return [
+        (W.cycle_graph(14), (1, 2)),
+        (W.random_regular(14, 3, 6), (1,)),
+        (path_graph(14), (1, 2, 3)),
+        (caterpillar_graph(), (1, 2, 3)),
+        (W.star_graph(9), (1, 2)),
+    ]
+
+
+def _distances(n, edges, u, v):
+    adj = [[] for _ in range(n)]
+    for a, b in np.asarray(edges).reshape(-1, 2):
+        adj[int(a)].append(int(b))
+        adj[int(b)].append(int(a))
+    dist = {u: 0, v: 0}
+    frontier = [u, v]
+    while frontier:
+        nxt = []
+        for a in frontier:
+            for b in adj[a]:
+                if b not in dist:
+                    dist[b] = dist[a] + 1
+                    nxt.append(b)
+        frontier = nxt
+    return dist
+
+
+def check_lightcone(lc=None):
+    """Per-edge light cones (Sec. 5.1, reverse causal cone) against the full
+    statevector: E and every gradient component of H_C, and of a weighted
+    subset of edges (the form H_red takes), on graphs whose balls leave
+    vertices out. Also the cone's own claim that the edges joining two
+    vertices at distance exactly p do not matter: removing them from the
+    subproblem leaves every per-edge value unchanged."""
+    lc = LC if lc is None else lc
+    worst = 0.0
+    for k, ((n, e), depths) in enumerate(lightcone_cases()):
+        for p in depths:
+            g, b = W.random_angles(p, 600 + 10 * k + p)
+            E, dg, db = O.energy_grad(n, e, g, b)
+            El, dgl, dbl = lc.energy_grad(n, e, g, b)
+            scale = max(abs(E), 1.0)
+            worst = max(worst, abs(El - E) / scale, _rel(dgl, dg, scale), _rel(dbl, db, scale))
+            r = W.rng(700 + 10 * k + p)
+            idx = np.sort(r.choice(len(e), size=max(1, len(e) // 3), replace=False))
+            wts = r.integers(1, 6, size=len(idx)).astype(np.float64)
+            obs = (np.asarray(e)[idx], wts)
+            Ew, dgw, dbw = O.energy_grad(n, e, g, b, obs)
+            Elw, dglw, dblw = lc.energy_grad(n, e, g, b, weights=wts, edge_subset=idx)
+            sw = max(abs(Ew), 1.0)
+            worst = max(worst, abs(Elw - Ew) / sw, _rel(dglw, dgw, sw), _rel(dblw, dbw, sw))
+            # edges whose two ends are both at distance p cancel
+            u, v = (int(x) for x in np.asarray(e)[len(e) // 2])
+            dist = _distances(n, e, u, v)
+            verts = sorted(a for a in dist if dist[a] <= p)
+            index = {a: i for i, a in enumerate(verts)}
+            keep = [(index[int(a)], index[int(c)]) for a, c in np.asarray(e)
+                    if int(a) in index and int(c) in index and not (dist[int(a)] == p and dist[int(c)] == p)]
+            sub = W.canonical_edges(keep)
+            one = (W.canonical_edges([(index[u], index[v])]), np.ones(1))
+            Eb, dgb, dbb = O.energy_grad(len(verts), sub, g, b, one)
+            Ee, dge, dbe = lc.edge_energy_grad(n, e, u, v, g, b)
+            worst = max(worst, abs(Eb - Ee), _rel(dgb, dge, 1.0), _rel(dbb, dbe, 1.0))
+    return worst
+
+
+ALL_CHECKS["lightcone"] = check_lightcone
+
+
+def lightcone_cases_leave_vertices_out():
+    """How many (graph, p) light-cone cases have a ball smaller than the graph."""
+    return sum(1 for (n, e), depths in lightcone_cases() for p in depths if LC.max_ball(n, e, p) < n)

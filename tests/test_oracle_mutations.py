@@ -45,3 +45,39 @@ def test_pins_catch_planted_mistake(name, tmp_path, monkeypatch, oracle_lib):
     monkeypatch.setattr(O, "_lib", O.load_library(str(so)))
     worst = {k: f() for k, f in P.ALL_CHECKS.items()}
     assert max(worst.values()) > 1e-3, worst
+
+
+# Planted mistakes in a copy of oracle/lightcone.py. Removing the edges whose
+# two ends both lie at distance p is not among them: those edges cancel in the
+# reverse causal cone (Sec. 5.1), and check_lightcone verifies that identity.
+LC_SRC = os.path.join(os.path.dirname(O.__file__), "lightcone.py")
+LC_MUTATIONS = {
+    "ball_radius_p_minus_1": ("if dist[a] == p:", "if dist[a] == p - 1:"),
+    "ball_grown_from_one_end": ("q = deque([u, v])", "q = deque([u])"),
+    "observed_edge_left_out_of_the_cost": ("if int(a) in index and int(b) in index]",
+                                           "if int(a) in index and int(b) in index and {int(a), int(b)} != {u, v}]"),
+    "subset_weight_dropped": ("wk = w[e] if w is not None else float(weights[k])", "wk = 1.0"),
+    "gradient_of_one_layer_dropped": ("dg += wk * dge", "dg[1:] += wk * dge[1:]"),
+}
+
+
+def _load_mutated_lightcone(src, tag):
+    import types
+    mod = types.ModuleType(f"oracle.lightcone_{tag}")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(src, f"lightcone_{tag}.py", "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(LC_MUTATIONS))
+def test_lightcone_pin_catches_planted_mistake(name, oracle_lib):
+    old, new = LC_MUTATIONS[name]
+    src = open(LC_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    mutated = _load_mutated_lightcone(src.replace(old, new), name)
+    worst = P.check_lightcone(mutated)
+    assert worst > 1e-3, worst
+
+
+def test_lightcone_unmutated_copy_passes(oracle_lib):
+    assert P.check_lightcone(_load_mutated_lightcone(open(LC_SRC).read(), "copy")) < 1e-11

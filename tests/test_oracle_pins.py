@@ -113,3 +113,13 @@ def test_weighted_max_cut_pins(oracle_lib):
     # triangle with weights (1, 2, 3): the best cut leaves out the lightest edge
     tri = W.canonical_edges([(0, 1), (0, 2), (1, 2)])
     assert O.max_cut_w(3, tri, [1, 2, 3])[0] == 5
+
+
+def test_lightcone_matches_full_statevector(oracle_lib):
+    """oracle/lightcone.py (per-edge reverse causal cones, Sec. 5.1) against
+    the full C oracle: energy and every gradient component of H_C and of a
+    weighted edge subset, to 1e-11, on graphs whose radius-p balls leave
+    vertices out (cycle, 3-regular, path, caterpillar) and on a star, whose
+    ball is the whole graph."""
+    assert P.lightcone_cases_leave_vertices_out() >= 8
+    assert P.check_lightcone() < 1e-11
