@@ -446,10 +446,12 @@ def batch_extras(dev, stream):
                stream=stream, device=dev)
     with torch.cuda.stream(stream):
         t_batch = timed(lambda: pl3.grad_batch_device(g3, b3, o3, "red"), 5, stream)
+        batch_launches = pl3.launch_count()  # launches of the last batched call
         t_single = timed(lambda: [pl3.grad_device(g3[k], b3[k], o3[k], "red") for k in range(B3)], 2, stream)
     res["grad_batch_prufer_n22_p2_16pts_c64"] = {"ms_per_call": t_batch, "evals_per_s": B3 / (t_batch / 1000.0),
                                                   "one_point_calls_evals_per_s": B3 / (t_single / 1000.0),
-                                                  "launches_per_call": pl3.launch_count()}
+                                                  "launches_per_call": batch_launches,
+                                                  "launches_per_one_point_call": pl3.launch_count()}
     pl3.close()
     del pl3
     torch.cuda.empty_cache()

@@ -306,7 +306,10 @@ int aaqaoa_aggregate_only(aaqaoa_plan *plan, int observable, int agg_mode, doubl
  *
  * The first call on a device looks up the array's device address (and so
  * makes the CUDA runtime load the library's device module); make that first
- * call before any stream capture. Every call shares the one array: the entry
+ * call before any stream capture. The address is kept for the life of the
+ * process: it does not survive cudaDeviceReset (or anything else that
+ * replaces the device's primary context), after which this entry point must
+ * not be called again in that process. Every call shares the one array: the entry
  * point clears what must start at zero, but calls that overlap on the GPU
  * (other streams, other host threads, concurrent graph replays) race on it.
  *

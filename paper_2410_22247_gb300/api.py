@@ -94,10 +94,16 @@ class Plan:
                               _ptr(db, ctypes.c_double)), "aaqaoa_grad")
         return E.value, dg, db
 
+    def _batch_points(self, g, b):
+        """Number of points B of flat (gamma, beta) arrays of B*p values each."""
+        if len(g) != len(b) or len(g) == 0 or len(g) % self.p:
+            raise ValueError(f"gammas and betas need B*p values each (p = {self.p}); got {len(g)} and {len(b)}")
+        return len(g) // self.p
+
     def expect_batch(self, gammas, betas, observable="full"):
         g = _f64(gammas)
         b = _f64(betas)
-        B = len(g) // self.p
+        B = self._batch_points(g, b)
         out = np.zeros(B)
         N.check(N.aaqaoa_expect_batch(self.handle, B, _ptr(g, ctypes.c_double), _ptr(b, ctypes.c_double),
                                       OBSERVABLES[observable], _ptr(out, ctypes.c_double)), "aaqaoa_expect_batch")
@@ -108,7 +114,7 @@ class Plan:
         gammas, betas), in waves of the workspace's batch size."""
         g = _f64(gammas)
         b = _f64(betas)
-        B = len(g) // self.p
+        B = self._batch_points(g, b)
         E = np.zeros(B)
         dg = np.zeros(B * self.p)
         db = np.zeros(B * self.p)
@@ -230,20 +236,32 @@ class Plan:
         return out.value
 
     # -- device-pointer calls (asynchronous on the plan's stream) ----------
+    def _device_points(self, d_gamma, d_beta, d_out, row):
+        """B of device (gamma, beta) tensors of B*p doubles; d_out must hold B rows of `row` doubles."""
+        ng, nb = d_gamma.numel(), d_beta.numel()
+        if ng != nb or ng == 0 or ng % self.p:
+            raise ValueError(f"d_gamma and d_beta need B*p values each (p = {self.p}); got {ng} and {nb}")
+        B = ng // self.p
+        if d_out.numel() < B * row:
+            raise ValueError(f"output tensor holds {d_out.numel()} values; {B} points need {B * row}")
+        return B
+
     def expect_device(self, d_gamma, d_beta, d_energy, observable="full"):
-        B = d_gamma.numel() // self.p
+        B = self._device_points(d_gamma, d_beta, d_energy, 1)
         N.check(N.aaqaoa_expect_device(self.handle, B, ctypes.c_void_p(d_gamma.data_ptr()),
                                        ctypes.c_void_p(d_beta.data_ptr()), OBSERVABLES[observable],
                                        ctypes.c_void_p(d_energy.data_ptr())), "aaqaoa_expect_device")
 
     def grad_device(self, d_gamma, d_beta, d_out, observable="full"):
+        if self._device_points(d_gamma, d_beta, d_out, 1 + 2 * self.p) != 1:
+            raise ValueError("grad_device takes one point; use grad_batch_device for several")
         N.check(N.aaqaoa_grad_device(self.handle, ctypes.c_void_p(d_gamma.data_ptr()),
                                      ctypes.c_void_p(d_beta.data_ptr()), OBSERVABLES[observable],
                                      ctypes.c_void_p(d_out.data_ptr())), "aaqaoa_grad_device")
 
     def grad_batch_device(self, d_gamma, d_beta, d_out, observable="full"):
         """d_gamma, d_beta: B*p doubles on the device; d_out: B rows of 1 + 2p."""
-        B = d_gamma.numel() // self.p
+        B = self._device_points(d_gamma, d_beta, d_out, 1 + 2 * self.p)
         N.check(N.aaqaoa_grad_batch_device(self.handle, B, ctypes.c_void_p(d_gamma.data_ptr()),
                                            ctypes.c_void_p(d_beta.data_ptr()), OBSERVABLES[observable],
                                            ctypes.c_void_p(d_out.data_ptr())), "aaqaoa_grad_batch_device")
@@ -380,7 +398,7 @@ def maximize(plan, gamma0, beta0, steps=200, lr=0.05, observable="red", betas=(0
     """Adam ascent of F_p(gamma, beta) driven by the adjoint gradient
     (aaqaoa_grad). Returns (gamma, beta, history of F_p). The paper optimises
     with gradient-free COBYLA (Sec. 6); this is the gradient-based form of the
-    same outer loop."""
+    same outer loop. The last history entry is F_p at the returned point."""
     g = np.array(gamma0, dtype=np.float64)
     b = np.array(beta0, dtype=np.float64)
     x = np.concatenate([g, b])
@@ -396,6 +414,7 @@ def maximize(plan, gamma0, beta0, steps=200, lr=0.05, observable="red", betas=(0
         mh = m / (1 - betas[0] ** t)
         vh = v / (1 - betas[1] ** t)
         x = x + lr * mh / (np.sqrt(vh) + eps)
+    hist.append(plan.expect(x[:plan.p], x[plan.p:], observable))
     return x[:plan.p], x[plan.p:], np.array(hist)
 
 
@@ -404,7 +423,8 @@ def maximize_multistart(plan, gammas0, betas0, steps=200, lr=0.05, observable="r
     """Adam ascent from B starting points at once, each step one batched
     energy + gradient call (aaqaoa_grad_batch) for all of them. gammas0,
     betas0: arrays of shape (B, p). Returns (gamma, beta) of shape (B, p), the
-    history of F_p of shape (steps, B), and the index of the best final point."""
+    history of F_p of shape (steps + 1, B), whose last row is F_p at the
+    returned points, and the index of the best returned point."""
     g = np.array(gammas0, dtype=np.float64).reshape(-1, plan.p)
     b = np.array(betas0, dtype=np.float64).reshape(-1, plan.p)
     x = np.concatenate([g, b], axis=1)
@@ -420,5 +440,6 @@ def maximize_multistart(plan, gammas0, betas0, steps=200, lr=0.05, observable="r
         mh = m / (1 - betas[0] ** t)
         vh = v / (1 - betas[1] ** t)
         x = x + lr * mh / (np.sqrt(vh) + eps)
+    hist.append(plan.expect_batch(x[:, :plan.p], x[:, plan.p:], observable))
     hist = np.array(hist)
     return x[:, :plan.p], x[:, plan.p:], hist, int(np.argmax(hist[-1]))

@@ -13,9 +13,11 @@
 //     leaf by an automorphism, pruning nodes whose cell sizes leave the path's.
 // The automorphisms found (one transversal element per level of the
 // stabiliser chain) generate Aut(G); each is checked to map E onto E.
-// Algorithm 1 then seeds a class with every unclassified edge, in the caller's
-// edge order, and adds the images of dequeued edges under every generator
-// (normalised to (min, max)) that are unclassified edges. The seed is the
+// The edge classes are the orbits, on unordered edges, of the group the
+// generators span (the method of Sec. 4, Algorithm 1): a breadth-first closure
+// seeds a class with each unclassified edge, in the caller's edge order, and
+// adds the images of its members under every generator (normalised to
+// (min, max)). The seed is the
 // class representative and the class size its weight. With integer edge
 // weights (weighted MaxCut) refinement counts neighbours per edge weight and
 // only weight-preserving automorphisms are accepted.
@@ -268,7 +270,8 @@ extern "C" int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, co
         g.nb[v] |= 1ull << u;
     }
     const std::vector<std::vector<int>> gens = generators(g);
-    // Algorithm 1: breadth-first closure of each unclassified seed edge
+    // edge orbits of the generated group (Sec. 4, Algorithm 1): breadth-first
+    // closure of each unclassified seed edge
     std::vector<int> cls(num_edges, -1);
     int classes = 0;
     for (int seed = 0; seed < num_edges; seed++) {

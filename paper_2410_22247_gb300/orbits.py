@@ -15,10 +15,10 @@ come from this module's own individualisation-refinement search:
   generating set of Aut(G) (one transversal per level of the stabiliser chain).
 
 Every generator is checked to map the edge set onto itself before it is used.
-The edge classes then follow Algorithm 1 literally: edges (u, v), u < v, in
-sorted order; each unclassified edge seeds a class; a queue applies every
-generator to every dequeued edge, normalising the image to (min, max), and
-adds images that are unclassified edges.
+The edge classes are the orbits, on unordered edges, of the group the
+generators span (the method of Sec. 4, Algorithm 1), found by a breadth-first
+closure: each edge not yet classified seeds a class, and the images of its
+members under every generator, normalised to (min, max), join it.
 
 The representative of each class is its seed edge, which is the lowest-indexed
 edge of the class (the paper picks a random representative, Sec. 5.4; any

@@ -248,3 +248,22 @@ def test_schedule_without_fusion_cases():
         assert N.aaqaoa_get_schedule(h, 0, None, -1, ctypes.byref(ctypes.c_int())) == -1
     finally:
         N.aaqaoa_destroy(h)
+
+
+def test_batch_argument_checks():
+    """gamma/beta arrays of a batch call must hold B*p values each, B >= 1,
+    and a device output must hold B rows: checked before the C call (no GPU)."""
+    import types
+    from paper_2410_22247_gb300.api import Plan
+    fake = types.SimpleNamespace(p=2)
+    assert Plan._batch_points(fake, np.zeros(6), np.zeros(6)) == 3
+    for g, b in ((np.zeros(6), np.zeros(4)), (np.zeros(5), np.zeros(5)), (np.zeros(0), np.zeros(0))):
+        with pytest.raises(ValueError):
+            Plan._batch_points(fake, g, b)
+    torch = pytest.importorskip("torch")
+    d = torch.zeros(6, dtype=torch.float64)
+    assert Plan._device_points(fake, d, d, torch.zeros(15, dtype=torch.float64), 5) == 3
+    with pytest.raises(ValueError):
+        Plan._device_points(fake, d, d, torch.zeros(14, dtype=torch.float64), 5)
+    with pytest.raises(ValueError):
+        Plan._device_points(fake, d, torch.zeros(4, dtype=torch.float64), d, 1)

@@ -128,6 +128,7 @@ def test_adam_reaches_ring_p1_optimum():
     n, e = W.cycle_graph(16)
     pl = plan(n, e, 1, "c128", grad=True)
     gam, bet, hist = maximize(pl, [0.3], [0.2], steps=300, lr=0.03)
+    assert len(hist) == 301 and abs(hist[-1] - pl.expect(gam, bet, "red")) < 1e-12
     assert abs(hist[-1] / len(e) - 0.75) < 1e-4
     assert abs(CF.energy_p1(n, e, gam[0], bet[0]) / len(e) - 0.75) < 1e-4
     assert hist[10] > hist[0]
@@ -143,7 +144,9 @@ def test_multistart_adam_matches_single_runs_and_finds_ring_optimum():
     g0 = np.array([[0.3], [1.2], [2.0], [-0.4]])
     b0 = np.array([[0.2], [0.5], [-0.3], [0.9]])
     gam, bet, hist, best = maximize_multistart(pl, g0, b0, steps=200, lr=0.03)
-    assert hist.shape == (200, 4)
+    assert hist.shape == (201, 4)
+    # the last history row is F_p at the returned points
+    assert np.max(np.abs(hist[-1] - pl.expect_batch(gam, bet, "red"))) < 1e-12
     for k in range(4):
         g1, b1, h1 = maximize(pl, g0[k], b0[k], steps=200, lr=0.03)
         assert np.max(np.abs(h1 - hist[:, k])) < 1e-9

@@ -6,14 +6,18 @@ up), so they cannot hand the library a workspace. aaqaoa_expect_static keeps
 all of its scratch in a static device array inside the library. This test
 calls it through the C ABI with a plan that has no workspace, twice in a row
 (the second call must not see the first call's leftovers), and checks it
-against aaqaoa_expect of a plan with a workspace, to the same tolerance as the
-other parity tests (complex128 1e-10, complex64 1e-5 relative).
+against aaqaoa_expect of a plan with a workspace and against the FP64 oracle
+(the symmetric-subspace model for K_12 and the star, the C statevector oracle
+for the 3-regular graph), to the same tolerance as the other parity tests
+(complex128 1e-10, complex64 1e-5 relative).
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import oracle as O
+from oracle import symmetric as SYM
 from paper_2410_22247_gb300 import workloads as W
 from paper_2410_22247_gb300 import orbits as ORB
 
@@ -53,12 +57,19 @@ def _expect_static(h, g, b, obs):
     return E.value
 
 
+GRAPHS = {
+    "k12": (lambda: W.complete_graph(12), lambda g, b: SYM.energy(SYM.complete_graph_model(12), g, b)),
+    "reg18": (lambda: W.random_regular(18, 3, 4), None),
+    "star21": (lambda: W.star_graph(21), lambda g, b: SYM.energy(SYM.star_model(21), g, b)),
+}
+
+
 @pytest.mark.parametrize("precision", ["c64", "c128"])
-@pytest.mark.parametrize("maker", [lambda: W.complete_graph(12), lambda: W.random_regular(18, 3, 4),
-                                   lambda: W.star_graph(21)], ids=["k12", "reg18", "star21"])
-def test_static_scratch_energy_matches_workspace_energy(maker, precision):
+@pytest.mark.parametrize("case", sorted(GRAPHS))
+def test_static_scratch_energy_matches_workspace_energy(case, precision):
     from paper_2410_22247_gb300 import _native as N
     from paper_2410_22247_gb300.api import Plan
+    maker, model = GRAPHS[case]
     n, e = maker()
     orb = ORB.edge_orbits(n, e)
     p = 2
@@ -71,6 +82,8 @@ def test_static_scratch_energy_matches_workspace_energy(maker, precision):
                 got = _expect_static(h, g, b, obs)
                 want = ref_plan.expect(g, b, name)
                 assert abs(got - want) <= TOL[precision] * max(abs(want), 1.0), (call, name, got, want)
+                exact = model(g, b) if model is not None else O.energy(n, e, g, b)
+                assert abs(got - exact) <= TOL[precision] * max(abs(exact), 1.0), (call, name, got, exact)
     finally:
         N.aaqaoa_destroy(h)
 
