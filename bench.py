@@ -159,40 +159,102 @@ def angle_sets(count, seed):
 
 
 # ------------------------------------------------------------- CPU oracle
-def oracle_sample(max_seconds=20.0):
+# Everything in this section is the benchmark's CPU-baseline leg: the only
+# part of bench.py that loads oracle/ (timing it, and checking the GPU
+# results it is compared with).
+def oracle_sample(max_seconds=20.0, openmp=False, n_max=24):
     """FP64 oracle energy + adjoint gradient on a bounded sample.
 
-    The full n = 30 evaluation would take the single-threaded oracle tens of
-    minutes, so the sample is the same graph family and depth at n_s qubits
+    The full n = 30 evaluation would take the oracle minutes even on all host
+    cores, so the sample is the same graph family and depth at n_s qubits
     (star S_{n_s - 1}, p = 2), timed end to end, then scaled to n = 30 by the
     ratio of amplitude-qubit work (30 * 2^30) / (n_s * 2^n_s): every oracle
     step is a loop over all amplitudes per qubit or per edge, and the star's
-    edge count grows like n.
+    edge count grows like n. n_s grows by 2 from 18 while the next size is
+    expected to fit max_seconds (work x4.4 per step), up to n_max.
+    openmp=True times the -fopenmp build of the same oracle source on all
+    host cores; otherwise the plain build on one.
     """
     from oracle import oracle as O
     from paper_2410_22247_gb300 import orbits as ORB
     from paper_2410_22247_gb300 import workloads as W
     O.build()
+    lib = O.load_library(O.build(openmp=True)) if openmp else O._load()
     ns = 18
     times = []
-    while True:
-        n, e = W.star_graph(ns)
-        orb = ORB.edge_orbits(n, e)
-        obs = O.reduced_observable(e, orb.rep, orb.weight)
-        g, b = W.random_angles(P_LAYERS, 1)
-        t0 = time.perf_counter()
-        O.energy_grad(n, e, g, b, obs)
-        dt = time.perf_counter() - t0
-        times.append((ns, dt))
-        if dt * 4.4 > max_seconds or ns >= 24:
-            break
-        ns += 2
+    with O.use_library(lib):
+        threads = O.threads()
+        while True:
+            n, e = W.star_graph(ns)
+            orb = ORB.edge_orbits(n, e)
+            obs = O.reduced_observable(e, orb.rep, orb.weight)
+            g, b = W.random_angles(P_LAYERS, 1)
+            t0 = time.perf_counter()
+            O.energy_grad(n, e, g, b, obs)
+            dt = time.perf_counter() - t0
+            times.append((ns, dt))
+            if dt * 4.4 > max_seconds or ns + 2 > n_max:
+                break
+            ns += 2
     ns, dt = times[-1]
     scale = (N_QUBITS * 2.0 ** N_QUBITS) / (ns * 2.0 ** ns)
     evals_per_s = 1.0 / (dt * scale)
-    return {"value": evals_per_s, "unit": "evals/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle energy+adjoint gradient of star S_{ns - 1} (n={ns}), p=2, FP64, 1 thread, "
+    where = f"OpenMP build, {threads} threads" if openmp else "plain build, 1 thread"
+    return {"value": evals_per_s, "unit": "evals/s", "cores": threads, "kind": "oracle", "n_measured": ns,
+            "seconds_measured": dt,
+            "sample": f"oracle energy+adjoint gradient of star S_{ns - 1} (n={ns}), p=2, FP64, {where}, "
                       f"{dt:.2f} s, scaled by (30*2^30)/({ns}*2^{ns}) to the n=30 workload"}
+
+
+def cpu_baseline():
+    """The oracle on all host cores (the reported value) and on one core."""
+    allc = oracle_sample(max_seconds=25.0, openmp=True, n_max=28)
+    one = oracle_sample(max_seconds=12.0, openmp=False, n_max=24)
+    out = dict(allc)
+    out["one_core"] = {k: one[k] for k in ("value", "cores", "n_measured", "seconds_measured", "sample")}
+    out["host_cpus"] = os.cpu_count()
+    return out
+
+
+def _errors(E, dg, db, Er, dgr, dbr):
+    g = np.concatenate([np.ravel(dg), np.ravel(db)])
+    gr = np.concatenate([np.ravel(dgr), np.ravel(dbr)])
+    return {"E_rel": abs(E - Er) / max(abs(Er), 1.0),
+            "grad_max_abs": float(np.max(np.abs(g - gr))),
+            "grad_max_rel_to_component": float(np.max(np.abs(g - gr) / np.maximum(np.abs(gr), 1e-300))),
+            "grad_max_rel_to_E": float(np.max(np.abs(g - gr)) / max(abs(Er), 1.0))}
+
+
+def error_vs_oracle(rows, angles, checks):
+    """Error of every GPU result against the FP64 oracle.
+
+    rows/angles: the headline's timed steps (E, dE/dgamma, dE/dbeta per row)
+    on the star S_29, whose oracle is the exact symmetric-subspace model (the
+    centre qubit times the Dicke space of the 29 leaves). checks: further
+    results {name: (graph, precision, angles, (E, dg, db))} from the extras;
+    the 3-regular graph's oracle is the per-edge light cone (Sec. 5.1; balls
+    of at most 14 qubits at p = 2)."""
+    from oracle import symmetric as SYM
+    from oracle import lightcone as LC
+    from paper_2410_22247_gb300 import workloads as W
+    model = SYM.star_model(N_QUBITS)
+    worst = None
+    for r, (g, b) in zip(rows, angles):
+        Er, dgr, dbr = SYM.energy_grad(model, g, b)
+        e = _errors(r[0], r[1:1 + P_LAYERS], r[1 + P_LAYERS:], Er, dgr, dbr)
+        worst = e if worst is None else {k: max(worst[k], e[k]) for k in e}
+    out = {"headline_c64_max_over_timed_steps": dict(worst, steps=len(rows),
+                                                     oracle="star S_29 symmetric-subspace model (exact, FP64)")}
+    for name, (gname, prec, (g, b), res) in checks.items():
+        if gname == "star_S29":
+            ref = SYM.energy_grad(model, g, b)
+            how = "star S_29 symmetric-subspace model (exact, FP64)"
+        else:
+            n, e = W.random_regular(N_QUBITS, 3, 0)
+            ref = LC.energy_grad(n, e, g, b)
+            how = "per-edge light cones with the C statevector oracle (FP64)"
+        out[name] = dict(_errors(*res, *ref), precision=prec, oracle=how)
+    return out
 
 
 def run_reference(args, rank, world):
@@ -200,15 +262,15 @@ def run_reference(args, rank, world):
         return
     vals = []
     for _ in range(args.warmup):
-        oracle_sample(max_seconds=8.0)
+        oracle_sample(max_seconds=6.0, openmp=True, n_max=26)
     for _ in range(args.steps):
-        vals.append(oracle_sample(max_seconds=8.0))
+        vals.append(oracle_sample(max_seconds=6.0, openmp=True, n_max=26))
     v = float(np.median([x["value"] for x in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_QUBITS, "p": P_LAYERS, "graph": "star S_29"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[-1]["sample"], "value": v},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"], "value": v},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -298,6 +360,7 @@ def run_native(args, rank, world, local):
     t_e2e = max_over_ranks(time.perf_counter() - t0, world)
 
     result = {
+        "rows": res, "angles": list(zip(gs[Wm:], bs[Wm:])),
         "ms": ms_max, "evals_per_s": whole_job_rate(world, K, ms_max / 1000.0), "prof": prof, "launches": launches,
         "clocks": clk.summary(), "e2e_evals_per_s": whole_job_rate(world, k_e2e, t_e2e), "pass_classes": classes,
         "E0": float(res[0, 0]), "pass_plan": pass_plan, "layer_fusion": plan.layer_fusion(),
@@ -323,6 +386,9 @@ def timed(fn, reps, stream):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+RESULTS_FOR_ORACLE = {}  # energy + gradient of the extras, checked in the CPU-baseline leg
 
 
 def extras(dev, stream):
@@ -351,6 +417,9 @@ def extras(dev, stream):
                 t_fwd = timed(lambda: pl.expect_device(dg, db, oe, "red"), reps, stream)
             r = {"grad_ms": t_grad, "grad_evals_per_s": 1000.0 / t_grad, "energy_ms": t_fwd,
                  "energy_evals_per_s": 1000.0 / t_fwd}
+            row = o.cpu().numpy()
+            RESULTS_FOR_ORACLE[f"{name}_{prec}"] = (name, prec, (g, b), (float(row[0]), row[1:1 + P_LAYERS],
+                                                                        row[1 + P_LAYERS:]))
             # aggregation alone on the stored final state, H_C vs H_red
             pl.expect(g, b, "full", "singlepass")
             agg = {}
@@ -553,7 +622,15 @@ def main():
     achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
     S = (1 << N_QUBITS) * 8
     B_alg = (6 * P_LAYERS + 1) * S
-    cpu = oracle_sample()
+    K = args.steps
+    adj = prof.get("adjoint_pass")
+    # algorithmic bytes of the adjoint per step (Sec. 8(d) model): lambda
+    # written once and phi, lambda read and written once per layer
+    adj_alg = (4 * P_LAYERS + 1) * S
+    adj_alg_gbps = adj_alg * K / (adj["ms"] / 1000.0) / 1e9 if adj else None
+    step_gbps = B_alg / (result["ms"] / K / 1000.0) / 1e9
+    cpu = cpu_baseline()
+    errs = error_vs_oracle(result["rows"], result["angles"], RESULTS_FOR_ORACLE)
     line = {
         "metric": METRIC,
         "value": result["evals_per_s"],
@@ -578,10 +655,15 @@ def main():
                                  "passes_forward_adjoint": result["launches_per_sweep"]}},
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "frac_basis": "bytes the kernel streams (vectors loaded + stored per launch)",
+                     "achieved_algorithmic": adj_alg_gbps,
+                     "frac_algorithmic": (adj_alg_gbps / peak) if adj_alg_gbps else None,
+                     "algorithmic_bytes_per_step": adj_alg, "algorithmic_formula": "(4p+1)*2^n*8",
                      "traffic": traffic_from_profiles(),
                      "bytes_per_launch": d["bytes"] / d["launches"], "launches": d["launches"]},
-        "step_algorithmic": {"bytes": B_alg, "formula": "(6p+1)*2^n*8",
-                             "GBps": B_alg / (result["ms"] / args.steps / 1000.0) / 1e9},
+        "step_algorithmic": {"bytes": B_alg, "formula": "(6p+1)*2^n*8", "GBps": step_gbps,
+                             "frac": step_gbps / peak},
+        "error_vs_oracle": errs,
         "kernels": prof,
         "pass_classes": result["pass_classes"],
         "cpu_baseline": cpu,

@@ -20,18 +20,25 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qaoa_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_OMP_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_omp.so")
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with the host C compiler (plain -O2, no fast-math)."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
-        return _LIB_PATH
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with the host C compiler (plain -O2, no fast-math).
+
+    openmp=True builds the same source with -fopenmp into a second library,
+    used only to time the oracle on all host cores; the pinned oracle that
+    the tests load is always the plain build."""
+    path = _OMP_LIB_PATH if openmp else _LIB_PATH
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
     os.makedirs(_OUT_DIR, exist_ok=True)
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared"] + (["-fopenmp"] if openmp else [])
+    subprocess.check_call(cmd + ["-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, path)
+    return path
 
 
 def load_library(path):
@@ -65,6 +72,8 @@ def load_library(path):
                                        ctypes.c_int, i32p, f64p, f64p, f64p, c128p, c128p]
     lib.oracle_max_cut.restype = ctypes.c_int64
     lib.oracle_max_cut.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_uint64)]
+    lib.oracle_threads.restype = ctypes.c_int
+    lib.oracle_threads.argtypes = []
     lib.oracle_sample.restype = ctypes.c_int
     lib.oracle_sample.argtypes = [ctypes.c_int, c128p, ctypes.c_int, f64p, ctypes.POINTER(ctypes.c_uint64)]
     return lib
@@ -75,6 +84,29 @@ def _load():
     if _lib is None:
         _lib = load_library(build())
     return _lib
+
+
+class use_library:
+    """Context manager: run the oracle functions of this module on another
+    build of qaoa_oracle.c (the OpenMP timing build) inside the block."""
+
+    def __init__(self, lib):
+        self.lib = lib
+
+    def __enter__(self):
+        global _lib
+        self.saved = _load()
+        _lib = self.lib
+        return self.lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
+def threads() -> int:
+    """Threads the currently loaded build runs its loops on."""
+    return int(_load().oracle_threads())
 
 
 def _edges(e):

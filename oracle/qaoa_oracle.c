@@ -21,13 +21,19 @@
  *     orbit representatives at weight |S~_m| it is H_red (Sec. 5, "Reducing the Hamiltonian").
  *
  * Nothing is blocked, fused or reordered: each function is the textbook loop
- * over basis states.
+ * over basis states. The "#pragma omp" lines mark loops whose iterations are
+ * independent (or a plain sum); the pinned oracle is compiled without OpenMP,
+ * which ignores them. A separate -fopenmp build of this same file serves only
+ * to time the oracle on all host cores (its sums then run in another order).
  */
 #include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
@@ -64,6 +70,7 @@ void oracle_plus_state(int n, cplx *psi)
 {
     uint64_t N = 1ull << n;
     double a = 1.0 / sqrt((double)N);
+#pragma omp parallel for
     for (uint64_t x = 0; x < N; x++)
         psi[x] = a;
 }
@@ -72,6 +79,7 @@ void oracle_plus_state(int n, cplx *psi)
 void oracle_apply_cost(int n, int m, const int32_t *edges, double gamma, cplx *psi)
 {
     uint64_t N = 1ull << n;
+#pragma omp parallel for
     for (uint64_t x = 0; x < N; x++) {
         double c = (double)oracle_cut_value(m, edges, x);
         psi[x] *= cexp(-I * gamma * c);
@@ -83,6 +91,7 @@ void oracle_apply_rx(int n, int q, double beta, cplx *psi)
 {
     uint64_t N = 1ull << n, bit = 1ull << q;
     double c = cos(beta), s = sin(beta);
+#pragma omp parallel for
     for (uint64_t x = 0; x < N; x++) {
         if (x & bit)
             continue;
@@ -116,6 +125,7 @@ double oracle_expect_diag(int n, const cplx *psi, int k, const int32_t *obs_edge
 {
     uint64_t N = 1ull << n;
     double s = 0.0;
+#pragma omp parallel for reduction(+ : s)
     for (uint64_t x = 0; x < N; x++) {
         double pr = creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]);
         s += pr * oracle_observable_value(k, obs_edges, w, x);
@@ -129,6 +139,7 @@ double oracle_zz(int n, const cplx *psi, int u, int v)
 {
     uint64_t N = 1ull << n;
     double s = 0.0;
+#pragma omp parallel for reduction(+ : s)
     for (uint64_t x = 0; x < N; x++) {
         double pr = creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]);
         int sign = (((x >> u) ^ (x >> v)) & 1u) ? -1 : 1;
@@ -166,27 +177,30 @@ double oracle_energy_grad(int n, int m, const int32_t *edges, int p,
     uint64_t N = 1ull << n;
     oracle_qaoa_state(n, m, edges, p, gamma, beta, phi);
     double energy = 0.0;
+#pragma omp parallel for reduction(+ : energy)
     for (uint64_t x = 0; x < N; x++) {
         double o = oracle_observable_value(k, obs_edges, w, x);
         lam[x] = o * phi[x];
         energy += o * (creal(phi[x]) * creal(phi[x]) + cimag(phi[x]) * cimag(phi[x]));
     }
     for (int l = p - 1; l >= 0; l--) {
-        /* <lambda| sum_i X_i |phi> */
-        cplx acc = 0.0;
+        /* <lambda| sum_i X_i |phi>; only its imaginary part is used */
+        double acc_im = 0.0;
         for (int q = 0; q < n; q++) {
             uint64_t bit = 1ull << q;
+#pragma omp parallel for reduction(+ : acc_im)
             for (uint64_t x = 0; x < N; x++)
-                acc += conj(lam[x]) * phi[x ^ bit];
+                acc_im += cimag(conj(lam[x]) * phi[x ^ bit]);
         }
-        dbeta[l] = 2.0 * cimag(acc);
+        dbeta[l] = 2.0 * acc_im;
         oracle_apply_mixer(n, -beta[l], phi);
         oracle_apply_mixer(n, -beta[l], lam);
-        /* <lambda| H_C |phi> */
-        acc = 0.0;
+        /* <lambda| H_C |phi>; only its imaginary part is used */
+        acc_im = 0.0;
+#pragma omp parallel for reduction(+ : acc_im)
         for (uint64_t x = 0; x < N; x++)
-            acc += conj(lam[x]) * (double)oracle_cut_value(m, edges, x) * phi[x];
-        dgamma[l] = 2.0 * cimag(acc);
+            acc_im += cimag(conj(lam[x]) * (double)oracle_cut_value(m, edges, x) * phi[x]);
+        dgamma[l] = 2.0 * acc_im;
         oracle_apply_cost(n, m, edges, -gamma[l], phi);
         oracle_apply_cost(n, m, edges, -gamma[l], lam);
     }
@@ -241,4 +255,14 @@ int oracle_sample(int n, const cplx *psi, int K, const double *u, uint64_t *x_ou
     }
     free(cdf);
     return 0;
+}
+
+/* Threads the loops above run on: 1 unless built with OpenMP. */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -678,28 +678,14 @@ __device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int
     }
 }
 
-// A thread's running sum over its tiles. complex64: a pair (hi, lo) of floats
-// updated by Knuth's TwoSum, so that hi + lo is the exact sum of the added
-// floats up to about 2^-47 relative, with the work on the FP32 pipes (FP64
-// instructions are slow on this part). complex128: a double.
-template <typename R> struct Acc;
-template <> struct Acc<double> {
+// A thread's running sum over its tiles, in FP64 for both precisions: each
+// register stage sums its 2^RB products in the amplitude type, and every sum
+// across stages, tiles, threads and CTAs is an FP64 add.
+template <typename R> struct Acc {
     double v;
     __device__ __forceinline__ void zero() { v = 0.0; }
-    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void add(R x) { v += (double)x; }
     __device__ __forceinline__ double get() const { return v; }
-};
-template <> struct Acc<float> {
-    float hi, lo;
-    __device__ __forceinline__ void zero() { hi = lo = 0.f; }
-    __device__ __forceinline__ void add(float x)
-    {
-        const float t = hi + x;
-        const float bp = t - hi;
-        lo += (hi - (t - bp)) + (x - bp);
-        hi = t;
-    }
-    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
 
 // The butterflies of stage ST due in this pass, with rotation t = tq and

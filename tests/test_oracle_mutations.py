@@ -24,8 +24,9 @@ MUTATIONS = {
     "cut_wrong_index": ("uint64_t bv = (x >> edges[2 * e + 1]) & 1u;", "uint64_t bv = (x >> edges[2 * e]) & 1u;"),
     "layer_order": ("oracle_apply_cost(n, m, edges, gamma[l], psi);\n        oracle_apply_mixer(n, beta[l], psi);",
                     "oracle_apply_mixer(n, beta[l], psi);\n        oracle_apply_cost(n, m, edges, gamma[l], psi);"),
-    "grad_beta_real_part": ("dbeta[l] = 2.0 * cimag(acc);", "dbeta[l] = 2.0 * creal(acc);"),
-    "grad_gamma_dropped_factor": ("dgamma[l] = 2.0 * cimag(acc);", "dgamma[l] = cimag(acc);"),
+    "grad_beta_real_part": ("acc_im += cimag(conj(lam[x]) * phi[x ^ bit]);",
+                            "acc_im += creal(conj(lam[x]) * phi[x ^ bit]);"),
+    "grad_gamma_dropped_factor": ("dgamma[l] = 2.0 * acc_im;", "dgamma[l] = acc_im;"),
     "grad_skips_undo_cost": ("oracle_apply_cost(n, m, edges, -gamma[l], lam);", ";"),
     "observable_weight_dropped": ("s += w[e];", "s += 1.0;"),
     "zz_sign": ("int sign = (((x >> u) ^ (x >> v)) & 1u) ? -1 : 1;", "int sign = (((x >> u) ^ (x >> v)) & 1u) ? 1 : -1;"),
