@@ -72,6 +72,15 @@ def load_library(path):
                                        ctypes.c_int, i32p, f64p, f64p, f64p, c128p, c128p]
     lib.oracle_max_cut.restype = ctypes.c_int64
     lib.oracle_max_cut.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_uint64)]
+    lib.oracle_ising_value.restype = ctypes.c_double
+    lib.oracle_ising_value.argtypes = [ctypes.c_int, i32p, f64p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64]
+    lib.oracle_ising_state.restype = None
+    lib.oracle_ising_state.argtypes = [ctypes.c_int, ctypes.c_int, i32p, f64p, ctypes.c_void_p, ctypes.c_int, f64p,
+                                       f64p, c128p]
+    lib.oracle_ising_energy_grad.restype = ctypes.c_double
+    lib.oracle_ising_energy_grad.argtypes = [ctypes.c_int, ctypes.c_int, i32p, f64p, ctypes.c_void_p, ctypes.c_int,
+                                             f64p, f64p, ctypes.c_int, i32p, f64p, ctypes.c_void_p, f64p, f64p,
+                                             c128p, c128p]
     lib.oracle_threads.restype = ctypes.c_int
     lib.oracle_threads.argtypes = []
     lib.oracle_sample.restype = ctypes.c_int
@@ -272,3 +281,72 @@ def energy_grad_w(n, edges, weights, gamma, beta, obs=None):
 
 def max_cut_w(n, edges, weights):
     return max_cut(n, weighted_cost_edges(edges, weights))
+
+
+# ------------------------------------------------ Ising-form objectives
+# H = sum_e w_e 1/2 (1 - Z_u Z_v) + sum_i h_i 1/2 (1 - Z_i) with real w_e, h_i;
+# diagonal C(x) = sum_e w_e [x_u != x_v] + sum_i h_i x_i. An Ising function is
+# (edges, w, h), h None for no fields; it serves as cost and as observable.
+
+def ising(edges, w, h=None):
+    """Normalise an Ising function: int32 edges, float64 weights and fields (or None)."""
+    e = _edges(edges)
+    wv = _f64(w) if w is not None else np.ones(len(e))
+    hv = None if h is None else _f64(h)
+    if len(wv) != len(e):
+        raise ValueError("one weight per edge")
+    return e, wv, hv
+
+
+def _hptr(h):
+    return None if h is None else h.ctypes.data_as(ctypes.c_void_p)
+
+
+def ising_value(fn, n, x: int) -> float:
+    e, w, h = fn
+    return float(_load().oracle_ising_value(len(e), e, w, n, _hptr(h), x))
+
+
+def ising_state(n, fn, gamma, beta):
+    """The p-layer state of Eq. (1) with cost layers exp(-i gamma_l H)."""
+    e, w, h = fn
+    g, b = _f64(gamma), _f64(beta)
+    psi = np.empty(1 << n, dtype=np.complex128)
+    _load().oracle_ising_state(n, len(e), e, w, _hptr(h), len(g), g, b, psi)
+    return psi
+
+
+def ising_energy_grad(n, fn, gamma, beta, obs=None):
+    """(E, dE/dgamma, dE/dbeta) of the Ising observable obs (default: the cost
+    function itself) by the adjoint recursion, FP64."""
+    e, w, h = fn
+    oe, ow, oh = fn if obs is None else obs
+    g, b = _f64(gamma), _f64(beta)
+    p = len(g)
+    dg, db = np.zeros(p), np.zeros(p)
+    phi = np.empty(1 << n, dtype=np.complex128)
+    lam = np.empty(1 << n, dtype=np.complex128)
+    E = _load().oracle_ising_energy_grad(n, len(e), e, w, _hptr(h), p, g, b, len(oe), oe, ow, _hptr(oh), dg, db,
+                                         phi, lam)
+    return float(E), dg, db
+
+
+def ising_energy(n, fn, gamma, beta, obs=None):
+    """E = <psi|O|psi>, O the Ising observable obs (default: the cost function)."""
+    return ising_energy_grad(n, fn, gamma, beta, obs)[0]
+
+
+def ising_reduced_observable(fn, edge_rep, edge_weight, vertex_rep=None, vertex_weight=None, n=None):
+    """H_red of an Ising function: one representative edge per edge orbit at
+    weight |orbit| w_rep, one representative vertex per vertex orbit at weight
+    |orbit| h_rep (no fields when the function has none)."""
+    e, w, h = fn
+    rep = np.asarray(edge_rep, dtype=np.int64)
+    oe = _edges(e[rep]) if len(rep) else np.zeros((0, 2), dtype=np.int32)
+    ow = _f64(np.asarray(edge_weight, dtype=np.float64) * w[rep]) if len(rep) else np.zeros(0)
+    oh = None
+    if h is not None:
+        oh = np.zeros(len(h))
+        for v, k in zip(np.asarray(vertex_rep, dtype=np.int64), np.asarray(vertex_weight, dtype=np.float64)):
+            oh[v] = k * h[v]
+    return oe, ow, oh

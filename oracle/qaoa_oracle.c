@@ -257,6 +257,91 @@ int oracle_sample(int n, const cplx *psi, int K, const double *u, uint64_t *x_ou
     return 0;
 }
 
+/* ------------------------------------------------------------------
+ * Ising-form objectives (the generalisation named in the paper's
+ * conclusion: weighted MaxCut and Ising objectives with fields):
+ *   H = sum_e w_e 1/2 (1 - Z_u Z_v) + sum_i h_i 1/2 (1 - Z_i),
+ * real w_e and h_i, whose diagonal is
+ *   C(x) = sum_e w_e [x_u != x_v] + sum_i h_i x_i.
+ * With every h_i = 0 and every w_e = 1 this is H_C of MaxCut. The same form
+ * serves as the observable: H_red keeps one representative edge per edge
+ * orbit at weight |orbit| w_rep and one representative vertex per vertex
+ * orbit at weight |orbit| h_rep. h may be NULL (no fields). */
+double oracle_ising_value(int m, const int32_t *edges, const double *w, int n, const double *h, uint64_t x)
+{
+    double s = 0.0;
+    for (int e = 0; e < m; e++) {
+        uint64_t xu = (x >> edges[2 * e]) & 1u, xv = (x >> edges[2 * e + 1]) & 1u;
+        s += (xu != xv) ? w[e] : 0.0;
+    }
+    if (h)
+        for (int i = 0; i < n; i++)
+            if ((x >> i) & 1u)
+                s += h[i];
+    return s;
+}
+
+/* psi <- exp(-i gamma H) psi for the Ising-form H above. */
+void oracle_ising_apply_cost(int n, int m, const int32_t *edges, const double *w, const double *h, double gamma,
+                             cplx *psi)
+{
+    uint64_t N = 1ull << n;
+#pragma omp parallel for
+    for (uint64_t x = 0; x < N; x++)
+        psi[x] *= cexp(-I * gamma * oracle_ising_value(m, edges, w, n, h, x));
+}
+
+/* The p-layer state of Eq. (1) with the Ising-form cost layer. */
+void oracle_ising_state(int n, int m, const int32_t *edges, const double *w, const double *h, int p,
+                        const double *gamma, const double *beta, cplx *psi)
+{
+    oracle_plus_state(n, psi);
+    for (int l = 0; l < p; l++) {
+        oracle_ising_apply_cost(n, m, edges, w, h, gamma[l], psi);
+        oracle_apply_mixer(n, beta[l], psi);
+    }
+}
+
+/* Energy <psi|O|psi> of an Ising-form observable O (edges ok, weights ow,
+ * fields oh) and its gradient by the same adjoint recursion as
+ * oracle_energy_grad, with the Ising-form cost as the generator of the
+ * phase layers. Returns E. */
+double oracle_ising_energy_grad(int n, int m, const int32_t *edges, const double *w, const double *h, int p,
+                                const double *gamma, const double *beta, int k, const int32_t *oedges,
+                                const double *ow, const double *oh, double *dgamma, double *dbeta, cplx *phi,
+                                cplx *lam)
+{
+    uint64_t N = 1ull << n;
+    oracle_ising_state(n, m, edges, w, h, p, gamma, beta, phi);
+    double e_sum = 0.0;
+#pragma omp parallel for reduction(+ : e_sum)
+    for (uint64_t x = 0; x < N; x++) {
+        double o = oracle_ising_value(k, oedges, ow, n, oh, x);
+        lam[x] = o * phi[x];
+        e_sum += o * (creal(phi[x]) * creal(phi[x]) + cimag(phi[x]) * cimag(phi[x]));
+    }
+    for (int l = p - 1; l >= 0; l--) {
+        double im_sum = 0.0;
+        for (int q = 0; q < n; q++) {
+            uint64_t bit = 1ull << q;
+#pragma omp parallel for reduction(+ : im_sum)
+            for (uint64_t x = 0; x < N; x++)
+                im_sum += cimag(conj(lam[x]) * phi[x ^ bit]);
+        }
+        dbeta[l] = 2.0 * im_sum;
+        oracle_apply_mixer(n, -beta[l], phi);
+        oracle_apply_mixer(n, -beta[l], lam);
+        im_sum = 0.0;
+#pragma omp parallel for reduction(+ : im_sum)
+        for (uint64_t x = 0; x < N; x++)
+            im_sum += cimag(conj(lam[x]) * oracle_ising_value(m, edges, w, n, h, x) * phi[x]);
+        dgamma[l] = 2.0 * im_sum;
+        oracle_ising_apply_cost(n, m, edges, w, h, -gamma[l], phi);
+        oracle_ising_apply_cost(n, m, edges, w, h, -gamma[l], lam);
+    }
+    return e_sum;
+}
+
 /* Threads the loops above run on: 1 unless built with OpenMP. */
 int oracle_threads(void)
 {

@@ -48,7 +48,7 @@ def _op_on(n, q, a):
     return m
 
 
-def dense_state(n, edges, gamma, beta, weights=None):
+def dense_state(n, edges, gamma, beta, weights=None, fields=None):
     X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
     Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
     dim = 1 << n
@@ -57,6 +57,9 @@ def dense_state(n, edges, gamma, beta, weights=None):
     w = np.ones(len(e)) if weights is None else np.asarray(weights, dtype=np.float64)
     for (u, v), we in zip(e, w):
         HC += 0.5 * we * (np.eye(dim) - _op_on(n, int(u), Z) @ _op_on(n, int(v), Z))
+    if fields is not None:  # sum_i h_i 1/2 (1 - Z_i)
+        for i, hi in enumerate(np.asarray(fields, dtype=np.float64)):
+            HC += 0.5 * hi * (np.eye(dim) - _op_on(n, i, Z))
     HM = sum(_op_on(n, q, X) for q in range(n))
     psi = np.ones(dim, dtype=np.complex128) / math.sqrt(dim)
     for g, b in zip(gamma, beta):
@@ -295,3 +298,152 @@ ALL_CHECKS["lightcone"] = check_lightcone
 def lightcone_cases_leave_vertices_out():
     """How many (graph, p) light-cone cases have a ball smaller than the graph."""
     return sum(1 for (n, e), depths in lightcone_cases() for p in depths if LC.max_ball(n, e, p) < n)
+
+
+# ------------------------------------------------ Ising-form objectives
+def ising_cases():
+    """Small graphs with real edge weights of both signs and real fields."""
+    out = []
+    for k, (n, e) in enumerate(small_graphs()):
+        r = W.rng(900 + k)
+        w = r.uniform(-2.0, 3.0, size=len(e))
+        h = r.uniform(-1.5, 1.5, size=n)
+        out.append((n, e, w, h))
+    return out
+
+
+def check_ising_dense():
+    """The Ising oracle's state against dense exponentials of
+    H = sum w_e 1/2 (1 - Z_u Z_v) + sum h_i 1/2 (1 - Z_i), amplitude by amplitude."""
+    worst = 0.0
+    for k, (n, e, w, h) in enumerate(ising_cases()):
+        g, b = W.random_angles(2, 950 + k)
+        ref = dense_state(n, e, g, b, w, h)
+        got = O.ising_state(n, O.ising(e, w, h), g, b)
+        worst = max(worst, float(np.max(np.abs(got - ref))))
+    return worst
+
+
+def fields_only_p1(h, gamma, beta):
+    """No edges, p = 1: the qubits evolve independently and
+    <x_i> = 1/2 (1 + sin(2 beta) sin(gamma h_i)), so
+    E = sum_i h_i/2 (1 + sin 2b sin(g h_i)) with its two derivatives."""
+    h = np.asarray(h, dtype=np.float64)
+    s2, c2 = math.sin(2 * beta), math.cos(2 * beta)
+    E = float(np.sum(0.5 * h * (1 + s2 * np.sin(gamma * h))))
+    dg = float(np.sum(0.5 * h * s2 * np.cos(gamma * h) * h))
+    db = float(np.sum(h * c2 * np.sin(gamma * h)))
+    return E, dg, db
+
+
+def check_ising_fields_closed_form():
+    worst = 0.0
+    for k in range(4):
+        n = 3 + k
+        h = W.rng(970 + k).uniform(-2.0, 2.0, size=n)
+        g, b = W.random_angles(1, 980 + k)
+        E, dg, db = O.ising_energy_grad(n, O.ising(np.zeros((0, 2)), np.zeros(0), h), g, b)
+        Ec, dgc, dbc = fields_only_p1(h, g[0], b[0])
+        worst = max(worst, abs(E - Ec), abs(dg[0] - dgc), abs(db[0] - dbc))
+    return worst
+
+
+def check_ising_reductions():
+    """Without fields and with unit weights the Ising routines give the MaxCut
+    oracle's energy and gradient; with integer weights, the weighted-MaxCut
+    route (edge e repeated w_e times); scaling every weight and field by c
+    is the same as scaling gamma by c and the energy by c."""
+    worst = 0.0
+    for k, (n, e) in enumerate(small_graphs()):
+        g, b = W.random_angles(2, 990 + k)
+        E1, dg1, db1 = O.ising_energy_grad(n, O.ising(e, np.ones(len(e)), None), g, b)
+        E0, dg0, db0 = O.energy_grad(n, e, g, b)
+        s = max(abs(E0), 1.0)
+        worst = max(worst, abs(E1 - E0) / s, _rel(dg1, dg0, s), _rel(db1, db0, s))
+        wi = W.rng(995 + k).integers(1, 4, size=len(e))
+        E2 = O.ising_energy_grad(n, O.ising(e, wi.astype(float), None), g, b)[0]
+        E3 = O.energy_grad_w(n, e, wi, g, b)[0]
+        worst = max(worst, abs(E2 - E3) / max(abs(E3), 1.0))
+    for k, (n, e, w, h) in enumerate(ising_cases()):
+        g, b = W.random_angles(2, 1000 + k)
+        c = 2.5
+        E1 = O.ising_energy_grad(n, O.ising(e, w, h), g, b)[0]
+        Ec = O.ising_energy_grad(n, O.ising(e, c * w, c * h), np.asarray(g) / c, b)[0]
+        worst = max(worst, abs(Ec - c * E1) / max(abs(E1), 1.0))
+    return worst
+
+
+def check_ising_finite_difference():
+    worst = 0.0
+    for k, (n, e, w, h) in enumerate(ising_cases()[:4]):
+        fn = O.ising(e, w, h)
+        # an observable that is not the cost function (other weights, fields)
+        r = W.rng(1015 + k)
+        obs = O.ising(e, r.uniform(-1, 2, size=len(e)), r.uniform(-1, 1, size=n))
+        g, b = (np.array(x) for x in W.random_angles(3, 1010 + k))
+        E, dg, db = O.ising_energy_grad(n, fn, g, b, obs)
+        hh = 1e-5
+        for vec, got in ((g, dg), (b, db)):
+            for i in range(len(vec)):
+                old = vec[i]
+                vec[i] = old + hh
+                ep = O.ising_energy(n, fn, g, b, obs)
+                vec[i] = old - hh
+                em = O.ising_energy(n, fn, g, b, obs)
+                vec[i] = old
+                worst = max(worst, abs((ep - em) / (2 * hh) - got[i]) / max(abs(E), 1.0))
+    return worst
+
+
+def check_ising_invariants():
+    """Automorphisms that preserve weights and fields (brute force) leave the
+    state invariant (Eq. A2), give equal <Z_u Z_v> within an edge orbit and
+    equal <Z_i> within a vertex orbit (Eq. A3), and H_red built from both
+    kinds of orbits has the energy and gradient of H (Eq. exact)."""
+    worst = 0.0
+    cases = [W.cycle_graph(6), W.star_graph(7), W.complete_graph(5), W.heap_binary_tree(7)]
+    for k, (n, e) in enumerate(cases):
+        r = W.rng(1020 + k)
+        # weights and fields that depend on vertex degrees (kept by every
+        # automorphism), plus a field singling out vertex 0, which breaks
+        # part of the group
+        deg = np.bincount(np.asarray(e).reshape(-1), minlength=n)
+        w = np.array([1.5 if (deg[u] + deg[v]) % 2 else -0.75 for u, v in e]) * (1 + 0.1 * r.uniform())
+        h = np.array([0.6 if i == 0 else -0.4 * deg[i] / deg.max() for i in range(n)])
+        group = AUT.automorphism_group(n, e, w, h)
+        assert len(group) > 1
+        fn = O.ising(e, w, h)
+        g, b = W.random_angles(2, 1030 + k)
+        psi = O.ising_state(n, fn, g, b)
+        xs = np.arange(1 << n)
+        for perm in group[: min(len(group), 12)]:
+            px = np.zeros_like(xs)
+            for i in range(n):
+                px |= ((xs >> i) & 1) << perm[i]
+            worst = max(worst, float(np.max(np.abs(psi[px] - psi))))
+        eorb, vorb = AUT.ising_orbit_partition(n, e, w, h)
+        pr = np.abs(psi) ** 2
+        for orb in eorb:
+            vals = [O.zz(n, psi, u, v) for u, v in orb]
+            worst = max(worst, max(vals) - min(vals))
+        for orb in vorb:
+            vals = [float(np.sum(pr * (1 - 2 * ((xs >> i) & 1)))) for i in orb]
+            worst = max(worst, max(vals) - min(vals))
+        idx = {tuple(map(int, x)): i for i, x in enumerate(e)}
+        erep = [idx[min(o)] for o in eorb]
+        ewt = [len(o) for o in eorb]
+        vrep = [min(o) for o in vorb]
+        vwt = [len(o) for o in vorb]
+        red = O.ising_reduced_observable(fn, erep, ewt, vrep, vwt)
+        Er, dgr, dbr = O.ising_energy_grad(n, fn, g, b, red)
+        Ef, dgf, dbf = O.ising_energy_grad(n, fn, g, b)
+        s = max(abs(Ef), 1.0)
+        worst = max(worst, abs(Er - Ef) / s, _rel(dgr, dgf, s), _rel(dbr, dbf, s))
+    return worst
+
+
+ALL_CHECKS["ising_dense"] = check_ising_dense
+ALL_CHECKS["ising_fields_closed_form"] = check_ising_fields_closed_form
+ALL_CHECKS["ising_reductions"] = check_ising_reductions
+ALL_CHECKS["ising_invariants"] = check_ising_invariants
+ALL_CHECKS["ising_finite_difference"] = check_ising_finite_difference

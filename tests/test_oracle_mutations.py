@@ -31,6 +31,13 @@ MUTATIONS = {
     "observable_weight_dropped": ("s += w[e];", "s += 1.0;"),
     "zz_sign": ("int sign = (((x >> u) ^ (x >> v)) & 1u) ? -1 : 1;", "int sign = (((x >> u) ^ (x >> v)) & 1u) ? 1 : -1;"),
     "plus_state_norm": ("double a = 1.0 / sqrt((double)N);", "double a = 1.0 / (double)N;"),
+    "ising_field_dropped": ("                s += h[i];", "                s += 0.0;"),
+    "ising_field_on_wrong_value": ("if ((x >> i) & 1u)", "if (!((x >> i) & 1u))"),
+    "ising_cost_sign": ("psi[x] *= cexp(-I * gamma * oracle_ising_value(m, edges, w, n, h, x));",
+                        "psi[x] *= cexp(I * gamma * oracle_ising_value(m, edges, w, n, h, x));"),
+    "ising_gamma_grad_uses_observable": (
+        "im_sum += cimag(conj(lam[x]) * oracle_ising_value(m, edges, w, n, h, x) * phi[x]);",
+        "im_sum += cimag(conj(lam[x]) * oracle_ising_value(k, oedges, ow, n, oh, x) * phi[x]);"),
 }
 
 

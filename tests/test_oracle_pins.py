@@ -123,3 +123,27 @@ def test_lightcone_matches_full_statevector(oracle_lib):
     ball is the whole graph."""
     assert P.lightcone_cases_leave_vertices_out() >= 8
     assert P.check_lightcone() < 1e-11
+
+
+def test_ising_oracle_matches_dense_exponentials(oracle_lib):
+    """Real weights of both signs and real fields: the Ising-form oracle's
+    state against expm of the dense H and H_M, amplitude by amplitude."""
+    assert P.check_ising_dense() < 1e-12
+
+
+def test_ising_oracle_fields_only_closed_form(oracle_lib):
+    """No edges, p = 1: E = sum_i h_i/2 (1 + sin 2 beta sin gamma h_i) and its
+    derivatives (independent qubits)."""
+    assert P.check_ising_fields_closed_form() < 1e-12
+
+
+def test_ising_oracle_reduces_to_maxcut_and_weighted_maxcut(oracle_lib):
+    assert P.check_ising_reductions() < 1e-11
+
+
+def test_ising_oracle_gradient_matches_finite_differences(oracle_lib):
+    assert P.check_ising_finite_difference() < 1e-6
+
+
+def test_ising_oracle_invariants_under_weight_and_field_preserving_automorphisms(oracle_lib):
+    assert P.check_ising_invariants() < 1e-11
