@@ -249,12 +249,24 @@ def error_vs_oracle(rows, angles, checks):
         if gname == "star_S29":
             ref = SYM.energy_grad(model, g, b)
             how = "star S_29 symmetric-subspace model (exact, FP64)"
+        elif gname == "ising_regular3_n30":
+            ref = ising_light_cone(g, b)
+            how = "per-term light cones of the Ising objective with the C statevector oracle (FP64)"
         else:
             n, e = W.random_regular(N_QUBITS, 3, 0)
             ref = LC.energy_grad(n, e, g, b)
             how = "per-edge light cones with the C statevector oracle (FP64)"
         out[name] = dict(_errors(*res, *ref), precision=prec, oracle=how)
     return out
+
+
+def ising_light_cone(gamma, beta):
+    """E and gradient of the n = 30 Ising extra by per-term light cones."""
+    from oracle import lightcone as LC
+    from paper_2410_22247_gb300 import workloads as W
+    n, e = W.random_regular(N_QUBITS, 3, 0)
+    w, h = W.ising_couplings(n, e, 30)
+    return LC.ising_energy_grad(n, e, w, h, gamma, beta)
 
 
 def run_reference(args, rank, world):
@@ -437,7 +449,37 @@ def extras(dev, stream):
         out[name] = rec
     out["batch"] = batch_extras(dev, stream)
     out["next"] = next_extras(dev, stream)
+    out["ising"] = ising_extras(dev, stream)
     return out
+
+
+def ising_extras(dev, stream):
+    """Ising-form objective at n = 30: the random 3-regular graph with seeded
+    real couplings and fields (generic, trivial automorphism group), p = 2,
+    complex64, energy + gradient and energy only, against the MaxCut plan of
+    the same graph (the cost phase built from unit phase factors instead of a
+    table, the cot form of the rotation where a layer needs it)."""
+    import torch
+    from paper_2410_22247_gb300 import workloads as W
+    from paper_2410_22247_gb300.api import Plan
+    n, e = W.random_regular(30, 3, 0)
+    w, h = W.ising_couplings(n, e, 30)
+    g, b = W.random_angles(P_LAYERS, 5)
+    dg, db = torch.tensor(g, device=dev), torch.tensor(b, device=dev)
+    o = torch.zeros(1 + 2 * P_LAYERS, dtype=torch.float64, device=dev)
+    oe = torch.zeros(1, dtype=torch.float64, device=dev)
+    pl = Plan(n, e, P_LAYERS, precision="c64", with_grad=True, stream=stream, device=dev, couplings=w, fields=h)
+    with torch.cuda.stream(stream):
+        t_grad = timed(lambda: pl.grad_device(dg, db, o, "full"), 3, stream)
+        t_fwd = timed(lambda: pl.expect_device(dg, db, oe, "full"), 3, stream)
+    row = o.cpu().numpy()
+    RESULTS_FOR_ORACLE["ising_regular3_n30_c64"] = ("ising_regular3_n30", "c64", (g, b),
+                                                    (float(row[0]), row[1:1 + P_LAYERS], row[1 + P_LAYERS:]))
+    pl.close()
+    del pl
+    torch.cuda.empty_cache()
+    return {"regular3_n30_real_couplings_fields_c64": {"grad_ms": t_grad, "grad_evals_per_s": 1000.0 / t_grad,
+                                                       "energy_ms": t_fwd, "energy_evals_per_s": 1000.0 / t_fwd}}
 
 
 def next_extras(dev, stream):

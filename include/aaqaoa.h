@@ -131,6 +131,41 @@ int aaqaoa_prepare_weighted(int n, int num_edges, const int32_t *edges, const in
                             unsigned flags, void *stream, aaqaoa_plan **out);
 
 /*
+ * aaqaoa_prepare_ising -- a plan for an Ising-form objective with real
+ * couplings and fields, the generalisation the paper's conclusion names
+ * (weighted MaxCut and more general Ising objectives with non-trivial
+ * automorphism groups):
+ *   H_C = sum_e w_e 1/2 (1 - Z_u Z_v) + sum_i h_i 1/2 (1 - Z_i),
+ * whose diagonal is C(x) = sum_e w_e [x_u != x_v] + sum_i h_i x_i. The ansatz
+ * is Eq. (1) with this H_C in the cost layer; E = <H_C> (or <H_red>).
+ * edge_weight: num_edges doubles (any finite sign). field: n doubles, or NULL
+ * for no fields. Edges, p, flags and the edge orbits are as for
+ * aaqaoa_prepare; H_red keeps one representative edge per edge orbit at
+ * |orbit| * w_rep and, with fields, one representative vertex per vertex
+ * orbit at |orbit| * h_rep (vorbit_rep, vorbit_weight: num_vorbits int32
+ * each; vertex_orbit: n int32 or NULL). Both kinds of orbits must come from
+ * automorphisms that preserve the couplings and the fields (Eq. A3 then makes
+ * <H_red> = <H_C>); edge_orbit / vertex_orbit, when given, are checked for
+ * equal weights / fields within a class. Vertex orbits are required when
+ * there are fields and edge orbits.
+ * The cost phase exp(-i gamma C(x)) is built per amplitude from products of
+ * unit phase factors whose angles are reduced in FP64; C(x) and the
+ * observables are real (not exact integers). Ising plans support the fused
+ * aggregation only: aaqaoa_expect with PERTERM/SINGLEPASS,
+ * aaqaoa_aggregate_only, aaqaoa_max_cut, aaqaoa_sample and
+ * aaqaoa_expect_static return AAQAOA_ERR_UNSUPPORTED. Every other call on a
+ * plan (energies, gradients, batches, statevector, edge_zz, verify_orbits,
+ * pass plans) works as for MaxCut.
+ * Errors: INVALID_ARG (also a weight or field that is not finite),
+ * BAD_ORBITS. Host arrays are copied; no device memory is allocated.
+ */
+int aaqaoa_prepare_ising(int n, int num_edges, const int32_t *edges, const double *edge_weight, const double *field,
+                         int num_orbits, const int32_t *orbit_rep, const int32_t *orbit_weight,
+                         const int32_t *edge_orbit, int num_vorbits, const int32_t *vorbit_rep,
+                         const int32_t *vorbit_weight, const int32_t *vertex_orbit, int p, unsigned flags, void *stream,
+                         aaqaoa_plan **out);
+
+/*
  * aaqaoa_workspace_bytes -- device bytes needed for a workspace able to hold
  * `batch` statevectors (batch >= 1), with room for the adjoint gradient's
  * second statevector when with_grad != 0. Writes *bytes.
@@ -443,6 +478,25 @@ int aaqaoa_get_schedule(aaqaoa_plan *plan, int adjoint, int32_t *steps, int cap,
  */
 int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, const int32_t *edge_weight, int32_t *edge_orbit,
                        int32_t *num_orbits, int32_t *orbit_rep, int32_t *orbit_weight);
+
+/*
+ * aaqaoa_ising_orbits -- edge and vertex classes for an Ising-form objective
+ * (aaqaoa_prepare_ising): the same search and closure as aaqaoa_edge_orbits
+ * over the automorphisms that keep every edge's real coupling (equal values)
+ * and, when field is not NULL, every vertex's real field (Sec. 4 with the
+ * couplings and fields as edge and vertex colours). No GPU is used.
+ * n: 1..64. edges: 2*num_edges int32. edge_weight: num_edges doubles.
+ * field: n doubles or NULL. Outputs (host, caller-owned): edge_orbit,
+ * *num_orbits, orbit_rep, orbit_weight as for aaqaoa_edge_orbits;
+ * vertex_orbit[n] class of each vertex, *num_vorbits, vorbit_rep[<= n] the
+ * smallest vertex of each class, vorbit_weight[<= n] class sizes; classes are
+ * numbered by smallest member. These are the orbit arguments of
+ * aaqaoa_prepare_ising. Returns AAQAOA_ERR_INVALID_ARG for bad sizes,
+ * pointers, edges, or a NaN weight or field.
+ */
+int aaqaoa_ising_orbits(int n, int num_edges, const int32_t *edges, const double *edge_weight, const double *field,
+                        int32_t *edge_orbit, int32_t *num_orbits, int32_t *orbit_rep, int32_t *orbit_weight,
+                        int32_t *vertex_orbit, int32_t *num_vorbits, int32_t *vorbit_rep, int32_t *vorbit_weight);
 
 /* Plan properties: qubits, layers, edges, orbits, precision flag. */
 int aaqaoa_plan_info(const aaqaoa_plan *plan, int *n, int *p, int *num_edges, int *num_orbits,

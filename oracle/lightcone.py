@@ -81,3 +81,36 @@ def energy_grad(n, edges, gamma, beta, weights=None, edge_subset=None):
         dg += wk * dge
         db += wk * dbe
     return E, dg, db
+
+
+def ising_energy_grad(n, edges, weights, fields, gamma, beta):
+    """E and gradient of an Ising-form objective (real couplings per edge,
+    real fields per vertex or None), term by term: each ZZ term sees the
+    radius-p ball around its edge, each field term Z_i the radius-p ball
+    around i, and the subproblem carries the couplings and fields inside the
+    ball (the reverse causal cone of Sec. 5.1 holds for any diagonal cost:
+    terms outside the cone commute through and cancel)."""
+    edges = np.asarray(edges).reshape(-1, 2)
+    w = np.asarray(weights, dtype=np.float64)
+    h = np.zeros(n) if fields is None else np.asarray(fields, dtype=np.float64)
+    p = len(np.asarray(gamma).reshape(-1))
+    E, dg, db = 0.0, np.zeros(p), np.zeros(p)
+    terms = [((int(u), int(v)), wk, None) for (u, v), wk in zip(edges, w)]
+    if fields is not None:
+        terms += [((i, i), None, h[i]) for i in range(n)]
+    for (u, v), wk, hk in terms:
+        verts = ball(n, edges, u, v, p)
+        index = {a: k for k, a in enumerate(verts)}
+        inside = [k for k, (a, b) in enumerate(edges) if {int(a), int(b)} <= index.keys()]
+        sub = np.array([(index[int(edges[k][0])], index[int(edges[k][1])]) for k in inside],
+                       dtype=np.int32).reshape(-1, 2)
+        fn = oracle.ising(sub, w[inside], np.array([h[a] for a in verts]))
+        if hk is None:
+            obs = oracle.ising(np.array([[index[u], index[v]]]), np.array([wk]), np.zeros(len(verts)))
+        else:
+            oh = np.zeros(len(verts))
+            oh[index[u]] = hk
+            obs = oracle.ising(np.zeros((0, 2)), np.zeros(0), oh)
+        Et, dgt, dbt = oracle.ising_energy_grad(len(verts), fn, gamma, beta, obs)
+        E, dg, db = E + Et, dg + dgt, db + dbt
+    return E, dg, db

@@ -43,6 +43,9 @@ _PROTOS = [
                                       ctypes.c_int, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
     ("aaqaoa_prepare_weighted", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
                                                _i32p, ctypes.c_int, ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
+    ("aaqaoa_prepare_ising", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _f64p, _f64p, ctypes.c_int, _i32p,
+                                            _i32p, _i32p, ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_int,
+                                            ctypes.c_uint, _vp, ctypes.POINTER(_vp)]),
     ("aaqaoa_workspace_bytes", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("aaqaoa_set_workspace", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
     ("aaqaoa_set_stream", ctypes.c_int, [_vp, _vp]),
@@ -70,6 +73,8 @@ _PROTOS = [
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("aaqaoa_destroy_multi", None, [_vp]),
     ("aaqaoa_inject_fault", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("aaqaoa_ising_orbits", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _f64p, _f64p, _i32p, _i32p, _i32p,
+                                           _i32p, _i32p, _i32p, _i32p, _i32p]),
     ("aaqaoa_edge_orbits", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
     ("aaqaoa_get_pass_plan", ctypes.c_int, [_vp, _i32p]),
     ("aaqaoa_set_pass_plan", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),

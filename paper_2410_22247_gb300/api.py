@@ -34,10 +34,16 @@ class Plan:
     ``orbits`` is an object with ``rep``, ``weight`` and ``edge_orbit``
     attributes (e.g. :class:`paper_2410_22247_gb300.orbits.EdgeOrbits`), a
     ``(rep, weight[, edge_orbit])`` tuple, or None for no reduced observable.
+
+    ``weights`` (integer, >= 1) makes a weighted-MaxCut plan with exact
+    integer cut values. ``couplings`` (real, one per edge) and ``fields``
+    (real, one per vertex, or None) make an Ising plan (aaqaoa_prepare_ising);
+    its H_red also needs vertex orbits: ``orbits`` with ``vrep``, ``vweight``
+    and ``vertex_orbit`` attributes (:class:`paper_2410_22247_gb300.orbits.IsingOrbits`).
     """
 
     def __init__(self, n, edges, p, orbits=None, precision="c64", batch=1, with_grad=True,
-                 stream=None, device=None, weights=None):
+                 stream=None, device=None, weights=None, couplings=None, fields=None):
         import torch
 
         self._lib = N.load()
@@ -60,12 +66,34 @@ class Plan:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         handle = ctypes.c_void_p()
         self.weights = None if weights is None else _i32(weights)
-        N.check(N.aaqaoa_prepare_weighted(self.n, len(self.edges), _ptr(e, ctypes.c_int32),
-                                          _ptr(self.weights, ctypes.c_int32), self.num_orbits,
-                                          _ptr(rep, ctypes.c_int32), _ptr(weight, ctypes.c_int32),
-                                          _ptr(eo, ctypes.c_int32), self.p, flags,
-                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)),
-                "aaqaoa_prepare_weighted")
+        self.ising = couplings is not None
+        if self.ising:
+            if weights is not None:
+                raise ValueError("give integer weights or real couplings, not both")
+            cw = _f64(couplings)
+            fh = None if fields is None else _f64(fields)
+            if len(cw) != len(self.edges) or (fh is not None and len(fh) != self.n):
+                raise ValueError("couplings need one value per edge and fields one per vertex")
+            vr = vw = vo = None
+            if orbits is not None and getattr(orbits, "vrep", None) is not None:
+                vr, vw = _i32(orbits.vrep), _i32(orbits.vweight)
+                vo = None if getattr(orbits, "vertex_orbit", None) is None else _i32(orbits.vertex_orbit)
+            self.couplings, self.fields = cw, fh
+            N.check(N.aaqaoa_prepare_ising(self.n, len(self.edges), _ptr(e, ctypes.c_int32),
+                                           _ptr(cw, ctypes.c_double), _ptr(fh, ctypes.c_double), self.num_orbits,
+                                           _ptr(rep, ctypes.c_int32), _ptr(weight, ctypes.c_int32),
+                                           _ptr(eo, ctypes.c_int32), 0 if vr is None else len(vr),
+                                           _ptr(vr, ctypes.c_int32), _ptr(vw, ctypes.c_int32),
+                                           _ptr(vo, ctypes.c_int32), self.p, flags,
+                                           ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)),
+                    "aaqaoa_prepare_ising")
+        else:
+            N.check(N.aaqaoa_prepare_weighted(self.n, len(self.edges), _ptr(e, ctypes.c_int32),
+                                              _ptr(self.weights, ctypes.c_int32), self.num_orbits,
+                                              _ptr(rep, ctypes.c_int32), _ptr(weight, ctypes.c_int32),
+                                              _ptr(eo, ctypes.c_int32), self.p, flags,
+                                              ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)),
+                    "aaqaoa_prepare_weighted")
         self.handle = handle
         self.batch = int(batch)
         self.with_grad = bool(with_grad)

@@ -95,7 +95,7 @@ struct Pass {
 };
 
 struct Layout {
-    size_t ctrl, out, params, cs, tab, partials, zz, samp, phi, lam, total;
+    size_t ctrl, out, params, cs, tab, partials, zz, samp, ising, phi, lam, total;
     size_t partial_count;
 };
 
@@ -111,6 +111,13 @@ struct aaqaoa_plan {
     int wsum = 0;                     // sum of the edge weights: the largest cut value
     CostFn cost{};
     CutFn obs[2]{};
+    // Ising plans (aaqaoa_prepare_ising): real couplings and fields; the
+    // cost and both observables as dense functions, copied into the workspace
+    bool ising = false;
+    std::vector<double> ising_w, ising_h;   // per edge; per vertex (empty: no fields)
+    std::vector<int32_t> vorbit_rep, vorbit_weight;
+    IsingFn ifn[3]{};                       // cost, H_C, H_red
+    const double *cur_gamma = nullptr;      // device gamma of the call being enqueued
     cudaStream_t stream = nullptr;
     // workspace
     unsigned char *ws = nullptr;
@@ -163,6 +170,7 @@ struct aaqaoa_plan {
     unsigned long long *d_samp_x() const { return reinterpret_cast<unsigned long long *>(d_samp_u() + AAQAOA_SAMPLE_MAX); }
     int *d_samp_cut() const { return reinterpret_cast<int *>(d_samp_x() + AAQAOA_SAMPLE_MAX); }
     unsigned long long *d_maxcut_key() const { return reinterpret_cast<unsigned long long *>(ws + L.ctrl + 32); }
+    const IsingFn *d_ifn(int k) const { return reinterpret_cast<const IsingFn *>(ws + L.ising) + k; }
     void *d_phi() const { return ws + L.phi; }
     void *d_lam() const { return ws + L.lam; }
 };
@@ -238,6 +246,8 @@ Layout layout(const aaqaoa_plan *pl, int batch, bool grad)
     L.samp = off;
     off = align256(off + (sample_chunk_count(pl->n) + 32 + 2 * (size_t)AAQAOA_SAMPLE_MAX) * sizeof(double) +
                    (size_t)AAQAOA_SAMPLE_MAX * sizeof(int));
+    L.ising = off;
+    off = align256(off + (pl->ising ? 3 * sizeof(IsingFn) : 0));
     L.phi = off;
     off = align256(off + B * ((size_t)1 << pl->n) * pl->amp());
     L.lam = off;
@@ -367,6 +377,11 @@ PassArgs base_args(const aaqaoa_plan *pl, int obs)
     a.cost = pl->cost;
     a.pt = pl->pt_dev;
     a.pt_obs = obs;
+    if (pl->ising) {
+        a.icost = pl->d_ifn(0);
+        a.iobs = pl->d_ifn(1 + obs);
+        a.gam = pl->cur_gamma;
+    }
     return a;
 }
 
@@ -557,6 +572,11 @@ SmallArgs small_args(const aaqaoa_plan *pl, int obs, int mode, int write_state)
     s.state = pl->d_phi();
     s.obs = pl->obs[obs];
     s.cost = pl->cost;
+    if (pl->ising) {
+        s.icost = pl->d_ifn(0);
+        s.iobs = pl->d_ifn(1 + obs);
+        s.gam = pl->cur_gamma;
+    }
     return s;
 }
 
@@ -581,6 +601,7 @@ int check_ready(aaqaoa_plan *pl, int obs, bool grad, int B)
 int enqueue_params(aaqaoa_plan *pl, int B, const double *d_gamma, const double *d_beta)
 {
     (void)cudaGetLastError();  // a stale error of an unrelated earlier call must not be reported here
+    pl->cur_gamma = d_gamma;
     ProfScope ps_(pl, PK_PARAMS, 0.0);
     CKL(launch_params(pl->c128, B, pl->p, pl->tab_len(), pl->n, d_gamma, d_beta, pl->d_tab(), pl->d_cs(), pl->stream),
         "parameter tables");
@@ -886,6 +907,107 @@ int aaqaoa_prepare_weighted(int n, int num_edges, const int32_t *edges, const in
     return AAQAOA_OK;
 }
 
+int aaqaoa_prepare_ising(int n, int num_edges, const int32_t *edges, const double *edge_weight, const double *field,
+                         int num_orbits, const int32_t *orbit_rep, const int32_t *orbit_weight,
+                         const int32_t *edge_orbit, int num_vorbits, const int32_t *vorbit_rep,
+                         const int32_t *vorbit_weight, const int32_t *vertex_orbit, int p, unsigned flags, void *stream,
+                         aaqaoa_plan **out)
+{
+    // edges, p, flags and the edge-orbit partition are checked as for MaxCut
+    aaqaoa_plan *pl = nullptr;
+    int r = aaqaoa_prepare_weighted(n, num_edges, edges, nullptr, num_orbits, orbit_rep, orbit_weight, edge_orbit, p,
+                                    flags, stream, &pl);
+    if (r)
+        return r;
+    *out = nullptr;
+    auto reject = [&](int code, const char *fmt, auto... args) {
+        aaqaoa_destroy(pl);
+        return fail(code, fmt, args...);
+    };
+    if (num_edges > 0 && !edge_weight)
+        return reject(AAQAOA_ERR_INVALID_ARG, "edge_weight is NULL (%d edges)", num_edges);
+    for (int i = 0; i < num_edges; i++)
+        if (!std::isfinite(edge_weight[i]))
+            return reject(AAQAOA_ERR_INVALID_ARG, "edge %d has a weight that is not finite", i);
+    if (field)
+        for (int u = 0; u < n; u++)
+            if (!std::isfinite(field[u]))
+                return reject(AAQAOA_ERR_INVALID_ARG, "vertex %d has a field that is not finite", u);
+    if (edge_orbit)  // automorphisms keep the couplings: one weight per class
+        for (int i = 0; i < num_edges; i++)
+            if (edge_weight[i] != edge_weight[orbit_rep[edge_orbit[i]]])
+                return reject(AAQAOA_ERR_BAD_ORBITS, "orbit %d mixes edge weights (edge %d)", edge_orbit[i], i);
+    // vertex orbits: needed for H_red when there are fields
+    if (num_vorbits < 0 || num_vorbits > n)
+        return reject(AAQAOA_ERR_BAD_ORBITS, "num_vorbits=%d outside [0, n=%d]", num_vorbits, n);
+    if (field && num_orbits > 0 && num_vorbits == 0)
+        return reject(AAQAOA_ERR_BAD_ORBITS, "fields with edge orbits need vertex orbits for H_red");
+    if (num_vorbits > 0) {
+        if (!vorbit_rep || !vorbit_weight)
+            return reject(AAQAOA_ERR_BAD_ORBITS, "vorbit_rep / vorbit_weight is NULL");
+        std::vector<char> isrep(n, 0);
+        long long sum = 0;
+        for (int c = 0; c < num_vorbits; c++) {
+            if (vorbit_rep[c] < 0 || vorbit_rep[c] >= n)
+                return reject(AAQAOA_ERR_BAD_ORBITS, "vertex orbit %d representative %d is not a vertex", c,
+                              vorbit_rep[c]);
+            if (isrep[vorbit_rep[c]])
+                return reject(AAQAOA_ERR_BAD_ORBITS, "vertex %d represents two orbits", vorbit_rep[c]);
+            isrep[vorbit_rep[c]] = 1;
+            if (vorbit_weight[c] < 1)
+                return reject(AAQAOA_ERR_BAD_ORBITS, "vertex orbit %d has weight %d < 1", c, vorbit_weight[c]);
+            sum += vorbit_weight[c];
+        }
+        if (sum != n)
+            return reject(AAQAOA_ERR_BAD_ORBITS, "vertex orbit weights sum to %d, not n = %d", (int)sum, n);
+        if (vertex_orbit) {
+            std::vector<int> count(num_vorbits, 0);
+            for (int u = 0; u < n; u++) {
+                if (vertex_orbit[u] < 0 || vertex_orbit[u] >= num_vorbits)
+                    return reject(AAQAOA_ERR_BAD_ORBITS, "vertex %d has orbit %d out of range", u, vertex_orbit[u]);
+                count[vertex_orbit[u]]++;
+            }
+            for (int c = 0; c < num_vorbits; c++) {
+                if (vertex_orbit[vorbit_rep[c]] != c)
+                    return reject(AAQAOA_ERR_BAD_ORBITS, "representative of vertex orbit %d lies in orbit %d", c,
+                                  vertex_orbit[vorbit_rep[c]]);
+                if (count[c] != vorbit_weight[c])
+                    return reject(AAQAOA_ERR_BAD_ORBITS, "vertex orbit %d has %d vertices, not its weight %d", c, count[c], vorbit_weight[c]);
+            }
+            if (field)  // automorphisms keep the fields
+                for (int u = 0; u < n; u++)
+                    if (field[u] != field[vorbit_rep[vertex_orbit[u]]])
+                        return reject(AAQAOA_ERR_BAD_ORBITS, "vertex orbit %d mixes fields (vertex %d)",
+                                      vertex_orbit[u], u);
+        }
+    }
+    pl->ising = true;
+    pl->wsum = 0;  // the phase tables carry only the butterfly scale (one entry)
+    pl->ising_w.assign(edge_weight, edge_weight + num_edges);
+    if (field)
+        pl->ising_h.assign(field, field + n);
+    pl->vorbit_rep.assign(vorbit_rep, vorbit_rep + num_vorbits);
+    pl->vorbit_weight.assign(vorbit_weight, vorbit_weight + num_vorbits);
+    memset(pl->ifn, 0, sizeof pl->ifn);
+    for (int i = 0; i < num_edges; i++) {
+        const int u = pl->edges[2 * i], v = pl->edges[2 * i + 1];
+        pl->ifn[0].W[u][v] = pl->ifn[0].W[v][u] = edge_weight[i];
+    }
+    if (field)
+        for (int u = 0; u < n; u++)
+            pl->ifn[0].h[u] = field[u];
+    pl->ifn[1] = pl->ifn[0];  // H_C: the cost itself
+    for (int c = 0; c < num_orbits; c++) {  // H_red: representatives at orbit size x weight
+        const int i = orbit_rep[c], u = pl->edges[2 * i], v = pl->edges[2 * i + 1];
+        pl->ifn[2].W[u][v] = pl->ifn[2].W[v][u] = orbit_weight[c] * edge_weight[i];
+    }
+    if (field)
+        for (int c = 0; c < num_vorbits; c++)
+            pl->ifn[2].h[vorbit_rep[c]] = vorbit_weight[c] * field[vorbit_rep[c]];
+    *out = pl;
+    return AAQAOA_OK;
+}
+
 int aaqaoa_workspace_bytes(const aaqaoa_plan *plan, int batch, int with_grad, size_t *bytes)
 {
     if (!plan || !bytes || batch < 1)
@@ -944,6 +1066,8 @@ int aaqaoa_set_workspace(aaqaoa_plan *pl, void *device_ptr, size_t bytes, int ba
     if (r)
         return r;
     CK(cudaMemsetAsync(pl->ws + L.ctrl, 0, 256, pl->stream));
+    if (pl->ising)
+        CK(cudaMemcpyAsync(pl->ws + L.ising, pl->ifn, sizeof pl->ifn, cudaMemcpyHostToDevice, pl->stream));
     CK(cudaStreamSynchronize(pl->stream));
     return AAQAOA_OK;
 }
@@ -1177,6 +1301,8 @@ int aaqaoa_expect(aaqaoa_plan *pl, const double *gamma, const double *beta, int 
         return r;
     if (agg_mode < AAQAOA_AGG_FUSED || agg_mode > AAQAOA_AGG_SINGLEPASS)
         return fail(AAQAOA_ERR_INVALID_ARG, "agg_mode %d unknown", agg_mode);
+    if (pl->ising && agg_mode != AAQAOA_AGG_FUSED)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "Ising plans aggregate in the fused mode only");
     if (!energy)
         return fail(AAQAOA_ERR_INVALID_ARG, "energy is NULL");
     pl->launches = 0;
@@ -1356,7 +1482,8 @@ int aaqaoa_statevector(aaqaoa_plan *pl, const double *gamma, const double *beta,
         if ((r = enqueue_forward(pl, 1, AAQAOA_OBS_FULL, FWD_STATE)))
             return r;
         // the passes store the twisted, shifted-angle state: map it back
-        CKL(launch_untwist(pl->c128, pl->d_phi(), pl->n, pl->d_cs(), pl->p, pl->stream), "statevector export");
+        CKL(launch_untwist(pl->c128, pl->d_phi(), pl->n, pl->d_cs(), pl->p, pl->ising ? 1 : 0, pl->stream),
+            "statevector export");
         pl->launches++;
     }
     pl->state_valid = true;
@@ -1449,6 +1576,8 @@ int aaqaoa_max_cut(aaqaoa_plan *pl, int32_t *c_max, uint64_t *argmax)
         return fail(AAQAOA_ERR_INVALID_ARG, "plan, c_max or argmax is NULL");
     if (!pl->ws)
         return fail(AAQAOA_ERR_WORKSPACE, "no workspace set (aaqaoa_set_workspace)");
+    if (pl->ising)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "the maximum cut needs an integer cut function (not an Ising plan)");
     (void)cudaGetLastError();
     CK(cudaMemsetAsync(pl->d_maxcut_key(), 0, sizeof(unsigned long long), pl->stream));
     CKL(launch_maxcut(pl->cost, pl->n, pl->d_maxcut_key(), pl->stream), "maximum cut");
@@ -1470,6 +1599,8 @@ int aaqaoa_sample(aaqaoa_plan *pl, const double *gamma, const double *beta, int 
         return r;
     if (K < 1 || K > AAQAOA_SAMPLE_MAX)
         return fail(AAQAOA_ERR_INVALID_ARG, "K = %d outside [1, %d]", K, AAQAOA_SAMPLE_MAX);
+    if (pl->ising)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "sampling reports integer cut values (not an Ising plan)");
     if (!u || !x_out)
         return fail(AAQAOA_ERR_INVALID_ARG, "u or x_out is NULL");
     for (int k = 0; k < K; k++)
@@ -1512,6 +1643,8 @@ int aaqaoa_aggregate_only(aaqaoa_plan *pl, int observable, int agg_mode, double 
         return fail(AAQAOA_ERR_INVALID_ARG, "energy is NULL");
     if (agg_mode != AAQAOA_AGG_PERTERM && agg_mode != AAQAOA_AGG_SINGLEPASS)
         return fail(AAQAOA_ERR_INVALID_ARG, "aggregate_only needs PERTERM or SINGLEPASS");
+    if (pl->ising)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "Ising plans aggregate in the fused mode only");
     if (!pl->state_valid)
         return fail(AAQAOA_ERR_INVALID_ARG, "no stored state: run aaqaoa_statevector or a non-fused expect first");
     pl->launches = 0;
@@ -1674,6 +1807,8 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
         return fail(AAQAOA_ERR_INVALID_ARG, "observable %d unknown", observable);
     if (observable == AAQAOA_OBS_RED && pl->num_orbits == 0)
         return fail(AAQAOA_ERR_INVALID_ARG, "H_red requested but the plan has no edge orbits");
+    if (pl->ising)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "the static-scratch entry point takes MaxCut plans only");
     const size_t state_bytes = ((size_t)1 << pl->n) * pl->amp();
     if (state_bytes > STATIC_STATE_BYTES)
         return fail(AAQAOA_ERR_UNSUPPORTED,

@@ -25,6 +25,16 @@ struct CutFn {
 // integer edge weights grouped into classes for weighted MaxCut.
 using CostFn = CutFn;
 
+// An Ising-form function O(x) = sum_{u<v} W[u][v] [x_u != x_v] + sum_u h[u] x_u
+// with real couplings (W symmetric, zero where there is no edge) and real
+// fields: the cost of an Ising plan, and its observables (H_red keeps one
+// representative edge per edge orbit and one vertex per vertex orbit, each at
+// orbit size times its weight or field).
+struct IsingFn {
+    double W[MAXN][MAXN];
+    double h[MAXN];
+};
+
 // Cut functions of one graph of a batch of graphs with the same n: the cost
 // C(x) and the two observables (0 = H_C, 1 = H_red).
 struct GraphFns {
@@ -82,6 +92,13 @@ struct PassArgs {
     CostFn cost;      // C(x) for the phase and dE/dgamma
     const GraphFns *pt;  // non-null: point b is its own graph, pt[b] (obs and cost above unused)
     int pt_obs;          // which observable of pt[b]
+    // Ising plans (real couplings and fields): the cost and the observable as
+    // dense couplings, gamma per (point, layer); obs and cost above unused.
+    // Their layers never drop a factor -iX: a layer with |sin| > |cos| uses
+    // the cot form of the rotation instead.
+    const IsingFn *icost;
+    const IsingFn *iobs;
+    const double *gam;   // [B][p]
 };
 
 // Whole-circuit kernel for states that fit one CTA's shared memory.
@@ -98,6 +115,9 @@ struct SmallArgs {
     void *state;       // [B][2^n] (optional)
     CutFn obs;
     CostFn cost;
+    const IsingFn *icost;  // non-null: an Ising plan (obs and cost above unused)
+    const IsingFn *iobs;
+    const double *gam;     // [B][p]
 };
 
 // Device descriptor of one small graph in an uneven batch (whole circuit in
@@ -138,13 +158,13 @@ int launch_params(bool c128, int B, int p, int tab_len, int n, const double *d_g
 int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a,
                 int grid, cudaStream_t st);
 int launch_small(bool c128, const SmallArgs &a, int B, cudaStream_t st);
-size_t small_smem_bytes(bool c128, int n, int mode);
+size_t small_smem_bytes(bool c128, int n, int mode, bool ising);
 int small_max_qubits(bool c128, int mode);
 int launch_agg_fused(bool c128, const AggArgs &a, cudaStream_t st, int grid);
 int launch_agg_terms(bool c128, const AggArgs &a, cudaStream_t st, int grid);
 int agg_grid(bool c128);
 size_t small_multi_smem_bytes(bool c128, int max_n, int max_tab);
-int launch_untwist(bool c128, void *psi, int n, const double2 *cs, int p, cudaStream_t st);
+int launch_untwist(bool c128, void *psi, int n, const double2 *cs, int p, int noshift, cudaStream_t st);
 int launch_maxcut(const CostFn &cost, int n, unsigned long long *d_key, cudaStream_t st);
 size_t sample_chunk_count(int n);
 int launch_sample(bool c128, const void *psi, int n, double *d_sums, double *d_total, int K, const double *d_u,

@@ -107,6 +107,49 @@ __device__ __forceinline__ void rot(C &a, C &b, R t)
     }
 }
 
+// (a, b) <- (t a - b, t b + a): the same twisted-frame rotation by beta with
+// the factor f = sin beta dropped instead (t = cot beta). Ising plans use it
+// when |sin| > |cos|: with fields the cost no longer commutes with X^n, so
+// the -iX factor that the shifted form drops cannot be dropped there.
+template <typename C, typename R>
+__device__ __forceinline__ void rotc(C &a, C &b, R t)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        const float2 a0 = a;
+        a = __ffma2_rn(make_float2(t, t), a0, make_float2(-b.x, -b.y));
+        b = __ffma2_rn(make_float2(t, t), b, a0);
+    } else {
+        const C a0 = a;
+        a.x = fma(t, a0.x, -b.x);
+        a.y = fma(t, a0.y, -b.y);
+        b.x = fma(t, b.x, a0.x);
+        b.y = fma(t, b.y, a0.y);
+    }
+}
+
+// exp(i theta) for a phase angle given in FP64: reduced mod 2 pi in FP64,
+// then cos/sin in the amplitude precision (the reduced argument is exact to
+// the rounding of a float in [0, 2 pi)).
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T unit_phase(double theta)
+{
+    const double TWO_PI = 6.283185307179586476925286766559;
+    const double a = theta - TWO_PI * floor(theta * (1.0 / TWO_PI));  // in [0, 2 pi)
+    typename CT<R>::T z;
+    if constexpr (std::is_same<R, float>::value) {
+        float sn, cn;
+        sincosf((float)a, &sn, &cn);
+        z.x = cn;
+        z.y = sn;
+    } else {
+        double sn, cn;
+        sincos(a, &sn, &cn);
+        z.x = cn;
+        z.y = sn;
+    }
+    return z;
+}
+
 // acc += (u.x v.x, u.y v.y): Re(conj(u) v) summed over the two lanes later
 template <typename C>
 __device__ __forceinline__ void dot_acc(C &acc, const C &u, const C &v)
@@ -381,27 +424,38 @@ static_assert(stages_partition<Geo<double, 2>>(), "c128 two-vector stage plan");
 template <typename R, int NV>
 __host__ __device__ constexpr size_t tile_bytes() { return ((size_t)1 << Geo<R, NV>::T) * sizeof(R) * 2; }
 
-// shared memory of one pass CTA: pipeline buffers, phase table, cut masks
-template <typename R, int NV>
+// shared memory of one pass CTA: pipeline buffers, phase table, cut masks;
+// for Ising plans (IS) pipeline buffers, per-thread values of both functions
+// and per-thread cost phases
+template <typename R, int NV, bool IS = false>
 __host__ __device__ constexpr size_t pass_smem_total()
 {
-    return (size_t)Geo<R, NV>::NSTAGE * NV * tile_bytes<R, NV>() + 2 * (size_t)MAXTAB * sizeof(R) * 2 +
-           (size_t)(2 * MAXK) * MAXN * 8 + 1024;
+    using G = Geo<R, NV>;
+    return IS ? (size_t)G::NSTAGE * NV * tile_bytes<R, NV>() + (size_t)4 * (G::RB + 1) * G::NTHR * sizeof(R) + 1024
+              : (size_t)G::NSTAGE * NV * tile_bytes<R, NV>() + 2 * (size_t)MAXTAB * sizeof(R) * 2 +
+                    (size_t)(2 * MAXK) * MAXN * 8 + 1024;
 }
 // static shared memory of the pass kernel (mbarriers, per-point sums, cut
 // constants) plus slack for the final reduction's flag
-template <typename R, int NV>
+template <typename R, int NV, bool IS = false>
 __host__ __device__ constexpr size_t pass_static_smem()
 {
     using G = Geo<R, NV>;
-    return 2 * G::NSTAGE * 8 + 2 * 3 * 32 * 8 + 4 + 2 * MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
-           2 * (G::RB + 1) * G::NTHR * 4 + 2 * 2 * 2 * 32 * 4 + 256;
+    return IS ? 2 * G::NSTAGE * 8 + 2 * 3 * 32 * 8 + 4 + 2 * MAXK * 4 + 4 + 4 + 2 * 2 * 2 * 32 * 4 +
+                    G::NSTAGE * 2 * 16 * sizeof(R) + G::NSTAGE * 16 * 2 * sizeof(R) + 2 * 32 * sizeof(R) +
+                    2 * 32 * 2 * sizeof(R) + 256
+              : 2 * G::NSTAGE * 8 + 2 * 3 * 32 * 8 + 4 + 2 * MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
+                    2 * (G::RB + 1) * G::NTHR * 4 + 2 * 2 * 2 * 32 * 4 + 256;
 }
 static_assert(pass_smem_total<float, 1>() + pass_static_smem<float, 1>() <= 227 * 1024, "c64 pipeline smem");
 static_assert(pass_smem_total<float, 2>() + pass_static_smem<float, 2>() <= 227 * 1024, "c64 adjoint pipeline smem");
 static_assert(pass_smem_total<double, 1>() + pass_static_smem<double, 1>() <= 227 * 1024, "c128 pipeline smem");
 static_assert(pass_smem_total<double, 2>() + pass_static_smem<double, 2>() <= 227 * 1024,
               "c128 adjoint pipeline smem");
+static_assert(pass_smem_total<float, 1, true>() + pass_static_smem<float, 1, true>() <= 227 * 1024, "Ising smem");
+static_assert(pass_smem_total<float, 2, true>() + pass_static_smem<float, 2, true>() <= 227 * 1024, "Ising smem");
+static_assert(pass_smem_total<double, 1, true>() + pass_static_smem<double, 1, true>() <= 227 * 1024, "Ising smem");
+static_assert(pass_smem_total<double, 2, true>() + pass_static_smem<double, 2, true>() <= 227 * 1024, "Ising smem");
 
 template <typename G>
 __host__ __device__ constexpr uint32_t reg_offset(int st, int m)
@@ -595,6 +649,15 @@ struct StageCtx {
     R amp0;        // 2^(-n/2), the amplitude of the generated |+>^n
     R tq2, f2;     // fused pass: rotation of the second layer
     R run2;        // its f^j (the second layer starts on exact vectors: j = 0)
+    bool cot, cot2;  // Ising plans: the layer (second layer) uses the cot form
+    // Ising plans: tile values [2][16], tile cost phases [16], per-thread
+    // values [2][RB+1][NTHR] and cost phases [RB+1][NTHR], stage terms
+    const R *tv;
+    const typename CT<R>::T *tp;
+    const R *ptv;
+    const typename CT<R>::T *ptp;
+    const R *qv;                  // [2][32]
+    const typename CT<R>::T *qp;  // [32]
 };
 
 // ------------------------------------------------ cut values in a stage
@@ -610,8 +673,8 @@ struct StageCtx {
 // producer warp computes them per tile), the t-only sums on the thread only
 // (computed once per launch), Qr on the stage only. What is left per thread
 // and tile is a subset sum over the 2^RB register states.
-template <typename G, int ST>
-__device__ __forceinline__ void cut_terms(const int *tc, const int *pt, int tid, int &base, int (&d)[G::RB])
+template <typename G, int ST, typename V>
+__device__ __forceinline__ void cut_terms(const V *tc, const V *pt, int tid, V &base, V (&d)[G::RB])
 {
     constexpr int NTB = G::T - G::RB;
     base = tc[15] + pt[0];
@@ -678,6 +741,56 @@ __device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int
     }
 }
 
+// Ising plans: the same quadratic decomposition with real couplings and
+// fields. Values O(x) of the thread's 2^RB states from constants rounded
+// once to R (tile: tc[15] = O(f), tc[L] = h_L(f); thread: pt; stage: q).
+template <typename G, typename R, int ST>
+__device__ __forceinline__ void ising_vals(const R *tc, const R *pt, const R *q, int tid, R (&v)[1 << G::RB])
+{
+    constexpr int RB = G::RB;
+    R base, d[RB];
+    cut_terms<G, ST, R>(tc, pt, tid, base, d);
+    v[0] = base;
+#pragma unroll
+    for (int m = 1; m < (1 << RB); m++) {
+        const int top = hibit(m);
+        v[m] = v[m ^ (1 << top)] + d[top];
+    }
+#pragma unroll
+    for (int m = 1; m < (1 << RB); m++)
+        v[m] += q[m];
+}
+
+// Ising phases P[m] = scale * exp(-i s gamma O(x)) of the thread's states as
+// products of unit factors, each computed in FP64 from its exact term and
+// rounded once: tp[15] = scale * exp(..O(f)), tp[L] = exp(..h_L(f)) per tile;
+// pp[0] (thread-bit pairs), pp[(1 + k) NTHR] (register bit k with the thread
+// bits) per thread; qp[m] (register-bit pairs) per stage.
+template <typename G, typename C, int ST>
+__device__ __forceinline__ void ising_phases(const C *tp, const C *pp, const C *qp, int tid, C (&P)[1 << G::RB])
+{
+    constexpr int RB = G::RB, NTB = G::T - G::RB;
+    C base = cmul(tp[15], pp[0]);
+#pragma unroll
+    for (int j = 0; j < NTB; j++)
+        if ((tid >> j) & 1)
+            base = cmul(base, tp[G::thr(ST, j)]);
+    C d[RB];
+#pragma unroll
+    for (int k = 0; k < RB; k++)
+        d[k] = cmul(tp[G::reg(ST, k)], pp[(1 + k) * G::NTHR]);
+    P[0] = base;
+#pragma unroll
+    for (int m = 1; m < (1 << RB); m++) {
+        const int top = hibit(m);
+        P[m] = cmul(P[m ^ (1 << top)], d[top]);
+    }
+#pragma unroll
+    for (int m = 1; m < (1 << RB); m++)
+        if (m & (m - 1))
+            P[m] = cmul(P[m], qp[m]);
+}
+
 // A thread's running sum over its tiles, in FP64 for both precisions: each
 // register stage sums its 2^RB products in the amplitude type, and every sum
 // across stages, tiles, threads and CTAs is an FP64 add.
@@ -695,10 +808,11 @@ template <typename R> struct Acc {
 // table or the last pass), so an inner product taken before butterfly j+1 is
 // scaled by f^(2j). In the twisted frame Im<lambda|X_q|phi> sums, over the
 // pairs (x, x'), Re(conj(lambda_x') phi_x) - Re(conj(lambda_x) phi_x').
-template <typename R, int NV, int ST>
+template <typename R, int NV, int ST, bool IS = false>
 __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R &run,
                                          typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
-                                         typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc)
+                                         typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc,
+                                         bool cot = false)
 {
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
@@ -726,9 +840,15 @@ __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R
                 const int c = (m >> (k == 0 ? 1 : 0)) & 1;
                 dot_acc(ipp[c], l[m1], a[m]);
                 dot_acc(ipn[c], l[m], a[m1]);
-                rot(l[m], l[m1], tq);
+                if (IS && cot)
+                    rotc(l[m], l[m1], tq);
+                else
+                    rot(l[m], l[m1], tq);
             }
-            rot(a[m], a[m1], tq);
+            if (IS && cot)
+                rotc(a[m], a[m1], tq);
+            else
+                rot(a[m], a[m1], tq);
         }
         if constexpr (NV == 2) {
             const R q = ((ipp[0].x + ipp[0].y) + (ipp[1].x + ipp[1].y)) - ((ipn[0].x + ipn[0].y) + (ipn[1].x + ipn[1].y));
@@ -744,7 +864,9 @@ __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
 // FUSE (last stage of a fused pass): after this layer's operations the second
 // layer's butterflies of the same stage follow, their dE/dbeta into acc2.
-template <typename R, int NV, int ST, bool OPS, bool FUSE = false>
+// IS: an Ising plan (real values, phases as products of unit factors, cot form
+// of the rotation where the layer needs it).
+template <typename R, int NV, int ST, bool OPS, bool FUSE = false, bool IS = false>
 __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                           typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc0,
@@ -782,25 +904,44 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     // cut-function constants: function 0 is C (cost), 1 the observable O
     const int *tc0 = X.tc, *tc1 = X.tc + 16;
     const int *pt0 = X.ptc + X.tid, *pt1 = X.ptc + (RB + 1) * G::NTHR + X.tid;
+    // the values O_e(x) of the thread's states (real; exact integers for cut functions)
+    auto values = [&](int e, R (&v)[NR]) {
+        if constexpr (IS)
+            ising_vals<G, R, ST>(X.tv + 16 * e, X.ptv + e * (RB + 1) * G::NTHR + X.tid, X.qv + 32 * e, X.tid, v);
+        else
+            cut_real<G, R, ST>(e ? tc1 : tc0, e ? pt1 : pt0, X.qr + 32 * e, X.qrf + 32 * e, X.tid, v);
+    };
+    // the cost layer's phase factors of the thread's states (this pass's table)
+    auto phases = [&](C (&P)[NR]) {
+        if constexpr (IS) {
+            ising_phases<G, C, ST>(X.tp, X.ptp + X.tid, X.qp, X.tid, P);
+        } else {
+            int cv[NR];
+            cut_int<G, ST>(tc0, pt0, X.qr, X.tid, cv);
+#pragma unroll
+            for (int m = 0; m < NR; m++)
+                P[m] = X.tab[cv[m]];
+        }
+    };
 
     if (OPS && ST == 0 && A.pre_phase) {
-        int cv[NR];
-        cut_int<G, ST>(tc0, pt0, X.qr, X.tid, cv);
+        C P[NR];
+        phases(P);
 #pragma unroll
         for (int m = 0; m < NR; m++)
-            a[m] = cmul(a[m], X.tab[cv[m]]);
+            a[m] = cmul(a[m], P[m]);
     }
     if constexpr (NV == 2) {
         if (OPS && X.first && A.pre_lambda) {  // lambda = O phi, from the stored final state
             R ov[NR];
-            cut_real<G, R, ST>(tc1, pt1, X.qr + 32, X.qrf + 32, X.tid, ov);
+            values(1, ov);
 #pragma unroll
             for (int m = 0; m < NR; m++)
                 l[m] = mkc<C>(a[m].x * ov[m], a[m].y * ov[m]);
         }
     }
 
-    mix_regs<R, NV, ST>(A, X.cb, X.tq, X.f, X.run, a, l, acc0);
+    mix_regs<R, NV, ST, IS>(A, X.cb, X.tq, X.f, X.run, a, l, acc0, X.cot);
 
     if (OPS && LAST && (A.post & POST_RESCALE)) {  // the stored state is the exact one
 #pragma unroll
@@ -812,7 +953,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
 
     if (OPS && LAST && (A.post & POST_REDUCE)) {
         R ov[NR];
-        cut_real<G, R, ST>(tc1, pt1, X.qr + 32, X.qrf + 32, X.tid, ov);
+        values(1, ov);
         R e = 0;
 #pragma unroll
         for (int m = 0; m < NR; m++)
@@ -823,7 +964,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         if (OPS && LAST && (A.post & (POST_GAMMA | POST_PHASE_CONJ))) {
             if (A.post & POST_GAMMA) {
                 R cr[NR];
-                cut_real<G, R, ST>(tc0, pt0, X.qr, X.qrf, X.tid, cr);
+                values(0, cr);
                 R g = 0;
 #pragma unroll
                 for (int m = 0; m < NR; m++)
@@ -831,28 +972,27 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
                 acc1.add(g * X.fn2);  // both vectors carry 1/f^n here
             }
             if (A.post & POST_PHASE_CONJ) {  // inverse cost layer, restoring f^n
-                int cv[NR];
-                cut_int<G, ST>(tc0, pt0, X.qr, X.tid, cv);
+                C P[NR];
+                phases(P);
 #pragma unroll
                 for (int m = 0; m < NR; m++) {
-                    const C t = X.tab[cv[m]];
-                    a[m] = cmul(a[m], t);
-                    l[m] = cmul(l[m], t);
+                    a[m] = cmul(a[m], P[m]);
+                    l[m] = cmul(l[m], P[m]);
                 }
             }
         }
     }
     if constexpr (NV == 1) {
         if (OPS && LAST && (A.post & POST_PHASE)) {  // the next layer's cost phase
-            int cv[NR];
-            cut_int<G, ST>(tc0, pt0, X.qr, X.tid, cv);
+            C P[NR];
+            phases(P);
 #pragma unroll
             for (int m = 0; m < NR; m++)
-                a[m] = cmul(a[m], X.tab[cv[m]]);
+                a[m] = cmul(a[m], P[m]);
         }
     }
     if constexpr (FUSE && LAST)
-        mix_regs<R, NV, ST>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2);
+        mix_regs<R, NV, ST, IS>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2, X.cot2);
     if (!LAST || A.write) {
         store_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
@@ -861,19 +1001,18 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
 }
 
 // A stage of the second layer of a fused pass: load, its butterflies, store.
-template <typename R, int NV, int ST>
+template <typename R, int NV, int ST, bool IS = false>
 __device__ __forceinline__ void mix_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                           typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc2)
 {
     using G = Geo<R, NV>;
-    constexpr int NTB = G::T - G::RB;
     const uint32_t base = stage_base<G, ST>((uint32_t)X.tid);
     const uint32_t sb = G::swz(base);
     load_regs<R, NV, ST>(X.sv0, sb, a);
     if constexpr (NV == 2)
         load_regs<R, NV, ST>(X.sv1, sb, l);
-    mix_regs<R, NV, ST>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2);
+    mix_regs<R, NV, ST, IS>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2, X.cot2);
     store_regs<R, NV, ST>(X.sv0, sb, a);
     if constexpr (NV == 2)
         store_regs<R, NV, ST>(X.sv1, sb, l);
@@ -993,7 +1132,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     k_pass(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
            const __grid_constant__ PassArgs A)
 {
-    constexpr bool OPS = MODE != 0, MG = MODE == 2, FUSE = MODE == 3;
+    constexpr bool OPS = MODE != 0, MG = MODE == 2, FUSE = MODE == 3 || MODE == 5, IS = MODE >= 4;
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
     constexpr int NR = 1 << G::RB, NS = G::NSTAGE, NTHR = G::NTHR;
@@ -1006,15 +1145,24 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     __shared__ double pred[2][3][32];  // per-warp sums of a finished point, two buffers
     __shared__ int s_flag;
     __shared__ int obs_w[MAXK], cost_w[MAXK];
-    __shared__ int tcs[NS][2][16];                  // per buffer: O(f) and h_u(f) of its tile
-    __shared__ int ptc[2 * (G::RB + 1) * NTHR];     // per thread: t-only terms of each function
-    __shared__ int qr[2][2][32];                    // [slot][function]: register-pair terms
+    __shared__ int tcs[IS ? 1 : NS][2][16];              // per buffer: O(f) and h_u(f) of its tile
+    __shared__ int ptc[IS ? 1 : 2 * (G::RB + 1) * NTHR];  // per thread: t-only terms of each function
+    __shared__ int qr[2][2][32];                         // [slot][function]: register-pair terms
     __shared__ float qrf[2][2][32];
+    // Ising plans: tile values and cost phases per buffer, stage terms (the
+    // per-thread terms live in the dynamic region after the tiles)
+    __shared__ R tvs[IS ? NS : 1][2][16];
+    __shared__ C tps[IS ? NS : 1][16];
+    __shared__ R qvs[IS ? 2 : 1][32];
+    __shared__ C qps[IS ? 2 : 1][32];
 
     const int tid = threadIdx.x;
     C *tab = reinterpret_cast<C *>(sm + (size_t)NS * NV * TB);
     uint64_t *cost_nbr = reinterpret_cast<uint64_t *>(tab + 2 * MAXTAB);  // two table slots
     uint64_t *obs_nbr = cost_nbr + MAXK * MAXN;
+    // Ising plans reuse that region: per-thread values [2][RB+1][NTHR] and cost phases [RB+1][NTHR]
+    R *ptv = reinterpret_cast<R *>(sm + (size_t)NS * NV * TB);
+    C *ptp = reinterpret_cast<C *>(ptv + 2 * (G::RB + 1) * NTHR);
 
     const unsigned total = (unsigned)A.tiles * (unsigned)A.B;
     const unsigned grid = gridDim.x;
@@ -1033,13 +1181,15 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         }
         fence_barrier_init();
     }
-    for (int i = tid; i < A.cost.K * MAXN; i += blockDim.x)
-        cost_nbr[i] = A.cost.nbr[i / MAXN][i % MAXN];
-    for (int i = tid; i < A.obs.K * MAXN; i += blockDim.x)
-        obs_nbr[i] = A.obs.nbr[i / MAXN][i % MAXN];
-    if (tid < MAXK) {
-        obs_w[tid] = A.obs.w[tid];
-        cost_w[tid] = A.cost.w[tid];
+    if constexpr (!IS) {
+        for (int i = tid; i < A.cost.K * MAXN; i += blockDim.x)
+            cost_nbr[i] = A.cost.nbr[i / MAXN][i % MAXN];
+        for (int i = tid; i < A.obs.K * MAXN; i += blockDim.x)
+            obs_nbr[i] = A.obs.nbr[i / MAXN][i % MAXN];
+        if (tid < MAXK) {
+            obs_w[tid] = A.obs.w[tid];
+            cost_w[tid] = A.cost.w[tid];
+        }
     }
     __syncthreads();
     if (s_flag)
@@ -1122,8 +1272,53 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             }
         }
     };
-    if (tid < NTHR && !MG && (est[0] >= 0 || est[1] >= 0))
+    // Ising plans: the real couplings of function e between vertices u and v
+    auto ising_fn = [&](int e) -> const IsingFn * { return e == 0 ? A.icost : A.iobs; };
+    // this thread's terms of function e in stage st, in FP64: thread-bit
+    // pairs (q), register bit k with the thread bits (dk), and for tid < 2^RB
+    // the register-bit pairs of subset tid (qq)
+    auto ising_terms = [&](int e, int st, double &q, double (&dk)[G::RB], double &qq) {
+        constexpr int RB = G::RB, NTB = G::T - G::RB;
+        const IsingFn *F = ising_fn(e);
+        q = 0.0;
+        for (int j = 0; j < NTB; j++)
+            for (int j2 = 0; j2 < j; j2++)
+                if (((tid >> j) & 1) && ((tid >> j2) & 1))
+                    q -= 2.0 * F->W[gq(G::thr(st, j))][gq(G::thr(st, j2))];
+        for (int kk = 0; kk < RB; kk++) {
+            dk[kk] = 0.0;
+            for (int j = 0; j < NTB; j++)
+                if ((tid >> j) & 1)
+                    dk[kk] -= 2.0 * F->W[gq(G::reg(st, kk))][gq(G::thr(st, j))];
+        }
+        qq = 0.0;
+        if (tid < (1 << RB))
+            for (int kk = 0; kk < RB; kk++)
+                for (int k2 = 0; k2 < kk; k2++)
+                    if (((tid >> kk) & 1) && ((tid >> k2) & 1))
+                        qq -= 2.0 * F->W[gq(G::reg(st, kk))][gq(G::reg(st, k2))];
+    };
+    // the cost layer's phase angle per unit of the cost function for point b:
+    // -gamma forward (exp(-i gamma C)), +gamma for the inverse layer
+    auto ising_angle = [&](unsigned b) { return -A.sign_s * A.gam[(size_t)b * A.p + A.tab_layer]; };
+    const bool cost_phase = A.pre_phase || (A.post & (POST_PHASE | POST_PHASE_CONJ));
+    if constexpr (IS) {
+        if (tid < NTHR) {
+            for (int e = 0; e < 2; e++) {
+                if (est[e] < 0)
+                    continue;
+                double q, dk[G::RB], qq;
+                ising_terms(e, est[e], q, dk, qq);
+                ptv[(e * (G::RB + 1)) * NTHR + tid] = (R)q;
+                for (int kk = 0; kk < G::RB; kk++)
+                    ptv[(e * (G::RB + 1) + 1 + kk) * NTHR + tid] = (R)dk[kk];
+                if (tid < (1 << G::RB))
+                    qvs[e][tid] = (R)qq;
+            }
+        }
+    } else if (tid < NTHR && !MG && (est[0] >= 0 || est[1] >= 0)) {
         launch_consts(0);
+    }
 
     const int tiles_log2 = __ffs(A.tiles) - 1;  // tiles per state: a power of two
     auto tile_coords = [&](unsigned k, unsigned &b, unsigned &t, unsigned &mid, int &c4) {
@@ -1141,9 +1336,62 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         // warp computes each tile's cut constants O(f), h_u(f) before the
         // tile's buffer is handed over (the arrive on full[s] releases them).
         const int lane = tid - NTHR;
+        // Ising plans: O(f) and h_L(f) in FP64 (lanes over vertices), rounded
+        // once to R, and for the cost the unit phase factors of this tile's
+        // point (O(f)'s carrying the table's scale f^n)
+        auto tile_consts_ising = [&](unsigned k, int s) {
+            unsigned b, t, mid;
+            int c4;
+            tile_coords(k, b, t, mid, c4);
+            const uint64_t f = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
+            for (int e = 0; e < 2; e++) {
+                if (est[e] < 0)
+                    continue;
+                const IsingFn *F = ising_fn(e);
+                double os = 0.0;
+                for (int u = lane; u < A.n; u += 32) {
+                    const bool fu = (f >> u) & 1ull;
+                    double su = fu ? F->h[u] : 0.0;
+                    for (int v = u + 1; v < A.n; v++)
+                        if ((bool)((f >> v) & 1ull) != fu)
+                            su += F->W[u][v];
+                    os += su;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    os += __shfl_xor_sync(0xffffffffu, os, o);
+                double hs = 0.0;
+                if (lane < G::T) {
+                    const int u = gq(lane);
+                    hs = F->h[u];
+                    for (int v = 0; v < A.n; v++)
+                        if (v != u)
+                            hs += ((f >> v) & 1ull) ? -F->W[u][v] : F->W[u][v];
+                    tvs[s][e][lane] = (R)hs;
+                }
+                if (lane == 0)
+                    tvs[s][e][15] = (R)os;
+                if (e == 0 && cost_phase) {
+                    const double ang = ising_angle(b);
+                    if (lane < G::T)
+                        tps[s][lane] = unit_phase<R>(ang * hs);
+                    if (lane == 0) {
+                        const C sc = reinterpret_cast<const C *>(A.tab)[(size_t)b * A.p + A.tab_layer];
+                        C z = unit_phase<R>(ang * os);
+                        z.x *= sc.x;
+                        z.y *= sc.x;
+                        tps[s][15] = z;
+                    }
+                }
+            }
+        };
         auto tile_consts = [&](unsigned k, int s) {
             if (est[0] < 0 && est[1] < 0)
                 return;
+            if constexpr (IS) {
+                tile_consts_ising(k, s);
+                return;
+            }
             unsigned b, t, mid;
             int c4;
             tile_coords(k, b, t, mid, c4);
@@ -1258,6 +1506,11 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         X.ptc = ptc;
         X.qr = &qr[0][0][0];
         X.qrf = &qrf[0][0][0];
+        X.ptv = ptv;
+        X.ptp = ptp;
+        X.qv = &qvs[0][0];
+        X.qp = &qps[0][0];
+        X.cot = X.cot2 = false;
         X.s = A.s;
         X.cb = cb;
         X.tid = tid;
@@ -1331,7 +1584,21 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                         X.qrf = &qrf[tslot][0][0];
                     }
                 }
-                if (A.pre_phase || (A.post & (POST_PHASE_CONJ | POST_PHASE))) {
+                if constexpr (IS) {
+                    // this point's cost phases of the thread's and the stage's terms
+                    // (each thread writes and reads only its own per-thread entries)
+                    if (cost_phase && est[0] >= 0) {
+                        const double ang = ising_angle(b);
+                        double q, dk[G::RB], qq;
+                        ising_terms(0, est[0], q, dk, qq);
+                        ptp[tid] = unit_phase<R>(ang * q);
+                        for (int kk = 0; kk < G::RB; kk++)
+                            ptp[(1 + kk) * NTHR + tid] = unit_phase<R>(ang * dk[kk]);
+                        if (tid < (1 << G::RB))
+                            qps[tslot][tid] = unit_phase<R>(ang * qq);
+                    }
+                    X.qp = &qps[tslot][0];
+                } else if (A.pre_phase || (A.post & (POST_PHASE_CONJ | POST_PHASE))) {
                     const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.tab_layer) * A.tab_len;
                     C *dst = tab + tslot * MAXTAB;
                     for (int i = tid; i < A.tab_len; i += NTHR)
@@ -1339,8 +1606,9 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 }
                 const double2 csd = A.cs[(size_t)b * A.p + A.layer];
                 const double cbv = csd.x, sbv = A.sign_s * csd.y;
-                const bool shifted = fabs(sbv) > fabs(cbv);  // rotate by beta - pi/2
-                X.tq = shifted ? (R)(-cbv / sbv) : (R)(sbv / cbv);
+                const bool shifted = fabs(sbv) > fabs(cbv);  // rotate by beta - pi/2 (Ising: cot form)
+                X.cot = IS && shifted;
+                X.tq = shifted ? (R)((IS ? cbv : -cbv) / sbv) : (R)(sbv / cbv);
                 const double f = shifted ? sbv : cbv;
                 double fj = 1.0, fn = 1.0;
                 for (int i = 0; i < A.n; i++) {
@@ -1356,14 +1624,17 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                     const double2 cs2 = A.cs[(size_t)b * A.p + A.layer2];
                     const double c2 = cs2.x, s2 = A.sign_s * cs2.y;
                     const bool sh2 = fabs(s2) > fabs(c2);
-                    X.tq2 = sh2 ? (R)(-c2 / s2) : (R)(s2 / c2);
+                    X.cot2 = IS && sh2;
+                    X.tq2 = sh2 ? (R)((IS ? c2 : -c2) / s2) : (R)(s2 / c2);
                     X.f2 = (R)(sh2 ? s2 : c2);
                 }
                 cur_b = (int)b;
             }
             X.sv0 = reinterpret_cast<C *>(buf);
             X.sv1 = reinterpret_cast<C *>(buf + TB);
-            X.tc = &tcs[s][0][0];
+            X.tc = &tcs[IS ? 0 : s][0][0];
+            X.tv = &tvs[IS ? s : 0][0][0];
+            X.tp = &tps[IS ? s : 0][0];
             X.fixed = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
 
             // No barrier between tiles unless a point starts: a warp may begin
@@ -1382,16 +1653,16 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             bool bad;
             X.run2 = (R)1;
             if (!FUSE && P.is_low) {
-                run_stage<R, NV, 0, OPS>(P, X, a, l, acc0, acc1, acc2);
+                run_stage<R, NV, 0, OPS, false, IS>(P, X, a, l, acc0, acc1, acc2);
                 X.first = false;
                 bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
                 if (!bad) {
-                    run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1, acc2);
+                    run_stage<R, NV, 1, OPS, false, IS>(P, X, a, l, acc0, acc1, acc2);
                     if (!P.skip_last)
                         compute_sync<NTHR>();
                 }
             } else {  // a high pass (every fused pass is one)
-                run_stage<R, NV, 1, OPS>(P, X, a, l, acc0, acc1, acc2);
+                run_stage<R, NV, 1, OPS, false, IS>(P, X, a, l, acc0, acc1, acc2);
                 X.first = false;
                 bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
             }
@@ -1404,11 +1675,11 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 break;
             }
             if (FUSE) {  // layer `layer` ends in stage 2, layer2 starts there and ends in stage 1
-                run_stage<R, NV, 2, OPS, true>(P, X, a, l, acc0, acc1, acc2);
+                run_stage<R, NV, 2, OPS, true, IS>(P, X, a, l, acc0, acc1, acc2);
                 compute_sync<NTHR>();
-                mix_stage<R, NV, 1>(P, X, a, l, acc2);
+                mix_stage<R, NV, 1, IS>(P, X, a, l, acc2);
             } else if (!P.skip_last) {  // a low pass over the qubits of stages 0 and 1 only ends here
-                run_stage<R, NV, 2, OPS>(P, X, a, l, acc0, acc1, acc2);
+                run_stage<R, NV, 2, OPS, false, IS>(P, X, a, l, acc0, acc1, acc2);
             }
             // results (if any) are in the buffer: hand it to the producer
             fence_proxy_async_smem();
@@ -1503,6 +1774,21 @@ __device__ __forceinline__ int cut_direct(const CutFn &f, int n, uint32_t x)
     return v;
 }
 
+// O(x) of an Ising function, term by term in FP64
+__device__ __forceinline__ double ising_direct(const IsingFn *F, int n, uint32_t x)
+{
+    double v = 0.0;
+    for (int u = 0; u < n; u++) {
+        const bool xu = (x >> u) & 1u;
+        if (xu)
+            v += F->h[u];
+        for (int w = u + 1; w < n; w++)
+            if ((bool)((x >> w) & 1u) != xu)
+                v += F->W[u][w];
+    }
+    return v;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallArgs A)
 {
@@ -1514,19 +1800,37 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallArgs
     C *phi = reinterpret_cast<C *>(smem_raw);
     C *lam = phi + N;
     C *tab = phi + (A.mode == SMALL_GRAD ? 2 * N : N);
+    // Ising plans: C(x) in FP64 for every basis state (after the table slot)
+    const bool ising = A.icost != nullptr;
+    double *cx = reinterpret_cast<double *>(tab + MAXTAB);
+    auto cost_value = [&](int x) -> double { return ising ? cx[x] : (double)cut_direct(A.cost, n, (uint32_t)x); };
+    auto obs_value = [&](int x) -> R {
+        return ising ? (R)ising_direct(A.iobs, n, (uint32_t)x) : (R)cut_direct(A.obs, n, (uint32_t)x);
+    };
 
+    if (ising)
+        for (int x = tid; x < N; x += NT)
+            cx[x] = ising_direct(A.icost, n, (uint32_t)x);
     for (int x = tid; x < N; x += NT)
         phi[x] = mkc<C>((R)A.amp0, (R)0);
     for (int l = 0; l < A.p; l++) {
         __syncthreads();
-        const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + l) * A.tab_len;
-        for (int i = tid; i < A.tab_len; i += NT)
-            tab[i] = src[i];
+        if (!ising) {
+            const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + l) * A.tab_len;
+            for (int i = tid; i < A.tab_len; i += NT)
+                tab[i] = src[i];
+        }
         const double2 cs = A.cs[(size_t)b * A.p + l];
         const R c = (R)cs.x, s = (R)cs.y;
         __syncthreads();
-        for (int x = tid; x < N; x += NT)
-            phi[x] = cmul(phi[x], tab[cut_direct(A.cost, n, (uint32_t)x)]);
+        if (ising) {  // exp(-i gamma_l C(x)), the angle in FP64
+            const double gl = A.gam[(size_t)b * A.p + l];
+            for (int x = tid; x < N; x += NT)
+                phi[x] = cmul(phi[x], unit_phase<R>(-gl * cx[x]));
+        } else {
+            for (int x = tid; x < N; x += NT)
+                phi[x] = cmul(phi[x], tab[cut_direct(A.cost, n, (uint32_t)x)]);
+        }
         for (int q = 0; q < n; q++) {
             __syncthreads();
             for (int j = tid; j < half; j += NT) {
@@ -1543,7 +1847,7 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallArgs
     }
     double e = 0.0, dummy = 0.0;
     for (int x = tid; x < N; x += NT)
-        e += (double)((phi[x].x * phi[x].x + phi[x].y * phi[x].y) * (R)cut_direct(A.obs, n, (uint32_t)x));
+        e += (double)((phi[x].x * phi[x].x + phi[x].y * phi[x].y) * obs_value(x));
     block_sum2<NT>(e, dummy, red);
     if (tid == 0)
         A.out[(size_t)b * A.out_stride] = e;
@@ -1551,7 +1855,7 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallArgs
         return;
 
     for (int x = tid; x < N; x += NT) {
-        const R o = (R)cut_direct(A.obs, n, (uint32_t)x);
+        const R o = obs_value(x);
         lam[x] = mkc<C>(phi[x].x * o, phi[x].y * o);
     }
     for (int l = A.p - 1; l >= 0; l--) {
@@ -1569,17 +1873,18 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallArgs
             }
         }
         __syncthreads();
-        if (l > 0) {
+        if (l > 0 && !ising) {
             const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + l) * A.tab_len;
             for (int i = tid; i < A.tab_len; i += NT)
                 tab[i] = src[i];
         }
         __syncthreads();
+        const double gl = ising ? A.gam[(size_t)b * A.p + l] : 0.0;
         for (int x = tid; x < N; x += NT) {
-            const int cv = cut_direct(A.cost, n, (uint32_t)x);
+            const double cv = cost_value(x);
             gg += (double)((R)cv * im_conj_mul(lam[x], phi[x]));
             if (l > 0) {
-                const C t = tab[cv];
+                const C t = ising ? unit_phase<R>(-gl * cv) : tab[(int)cv];
                 phi[x] = cmul_conj(phi[x], t);
                 lam[x] = cmul_conj(lam[x], t);
             }
@@ -1934,7 +2239,7 @@ template <typename R, int NV, int MODE>
 static int launch_pass_ops(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
                            cudaStream_t st)
 {
-    const size_t smem = pass_smem_total<R, NV>();
+    const size_t smem = pass_smem_total<R, NV, (MODE >= 4)>();
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e =
@@ -1956,6 +2261,13 @@ static int launch_pass_t(const CUtensorMap &m0, const CUtensorMap &m1, const Pas
     if (a.tiles < 1 || (a.tiles & (a.tiles - 1)))  // the kernel splits tile indices with shifts
         return (int)cudaErrorInvalidValue;
     const bool ops = a.pre_phase || a.pre_lambda || a.post || a.fuse;
+    if (a.icost) {  // Ising plan: every pass (its layers may use the cot form)
+        if (!a.iobs || !a.gam || a.pt)
+            return (int)cudaErrorInvalidValue;
+        if (a.fuse)
+            return a.is_low ? (int)cudaErrorInvalidValue : launch_pass_ops<R, NV, 5>(m0, m1, a, grid, st);
+        return launch_pass_ops<R, NV, 4>(m0, m1, a, grid, st);
+    }
     if (!ops)
         return launch_pass_ops<R, NV, 0>(m0, m1, a, grid, st);
     if (a.fuse)
@@ -1973,24 +2285,26 @@ int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorM
                           : launch_pass_t<float, 1>(m0, m1, a, grid, st);
 }
 
-size_t small_smem_bytes(bool c128, int n, int mode)
+size_t small_smem_bytes(bool c128, int n, int mode, bool ising)
 {
     const size_t amp = c128 ? 16 : 8;
-    return ((mode == SMALL_GRAD ? 2 : 1) * ((size_t)1 << n) + MAXTAB) * amp;
+    return ((mode == SMALL_GRAD ? 2 : 1) * ((size_t)1 << n) + MAXTAB) * amp + (ising ? ((size_t)1 << n) * 8 : 0);
 }
 
 int small_max_qubits(bool c128, int mode)
 {
     // largest n whose state(s) plus the phase table fit the opt-in shared memory
     int n = 1;
-    while (n < 20 && small_smem_bytes(c128, n + 1, mode) <= 200 * 1024)
+    while (n < 20 && small_smem_bytes(c128, n + 1, mode, false) <= 200 * 1024)
         n++;
     return n;
 }
 
 int launch_small(bool c128, const SmallArgs &a, int B, cudaStream_t st)
 {
-    const size_t smem = small_smem_bytes(c128, a.n, a.mode);
+    const size_t smem = small_smem_bytes(c128, a.n, a.mode, a.icost != nullptr);
+    if (smem > 227 * 1024)
+        return (int)cudaErrorInvalidValue;
     cudaError_t e;
     if (c128) {
         e = cudaFuncSetAttribute(k_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2013,12 +2327,13 @@ int launch_small(bool c128, const SmallArgs &a, int B, cudaStream_t st)
 //   psi = (-i)^(n K) (X^n)^K psi',
 // so psi(x) = (-i)^(nK) i^(-|y|) psi~(y), y = x with all bits flipped when K
 // is odd, else y = x. In place; for odd K each thread handles a pair (x, ~x).
+// Ising plans never rotate by beta_l - pi/2 (noshift): K = 0.
 template <typename R>
-__global__ void k_untwist(typename CT<R>::T *psi, int n, const double2 *cs, int p)
+__global__ void k_untwist(typename CT<R>::T *psi, int n, const double2 *cs, int p, int noshift)
 {
     using C = typename CT<R>::T;
     int K = 0;
-    for (int l = 0; l < p; l++)
+    for (int l = 0; l < p && !noshift; l++)
         K += fabs(cs[l].y) > fabs(cs[l].x) ? 1 : 0;
     const int ph = (4 - ((n * K) & 3)) & 3;  // (-i)^(nK) = i^ph
     auto turn = [](C v, int e) -> C {          // v * i^e
@@ -2251,13 +2566,13 @@ int launch_sample(bool c128, const void *psi, int n, double *d_sums, double *d_t
     return (int)cudaGetLastError();
 }
 
-int launch_untwist(bool c128, void *psi, int n, const double2 *cs, int p, cudaStream_t st)
+int launch_untwist(bool c128, void *psi, int n, const double2 *cs, int p, int noshift, cudaStream_t st)
 {
     const int grid = 4 * device_sms();
     if (c128)
-        k_untwist<double><<<grid, 256, 0, st>>>((double2 *)psi, n, cs, p);
+        k_untwist<double><<<grid, 256, 0, st>>>((double2 *)psi, n, cs, p, noshift);
     else
-        k_untwist<float><<<grid, 256, 0, st>>>((float2 *)psi, n, cs, p);
+        k_untwist<float><<<grid, 256, 0, st>>>((float2 *)psi, n, cs, p, noshift);
     return (int)cudaGetLastError();
 }
 

@@ -41,6 +41,7 @@ struct G {
     std::vector<uint64_t> nb;          // neighbour masks (n <= 64)
     bool weighted = false;
     std::map<std::pair<int, int>, int> w;  // edge (u < v) -> weight
+    Col init;  // initial vertex colours (vertex fields ranked), or empty for one colour
 };
 
 Col rank_keys(const std::vector<std::vector<int>> &keys)
@@ -135,6 +136,10 @@ bool is_automorphism(const G &g, const std::vector<int> &perm)
             if (g.w.at({std::min(a, b), std::max(a, b)}) != kv.second)
                 return false;
         }
+    if (!g.init.empty())
+        for (int u = 0; u < g.n; u++)
+            if (g.init[perm[u]] != g.init[u])
+                return false;
     return true;
 }
 
@@ -201,7 +206,7 @@ std::vector<std::vector<int>> generators(const G &g)
     std::vector<std::vector<int>> gens;
     if (g.n == 0)
         return gens;
-    Col col = refine(g, Col(g.n, 0));
+    Col col = refine(g, g.init.empty() ? Col(g.n, 0) : g.init);
     struct Level {
         Col col;
         std::vector<int> cell;
@@ -233,6 +238,45 @@ std::vector<std::vector<int>> generators(const G &g)
         }
     }
     return gens;
+}
+
+// Edge orbits of the group the generators span (Sec. 4, Algorithm 1): a
+// breadth-first closure of each unclassified seed edge, in the given edge
+// order. Returns the number of classes.
+int edge_closure(const std::vector<std::vector<int>> &gens, int num_edges, const int32_t *edges,
+                 const std::map<std::pair<int, int>, int> &index, int32_t *edge_orbit, int32_t *orbit_rep,
+                 int32_t *orbit_weight)
+{
+    std::vector<int> cls(num_edges, -1);
+    int classes = 0;
+    for (int seed = 0; seed < num_edges; seed++) {
+        if (cls[seed] >= 0)
+            continue;
+        const int c = classes++;
+        cls[seed] = c;
+        orbit_rep[c] = seed;
+        int size = 1;
+        std::deque<std::pair<int, int>> q;
+        int su = edges[2 * seed], sv = edges[2 * seed + 1];
+        q.push_back({std::min(su, sv), std::max(su, sv)});
+        while (!q.empty()) {
+            const auto e = q.front();
+            q.pop_front();
+            for (auto &gp : gens) {
+                const int a = gp[e.first], b = gp[e.second];
+                auto it = index.find({std::min(a, b), std::max(a, b)});
+                if (it != index.end() && cls[it->second] < 0) {
+                    cls[it->second] = c;
+                    size++;
+                    q.push_back(it->first);
+                }
+            }
+        }
+        orbit_weight[c] = size;
+    }
+    for (int i = 0; i < num_edges; i++)
+        edge_orbit[i] = cls[i];
+    return classes;
 }
 
 }  // namespace
@@ -270,37 +314,79 @@ extern "C" int aaqaoa_edge_orbits(int n, int num_edges, const int32_t *edges, co
         g.nb[v] |= 1ull << u;
     }
     const std::vector<std::vector<int>> gens = generators(g);
-    // edge orbits of the generated group (Sec. 4, Algorithm 1): breadth-first
-    // closure of each unclassified seed edge
-    std::vector<int> cls(num_edges, -1);
-    int classes = 0;
-    for (int seed = 0; seed < num_edges; seed++) {
-        if (cls[seed] >= 0)
-            continue;
-        const int c = classes++;
-        cls[seed] = c;
-        orbit_rep[c] = seed;
-        int size = 1;
-        std::deque<std::pair<int, int>> q;
-        int su = edges[2 * seed], sv = edges[2 * seed + 1];
-        q.push_back({std::min(su, sv), std::max(su, sv)});
-        while (!q.empty()) {
-            const auto e = q.front();
-            q.pop_front();
-            for (auto &gp : gens) {
-                const int a = gp[e.first], b = gp[e.second];
-                auto it = index.find({std::min(a, b), std::max(a, b)});
-                if (it != index.end() && cls[it->second] < 0) {
-                    cls[it->second] = c;
-                    size++;
-                    q.push_back(it->first);
-                }
-            }
-        }
-        orbit_weight[c] = size;
+    *num_orbits = edge_closure(gens, num_edges, edges, index, edge_orbit, orbit_rep, orbit_weight);
+    return AAQAOA_OK;
+}
+
+// Ising-form objectives: the same search with the distinct real couplings as
+// edge-weight classes and the distinct fields as initial vertex colours, so
+// only automorphisms that keep both are found; vertex orbits are numbered by
+// their smallest vertex.
+extern "C" int aaqaoa_ising_orbits(int n, int num_edges, const int32_t *edges, const double *edge_weight,
+                                   const double *field, int32_t *edge_orbit, int32_t *num_orbits, int32_t *orbit_rep,
+                                   int32_t *orbit_weight, int32_t *vertex_orbit, int32_t *num_vorbits,
+                                   int32_t *vorbit_rep, int32_t *vorbit_weight)
+{
+    if (n < 1 || n > 64 || num_edges < 0 || (num_edges > 0 && (!edges || !edge_weight)) || !num_orbits ||
+        (num_edges > 0 && (!edge_orbit || !orbit_rep || !orbit_weight)) || !vertex_orbit || !num_vorbits ||
+        !vorbit_rep || !vorbit_weight)
+        return AAQAOA_ERR_INVALID_ARG;
+    std::vector<double> wv(edge_weight, edge_weight + num_edges);
+    std::vector<double> distinct = wv;
+    std::sort(distinct.begin(), distinct.end());
+    distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
+    G g;
+    g.n = n;
+    g.adj.assign(n, {});
+    g.wt.assign(n, {});
+    g.nb.assign(n, 0);
+    g.weighted = true;
+    std::map<std::pair<int, int>, int> index;
+    for (int i = 0; i < num_edges; i++) {
+        int u = edges[2 * i], v = edges[2 * i + 1];
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v || !(wv[i] == wv[i]))
+            return AAQAOA_ERR_INVALID_ARG;
+        if (u > v)
+            std::swap(u, v);
+        if (!index.emplace(std::make_pair(u, v), i).second)
+            return AAQAOA_ERR_INVALID_ARG;
+        const int wi = 1 + (int)(std::lower_bound(distinct.begin(), distinct.end(), wv[i]) - distinct.begin());
+        g.w[{u, v}] = wi;
+        g.adj[u].push_back(v);
+        g.adj[v].push_back(u);
+        g.wt[u].push_back(wi);
+        g.wt[v].push_back(wi);
+        g.nb[u] |= 1ull << v;
+        g.nb[v] |= 1ull << u;
     }
-    for (int i = 0; i < num_edges; i++)
-        edge_orbit[i] = cls[i];
-    *num_orbits = classes;
+    if (field) {
+        std::vector<std::vector<int>> keys(n);
+        std::vector<double> hv(field, field + n), hd = hv;
+        std::sort(hd.begin(), hd.end());
+        hd.erase(std::unique(hd.begin(), hd.end()), hd.end());
+        for (int u = 0; u < n; u++) {
+            if (!(hv[u] == hv[u]))
+                return AAQAOA_ERR_INVALID_ARG;
+            keys[u] = {(int)(std::lower_bound(hd.begin(), hd.end(), hv[u]) - hd.begin())};
+        }
+        g.init = rank_keys(keys);
+    }
+    const std::vector<std::vector<int>> gens = generators(g);
+    *num_orbits = edge_closure(gens, num_edges, edges, index, edge_orbit, orbit_rep, orbit_weight);
+    const std::vector<int> root = orbit_ids(n, gens);
+    std::map<int, int> cls;  // root -> class, in order of smallest member
+    int k = 0;
+    for (int u = 0; u < n; u++) {
+        auto it = cls.find(root[u]);
+        if (it == cls.end()) {
+            it = cls.emplace(root[u], k).first;
+            vorbit_rep[k] = u;
+            vorbit_weight[k] = 0;
+            k++;
+        }
+        vertex_orbit[u] = it->second;
+        vorbit_weight[it->second]++;
+    }
+    *num_vorbits = k;
     return AAQAOA_OK;
 }

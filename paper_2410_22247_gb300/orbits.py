@@ -117,15 +117,17 @@ def _orbit_ids(n, gens):
     return [find(a) for a in range(n)]
 
 
-def automorphism_generators(n, edges, weights=None):
+def automorphism_generators(n, edges, weights=None, fields=None):
     """A generating set of Aut(G) as a list of permutations (lists of length n);
-    with integer edge weights, of the weight-preserving automorphisms."""
+    with edge weights (integer or real), of the weight-preserving
+    automorphisms; with vertex fields, of those that also map every vertex to
+    one of equal field (the fields colour the initial partition)."""
     edges = [tuple(map(int, e)) for e in np.asarray(edges).reshape(-1, 2)]
     if weights is None:
         edge_set = {(min(u, v), max(u, v)) for u, v in edges}
         wadj = None
     else:
-        wl = [int(w) for w in np.asarray(weights).reshape(-1)]
+        wl = [float(w) for w in np.asarray(weights).reshape(-1)]
         edge_set = {(min(u, v), max(u, v)): w for (u, v), w in zip(edges, wl)}
         wadj = [[] for _ in range(n)]
         for (u, v), w in zip(edges, wl):
@@ -134,7 +136,12 @@ def automorphism_generators(n, edges, weights=None):
     adj = _adjacency(n, edges)
     if n == 0:
         return []
-    col = _refine(adj, [0] * n, wadj)
+    hl = None if fields is None else [float(h) for h in np.asarray(fields).reshape(-1)]
+
+    def is_aut(g):
+        return is_automorphism(g, edge_set) and (hl is None or all(hl[g[u]] == hl[u] for u in range(n)))
+
+    col = _refine(adj, [0] * n if hl is None else _rank(hl), wadj)
     path = []
     while True:
         cell = _target_cell(col)
@@ -162,7 +169,7 @@ def automorphism_generators(n, edges, weights=None):
         cell = _target_cell(col)
         if cell is None:
             g = leaf_map(col)
-            return g if is_automorphism(g, edge_set) else None
+            return g if is_aut(g) else None
         for x in cell:
             r = search(_individualise(adj, col, x, wadj), depth + 1)
             if r is not None:
@@ -180,7 +187,7 @@ def automorphism_generators(n, edges, weights=None):
                 continue
             g = search(_individualise(adj, col_k, w, wadj), level + 1)
             if g is not None:
-                assert is_automorphism(g, edge_set)
+                assert is_aut(g)
                 gens.append(g)
     return gens
 
@@ -239,6 +246,39 @@ def edge_orbits(n, edges, generators=None, weights=None) -> EdgeOrbits:
                       np.asarray(weights, dtype=np.int32), generators)
 
 
+@dataclass
+class IsingOrbits(EdgeOrbits):
+    """Edge classes plus vertex classes of the automorphisms that preserve the
+    couplings and the fields: ``vertex_orbit[u]`` is the class of vertex u,
+    ``vrep[c]`` its smallest vertex, ``vweight[c]`` the class size."""
+    vertex_orbit: np.ndarray = None
+    vrep: np.ndarray = None
+    vweight: np.ndarray = None
+
+
+def vertex_classes(n, generators):
+    """Orbits of the generated group on vertices, numbered by smallest member."""
+    root = _orbit_ids(n, generators)
+    first = {}
+    for u in range(n):
+        first.setdefault(root[u], u)
+    reps = sorted(first.values())
+    index = {root[r]: c for c, r in enumerate(reps)}
+    vo = np.array([index[root[u]] for u in range(n)], dtype=np.int32)
+    vw = np.bincount(vo, minlength=len(reps)).astype(np.int32)
+    return vo, np.asarray(reps, dtype=np.int32), vw
+
+
+def ising_orbits(n, edges, couplings, fields=None) -> IsingOrbits:
+    """Edge and vertex classes for an Ising-form objective (real couplings
+    per edge, optional real fields per vertex): the orbits of the group of
+    automorphisms that keep both."""
+    gens = automorphism_generators(n, edges, couplings, fields)
+    eo = edge_orbits(n, edges, generators=gens)
+    vo, vr, vw = vertex_classes(n, gens)
+    return IsingOrbits(eo.edge_orbit, eo.rep, eo.weight, gens, vo, vr, vw)
+
+
 def edge_orbits_native(n, edges, weights=None) -> EdgeOrbits:
     """The same classes from the library's C++ implementation
     (``aaqaoa_edge_orbits``: same refinement, search order and closure).
@@ -258,6 +298,29 @@ def edge_orbits_native(n, edges, weights=None) -> EdgeOrbits:
     N.check(N.aaqaoa_edge_orbits(int(n), m, P(e), P(wt) if wt is not None else None, P(eo), ctypes.byref(k), P(rep),
                                  P(w)), "aaqaoa_edge_orbits")
     return EdgeOrbits(eo[:m].copy(), rep[:k.value].copy(), w[:k.value].copy(), [])
+
+
+def ising_orbits_native(n, edges, couplings, fields=None) -> IsingOrbits:
+    """The classes of ising_orbits from the library's C++ implementation
+    (``aaqaoa_ising_orbits``). Generators are not returned."""
+    import ctypes
+
+    from . import _native as N
+
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    m = len(e) // 2
+    cw = np.ascontiguousarray(np.asarray(couplings, dtype=np.float64).reshape(-1))
+    fh = None if fields is None else np.ascontiguousarray(np.asarray(fields, dtype=np.float64).reshape(-1))
+    eo, rep, w = (np.zeros(max(m, 1), dtype=np.int32) for _ in range(3))
+    vo, vr, vw = (np.zeros(n, dtype=np.int32) for _ in range(3))
+    k, kv = ctypes.c_int32(), ctypes.c_int32()
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    D = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    N.check(N.aaqaoa_ising_orbits(int(n), m, P(e), D(cw) if m else None, D(fh) if fh is not None else None, P(eo),
+                                  ctypes.byref(k), P(rep), P(w), P(vo), ctypes.byref(kv), P(vr), P(vw)),
+            "aaqaoa_ising_orbits")
+    return IsingOrbits(eo[:m].copy(), rep[:k.value].copy(), w[:k.value].copy(), [], vo.copy(),
+                       vr[:kv.value].copy(), vw[:kv.value].copy())
 
 
 # ------------------------------------------------ structural descriptor eta_p

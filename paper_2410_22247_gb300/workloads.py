@@ -192,3 +192,26 @@ def mixed_graph_batch(count: int, n_lo: int, n_hi: int, seed: int):
             _, e = random_regular(n, 3, sub)
         out.append((fam, n, e))
     return out
+
+
+def ising_couplings(n: int, edges, seed: int, symmetric: bool = False, fields: bool = True):
+    """Seeded real couplings (one per edge) and fields (one per vertex, or
+    None) for an Ising-form objective.
+
+    symmetric=False: couplings ~ U[-1, 2], fields ~ U[-1, 1] (generic, the
+    automorphism group is usually trivial). symmetric=True: values drawn per
+    class of an automorphism-invariant key (the sorted degree pair of an edge,
+    the degree of a vertex), so every automorphism of the graph keeps them and
+    H_red stays nontrivial."""
+    e = np.asarray(edges).reshape(-1, 2)
+    r = rng(seed)
+    if not symmetric:
+        w = r.uniform(-1.0, 2.0, size=len(e))
+        h = r.uniform(-1.0, 1.0, size=n) if fields else None
+        return w, h
+    deg = np.bincount(e.reshape(-1), minlength=n) if len(e) else np.zeros(n, dtype=np.int64)
+    table_w = r.uniform(-1.0, 2.0, size=(n + 1, n + 1))
+    table_h = r.uniform(-1.0, 1.0, size=n + 1)
+    w = np.array([table_w[min(deg[u], deg[v]), max(deg[u], deg[v])] for u, v in e], dtype=np.float64)
+    h = np.array([table_h[deg[i]] for i in range(n)], dtype=np.float64) if fields else None
+    return w, h

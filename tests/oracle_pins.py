@@ -447,3 +447,19 @@ ALL_CHECKS["ising_fields_closed_form"] = check_ising_fields_closed_form
 ALL_CHECKS["ising_reductions"] = check_ising_reductions
 ALL_CHECKS["ising_invariants"] = check_ising_invariants
 ALL_CHECKS["ising_finite_difference"] = check_ising_finite_difference
+
+
+def check_ising_lightcone(lc=None):
+    """Per-term light cones of Ising objectives against the full Ising
+    oracle, on graphs whose radius-p balls leave vertices out."""
+    lc = LC if lc is None else lc
+    worst = 0.0
+    for k, ((n, e), depths) in enumerate(lightcone_cases()[:4]):
+        w, h = W.ising_couplings(n, e, 1100 + k)
+        for p in depths[:2]:
+            g, b = W.random_angles(p, 1110 + 10 * k + p)
+            E, dg, db = O.ising_energy_grad(n, O.ising(e, w, h), g, b)
+            El, dgl, dbl = lc.ising_energy_grad(n, e, w, h, g, b)
+            s = max(abs(E), 1.0)
+            worst = max(worst, abs(El - E) / s, _rel(dgl, dg, s), _rel(dbl, db, s))
+    return worst

@@ -267,3 +267,45 @@ def test_batch_argument_checks():
         Plan._device_points(fake, d, d, torch.zeros(14, dtype=torch.float64), 5)
     with pytest.raises(ValueError):
         Plan._device_points(fake, d, torch.zeros(4, dtype=torch.float64), d, 1)
+
+
+def _prepare_ising(n, edges, w, h=None, eorb=None, vorb=None, p=1):
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    m = len(e) // 2
+    wv = np.ascontiguousarray(w, dtype=np.float64)
+    hv = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if a is not None and a.size else None
+    D = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None and a.size else None
+    arr = lambda x: None if x is None else np.ascontiguousarray(x, dtype=np.int32)
+    er, ew, eo = (arr(x) for x in (eorb or (None, None, None)))
+    vr, vw, vo = (arr(x) for x in (vorb or (None, None, None)))
+    hdl = ctypes.c_void_p()
+    rc = N.aaqaoa_prepare_ising(n, m, P(e), D(wv), D(hv), 0 if er is None else len(er), P(er), P(ew), P(eo),
+                                0 if vr is None else len(vr), P(vr), P(vw), P(vo), p, 0, None, ctypes.byref(hdl))
+    if rc == 0:
+        N.aaqaoa_destroy(hdl)
+    return rc
+
+
+def test_prepare_ising_validation():
+    """Ising plans: real couplings and fields, vertex orbits for H_red; the
+    host rejects non-finite values, classes that mix couplings or fields,
+    vertex classes that do not partition the vertices, and fields with edge
+    orbits but no vertex orbits."""
+    path = [(0, 1), (1, 2), (2, 3)]
+    w = [0.5, -1.25, 0.5]
+    h = [0.3, -0.2, -0.2, 0.3]
+    eorb = ([0, 1], [2, 1], [0, 1, 0])
+    vorb = ([0, 1], [2, 2], [0, 1, 1, 0])
+    assert _prepare_ising(4, path, w, h, eorb, vorb) == 0
+    assert _prepare_ising(4, path, w, None, eorb) == 0
+    assert _prepare_ising(4, path, w, h) == 0                                   # no H_red
+    assert _prepare_ising(4, path, [0.5, np.nan, 0.5], h) == -1                # weight not finite
+    assert _prepare_ising(4, path, w, [0.3, np.inf, -0.2, 0.3]) == -1          # field not finite
+    assert _prepare_ising(4, path, [0.5, -1.25, 0.7], h, eorb, vorb) == -2     # class mixes couplings
+    assert _prepare_ising(4, path, w, [0.3, -0.2, -0.2, 0.4], eorb, vorb) == -2  # class mixes fields
+    assert _prepare_ising(4, path, w, h, eorb) == -2                           # fields, no vertex orbits
+    assert _prepare_ising(4, path, w, h, eorb, ([0, 1], [2, 1], [0, 1, 1, 0])) == -2  # sizes do not sum to n
+    assert _prepare_ising(4, path, w, h, eorb, ([0, 1], [2, 2], [0, 1, 0, 1])) == -2  # class {0, 2} mixes fields
+    assert _prepare_ising(4, [(0, 0)], [1.0]) == -1                            # edges checked as for MaxCut
+    assert N.aaqaoa_last_error_detail()

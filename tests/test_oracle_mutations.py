@@ -66,6 +66,9 @@ LC_MUTATIONS = {
                                            "if int(a) in index and int(b) in index and {int(a), int(b)} != {u, v}]"),
     "subset_weight_dropped": ("wk = w[e] if w is not None else float(weights[k])", "wk = 1.0"),
     "gradient_of_one_layer_dropped": ("dg += wk * dge", "dg[1:] += wk * dge[1:]"),
+    "ising_cone_without_fields": ("fn = oracle.ising(sub, w[inside], np.array([h[a] for a in verts]))",
+                                  "fn = oracle.ising(sub, w[inside], np.zeros(len(verts)))"),
+    "ising_field_term_without_cone": ("        terms += [((i, i), None, h[i]) for i in range(n)]", "        pass"),
 }
 
 
@@ -83,7 +86,7 @@ def test_lightcone_pin_catches_planted_mistake(name, oracle_lib):
     src = open(LC_SRC).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not unique"
     mutated = _load_mutated_lightcone(src.replace(old, new), name)
-    worst = P.check_lightcone(mutated)
+    worst = max(P.check_lightcone(mutated), P.check_ising_lightcone(mutated))
     assert worst > 1e-3, worst
 
 

@@ -147,3 +147,9 @@ def test_ising_oracle_gradient_matches_finite_differences(oracle_lib):
 
 def test_ising_oracle_invariants_under_weight_and_field_preserving_automorphisms(oracle_lib):
     assert P.check_ising_invariants() < 1e-11
+
+
+def test_ising_lightcone_matches_full_statevector(oracle_lib):
+    """Per-term light cones (ZZ terms and field terms) of Ising objectives
+    against the full Ising oracle, to 1e-11."""
+    assert P.check_ising_lightcone() < 1e-11

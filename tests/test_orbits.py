@@ -208,3 +208,39 @@ def test_eta_mean_is_the_enumerated_mean_and_bounds():
         assert abs(ORB.eta_mean(nn, e, 1) - (1 - (2 * n - 3) / (n * (n - 1) / 2))) < 1e-12
         assert ORB.eta_mean(*W.star_graph(n), 1) == 0.0
         assert abs(ORB.eta_mean(*W.cycle_graph(n), 1) - (1 - 3 / n)) < 1e-12
+
+
+def _ising_symmetric_instance(n, e, seed):
+    """Couplings and fields that depend on vertex degrees (kept by every
+    automorphism) plus a field that singles out vertex 0."""
+    deg = np.bincount(np.asarray(e).reshape(-1), minlength=n)
+    r = W.rng(seed)
+    vals = r.uniform(-2, 2, size=2 * n + 2)
+    w = np.array([vals[(deg[u] + deg[v]) % len(vals)] for u, v in e])
+    h = np.array([vals[-1] if i == 0 else vals[n + deg[i] % n] for i in range(n)])
+    return w, h
+
+
+@pytest.mark.parametrize("maker", [lambda: W.cycle_graph(6), lambda: W.star_graph(7), lambda: W.complete_graph(5),
+                                   lambda: W.heap_binary_tree(7), lambda: W.prufer_tree(8, 2),
+                                   lambda: W.random_regular(8, 3, 1)],
+                         ids=["c6", "star7", "k5", "bintree7", "prufer8", "reg8"])
+def test_ising_orbits_match_brute_force(maker):
+    """Edge and vertex classes of the coupling- and field-preserving
+    automorphisms equal the brute-force orbits (all permutations), from both
+    finders."""
+    from oracle import automorphisms as AUT
+    n, e = maker()
+    for seed in (1, 2):
+        w, h = _ising_symmetric_instance(n, e, seed)
+        eorb, vorb = AUT.ising_orbit_partition(n, e, w, h)
+        io = ORB.ising_orbits(n, e, w, h)
+        canon = [tuple(map(int, x)) for x in e]
+        got_e = {frozenset(canon[i] for i in range(len(e)) if io.edge_orbit[i] == c) for c in range(io.num_orbits)}
+        got_v = {frozenset(u for u in range(n) if io.vertex_orbit[u] == c) for c in range(len(io.vrep))}
+        assert got_e == set(eorb) and got_v == set(vorb)
+        assert all(io.vertex_orbit[io.vrep[c]] == c and io.vweight[c] == len([u for u in range(n)
+                   if io.vertex_orbit[u] == c]) for c in range(len(io.vrep)))
+        nat = ORB.ising_orbits_native(n, e, w, h)
+        for k in ("edge_orbit", "rep", "weight", "vertex_orbit", "vrep", "vweight"):
+            assert np.array_equal(getattr(io, k), getattr(nat, k)), k
