@@ -420,10 +420,17 @@ int aaqaoa_inject_fault(aaqaoa_plan *plan, int kind);
  * aaqaoa_get_pass_plan: plan4 (host, 4 ints) receives the current plan.
  * aaqaoa_set_pass_plan: 0 keeps the default for that entry (the fewest high
  *   passes; a two-register-stage low pass when they can take the rest).
+ *   For complex64 plans the adjoint's low pass may span 14 qubits (bwd_low =
+ *   14): a cluster of 4 CTAs loads the 2^14 contiguous amplitudes of a tile,
+ *   a quarter each, and exchanges them through distributed shared memory so
+ *   that the last two of the 14 qubits are mixed too; a layer then needs one
+ *   high pass fewer (n = 30: 14 + 8 + 8 instead of 8 + 8 + 7 + 7). A batch of
+ *   B points runs that pass once per point.
  *   INVALID_ARG if an (L, K) does not tile n with rows of >= 128 bytes.
  *   Rebuilds the workspace's tensor maps; the stored state becomes invalid.
  * aaqaoa_autotune: times each candidate (the fewest and one more high pass,
- *   each with the full and the two-stage low pass) on the plan's workspace
+ *   each with the full and the two-stage low pass, and for the complex64
+ *   adjoint the 14-qubit cluster low pass) on the plan's workspace
  *   and stream and keeps the fastest forward and adjoint plans; the choice is
  *   cached per process by (device, precision, n, p, batch, gradient, layer
  *   fusion). Leaves
@@ -525,7 +532,8 @@ int aaqaoa_profile_read(aaqaoa_plan *plan, int kind, double *ms_total, int *laun
  * aaqaoa_profile_launches -- the recorded launches one by one, in launch
  * order: per launch its kind (as above), flags (bit 0: the pass carries
  * cut-function work -- phase, lambda = O phi, energy, dE/dgamma, inverse
- * phase; bit 1: a fused layer boundary), event duration (ms) and bytes to
+ * phase; bit 1: a fused layer boundary; bit 2: the cluster low pass), event
+ * duration (ms) and bytes to
  * move. kind, flags, ms, bytes: host arrays of at least max entries, each may
  * be NULL. *count (host int) receives the number of records, also when it
  * exceeds max. Synchronises the plan's stream. INVALID_ARG for a NULL plan

@@ -217,6 +217,7 @@ class Plan:
                                           _ptr(flags, ctypes.c_int32), _ptr(ms, ctypes.c_double),
                                           _ptr(by, ctypes.c_double)), "aaqaoa_profile_launches")
         return [{"kind": int(kind[i]), "cut_work": bool(flags[i] & 1), "fused": bool(flags[i] & 2),
+                 "cluster": bool(flags[i] & 4),
                  "ms": float(ms[i]), "bytes": float(by[i])} for i in range(n)]
 
     def autotune(self):

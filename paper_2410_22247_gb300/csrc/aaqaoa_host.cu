@@ -92,6 +92,7 @@ struct Pass {
     int wide;    // tensor-map form (rows of more than 128 bytes)
     int skip_last = 0;  // low pass done after register stage 1
     int qubits = 0;     // butterflies of this pass
+    int cluster = 0;    // the 14-qubit low pass of a cluster of 4 CTAs (complex64 adjoint)
 };
 
 struct Layout {
@@ -129,6 +130,7 @@ struct aaqaoa_plan {
     std::vector<Pass> bwd_passes;  // adjoint passes (two-vector tile geometry)
     std::vector<CUtensorMap> map_phi;            // forward, per pass
     std::vector<CUtensorMap> map_bphi, map_blam; // adjoint, per pass
+    std::vector<std::array<CUtensorMap, 4>> map_bcl;  // cluster passes: load phi, lambda; store phi, lambda
     int launches = 0;
     bool state_valid = false;
     int inject = 0;  // pending test fault (aaqaoa_inject_fault)
@@ -296,19 +298,49 @@ int make_map(CUtensorMap *map, void *base, int n, int s, int cb, int T, int cbmi
     return AAQAOA_OK;
 }
 
+// The cluster low pass's views of B complex64 statevectors: 5-D
+// [16 amplitudes][64 rows: qubits 4..9][qubits 10, 11][qubits 12, 13]
+// [2^(n-14) B cluster tiles]. A CTA loads the box with qubits 12, 13 fixed
+// (its rank) and stores the box with qubits 10, 11 fixed.
+int make_cluster_map(CUtensorMap *map, void *base, int n, int B, bool load)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return fail(AAQAOA_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable from the driver");
+    if (n < CLUSTER_LOW_QUBITS)
+        return fail(AAQAOA_ERR_UNSUPPORTED, "cluster low pass needs n >= %d", CLUSTER_LOW_QUBITS);
+    const cuuint64_t amp = 8;
+    cuuint64_t dims[5] = {16, 64, 4, 4, ((cuuint64_t)1 << (n - CLUSTER_LOW_QUBITS)) * (cuuint64_t)B};
+    cuuint64_t strides[4] = {16 * amp, ((cuuint64_t)1 << 10) * amp, ((cuuint64_t)1 << 12) * amp,
+                             ((cuuint64_t)1 << 14) * amp};
+    cuuint32_t box[5] = {16, 64, load ? 4u : 1u, load ? 1u : 4u, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(AAQAOA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the cluster pass, n=%d", (int)r, n);
+    return AAQAOA_OK;
+}
+
 // Passes of one layer for tiles of T qubits: a low pass over qubits 0..L-1
 // (contiguous tiles), then K high passes that share the remaining n-L qubits
 // evenly. A high pass with h < hbmax row qubits spends the spare tile bits on
 // longer contiguous rows (cb = T-h), which keeps the strided passes close to
 // streaming bandwidth. Returns false when (L, K) does not give valid tiles.
-bool layer_passes(int n, int T, int cbmin, int hbmax, int L2, int L, int K, std::vector<Pass> &v)
+// cluster_low: the geometry allows a low pass of CLUSTER_LOW_QUBITS qubits by
+// a cluster of 4 CTAs (the complex64 two-vector tiles), chosen by L = 14.
+bool layer_passes(int n, int T, int cbmin, int hbmax, int L2, int L, int K, std::vector<Pass> &v,
+                  bool cluster_low = false)
 {
     v.clear();
-    if (n <= T || L < cbmin || L > T || K < 1 || n - L < K || n - L > K * hbmax || K + 1 > MAX_PASSES)
+    const bool cl = cluster_low && L == CLUSTER_LOW_QUBITS && T + 2 == CLUSTER_LOW_QUBITS;
+    if (n <= T || L < cbmin || (L > T && !cl) || K < 1 || n - L < K || n - L > K * hbmax || K + 1 > MAX_PASSES)
         return false;
-    Pass low{cbmin, cbmin, 1, (1 << (L - cbmin)) - 1, 0};
-    low.skip_last = L <= L2 && L < T ? 1 : 0;
+    Pass low{cbmin, cbmin, 1, (1 << ((cl ? T : L) - cbmin)) - 1, 0};
+    low.skip_last = !cl && L <= L2 && L < T ? 1 : 0;
     low.qubits = L;
+    low.cluster = cl ? 1 : 0;
     v.push_back(low);
     const int r = n - L;
     int s = L;
@@ -548,6 +580,20 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
             a.slot_scale[2] = 2.0;
         }
         const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
+        if (ps.cluster) {  // one launch per point, each over that point's cluster tiles
+            for (int b = 0; b < B; b++) {
+                PassArgs ab = a;
+                ab.B = 1;
+                ab.chunk = 0;
+                ab.tile0 = b << (pl->n - CLUSTER_LOW_QUBITS);
+                ab.cs = a.cs + (size_t)b * pl->p;
+                ab.out = a.out + (size_t)b * pl->out_stride();
+                ProfScope ps_(pl, PK_ADJ, S / B * (a.nvec_io + 2), pass_flags(a) | 4);
+                CKL(launch_cluster_pass(pl->map_bcl[sp.k].data(), ab, pl->stream), "adjoint cluster pass");
+                pl->launches++;
+            }
+            continue;
+        }
         ProfScope ps_(pl, PK_ADJ, S * (a.nvec_io + (a.write ? 2 : 0)), pass_flags(a));
         CKL(launch_pass(pl->c128, 2, pl->map_bphi[sp.k], pl->map_blam[sp.k], a, grid, pl->stream), "adjoint pass");
         pl->launches++;
@@ -1022,6 +1068,7 @@ int build_maps(aaqaoa_plan *pl)
     pl->map_phi.assign(pl->passes.size(), CUtensorMap{});
     pl->map_bphi.assign(pl->bwd_passes.size(), CUtensorMap{});
     pl->map_blam.assign(pl->bwd_passes.size(), CUtensorMap{});
+    pl->map_bcl.assign(pl->bwd_passes.size(), std::array<CUtensorMap, 4>{});
     if (!pl->ws)
         return AAQAOA_OK;
     int T, CB, HB;
@@ -1036,6 +1083,15 @@ int build_maps(aaqaoa_plan *pl)
         pass_geometry(pl->c128, 2, &T, &CB, &HB);
         for (size_t k = 0; k < pl->bwd_passes.size(); k++) {
             Pass &ps = pl->bwd_passes[k];
+            if (ps.cluster) {
+                for (int j = 0; j < 4; j++) {
+                    int r = make_cluster_map(&pl->map_bcl[k][j], j % 2 ? pl->d_lam() : pl->d_phi(), pl->n, pl->cap,
+                                             j < 2);
+                    if (r)
+                        return r;
+                }
+                continue;
+            }
             int r = make_map(&pl->map_bphi[k], pl->d_phi(), pl->n, ps.s, ps.cb, T, CB, pl->amp(), pl->cap, &ps.wide);
             if (r)
                 return r;
@@ -1090,7 +1146,7 @@ static int set_layers(aaqaoa_plan *pl, const int plan4[4])
             L = plan4[2 * (nv - 1)];
         if (plan4[2 * (nv - 1) + 1] > 0)
             K = plan4[2 * (nv - 1) + 1];
-        if (!layer_passes(pl->n, T, CB, HB, L2, L, K, v[nv - 1]))
+        if (!layer_passes(pl->n, T, CB, HB, L2, L, K, v[nv - 1], nv == 2 && !pl->c128))
             return fail(AAQAOA_ERR_INVALID_ARG, "%s plan: low pass of %d qubits + %d high passes does not tile n=%d",
                         nv == 1 ? "forward" : "adjoint", L, K, pl->n);
     }
@@ -1183,10 +1239,11 @@ std::vector<std::array<int, 2>> layer_candidates(const aaqaoa_plan *pl, int nv)
     const int L2 = low_two_stage_bits(pl->c128, nv);
     default_layer(pl->n, T, CB, HB, L2, &L, &K);
     std::vector<std::array<int, 2>> c;
-    for (int k = K; k <= K + 1; k++)
-        for (int l : {T, L2}) {
+    const bool cl = nv == 2 && !pl->c128;
+    for (int k = (cl && K > 1 ? K - 1 : K); k <= K + 1; k++)
+        for (int l : {T, L2, CLUSTER_LOW_QUBITS}) {
             std::vector<Pass> v;
-            if (layer_passes(pl->n, T, CB, HB, L2, l, k, v) &&
+            if (layer_passes(pl->n, T, CB, HB, L2, l, k, v, cl) &&
                 std::find(c.begin(), c.end(), std::array<int, 2>{l, k}) == c.end())
                 c.push_back({l, k});
         }

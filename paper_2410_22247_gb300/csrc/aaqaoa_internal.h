@@ -99,6 +99,7 @@ struct PassArgs {
     const IsingFn *icost;
     const IsingFn *iobs;
     const double *gam;   // [B][p]
+    int tile0;           // cluster low pass: first cluster tile (point b of a batch starts at b * 2^(n-14))
 };
 
 // Whole-circuit kernel for states that fit one CTA's shared memory.
@@ -157,6 +158,10 @@ int launch_params(bool c128, int B, int p, int tab_len, int n, const double *d_g
                   void *d_tab, double2 *d_cs, cudaStream_t st);
 int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a,
                 int grid, cudaStream_t st);
+// The adjoint's complex64 low pass over 14 qubits by clusters of 4 CTAs: maps
+// = {load phi, load lambda, store phi, store lambda}; one parameter point.
+int launch_cluster_pass(const CUtensorMap *maps, const PassArgs &a, cudaStream_t st);
+constexpr int CLUSTER_LOW_QUBITS = 14;
 int launch_small(bool c128, const SmallArgs &a, int B, cudaStream_t st);
 size_t small_smem_bytes(bool c128, int n, int mode, bool ising);
 int small_max_qubits(bool c128, int mode);

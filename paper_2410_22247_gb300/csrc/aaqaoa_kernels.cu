@@ -345,7 +345,9 @@ template <> struct Geo<float, 1> {
     __host__ __device__ static constexpr uint32_t swz(uint32_t i) { return i ^ (((i >> 4) & 7u) << 1); }
 };
 
-// complex64, two vectors (adjoint): 2 x 32 KB tiles (12 qubits), 16 per thread
+// complex64, two vectors (adjoint): 2 x 32 KB tiles (12 qubits), 16 per thread.
+// Stage 3 exists only in the cluster pass: the stage-2 layout again, whose
+// register bits 2, 3 (local bits 10, 11) then hold the cluster's qubits.
 template <> struct Geo<float, 2> {
     static constexpr int CB = 4, HB = 8, T = 12, RB = 4, NTHR = 256, NST = 3, NSTAGE = 3;
     static constexpr int MAXREG = 168;  // 9 warps: 3 share a sub-partition's 16K registers
@@ -354,7 +356,7 @@ template <> struct Geo<float, 2> {
     {
         return st == 0 ? 4 + j : st == 1 ? (j < 4 ? j : 4 + j) : j;
     }
-    __host__ __device__ static constexpr int own(int st) { return 0xF; }
+    __host__ __device__ static constexpr int own(int st) { return st == 3 ? 0xC : 0xF; }
     __host__ __device__ static constexpr uint32_t swz(uint32_t i) { return i ^ (((i >> 4) & 7u) << 1); }
 };
 
@@ -1698,6 +1700,367 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         pass_final_reduce(A, total);
 }
 
+// ------------------------------------------------- cluster low pass
+// The adjoint's low pass over 14 qubits by a cluster of 4 CTAs (complex64,
+// one parameter point). Cluster tile t is the 2^14 contiguous amplitudes
+// t * 2^14 ...; CTA r of the cluster loads the slice whose qubits 12, 13
+// equal r and applies the butterflies of qubits 0..11 in register stages 0,
+// 1 and 2 as a plain low pass does. Stage 2 holds local bits 8..11 in
+// registers; after its butterflies every thread stores each register into
+// the shared memory of the CTA q whose slice has qubits 10, 11 = q (the
+// register's local bits 10, 11), at local bits 10, 11 = r. Each CTA then
+// holds the slice with qubits 10, 11 = its rank, qubits 12, 13 at local bits
+// 10, 11, applies their butterflies in stage 3 (the stage-2 layout) and TMA-
+// stores that slice. Two mbarriers per buffer order the exchange across the
+// cluster: xl (every CTA has read its stage-2 registers, so its buffer may
+// be overwritten) and xw (every CTA's stores into this buffer are done).
+// Each CTA arrives once on every CTA's barrier (count 4) with release
+// semantics at cluster scope and waits with acquire. All waits are bounded;
+// a cluster barrier at the end keeps every CTA's shared memory alive while a
+// peer may still reach it.
+constexpr int CLUSTER_CTAS = 4;  // 2 qubits across the cluster
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_index()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared-memory location in CTA `cta`
+__device__ __forceinline__ uint32_t map_to_cta(uint32_t addr, uint32_t cta)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(cta));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+        if (clock64() - t0 > WAIT_BUDGET_CYCLES)
+            return false;
+    }
+}
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v)
+{
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// MODE 0: mixer only; 1: the first adjoint pass (phi loaded alone, lambda =
+// O phi formed in stage 0). A.tiles counts 2^12-amplitude slices (2^(n-12)).
+template <int MODE>
+__global__ void __maxnreg__((Geo<float, 2>::MAXREG))
+    k_cpass(const __grid_constant__ CUtensorMap ld0, const __grid_constant__ CUtensorMap ld1,
+            const __grid_constant__ CUtensorMap st0, const __grid_constant__ CUtensorMap st1,
+            const __grid_constant__ PassArgs A)
+{
+    using R = float;
+    using G = Geo<float, 2>;
+    using C = float2;
+    constexpr bool OPS = MODE != 0;
+    constexpr int NR = 1 << G::RB, NS = G::NSTAGE, NTHR = G::NTHR, RB = G::RB, NTB = G::T - G::RB;
+    constexpr uint32_t TB = (uint32_t)tile_bytes<float, 2>();
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    __shared__ __align__(8) uint64_t full[NS], done[NS], xl[NS], xw[NS];
+    __shared__ double pred[32];
+    __shared__ int s_flag;
+    __shared__ int obs_w[MAXK];
+    __shared__ int tcs[NS][2][16];
+    __shared__ int ptc[2 * (RB + 1) * NTHR];
+    __shared__ int qr[2][32];
+    __shared__ float qrf[2][32];
+
+    const int tid = threadIdx.x;
+    const uint32_t rank = cluster_ctarank();
+    const unsigned cid = cluster_index(), ncl = cluster_count();
+    uint64_t *obs_nbr = reinterpret_cast<uint64_t *>(sm + (size_t)NS * 2 * TB);
+    const unsigned ctiles = (unsigned)A.tiles / CLUSTER_CTAS;
+    const unsigned niter = cid < ctiles ? (ctiles - cid + ncl - 1) / ncl : 0;
+
+    if (tid == 0) {
+        s_flag = *reinterpret_cast<volatile int *>(A.err) ? 1 : 0;
+        for (int q = 0; q < NS; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&done[q], NTHR);
+            mbar_init(&xl[q], CLUSTER_CTAS);
+            mbar_init(&xw[q], CLUSTER_CTAS);
+        }
+        fence_barrier_init();
+    }
+    if (OPS) {
+        for (int i = tid; i < A.obs.K * MAXN; i += blockDim.x)
+            obs_nbr[i] = A.obs.nbr[i / MAXN][i % MAXN];
+        if (tid < MAXK)
+            obs_w[tid] = A.obs.w[tid];
+    }
+    __syncthreads();
+    cluster_barrier();  // every CTA's mbarriers are initialised before any remote arrive
+    const bool skip = s_flag != 0;
+
+    // O's launch constants for stage 0 (lambda = O phi); local bit L is qubit L
+    if (OPS && !skip && tid < NTHR) {
+        auto wgt = [&](int u, int v) -> int {
+            int w = 0;
+            for (int c = 0; c < A.obs.K; c++)
+                w += obs_w[c] * (int)((obs_nbr[c * MAXN + u] >> v) & 1ull);
+            return w;
+        };
+        int q = 0;
+        for (int j = 0; j < NTB; j++)
+            for (int j2 = 0; j2 < j; j2++)
+                if (((tid >> j) & 1) && ((tid >> j2) & 1))
+                    q -= 2 * wgt(G::thr(0, j), G::thr(0, j2));
+        ptc[(RB + 1) * NTHR + tid] = q;
+        for (int kk = 0; kk < RB; kk++) {
+            int dk = 0;
+            for (int j = 0; j < NTB; j++)
+                if ((tid >> j) & 1)
+                    dk -= 2 * wgt(G::reg(0, kk), G::thr(0, j));
+            ptc[(RB + 1 + 1 + kk) * NTHR + tid] = dk;
+        }
+        if (tid < (1 << RB)) {
+            int qq = 0;
+            for (int kk = 0; kk < RB; kk++)
+                for (int k2 = 0; k2 < kk; k2++)
+                    if (((tid >> kk) & 1) && ((tid >> k2) & 1))
+                        qq -= 2 * wgt(G::reg(0, kk), G::reg(0, k2));
+            qr[1][tid] = qq;
+            qrf[1][tid] = (float)qq;
+        }
+    }
+    // fixed bits of this CTA's slice of cluster tile k
+    auto slice_fixed = [&](unsigned k) -> uint64_t {  // within the point's state
+        const uint64_t ct = (uint64_t)cid + (uint64_t)k * ncl;
+        return (ct << 14) | ((uint64_t)rank << 12);
+    };
+
+    bool ok = !skip;
+    if (!skip && tid >= NTHR) {
+        // ------------------------------------------------------ producer
+        const int lane = tid - NTHR;
+        long long last_fill[NS];
+        for (int q = 0; q < NS; q++)
+            last_fill[q] = -1;
+        auto fill = [&](unsigned k) {
+            const int q = (int)(k % NS);
+            if (OPS) {  // O(f) and h_L(f) of the slice (local bit L = qubit L)
+                const uint64_t f = slice_fixed(k);
+                int hs = 0, os = 0;
+                for (int c = 0; c < A.obs.K; c++) {
+                    const uint64_t *nb = obs_nbr + c * MAXN;
+                    if (lane < G::T)
+                        hs += obs_w[c] * (__popcll(nb[lane]) - 2 * __popcll(nb[lane] & f));
+                    for (int u = lane; u < A.n; u += 32)
+                        if ((f >> u) & 1ull)
+                            os += obs_w[c] * __popcll(nb[u] & ~f);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    os += __shfl_xor_sync(0xffffffffu, os, o);
+                if (lane < G::T)
+                    tcs[q][1][lane] = hs;
+                if (lane == 0)
+                    tcs[q][1][15] = os;
+            }
+            __syncwarp();
+            if (lane != 0)
+                return;
+            last_fill[q] = (long long)k;
+            const int ct = A.tile0 + (int)(cid + k * ncl);
+            unsigned char *buf = sm + (size_t)q * 2 * TB;
+            mbar_arrive_expect_tx(&full[q], (uint32_t)A.nvec_io * TB);
+            tma_load_5d(buf, &ld0, &full[q], 0, 0, 0, (int)rank, ct);
+            if (A.nvec_io == 2)
+                tma_load_5d(buf + TB, &ld1, &full[q], 0, 0, 0, (int)rank, ct);
+        };
+        for (unsigned k = 0; k < (unsigned)NS && k < niter; k++)
+            fill(k);
+        for (unsigned k = 0; k < niter && ok; k++) {
+            const int q = (int)(k % NS);
+            int good = 1;
+            if (lane == 0) {
+                good = mbar_wait_bounded(&done[q], (k / NS) & 1u) && !*reinterpret_cast<volatile int *>(&s_flag);
+                if (good) {
+                    const int ct = A.tile0 + (int)(cid + k * ncl);
+                    unsigned char *buf = sm + (size_t)q * 2 * TB;
+                    tma_store_5d(&st0, buf, 0, 0, (int)rank, 0, ct);
+                    tma_store_5d(&st1, buf + TB, 0, 0, (int)rank, 0, ct);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    if (k + NS < niter)
+                        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                }
+            }
+            good = __shfl_sync(0xffffffffu, good, 0);
+            if (!good) {
+                ok = false;
+                break;
+            }
+            if (k + NS < niter)
+                fill(k + NS);
+        }
+        if (lane == 0) {
+            if (!ok) {
+                atomicExch(A.err, 1);
+                s_flag = 1;
+                for (int q = 0; q < NS; q++)
+                    if (last_fill[q] >= 0)
+                        mbar_wait_bounded(&full[q], (unsigned)((last_fill[q] / NS) & 1));
+            }
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        }
+    } else if (!skip) {
+        // ------------------------------------------------------- compute
+        const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, 0, A.pre_lambda, 1, 0, A.j0, 0, A.amp0};
+        Acc<R> acc0, acc1, acc2;
+        acc0.zero();
+        acc1.zero();
+        acc2.zero();
+        StageCtx<R> X;
+        X.ptc = ptc;
+        X.qr = &qr[0][0];
+        X.qrf = &qrf[0][0];
+        X.s = A.s;
+        X.cb = A.cb;
+        X.tid = tid;
+        X.amp0 = (R)A.amp0;
+        X.cot = X.cot2 = false;
+        {
+            const double2 csd = A.cs[A.layer];
+            const double cbv = csd.x, sbv = A.sign_s * csd.y;
+            const bool shifted = fabs(sbv) > fabs(cbv);
+            X.tq = shifted ? (R)(-cbv / sbv) : (R)(sbv / cbv);
+            const double f = shifted ? sbv : cbv;
+            double fj = 1.0, fn = 1.0;
+            for (int i = 0; i < A.n; i++) {
+                if (i < A.j0)
+                    fj *= f;
+                fn *= f;
+            }
+            X.f = (R)f;
+            X.fn = (R)fn;
+            X.fn2 = (R)(fn * fn);
+            X.scale0 = (R)fj;
+        }
+        const uint32_t sb2 = G::swz(stage_base<G, 2>((uint32_t)tid));
+        constexpr uint32_t LOW2 = split_low<G, 2>();
+        const uint32_t sbh2 = sb2 & ~LOW2, sbl2 = sb2 & LOW2;
+        for (unsigned k = 0; k < niter; k++) {
+            const int q = (int)(k % NS);
+            const uint32_t par = (k / NS) & 1u;
+            unsigned char *buf = sm + (size_t)q * 2 * TB;
+            X.sv0 = reinterpret_cast<C *>(buf);
+            X.sv1 = reinterpret_cast<C *>(buf + TB);
+            X.tc = &tcs[q][0][0];
+            const bool late = !mbar_wait_bounded(&full[q], par);
+            if (k == 0)
+                compute_sync<NTHR>();  // launch constants
+            C a[NR], l[NR];
+            X.first = true;
+            X.run = X.scale0;
+            run_stage<R, 2, 0, OPS>(P, X, a, l, acc0, acc1, acc2);
+            X.first = false;
+            if (compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag))) {
+                ok = false;
+                break;
+            }
+            run_stage<R, 2, 1, OPS>(P, X, a, l, acc0, acc1, acc2);
+            compute_sync<NTHR>();
+            // stage 2: local bits 8..11, then the exchange
+            load_regs<R, 2, 2>(X.sv0, sb2, a);
+            load_regs<R, 2, 2>(X.sv1, sb2, l);
+            compute_sync<NTHR>();  // this CTA's stage-2 reads are done
+            if (tid < CLUSTER_CTAS)
+                mbar_arrive_remote(map_to_cta(smem_u32(&xl[q]), (uint32_t)tid));
+            mix_regs<R, 2, 2>(P, X.cb, X.tq, X.f, X.run, a, l, acc0);
+            const bool wl = mbar_wait_cluster_bounded(&xl[q], par);
+            if (compute_sync_or<NTHR>(!wl)) {
+                ok = false;
+                break;
+            }
+            const uint32_t base0 = smem_u32(X.sv0), base1 = smem_u32(X.sv1);
+#pragma unroll
+            for (int m = 0; m < NR; m++) {
+                const uint32_t idx = smem_index<G, 2>(sbh2, sbl2, m);
+                const uint32_t dst_cta = (idx >> 10) & 3u;
+                const uint32_t dst = ((idx & ~(3u << 10)) | (rank << 10)) * (uint32_t)sizeof(C);
+                st_cluster(map_to_cta(base0 + dst, dst_cta), a[m]);
+                st_cluster(map_to_cta(base1 + dst, dst_cta), l[m]);
+            }
+            asm volatile("fence.acq_rel.cluster;" ::: "memory");
+            compute_sync<NTHR>();
+            if (tid < CLUSTER_CTAS)
+                mbar_arrive_remote(map_to_cta(smem_u32(&xw[q]), (uint32_t)tid));
+            const bool ww = mbar_wait_cluster_bounded(&xw[q], par);
+            if (compute_sync_or<NTHR>(!ww)) {
+                ok = false;
+                break;
+            }
+            // stage 3: qubits 12, 13 at local bits 10, 11
+            load_regs<R, 2, 2>(X.sv0, sb2, a);
+            load_regs<R, 2, 2>(X.sv1, sb2, l);
+            mix_regs<R, 2, 3>(P, X.cb, X.tq, X.f, X.run, a, l, acc0);
+            store_regs<R, 2, 2>(X.sv0, sb2, a);
+            store_regs<R, 2, 2>(X.sv1, sb2, l);
+            fence_proxy_async_smem();
+            mbar_arrive(&done[q]);
+        }
+        if (!ok && tid == 0) {
+            atomicExch(A.err, 1);
+            s_flag = 1;
+        }
+        // this CTA's dE/dbeta partial (slot 0)
+        double s0 = acc0.get();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        if ((tid & 31) == 0)
+            pred[tid >> 5] = s0;
+        compute_sync<NTHR>();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NTHR / 32; w++)
+                t += pred[w];
+            A.partials[blockIdx.x] = t;
+        }
+    }
+    __syncthreads();
+    cluster_barrier();  // no CTA leaves while a peer may still address its shared memory
+    if (s_flag || skip)
+        return;
+    pass_final_reduce(A, (unsigned)gridDim.x);
+}
+
 // ------------------------------------------------------ parameter tables
 // The factor dropped by one tan/cot butterfly of the (inverse, sign = -1)
 // mixer: cos beta if |sin| <= |cos| else sign * sin beta. Mirrors the choice
@@ -2283,6 +2646,58 @@ int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorM
                               : launch_pass_t<double, 1>(m0, m1, a, grid, st);
     return nv_kernel == 2 ? launch_pass_t<float, 2>(m0, m1, a, grid, st)
                           : launch_pass_t<float, 1>(m0, m1, a, grid, st);
+}
+
+template <int MODE>
+static int launch_cpass_t(const CUtensorMap *maps, const PassArgs &a, cudaStream_t st)
+{
+    const size_t smem = pass_smem_total<float, 2>();
+    static bool attr_done = false;
+    static int max_clusters[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64)
+        return (int)(e != cudaSuccess ? e : cudaErrorInvalidDevice);
+    if (!attr_done) {
+        e = cudaFuncSetAttribute(k_cpass<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return (int)e;
+        attr_done = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CLUSTER_CTAS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(Geo<float, 2>::NTHR + 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (!max_clusters[dev]) {  // clusters of 4 that fit at once (one CTA per SM)
+        cfg.gridDim = dim3(CLUSTER_CTAS * 64);
+        int c = 0;
+        e = cudaOccupancyMaxActiveClusters(&c, k_cpass<MODE>, &cfg);
+        if (e != cudaSuccess)
+            return (int)e;
+        if (c < 1)
+            return (int)cudaErrorInvalidConfiguration;
+        max_clusters[dev] = c;
+    }
+    const int ctiles = a.tiles / CLUSTER_CTAS;
+    const int clusters = ctiles < max_clusters[dev] ? ctiles : max_clusters[dev];
+    cfg.gridDim = dim3(CLUSTER_CTAS * clusters);
+    e = cudaLaunchKernelEx(&cfg, k_cpass<MODE>, maps[0], maps[1], maps[2], maps[3], a);
+    return (int)(e != cudaSuccess ? e : cudaGetLastError());
+}
+
+int launch_cluster_pass(const CUtensorMap *maps, const PassArgs &a, cudaStream_t st)
+{
+    if (a.B != 1 || a.tiles < CLUSTER_CTAS || (a.tiles & (a.tiles - 1)) || a.post || a.fuse || a.pt || a.icost ||
+        !a.is_low)
+        return (int)cudaErrorInvalidValue;
+    return a.pre_lambda ? launch_cpass_t<1>(maps, a, st) : launch_cpass_t<0>(maps, a, st);
 }
 
 size_t small_smem_bytes(bool c128, int n, int mode, bool ising)

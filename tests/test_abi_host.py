@@ -309,3 +309,35 @@ def test_prepare_ising_validation():
     assert _prepare_ising(4, path, w, h, eorb, ([0, 1], [2, 2], [0, 1, 0, 1])) == -2  # class {0, 2} mixes fields
     assert _prepare_ising(4, [(0, 0)], [1.0]) == -1                            # edges checked as for MaxCut
     assert N.aaqaoa_last_error_detail()
+
+
+def test_cluster_low_pass_plan_and_schedule():
+    """The complex64 adjoint may take a 14-qubit low pass (cluster of 4 CTAs):
+    n = 30 then needs 14 + 8 + 8 qubits per layer; every layer of the
+    schedule still mixes every qubit once. complex128 rejects it."""
+    n, e = W.star_graph(30)
+    ee = np.ascontiguousarray(e.reshape(-1), dtype=np.int32)
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    for flags, ok in ((0, True), (1, False)):
+        h = ctypes.c_void_p()
+        assert N.aaqaoa_prepare(n, len(e), P(ee), 0, None, None, None, 2, flags, None, ctypes.byref(h)) == 0
+        rc = N.aaqaoa_set_pass_plan(h, 0, 0, 14, 2)
+        assert (rc == 0) == ok
+        if ok:
+            plan4 = (ctypes.c_int * 4)()
+            assert N.aaqaoa_get_pass_plan(h, plan4) == 0 and list(plan4)[2:] == [14, 2]
+            steps = (ctypes.c_int32 * (5 * 16))()
+            cnt = ctypes.c_int()
+            assert N.aaqaoa_get_schedule(h, 1, steps, 16, ctypes.byref(cnt)) == 0
+            rows = [list(steps[5 * i:5 * i + 5]) for i in range(cnt.value)]
+            assert cnt.value == 5  # 3 passes per layer, one boundary fused
+            assert rows[0][:2] == [0, 14]
+            for layer in (0, 1):
+                mixed = set()
+                for s0, q, l, l2, j0 in rows:
+                    if l == layer:
+                        mixed |= set(range(s0, s0 + q))
+                    if l2 == layer:
+                        mixed |= set(range(s0, s0 + q))
+                assert mixed == set(range(n))
+        N.aaqaoa_destroy(h)
