@@ -432,14 +432,20 @@ def extras(dev, stream):
             row = o.cpu().numpy()
             RESULTS_FOR_ORACLE[f"{name}_{prec}"] = (name, prec, (g, b), (float(row[0]), row[1:1 + P_LAYERS],
                                                                         row[1 + P_LAYERS:]))
-            # aggregation alone on the stored final state, H_C vs H_red
+            # aggregation alone on the stored final state, H_C vs H_red (CUDA
+            # events on the plan's stream around each read, mean of 3)
             pl.expect(g, b, "full", "singlepass")
             agg = {}
             for obs in ("full", "red"):
                 for mode in ("singlepass", "perterm"):
-                    t0 = time.perf_counter()
                     pl.aggregate_only(obs, mode)
-                    agg[f"{obs}_{mode}_ms"] = (time.perf_counter() - t0) * 1000.0
+                    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ea.record(stream)
+                    for _ in range(3):
+                        pl.aggregate_only(obs, mode)
+                    eb.record(stream)
+                    torch.cuda.synchronize()
+                    agg[f"{obs}_{mode}_ms"] = ea.elapsed_time(eb) / 3
             r["aggregation_only"] = agg
             r["energy_red_vs_full_abs_diff"] = abs(pl.expect(g, b, "red") - pl.expect(g, b, "full"))
             rec[prec] = r

@@ -64,10 +64,15 @@ typedef struct aaqaoa_plan aaqaoa_plan; /* opaque, owned by the library */
  *   SINGLEPASS one pass over the stored state that evaluates all terms of
  *              the observable per amplitude (sum_x |psi_x|^2 O(x) with
  *              O(x) = sum_terms w [x_u != x_v]), i.e. the whole aggregation
- *              in a single read. */
+ *              in a single read;
+ *   PERORBIT   the same single read, named for H_red: every orbit
+ *              representative's term (weighted by its orbit size) is
+ *              accumulated per amplitude in one pass; per-edge or per-orbit
+ *              <Z_u Z_v> values themselves come from aaqaoa_edge_zz. */
 #define AAQAOA_AGG_FUSED      0
 #define AAQAOA_AGG_PERTERM    1
 #define AAQAOA_AGG_SINGLEPASS 2
+#define AAQAOA_AGG_PERORBIT   AAQAOA_AGG_SINGLEPASS
 
 /* error codes */
 #define AAQAOA_OK               0
@@ -359,7 +364,8 @@ int aaqaoa_expect_static(aaqaoa_plan *plan, const double *gamma, const double *b
  * Uneven batches of graphs (many small instances of different n, one call).
  *
  * aaqaoa_graph_desc describes one graph exactly as the arguments of
- * aaqaoa_prepare (edges, optional orbit representatives and weights).
+ * aaqaoa_prepare (edges, optional orbit representatives and weights, and the
+ * optional class of every edge, edge_orbit, NULL when not given).
  * aaqaoa_prepare_multi validates every graph (same rules and errors as
  * aaqaoa_prepare, the detail names the graph) and copies all host arrays.
  * Graphs that fit one CTA (n <= 13 for C64, n <= 12 for C128) are evaluated
@@ -385,6 +391,7 @@ typedef struct {
     int num_orbits;
     const int32_t *orbit_rep;
     const int32_t *orbit_weight;
+    const int32_t *edge_orbit;  /* num_edges int32 or NULL */
 } aaqaoa_graph_desc;
 
 int aaqaoa_prepare_multi(int G, const aaqaoa_graph_desc *graphs, int p, unsigned flags, void *stream,

@@ -20,6 +20,7 @@ AAQAOA_OBS_RED = 1
 AAQAOA_AGG_FUSED = 0
 AAQAOA_AGG_PERTERM = 1
 AAQAOA_AGG_SINGLEPASS = 2
+AAQAOA_AGG_PERORBIT = AAQAOA_AGG_SINGLEPASS
 AAQAOA_FAULT_DROP_TILE = 1
 AAQAOA_OK = 0
 ERRORS = {
@@ -31,7 +32,7 @@ class GraphDesc(ctypes.Structure):
     """aaqaoa_graph_desc"""
     _fields_ = [("n", ctypes.c_int), ("num_edges", ctypes.c_int), ("edges", ctypes.POINTER(ctypes.c_int32)),
                 ("num_orbits", ctypes.c_int), ("orbit_rep", ctypes.POINTER(ctypes.c_int32)),
-                ("orbit_weight", ctypes.POINTER(ctypes.c_int32))]
+                ("orbit_weight", ctypes.POINTER(ctypes.c_int32)), ("edge_orbit", ctypes.POINTER(ctypes.c_int32))]
 
 
 # (name, restype, argtypes)

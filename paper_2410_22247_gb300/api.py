@@ -13,7 +13,8 @@ from . import _native as N
 
 OBSERVABLES = {"full": N.AAQAOA_OBS_FULL, "red": N.AAQAOA_OBS_RED,
                N.AAQAOA_OBS_FULL: N.AAQAOA_OBS_FULL, N.AAQAOA_OBS_RED: N.AAQAOA_OBS_RED}
-AGG_MODES = {"fused": N.AAQAOA_AGG_FUSED, "perterm": N.AAQAOA_AGG_PERTERM, "singlepass": N.AAQAOA_AGG_SINGLEPASS}
+AGG_MODES = {"fused": N.AAQAOA_AGG_FUSED, "perterm": N.AAQAOA_AGG_PERTERM, "singlepass": N.AAQAOA_AGG_SINGLEPASS,
+             "perorbit": N.AAQAOA_AGG_PERORBIT}
 
 
 def _i32(a):
@@ -335,17 +336,21 @@ class MultiPlan:
         descs = (N.GraphDesc * self.G)()
         for i, (n, edges, orbits) in enumerate(graphs):
             e = _i32(edges)
-            rep = weight = None
+            rep = weight = eo = None
             if orbits is not None:
                 rep = _i32(orbits.rep if hasattr(orbits, "rep") else orbits[0])
                 weight = _i32(orbits.weight if hasattr(orbits, "weight") else orbits[1])
-            self._keep += [e, rep, weight]
+                eo_src = getattr(orbits, "edge_orbit", None) if hasattr(orbits, "rep") else \
+                    (orbits[2] if len(orbits) > 2 else None)
+                eo = None if eo_src is None else _i32(eo_src)
+            self._keep += [e, rep, weight, eo]
             descs[i].n = int(n)
             descs[i].num_edges = len(e) // 2
             descs[i].edges = _ptr(e, ctypes.c_int32)
             descs[i].num_orbits = 0 if rep is None else len(rep)
             descs[i].orbit_rep = _ptr(rep, ctypes.c_int32)
             descs[i].orbit_weight = _ptr(weight, ctypes.c_int32)
+            descs[i].edge_orbit = _ptr(eo, ctypes.c_int32)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         flags = N.AAQAOA_C128 if precision == "c128" else N.AAQAOA_C64

@@ -2183,7 +2183,7 @@ int aaqaoa_prepare_multi(int G, const aaqaoa_graph_desc *graphs, int p, unsigned
     for (int gi = 0; gi < G; gi++) {
         const aaqaoa_graph_desc &d = graphs[gi];
         aaqaoa_plan *pl = nullptr;
-        int r = aaqaoa_prepare(d.n, d.num_edges, d.edges, d.num_orbits, d.orbit_rep, d.orbit_weight, nullptr, p,
+        int r = aaqaoa_prepare(d.n, d.num_edges, d.edges, d.num_orbits, d.orbit_rep, d.orbit_weight, d.edge_orbit, p,
                                flags, stream, &pl);
         if (r) {
             std::string why = g_detail;
@@ -2226,7 +2226,7 @@ int aaqaoa_prepare_multi(int G, const aaqaoa_graph_desc *graphs, int p, unsigned
         g.row0 = (int)m->order.size();
         g.members = kv.second;
         const aaqaoa_graph_desc &d = graphs[g.members[0]];
-        int r = aaqaoa_prepare(d.n, d.num_edges, d.edges, d.num_orbits, d.orbit_rep, d.orbit_weight, nullptr, p,
+        int r = aaqaoa_prepare(d.n, d.num_edges, d.edges, d.num_orbits, d.orbit_rep, d.orbit_weight, d.edge_orbit, p,
                                flags, stream, &g.pl);
         if (r) {
             aaqaoa_destroy_multi(m);

@@ -1771,9 +1771,21 @@ __device__ __forceinline__ void cluster_barrier()
 {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
-__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v)
+__device__ __forceinline__ void st_async_cluster4(uint32_t addr, float4 v, uint32_t bar)
 {
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     addr),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+                 : "memory");
+}
+
+// asynchronous store into a cluster CTA's shared memory that counts its
+// bytes on that CTA's mbarrier (complete_tx) when they have landed
+__device__ __forceinline__ void st_async_cluster(uint32_t addr, float2 v, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "f"(v.x), "f"(v.y), "r"(bar)
+                 : "memory");
 }
 
 // MODE 0: mixer only; 1: the first adjoint pass (phi loaded alone, lambda =
@@ -1814,7 +1826,7 @@ __global__ void __maxnreg__((Geo<float, 2>::MAXREG))
             mbar_init(&full[q], 1);
             mbar_init(&done[q], NTHR);
             mbar_init(&xl[q], CLUSTER_CTAS);
-            mbar_init(&xw[q], CLUSTER_CTAS);
+            mbar_init(&xw[q], 1);  // one local arrive with the expected bytes
         }
         fence_barrier_init();
     }
@@ -1975,6 +1987,33 @@ __global__ void __maxnreg__((Geo<float, 2>::MAXREG))
         const uint32_t sb2 = G::swz(stage_base<G, 2>((uint32_t)tid));
         constexpr uint32_t LOW2 = split_low<G, 2>();
         const uint32_t sbh2 = sb2 & ~LOW2, sbl2 = sb2 & LOW2;
+        // Software pipeline: stage 3 of tile k-1 (whose pushed quarters landed
+        // while this CTA ran stages 0 and 1 of tile k) comes before stage 2 of
+        // tile k, so the exchange's latency overlaps local work.
+        R run_after2 = X.scale0;  // f^(j0 + 12): the same for every tile
+        // the tile whose xl this CTA has signalled but whose incoming quarters
+        // it has not yet waited for: peers may still be writing into it
+        long long open_tile = -1;
+        auto finish = [&](unsigned kp) -> bool {  // stage 3 of tile kp
+            const int q = (int)(kp % NS);
+            const bool got = mbar_wait_bounded(&xw[q], (kp / NS) & 1u);
+            if (compute_sync_or<NTHR>(!got))
+                return false;
+            open_tile = -1;
+            C a[NR], l[NR];
+            C *sv0 = reinterpret_cast<C *>(sm + (size_t)q * 2 * TB);
+            C *sv1 = reinterpret_cast<C *>(sm + (size_t)q * 2 * TB + TB);
+            load_regs<R, 2, 2>(sv0, sb2, a);
+            load_regs<R, 2, 2>(sv1, sb2, l);
+            R run3 = run_after2;
+            mix_regs<R, 2, 3>(P, X.cb, X.tq, X.f, run3, a, l, acc0);
+            store_regs<R, 2, 2>(sv0, sb2, a);
+            store_regs<R, 2, 2>(sv1, sb2, l);
+            fence_proxy_async_smem();
+            mbar_arrive(&done[q]);
+            return true;
+        };
+        long long pending = -1;
         for (unsigned k = 0; k < niter; k++) {
             const int q = (int)(k % NS);
             const uint32_t par = (k / NS) & 1u;
@@ -1995,49 +2034,65 @@ __global__ void __maxnreg__((Geo<float, 2>::MAXREG))
                 break;
             }
             run_stage<R, 2, 1, OPS>(P, X, a, l, acc0, acc1, acc2);
+            if (pending >= 0 && !finish((unsigned)pending)) {
+                ok = false;
+                break;
+            }
+            pending = -1;
             compute_sync<NTHR>();
             // stage 2: local bits 8..11, then the exchange
             load_regs<R, 2, 2>(X.sv0, sb2, a);
             load_regs<R, 2, 2>(X.sv1, sb2, l);
-            compute_sync<NTHR>();  // this CTA's stage-2 reads are done
+            fence_proxy_async_smem();  // these reads precede the peers' asynchronous stores
+            compute_sync<NTHR>();      // this CTA's stage-2 reads are done
             if (tid < CLUSTER_CTAS)
                 mbar_arrive_remote(map_to_cta(smem_u32(&xl[q]), (uint32_t)tid));
+            open_tile = (long long)k;
             mix_regs<R, 2, 2>(P, X.cb, X.tq, X.f, X.run, a, l, acc0);
+            run_after2 = X.run;
             const bool wl = mbar_wait_cluster_bounded(&xl[q], par);
             if (compute_sync_or<NTHR>(!wl)) {
                 ok = false;
                 break;
             }
-            const uint32_t base0 = smem_u32(X.sv0), base1 = smem_u32(X.sv1);
+            if (tid == 0)  // 4 quarters x 2 vectors land here, each with its byte count
+                mbar_arrive_expect_tx(&xw[q], 2 * TB);
+            // 16-byte stores: lane bit 0 is local bit 0, so a lane pair holds
+            // two neighbouring amplitudes of every register; one shuffle per
+            // register pair gives the even lane register m's pair and the odd
+            // lane register m+1's (both go to the same CTA: bits 10, 11 agree)
+            const uint32_t base0 = smem_u32(X.sv0), base1 = smem_u32(X.sv1), xwa = smem_u32(&xw[q]);
+            const bool odd = tid & 1;
 #pragma unroll
-            for (int m = 0; m < NR; m++) {
-                const uint32_t idx = smem_index<G, 2>(sbh2, sbl2, m);
+            for (int m = 0; m < NR; m += 2) {
+                const uint32_t idx = smem_index<G, 2>(sbh2, sbl2, odd ? m + 1 : m) & ~1u;
                 const uint32_t dst_cta = (idx >> 10) & 3u;
                 const uint32_t dst = ((idx & ~(3u << 10)) | (rank << 10)) * (uint32_t)sizeof(C);
-                st_cluster(map_to_cta(base0 + dst, dst_cta), a[m]);
-                st_cluster(map_to_cta(base1 + dst, dst_cta), l[m]);
+                const uint32_t bar = map_to_cta(xwa, dst_cta);
+                const C sa = odd ? a[m] : a[m + 1], sl = odd ? l[m] : l[m + 1];
+                C ra, rl;
+                ra.x = __shfl_xor_sync(0xffffffffu, sa.x, 1);
+                ra.y = __shfl_xor_sync(0xffffffffu, sa.y, 1);
+                rl.x = __shfl_xor_sync(0xffffffffu, sl.x, 1);
+                rl.y = __shfl_xor_sync(0xffffffffu, sl.y, 1);
+                const float4 va = odd ? make_float4(ra.x, ra.y, a[m + 1].x, a[m + 1].y)
+                                      : make_float4(a[m].x, a[m].y, ra.x, ra.y);
+                const float4 vl = odd ? make_float4(rl.x, rl.y, l[m + 1].x, l[m + 1].y)
+                                      : make_float4(l[m].x, l[m].y, rl.x, rl.y);
+                st_async_cluster4(map_to_cta(base0 + dst, dst_cta), va, bar);
+                st_async_cluster4(map_to_cta(base1 + dst, dst_cta), vl, bar);
             }
-            asm volatile("fence.acq_rel.cluster;" ::: "memory");
-            compute_sync<NTHR>();
-            if (tid < CLUSTER_CTAS)
-                mbar_arrive_remote(map_to_cta(smem_u32(&xw[q]), (uint32_t)tid));
-            const bool ww = mbar_wait_cluster_bounded(&xw[q], par);
-            if (compute_sync_or<NTHR>(!ww)) {
-                ok = false;
-                break;
-            }
-            // stage 3: qubits 12, 13 at local bits 10, 11
-            load_regs<R, 2, 2>(X.sv0, sb2, a);
-            load_regs<R, 2, 2>(X.sv1, sb2, l);
-            mix_regs<R, 2, 3>(P, X.cb, X.tq, X.f, X.run, a, l, acc0);
-            store_regs<R, 2, 2>(X.sv0, sb2, a);
-            store_regs<R, 2, 2>(X.sv1, sb2, l);
-            fence_proxy_async_smem();
-            mbar_arrive(&done[q]);
+            pending = (long long)k;
         }
+        if (ok && pending >= 0 && !finish((unsigned)pending))
+            ok = false;
         if (!ok && tid == 0) {
             atomicExch(A.err, 1);
             s_flag = 1;
+            // peers that passed this tile's xl may have asynchronous stores in
+            // flight into this CTA: give them time to land before it leaves
+            if (open_tile >= 0)
+                mbar_wait_bounded(&xw[(int)(open_tile % NS)], (unsigned)((open_tile / NS) & 1));
         }
         // this CTA's dE/dbeta partial (slot 0)
         double s0 = acc0.get();

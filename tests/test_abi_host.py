@@ -129,6 +129,19 @@ def test_prepare_multi_names_the_bad_graph():
     h = ctypes.c_void_p()
     assert N.aaqaoa_prepare_multi(3, descs, 1, 0, None, ctypes.byref(h)) == -1
     assert b"graph 2" in N.aaqaoa_last_error_detail()
+    # the optional class of every edge is checked like aaqaoa_prepare's
+    rep, wt = (np.ascontiguousarray(np.array(v, dtype=np.int32)) for v in ([0], [2]))
+    # (on a host without a GPU a valid batch stops later, at stream creation: ERR_CUDA)
+    for eo_vals, codes in (([0, 0], (0, -4)), ([0, 1], (-2,))):
+        eo = np.ascontiguousarray(np.array(eo_vals, dtype=np.int32))
+        descs = (N.GraphDesc * 1)()
+        descs[0].n, descs[0].num_edges, descs[0].edges = 3, 2, P(good)
+        descs[0].num_orbits, descs[0].orbit_rep, descs[0].orbit_weight, descs[0].edge_orbit = 1, P(rep), P(wt), P(eo)
+        h = ctypes.c_void_p()
+        rc = N.aaqaoa_prepare_multi(1, descs, 1, 0, None, ctypes.byref(h))
+        assert rc in codes, N.aaqaoa_last_error_detail()
+        if rc == 0:
+            N.aaqaoa_destroy_multi(h)
 
 
 def _handle(n, edges, p):
