@@ -618,6 +618,24 @@ def profile_case(n, precision="c64"):
     print(json.dumps({"profile_case": n, "E": E, "dgamma": list(dg), "dbeta": list(db)}))
 
 
+def profile_cluster(n):
+    """Two energy+gradient evaluations (p = 2, H_red) of the star on n qubits
+    with the adjoint's 14-qubit cluster low pass (a small case for ncu)."""
+    import torch
+    from paper_2410_22247_gb300 import orbits as ORB
+    from paper_2410_22247_gb300 import workloads as W
+    from paper_2410_22247_gb300.api import Plan
+    nn, e = W.star_graph(n)
+    pl = Plan(nn, e, P_LAYERS, orbits=ORB.edge_orbits(nn, e), precision="c64", with_grad=True)
+    pl.set_pass_plan(0, 0, 14, -(-(n - 14) // 8))
+    g, b = W.random_angles(P_LAYERS, 3)
+    for _ in range(2):
+        E, dg, db = pl.grad(g, b, "red")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_cluster": n, "plan": list(pl.pass_plan()), "E": E, "dgamma": list(dg),
+                      "dbeta": list(db)}))
+
+
 def profile_landscape(points):
     """Two calls of the p = 1 landscape on the star S_19 (n = 20) over the
     first `points` points of the 64 x 64 grid (a small case for ncu)."""
@@ -646,6 +664,9 @@ def main():
                     help="run two energy+gradient evaluations of the star on N qubits (a small case for ncu) and exit")
     ap.add_argument("--profile-precision", default="c64", choices=["c64", "c128"],
                     help="precision of the --profile-case evaluations")
+    ap.add_argument("--profile-cluster", type=int, default=0, metavar="N",
+                    help="run two energy+gradient evaluations of the star on N qubits with the adjoint's cluster "
+                         "low pass (a small case for ncu) and exit")
     ap.add_argument("--profile-landscape", type=int, default=0, metavar="B",
                     help="run two calls of the S_19 landscape over B points (a small case for ncu) and exit")
     args = ap.parse_args()
@@ -654,6 +675,9 @@ def main():
         return
     if args.profile_landscape:
         profile_landscape(args.profile_landscape)
+        return
+    if args.profile_cluster:
+        profile_cluster(args.profile_cluster)
         return
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
