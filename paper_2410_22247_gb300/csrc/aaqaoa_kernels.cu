@@ -445,7 +445,7 @@ __host__ __device__ constexpr size_t pass_static_smem()
     using G = Geo<R, NV>;
     return IS ? 2 * G::NSTAGE * 8 + 2 * 3 * 32 * 8 + 4 + 2 * MAXK * 4 + 4 + 4 + 2 * 2 * 2 * 32 * 4 +
                     G::NSTAGE * 2 * 16 * sizeof(R) + G::NSTAGE * 16 * 2 * sizeof(R) + 2 * 32 * sizeof(R) +
-                    2 * 32 * 2 * sizeof(R) + 256
+                    2 * 32 * 2 * sizeof(R) + 2 * MAXN * 8 + 256
               : 2 * G::NSTAGE * 8 + 2 * 3 * 32 * 8 + 4 + 2 * MAXK * 4 + G::NSTAGE * 2 * 16 * 4 +
                     2 * (G::RB + 1) * G::NTHR * 4 + 2 * 2 * 2 * 32 * 4 + 256;
 }
@@ -810,11 +810,10 @@ template <typename R> struct Acc {
 // table or the last pass), so an inner product taken before butterfly j+1 is
 // scaled by f^(2j). In the twisted frame Im<lambda|X_q|phi> sums, over the
 // pairs (x, x'), Re(conj(lambda_x') phi_x) - Re(conj(lambda_x) phi_x').
-template <typename R, int NV, int ST, bool IS = false>
-__device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R &run,
-                                         typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
-                                         typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc,
-                                         bool cot = false)
+template <typename R, int NV, int ST, bool COT>
+__device__ __forceinline__ void mix_regs_form(const PassRegs &A, int cb, R tq, R f, R &run,
+                                              typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
+                                              typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc)
 {
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
@@ -842,12 +841,12 @@ __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R
                 const int c = (m >> (k == 0 ? 1 : 0)) & 1;
                 dot_acc(ipp[c], l[m1], a[m]);
                 dot_acc(ipn[c], l[m], a[m1]);
-                if (IS && cot)
+                if constexpr (COT)
                     rotc(l[m], l[m1], tq);
                 else
                     rot(l[m], l[m1], tq);
             }
-            if (IS && cot)
+            if constexpr (COT)
                 rotc(a[m], a[m1], tq);
             else
                 rot(a[m], a[m1], tq);
@@ -861,6 +860,20 @@ __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R
     run = sc;
     if constexpr (NV == 2)
         acc.add(gb);
+}
+
+// cot (Ising plans only, decided per layer) selects the butterfly form once
+// for the whole stage, outside the unrolled loops
+template <typename R, int NV, int ST, bool IS = false>
+__device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R &run,
+                                         typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
+                                         typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc,
+                                         bool cot = false)
+{
+    if (IS && cot)
+        mix_regs_form<R, NV, ST, true>(A, cb, tq, f, run, a, l, acc);
+    else
+        mix_regs_form<R, NV, ST, false>(A, cb, tq, f, run, a, l, acc);
 }
 
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
@@ -1128,13 +1141,15 @@ __device__ void pass_final_reduce(const PassArgs &A, unsigned total)
 // MODE 0: mixer only; 1: with cut-function work on one graph; 2: the same
 // with point b of the batch being its own graph (A.pt[b]); 3: as 1, and the
 // pass is fused (A.fuse): after the last stage's operations the mixer of
-// layer A.layer2 is applied to the same qubits, last stage first.
+// layer A.layer2 is applied to the same qubits, last stage first. Ising
+// plans: 4 (as 1), 5 (as 3), 6 (as 0), with real-valued cut functions, phase
+// factors built from products and the cot form where a layer needs it.
 template <typename R, int NV, int MODE>
 __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     k_pass(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
            const __grid_constant__ PassArgs A)
 {
-    constexpr bool OPS = MODE != 0, MG = MODE == 2, FUSE = MODE == 3 || MODE == 5, IS = MODE >= 4;
+    constexpr bool OPS = MODE != 0 && MODE != 6, MG = MODE == 2, FUSE = MODE == 3 || MODE == 5, IS = MODE >= 4;
     using G = Geo<R, NV>;
     using C = typename CT<R>::T;
     constexpr int NR = 1 << G::RB, NS = G::NSTAGE, NTHR = G::NTHR;
@@ -1157,6 +1172,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     __shared__ C tps[IS ? NS : 1][16];
     __shared__ R qvs[IS ? 2 : 1][32];
     __shared__ C qps[IS ? 2 : 1][32];
+    __shared__ double isd[IS ? 2 : 1][IS ? MAXN : 1];  // d_u = h_u + sum_v W_uv of both functions
 
     const int tid = threadIdx.x;
     C *tab = reinterpret_cast<C *>(sm + (size_t)NS * NV * TB);
@@ -1305,6 +1321,18 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     auto ising_angle = [&](unsigned b) { return -A.sign_s * A.gam[(size_t)b * A.p + A.tab_layer]; };
     const bool cost_phase = A.pre_phase || (A.post & (POST_PHASE | POST_PHASE_CONJ));
     if constexpr (IS) {
+        // flip costs from the all-zero state, for the producer's tile constants
+        if (tid < 2 * MAXN) {
+            const int e = tid / MAXN, u = tid % MAXN;
+            if (est[e] >= 0 && u < A.n) {
+                const IsingFn *F = ising_fn(e);
+                double d = F->h[u];
+                for (int v = 0; v < A.n; v++)
+                    d += F->W[u][v];
+                isd[e][u] = d;
+            }
+        }
+        __syncthreads();
         if (tid < NTHR) {
             for (int e = 0; e < 2; e++) {
                 if (est[e] < 0)
@@ -1338,9 +1366,13 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         // warp computes each tile's cut constants O(f), h_u(f) before the
         // tile's buffer is handed over (the arrive on full[s] releases them).
         const int lane = tid - NTHR;
-        // Ising plans: O(f) and h_L(f) in FP64 (lanes over vertices), rounded
-        // once to R, and for the cost the unit phase factors of this tile's
-        // point (O(f)'s carrying the table's scale f^n)
+        // Ising plans: O(f) and h_L(f) in FP64, rounded once to R, and for the
+        // cost the unit phase factors of this tile's point (O(f)'s carrying
+        // the table's scale f^n). With g_u(f) = sum_{v in f} W_uv and
+        // d_u = h_u + sum_v W_uv (the flip cost of u from an all-zero state):
+        //   O(f) = sum_{u in f} (d_u - g_u(f)),   h_u(f) = d_u - 2 g_u(f),
+        // since [f_u != f_v] = f_u + f_v - 2 f_u f_v. Lanes take vertices;
+        // every lane loops over the same set bits of f.
         auto tile_consts_ising = [&](unsigned k, int s) {
             unsigned b, t, mid;
             int c4;
@@ -1350,27 +1382,32 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 if (est[e] < 0)
                     continue;
                 const IsingFn *F = ising_fn(e);
-                double os = 0.0;
-                for (int u = lane; u < A.n; u += 32) {
-                    const bool fu = (f >> u) & 1ull;
-                    double su = fu ? F->h[u] : 0.0;
-                    for (int v = u + 1; v < A.n; v++)
-                        if ((bool)((f >> v) & 1ull) != fu)
-                            su += F->W[u][v];
-                    os += su;
+                double os = 0.0, hl[2] = {0.0, 0.0};  // lane's vertices u = lane, lane + 32
+                for (int j = 0; j < 2; j++) {
+                    const int u = lane + 32 * j;
+                    if (u >= A.n)
+                        continue;
+                    double g = 0.0;
+                    const double d = isd[e][u];
+                    for (uint64_t rest = f; rest; rest &= rest - 1)
+                        g += F->W[u][__ffsll((long long)rest) - 1];
+                    if ((f >> u) & 1ull)
+                        os += d - g;
+                    hl[j] = d - 2.0 * g;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
                     os += __shfl_xor_sync(0xffffffffu, os, o);
+                // h_L(f) of local bit L (vertex gq(L)) from the lane holding that vertex
                 double hs = 0.0;
-                if (lane < G::T) {
-                    const int u = gq(lane);
-                    hs = F->h[u];
-                    for (int v = 0; v < A.n; v++)
-                        if (v != u)
-                            hs += ((f >> v) & 1ull) ? -F->W[u][v] : F->W[u][v];
-                    tvs[s][e][lane] = (R)hs;
+                {
+                    const int u = lane < G::T ? gq(lane) : 0;
+                    const double h0 = __shfl_sync(0xffffffffu, hl[0], u & 31);
+                    const double h1 = __shfl_sync(0xffffffffu, hl[1], u & 31);
+                    hs = u < 32 ? h0 : h1;
                 }
+                if (lane < G::T)
+                    tvs[s][e][lane] = (R)hs;
                 if (lane == 0)
                     tvs[s][e][15] = (R)os;
                 if (e == 0 && cost_phase) {
@@ -2684,7 +2721,7 @@ static int launch_pass_t(const CUtensorMap &m0, const CUtensorMap &m1, const Pas
             return (int)cudaErrorInvalidValue;
         if (a.fuse)
             return a.is_low ? (int)cudaErrorInvalidValue : launch_pass_ops<R, NV, 5>(m0, m1, a, grid, st);
-        return launch_pass_ops<R, NV, 4>(m0, m1, a, grid, st);
+        return ops ? launch_pass_ops<R, NV, 4>(m0, m1, a, grid, st) : launch_pass_ops<R, NV, 6>(m0, m1, a, grid, st);
     }
     if (!ops)
         return launch_pass_ops<R, NV, 0>(m0, m1, a, grid, st);
