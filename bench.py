@@ -725,14 +725,16 @@ def main():
                                  "adjoint_high_passes": result["pass_plan"][3], "chosen_by": "autotune",
                                  "layer_fusion": result["layer_fusion"],
                                  "passes_forward_adjoint": result["launches_per_sweep"]}},
-        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "frac_basis": "bytes the kernel streams (vectors loaded + stored per launch)",
-                     "achieved_algorithmic": adj_alg_gbps,
-                     "frac_algorithmic": (adj_alg_gbps / peak) if adj_alg_gbps else None,
-                     "algorithmic_bytes_per_step": adj_alg, "algorithmic_formula": "(4p+1)*2^n*8",
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": adj_alg_gbps, "peak": peak,
+                     "unit": "GB/s", "frac": (adj_alg_gbps / peak) if adj_alg_gbps else None,
+                     "peak_source": peak_kind,
+                     "frac_basis": "algorithmic bytes of the adjoint per step, (4p+1)*2^n*8 (lambda written once, "
+                                   "phi and lambda read and written once per layer), over its launches' time",
+                     "algorithmic_bytes_per_step": adj_alg, "algorithmic_bytes_per_launch": adj_alg / (d["launches"] / K),
+                     "achieved_streamed": achieved, "frac_streamed": achieved / peak,
+                     "streamed_basis": "bytes the kernel streams (vectors loaded + stored per launch)",
                      "traffic": traffic_from_profiles(),
-                     "bytes_per_launch": d["bytes"] / d["launches"], "launches": d["launches"]},
+                     "streamed_bytes_per_launch": d["bytes"] / d["launches"], "launches": d["launches"]},
         "step_algorithmic": {"bytes": B_alg, "formula": "(6p+1)*2^n*8", "GBps": step_gbps,
                              "frac": step_gbps / peak},
         "error_vs_oracle": errs,
