@@ -183,3 +183,19 @@ def test_ising_unsupported_calls_are_reported():
     with pytest.raises(AAQAOAError, match="UNSUPPORTED"):
         pl.sample([0.1], [0.2], [0.5])
     assert np.isfinite(pl.expect([0.1], [0.2]))
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_ising_full_size_regular3_n30_matches_light_cones(precision):
+    """The bench's Ising workload: random 3-regular n = 30 with seeded real
+    couplings and fields, p = 2, against per-term light cones (Sec. 5.1; a
+    ZZ term's ball has at most 14 vertices, a field term's at most 10)."""
+    from oracle import lightcone as LC
+    n, e = W.random_regular(30, 3, 0)
+    w, h = W.ising_couplings(n, e, 30)
+    g, b = W.random_angles(2, 5)
+    ref = LC.ising_energy_grad(n, e, w, h, g, b)
+    pl = plan_for(n, e, w, h, 2, precision)
+    check(pl.grad(g, b, "full"), ref, scale(w, h), precision)
+    assert abs(pl.expect(g, b, "full") - ref[0]) <= TOL[precision] * scale(w, h)
+    pl.close()
