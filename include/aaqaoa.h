@@ -536,6 +536,21 @@ int aaqaoa_profile_enable(aaqaoa_plan *plan, int enable);
 int aaqaoa_profile_read(aaqaoa_plan *plan, int kind, double *ms_total, int *launches, double *bytes);
 
 /*
+ * aaqaoa_stats -- all kinds of aaqaoa_profile_read at once: per kind (index
+ * as above) the launches recorded since profiling was enabled, their summed
+ * event durations (ms) and the bytes they had to move. out: host struct.
+ * Synchronises the plan's stream (so the plan is not const). INVALID_ARG for
+ * a NULL plan or out; all zero when profiling was never enabled.
+ */
+#define AAQAOA_STAT_KINDS 5
+typedef struct {
+    int launches[AAQAOA_STAT_KINDS];
+    double ms[AAQAOA_STAT_KINDS];
+    double bytes[AAQAOA_STAT_KINDS];
+} aaqaoa_stats_t;
+int aaqaoa_stats(aaqaoa_plan *plan, aaqaoa_stats_t *out);
+
+/*
  * aaqaoa_profile_launches -- the recorded launches one by one, in launch
  * order: per launch its kind (as above), flags (bit 0: the pass carries
  * cut-function work -- phase, lambda = O phi, energy, dE/dgamma, inverse

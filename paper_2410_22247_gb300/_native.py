@@ -28,6 +28,11 @@ ERRORS = {
     -4: "AAQAOA_ERR_CUDA", -5: "AAQAOA_ERR_TIMEOUT", -6: "AAQAOA_ERR_UNSUPPORTED",
 }
 
+class Stats(ctypes.Structure):
+    """aaqaoa_stats_t"""
+    _fields_ = [("launches", ctypes.c_int * 5), ("ms", ctypes.c_double * 5), ("bytes", ctypes.c_double * 5)]
+
+
 class GraphDesc(ctypes.Structure):
     """aaqaoa_graph_desc"""
     _fields_ = [("n", ctypes.c_int), ("num_edges", ctypes.c_int), ("edges", ctypes.POINTER(ctypes.c_int32)),
@@ -89,6 +94,7 @@ _PROTOS = [
     ("aaqaoa_launch_count", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     ("aaqaoa_profile_enable", ctypes.c_int, [_vp, ctypes.c_int]),
     ("aaqaoa_profile_read", ctypes.c_int, [_vp, ctypes.c_int, _f64p, ctypes.POINTER(ctypes.c_int), _f64p]),
+    ("aaqaoa_stats", ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     ("aaqaoa_profile_launches", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i32p, _i32p, _f64p,
                                                _f64p]),
     ("aaqaoa_destroy", None, [_vp]),

@@ -1781,6 +1781,19 @@ int aaqaoa_profile_read(aaqaoa_plan *pl, int kind, double *ms_total, int *launch
     return AAQAOA_OK;
 }
 
+int aaqaoa_stats(aaqaoa_plan *pl, aaqaoa_stats_t *out)
+{
+    if (!pl || !out)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan or out is NULL");
+    static_assert(AAQAOA_STAT_KINDS == PK_COUNT, "one stats entry per kernel kind");
+    for (int k = 0; k < PK_COUNT; k++) {
+        int r = aaqaoa_profile_read(pl, k, &out->ms[k], &out->launches[k], &out->bytes[k]);
+        if (r)
+            return r;
+    }
+    return AAQAOA_OK;
+}
+
 int aaqaoa_profile_launches(aaqaoa_plan *pl, int max, int *count, int *kind, int *flags, double *ms, double *bytes)
 {
     if (!pl || !count || max < 0)

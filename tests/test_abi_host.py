@@ -354,3 +354,18 @@ def test_cluster_low_pass_plan_and_schedule():
                         mixed |= set(range(s0, s0 + q))
                 assert mixed == set(range(n))
         N.aaqaoa_destroy(h)
+
+
+def test_stats_summarises_an_unprofiled_plan_as_zero():
+    """aaqaoa_stats (host-side only here: a plan without a workspace and
+    without recorded launches) fills every kind with zeros; NULL is rejected."""
+    h = _handle(*W.cycle_graph(16), p=1)
+    try:
+        st = N.Stats()
+        rc = N.aaqaoa_stats(h, ctypes.byref(st))
+        assert rc in (0, -4)  # -4 (CUDA error): no device to synchronise with on this host
+        if rc == 0:
+            assert list(st.launches) == [0] * 5 and list(st.ms) == [0.0] * 5
+        assert N.aaqaoa_stats(h, None) == -1
+    finally:
+        N.aaqaoa_destroy(h)
