@@ -810,7 +810,19 @@ template <typename R> struct Acc {
 // table or the last pass), so an inner product taken before butterfly j+1 is
 // scaled by f^(2j). In the twisted frame Im<lambda|X_q|phi> sums, over the
 // pairs (x, x'), Re(conj(lambda_x') phi_x) - Re(conj(lambda_x) phi_x').
-template <typename R, int NV, int ST, bool COT>
+// DUE >= 0: which owned bits are due is fixed at compile time -- all but the
+// first DUE owned bits of the stage (the pass shapes the planner makes); DUE
+// = -1: decided per bit at run time from A.is_low, A.hmask and cb (any plan).
+template <typename G>
+__host__ __device__ constexpr int first_owned(int st)
+{
+    int k = 0;
+    while (k < G::RB && !((G::own(st) >> k) & 1))
+        k++;
+    return k;
+}
+
+template <typename R, int NV, int ST, bool COT, int DUE>
 __device__ __forceinline__ void mix_regs_form(const PassRegs &A, int cb, R tq, R f, R &run,
                                               typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                               typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc)
@@ -824,7 +836,9 @@ __device__ __forceinline__ void mix_regs_form(const PassRegs &A, int cb, R tq, R
         if (!((G::own(ST) >> k) & 1))
             continue;
         bool due = true;
-        if (G::reg(ST, k) >= cb)
+        if constexpr (DUE >= 0)
+            due = k >= first_owned<G>(ST) + DUE;
+        else if (G::reg(ST, k) >= cb)
             due = (A.hmask >> (G::reg(ST, k) - cb)) & 1;
         else
             due = A.is_low;
@@ -864,16 +878,16 @@ __device__ __forceinline__ void mix_regs_form(const PassRegs &A, int cb, R tq, R
 
 // cot (Ising plans only, decided per layer) selects the butterfly form once
 // for the whole stage, outside the unrolled loops
-template <typename R, int NV, int ST, bool IS = false>
+template <typename R, int NV, int ST, bool IS = false, int DUE = -1>
 __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R &run,
                                          typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                          typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc,
                                          bool cot = false)
 {
     if (IS && cot)
-        mix_regs_form<R, NV, ST, true>(A, cb, tq, f, run, a, l, acc);
+        mix_regs_form<R, NV, ST, true, DUE>(A, cb, tq, f, run, a, l, acc);
     else
-        mix_regs_form<R, NV, ST, false>(A, cb, tq, f, run, a, l, acc);
+        mix_regs_form<R, NV, ST, false, DUE>(A, cb, tq, f, run, a, l, acc);
 }
 
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
@@ -881,7 +895,7 @@ __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R
 // layer's butterflies of the same stage follow, their dE/dbeta into acc2.
 // IS: an Ising plan (real values, phases as products of unit factors, cot form
 // of the rotation where the layer needs it).
-template <typename R, int NV, int ST, bool OPS, bool FUSE = false, bool IS = false>
+template <typename R, int NV, int ST, bool OPS, bool FUSE = false, bool IS = false, int DUE = -1>
 __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                           typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc0,
@@ -956,7 +970,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         }
     }
 
-    mix_regs<R, NV, ST, IS>(A, X.cb, X.tq, X.f, X.run, a, l, acc0, X.cot);
+    mix_regs<R, NV, ST, IS, DUE>(A, X.cb, X.tq, X.f, X.run, a, l, acc0, X.cot);
 
     if (OPS && LAST && (A.post & POST_RESCALE)) {  // the stored state is the exact one
 #pragma unroll
@@ -1007,7 +1021,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         }
     }
     if constexpr (FUSE && LAST)
-        mix_regs<R, NV, ST, IS>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2, X.cot2);
+        mix_regs<R, NV, ST, IS, DUE>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2, X.cot2);
     if (!LAST || A.write) {
         store_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
@@ -1016,7 +1030,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
 }
 
 // A stage of the second layer of a fused pass: load, its butterflies, store.
-template <typename R, int NV, int ST, bool IS = false>
+template <typename R, int NV, int ST, bool IS = false, int DUE = -1>
 __device__ __forceinline__ void mix_stage(const PassRegs &A, StageCtx<R> &X,
                                           typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                           typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc2)
@@ -1027,10 +1041,60 @@ __device__ __forceinline__ void mix_stage(const PassRegs &A, StageCtx<R> &X,
     load_regs<R, NV, ST>(X.sv0, sb, a);
     if constexpr (NV == 2)
         load_regs<R, NV, ST>(X.sv1, sb, l);
-    mix_regs<R, NV, ST, IS>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2, X.cot2);
+    mix_regs<R, NV, ST, IS, DUE>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2, X.cot2);
     store_regs<R, NV, ST>(X.sv0, sb, a);
     if constexpr (NV == 2)
         store_regs<R, NV, ST>(X.sv1, sb, l);
+}
+
+// Which owned bits of stage st a pass with this shape transforms: 0 every
+// owned bit, 1 all but the first, -1 another set. A high pass transforms the
+// tile bits from cb up, a low pass those below cb plus the high bits in hmask.
+template <typename G>
+__host__ __device__ inline int due_form(int st, int is_low, int hmask, int cb)
+{
+    uint32_t own = 0, due = 0;
+    for (int k = 0; k < G::RB; k++) {
+        if (!((G::own(st) >> k) & 1))
+            continue;
+        own |= 1u << k;
+        const int bit = G::reg(st, k);
+        if (bit >= cb ? ((hmask >> (bit - cb)) & 1) : is_low)
+            due |= 1u << k;
+    }
+    return due == own ? 0 : due == (own & (own - 1u)) ? 1 : -1;
+}
+
+// A register stage in the compiled form of its due pattern d (complex64: the
+// run-time checks cost about a third of a stage's time; complex128 passes are
+// bound by FP64 arithmetic and keep the checks).
+template <typename R, int NV, int ST, bool OPS, bool FUSE, bool IS>
+__device__ __forceinline__ void run_stage_due(int d, const PassRegs &A, StageCtx<R> &X,
+                                              typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
+                                              typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc0,
+                                              Acc<R> &acc1, Acc<R> &acc2)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        if (d == 0)
+            return run_stage<R, NV, ST, OPS, FUSE, IS, 0>(A, X, a, l, acc0, acc1, acc2);
+        if (d == 1)
+            return run_stage<R, NV, ST, OPS, FUSE, IS, 1>(A, X, a, l, acc0, acc1, acc2);
+    }
+    run_stage<R, NV, ST, OPS, FUSE, IS, -1>(A, X, a, l, acc0, acc1, acc2);
+}
+
+template <typename R, int NV, int ST, bool IS>
+__device__ __forceinline__ void mix_stage_due(int d, const PassRegs &A, StageCtx<R> &X,
+                                              typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
+                                              typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc2)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        if (d == 0)
+            return mix_stage<R, NV, ST, IS, 0>(A, X, a, l, acc2);
+        if (d == 1)
+            return mix_stage<R, NV, ST, IS, 1>(A, X, a, l, acc2);
+    }
+    mix_stage<R, NV, ST, IS, -1>(A, X, a, l, acc2);
 }
 
 // Named barrier 1 spans the NTHR compute threads only (the producer warp
@@ -1601,6 +1665,9 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             pend_b = -1;
         };
 
+        // the compiled form of each stage's butterflies for this pass's shape
+        const int d0 = due_form<G>(0, A.is_low, A.hmask, cb), d1 = due_form<G>(1, A.is_low, A.hmask, cb),
+                  d2 = due_form<G>(2, A.is_low, A.hmask, cb);
         bool ok = true;
         for (unsigned k = 0; k < niter; k++) {
             unsigned b, t, mid;
@@ -1692,16 +1759,16 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             bool bad;
             X.run2 = (R)1;
             if (!FUSE && P.is_low) {
-                run_stage<R, NV, 0, OPS, false, IS>(P, X, a, l, acc0, acc1, acc2);
+                run_stage_due<R, NV, 0, OPS, false, IS>(d0, P, X, a, l, acc0, acc1, acc2);
                 X.first = false;
                 bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
                 if (!bad) {
-                    run_stage<R, NV, 1, OPS, false, IS>(P, X, a, l, acc0, acc1, acc2);
+                    run_stage_due<R, NV, 1, OPS, false, IS>(d1, P, X, a, l, acc0, acc1, acc2);
                     if (!P.skip_last)
                         compute_sync<NTHR>();
                 }
             } else {  // a high pass (every fused pass is one)
-                run_stage<R, NV, 1, OPS, false, IS>(P, X, a, l, acc0, acc1, acc2);
+                run_stage_due<R, NV, 1, OPS, false, IS>(d1, P, X, a, l, acc0, acc1, acc2);
                 X.first = false;
                 bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
             }
@@ -1714,11 +1781,11 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 break;
             }
             if (FUSE) {  // layer `layer` ends in stage 2, layer2 starts there and ends in stage 1
-                run_stage<R, NV, 2, OPS, true, IS>(P, X, a, l, acc0, acc1, acc2);
+                run_stage_due<R, NV, 2, OPS, true, IS>(d2, P, X, a, l, acc0, acc1, acc2);
                 compute_sync<NTHR>();
-                mix_stage<R, NV, 1, IS>(P, X, a, l, acc2);
+                mix_stage_due<R, NV, 1, IS>(d1, P, X, a, l, acc2);
             } else if (!P.skip_last) {  // a low pass over the qubits of stages 0 and 1 only ends here
-                run_stage<R, NV, 2, OPS, false, IS>(P, X, a, l, acc0, acc1, acc2);
+                run_stage_due<R, NV, 2, OPS, false, IS>(d2, P, X, a, l, acc0, acc1, acc2);
             }
             // results (if any) are in the buffer: hand it to the producer
             fence_proxy_async_smem();
