@@ -1195,6 +1195,23 @@ __device__ void pass_final_reduce(const PassArgs &A, unsigned total)
         *A.counter = 0u;
 }
 
+// A pass's operation flags as one word: load, pre_phase, pre_lambda and
+// write in bits 0-3, the PostOp bits from bit 4. The complex64 kernels run the
+// flag words of the planner's usual passes in a compute loop compiled for
+// them (branches and the code of operations not taken leave the per-tile
+// path); any other word runs the loop that reads the flags at run time.
+__host__ __device__ constexpr int flag_word(int load, int pre_phase, int pre_lambda, int write, int post)
+{
+    return (load ? 1 : 0) | (pre_phase ? 2 : 0) | (pre_lambda ? 4 : 0) | (write ? 8 : 0) | (post << 4);
+}
+constexpr int FW_FWD_FIRST = flag_word(0, 1, 0, 1, 0);                          // |+> generated, first phase
+constexpr int FW_FWD_LAST = flag_word(1, 0, 0, 1, POST_REDUCE | POST_RESCALE);  // energy, state kept
+constexpr int FW_FWD_ENERGY = flag_word(1, 0, 0, 0, POST_REDUCE);               // energy only
+constexpr int FW_FWD_FUSED = flag_word(1, 0, 0, 1, POST_PHASE);
+constexpr int FW_ADJ_FIRST = flag_word(1, 0, 1, 1, 0);                          // lambda = O phi
+constexpr int FW_ADJ_LAST = flag_word(1, 0, 0, 0, POST_GAMMA);                  // layer 0 ends
+constexpr int FW_ADJ_BOUNDARY = flag_word(1, 0, 0, 1, POST_GAMMA | POST_PHASE_CONJ);
+
 // Persistent tiled pass over A.B statevectors, warp-specialised. CTA c takes
 // tiles c, c+G, c+2G, ... (G = gridDim.x) of the B x tiles sequence. The last
 // warp is the producer: its lane 0 keeps NSTAGE tiles in flight (TMA loads)
@@ -1597,8 +1614,16 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         }
     } else {
         // ------------------------------------------------------- compute
-        const PassRegs P{A.n, A.s, A.is_low, A.hmask, A.load, A.pre_phase, A.pre_lambda, A.write, A.post, A.j0,
-                         A.skip_last, A.amp0};
+        // FL: the flag word this loop is compiled for, or -1 (read from A)
+        auto compute = [&](auto flc) {
+        constexpr int FL = decltype(flc)::value;
+        const PassRegs P{A.n, A.s, A.is_low, A.hmask,
+                         FL < 0 ? A.load : (FL & 1),
+                         FL < 0 ? A.pre_phase : (FL >> 1) & 1,
+                         FL < 0 ? A.pre_lambda : (FL >> 2) & 1,
+                         FL < 0 ? A.write : (FL >> 3) & 1,
+                         FL < 0 ? A.post : FL >> 4,
+                         A.j0, A.skip_last, A.amp0};
         Acc<R> acc0, acc1, acc2;
         acc0.zero();
         acc1.zero();
@@ -1796,6 +1821,31 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             compute_sync<NTHR>();
             write_pending();
         }
+        };
+        const int fw = flag_word(A.load, A.pre_phase, A.pre_lambda, A.write, A.post);
+        using std::integral_constant;
+        bool compiled = false;
+        auto run_if = [&](auto flc) {
+            if (!compiled && fw == decltype(flc)::value) {
+                compute(flc);
+                compiled = true;
+            }
+        };
+        if constexpr (std::is_same<R, float>::value && MODE == 1 && NV == 1) {
+            run_if(integral_constant<int, FW_FWD_FIRST>{});
+            run_if(integral_constant<int, FW_FWD_LAST>{});
+            run_if(integral_constant<int, FW_FWD_ENERGY>{});
+        }
+        if constexpr (std::is_same<R, float>::value && MODE == 3 && NV == 1)
+            run_if(integral_constant<int, FW_FWD_FUSED>{});
+        if constexpr (std::is_same<R, float>::value && MODE == 1 && NV == 2) {
+            run_if(integral_constant<int, FW_ADJ_FIRST>{});
+            run_if(integral_constant<int, FW_ADJ_LAST>{});
+        }
+        if constexpr (std::is_same<R, float>::value && MODE == 3 && NV == 2)
+            run_if(integral_constant<int, FW_ADJ_BOUNDARY>{});
+        if (!compiled)
+            compute(integral_constant<int, -1>{});
     }
     __syncthreads();
     if (s_flag)
