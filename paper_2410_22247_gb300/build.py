@@ -1,6 +1,7 @@
 """Build the CUDA library ``libaaqaoa.so`` in-tree for sm_103a.
 
-The translation units (kernels, host ABI, host orbit finder) are compiled in parallel with nvcc
+The translation units (pass kernel instantiations per precision and vector count, the other
+kernels, host ABI, host orbit finder) are compiled in parallel with nvcc
 and linked into ``paper_2410_22247_gb300/_lib/libaaqaoa.so``. The build is
 skipped when the library is newer than every source.
 """
@@ -35,7 +36,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    deps = (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            glob.glob(os.path.join(INCLUDE, "*.h")))
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -1,5 +1,6 @@
 // Internal declarations shared by the host side (aaqaoa_host.cu) and the
-// kernels (aaqaoa_kernels.cu). Not part of the public ABI.
+// kernels (aaqaoa_pass.cuh, aaqaoa_pass_*.cu, aaqaoa_kernels.cu). Not part
+// of the public ABI.
 #pragma once
 
 #include <cuda.h>
@@ -148,7 +149,7 @@ struct AggArgs {
     CutFn obs;           // fused mode
 };
 
-// Launchers (aaqaoa_kernels.cu). They return a cudaError_t as int.
+// Launchers (aaqaoa_kernels.cu, aaqaoa_pass_*.cu). They return a cudaError_t as int.
 int tile_bits(bool c128);
 void pass_geometry(bool c128, int nv, int *T, int *CB, int *HB);
 int low_two_stage_bits(bool c128, int nv);
@@ -158,6 +159,17 @@ int launch_params(bool c128, int B, int p, int tab_len, int n, const double *d_g
                   void *d_tab, double2 *d_cs, cudaStream_t st);
 int launch_pass(bool c128, int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a,
                 int grid, cudaStream_t st);
+// the pass instantiations, one unit each: complex64 cut-function plans
+// forward and adjoint, complex64 Ising plans forward and adjoint,
+// complex128 (both kinds)
+int launch_pass_c64_fwd(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid, cudaStream_t st);
+int launch_pass_c64_adj(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid, cudaStream_t st);
+int launch_pass_c64_ising_fwd(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
+                              cudaStream_t st);
+int launch_pass_c64_ising_adj(const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
+                              cudaStream_t st);
+int launch_pass_c128(int nv_kernel, const CUtensorMap &m0, const CUtensorMap &m1, const PassArgs &a, int grid,
+                     cudaStream_t st);
 // The adjoint's complex64 low pass over 14 qubits by clusters of 4 CTAs: maps
 // = {load phi, load lambda, store phi, store lambda}; one parameter point.
 int launch_cluster_pass(const CUtensorMap *maps, const PassArgs &a, cudaStream_t st);
