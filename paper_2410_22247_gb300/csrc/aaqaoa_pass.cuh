@@ -1620,211 +1620,211 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         // ------------------------------------------------------- compute
         // FL: the flag word this loop is compiled for, or -1 (read from A)
         auto compute = [&](auto flc) {
-        constexpr int FL = decltype(flc)::value;
-        const PassRegs P{A.n, A.s, A.is_low, A.hmask,
-                         FL < 0 ? A.load : (FL & 1),
-                         FL < 0 ? A.pre_phase : (FL >> 1) & 1,
-                         FL < 0 ? A.pre_lambda : (FL >> 2) & 1,
-                         FL < 0 ? A.write : (FL >> 3) & 1,
-                         FL < 0 ? A.post : FL >> 4,
-                         A.j0, A.skip_last, A.amp0};
-        Acc<R> acc0, acc1, acc2;
-        acc0.zero();
-        acc1.zero();
-        acc2.zero();
-        int cur_b = -1;
-        StageCtx<R> X;
-        X.tab = tab;
-        X.ptc = ptc;
-        X.qr = &qr[0][0][0];
-        X.qrf = &qrf[0][0][0];
-        X.ptv = ptv;
-        X.ptp = ptp;
-        X.qv = &qvs[0][0];
-        X.qp = &qps[0][0];
-        X.cot = X.cot2 = false;
-        X.s = A.s;
-        X.cb = cb;
-        X.tid = tid;
-        X.amp0 = (R)A.amp0;
-        X.first = true;
-
-        // A point change costs no extra barrier. The phase table has two
-        // slots (the one being replaced was last read before the previous
-        // barrier), and the finished point's sums are warp-reduced into
-        // pred[parity] and written out by thread 0 after the next barrier.
-        // pred alternates between two buffers, so a warp that stashes the
-        // following point cannot overwrite sums thread 0 has not read yet:
-        // that stash comes after a barrier thread 0 only reaches when done.
-        const int lane = tid & 31, warp = tid >> 5;
-        int pend_b = -1, tslot = 1, par = 1;
-        auto stash = [&](int b) {
-            double s0 = acc0.get(), s1 = acc1.get(), s2 = acc2.get();
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                if constexpr (FUSE)
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            }
-            par ^= 1;
-            if (lane == 0) {
-                pred[par][0][warp] = s0;
-                pred[par][1][warp] = s1;
-                pred[par][2][warp] = s2;
-            }
+            constexpr int FL = decltype(flc)::value;
+            const PassRegs P{A.n, A.s, A.is_low, A.hmask,
+                             FL < 0 ? A.load : (FL & 1),
+                             FL < 0 ? A.pre_phase : (FL >> 1) & 1,
+                             FL < 0 ? A.pre_lambda : (FL >> 2) & 1,
+                             FL < 0 ? A.write : (FL >> 3) & 1,
+                             FL < 0 ? A.post : FL >> 4,
+                             A.j0, A.skip_last, A.amp0};
+            Acc<R> acc0, acc1, acc2;
             acc0.zero();
             acc1.zero();
             acc2.zero();
-            pend_b = b;
-        };
-        auto write_pending = [&]() {  // after a barrier
-            if (pend_b >= 0 && tid == 0) {
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-                for (int w = 0; w < NTHR / 32; w++) {
-                    s0 += pred[par][0][w];
-                    s1 += pred[par][1][w];
-                    s2 += pred[par][2][w];
-                }
-                A.partials[((size_t)0 * A.B + pend_b) * grid + blockIdx.x] = s0;
-                A.partials[((size_t)1 * A.B + pend_b) * grid + blockIdx.x] = s1;
-                if (FUSE)
-                    A.partials[((size_t)2 * A.B + pend_b) * grid + blockIdx.x] = s2;
-            }
-            pend_b = -1;
-        };
+            int cur_b = -1;
+            StageCtx<R> X;
+            X.tab = tab;
+            X.ptc = ptc;
+            X.qr = &qr[0][0][0];
+            X.qrf = &qrf[0][0][0];
+            X.ptv = ptv;
+            X.ptp = ptp;
+            X.qv = &qvs[0][0];
+            X.qp = &qps[0][0];
+            X.cot = X.cot2 = false;
+            X.s = A.s;
+            X.cb = cb;
+            X.tid = tid;
+            X.amp0 = (R)A.amp0;
+            X.first = true;
 
-        // the compiled form of each stage's butterflies for this pass's shape
-        const int d0 = due_form<G>(0, A.is_low, A.hmask, cb), d1 = due_form<G>(1, A.is_low, A.hmask, cb),
-                  d2 = due_form<G>(2, A.is_low, A.hmask, cb);
-        bool ok = true;
-        for (unsigned k = 0; k < niter; k++) {
-            unsigned b, t, mid;
-            int c4;
-            tile_coords(k, b, t, mid, c4);
-            const int s = (int)(k % NS);
-            unsigned char *buf = sm + (size_t)s * NV * TB;
-            bool sync_now = (k == 0);  // launch constants (qr) and the table need a barrier
-            if ((int)b != cur_b) {  // new parameter point: its phase table and mixer angle
-                sync_now = true;
-                if (cur_b >= 0 && reduce)
-                    stash(cur_b);
-                tslot ^= 1;
-                X.tab = tab + tslot * MAXTAB;
-                if constexpr (MG) {  // this point's own graph
-                    if (est[0] >= 0 || est[1] >= 0) {
-                        views(b, curv);
-                        launch_consts(tslot);
-                        X.qr = &qr[tslot][0][0];
-                        X.qrf = &qrf[tslot][0][0];
+            // A point change costs no extra barrier. The phase table has two
+            // slots (the one being replaced was last read before the previous
+            // barrier), and the finished point's sums are warp-reduced into
+            // pred[parity] and written out by thread 0 after the next barrier.
+            // pred alternates between two buffers, so a warp that stashes the
+            // following point cannot overwrite sums thread 0 has not read yet:
+            // that stash comes after a barrier thread 0 only reaches when done.
+            const int lane = tid & 31, warp = tid >> 5;
+            int pend_b = -1, tslot = 1, par = 1;
+            auto stash = [&](int b) {
+                double s0 = acc0.get(), s1 = acc1.get(), s2 = acc2.get();
+    #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                    if constexpr (FUSE)
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                }
+                par ^= 1;
+                if (lane == 0) {
+                    pred[par][0][warp] = s0;
+                    pred[par][1][warp] = s1;
+                    pred[par][2][warp] = s2;
+                }
+                acc0.zero();
+                acc1.zero();
+                acc2.zero();
+                pend_b = b;
+            };
+            auto write_pending = [&]() {  // after a barrier
+                if (pend_b >= 0 && tid == 0) {
+                    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                    for (int w = 0; w < NTHR / 32; w++) {
+                        s0 += pred[par][0][w];
+                        s1 += pred[par][1][w];
+                        s2 += pred[par][2][w];
                     }
+                    A.partials[((size_t)0 * A.B + pend_b) * grid + blockIdx.x] = s0;
+                    A.partials[((size_t)1 * A.B + pend_b) * grid + blockIdx.x] = s1;
+                    if (FUSE)
+                        A.partials[((size_t)2 * A.B + pend_b) * grid + blockIdx.x] = s2;
                 }
-                if constexpr (IS) {
-                    // this point's cost phases of the thread's and the stage's terms
-                    // (each thread writes and reads only its own per-thread entries)
-                    if (cost_phase && est[0] >= 0) {
-                        const double ang = ising_angle(b);
-                        double q, dk[G::RB], qq;
-                        ising_terms(0, est[0], q, dk, qq);
-                        ptp[tid] = unit_phase<R>(ang * q);
-                        for (int kk = 0; kk < G::RB; kk++)
-                            ptp[(1 + kk) * NTHR + tid] = unit_phase<R>(ang * dk[kk]);
-                        if (tid < (1 << G::RB))
-                            qps[tslot][tid] = unit_phase<R>(ang * qq);
-                    }
-                    X.qp = &qps[tslot][0];
-                } else if (A.pre_phase || (A.post & (POST_PHASE_CONJ | POST_PHASE))) {
-                    const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.tab_layer) * A.tab_len;
-                    C *dst = tab + tslot * MAXTAB;
-                    for (int i = tid; i < A.tab_len; i += NTHR)
-                        dst[i] = src[i];
-                }
-                const double2 csd = A.cs[(size_t)b * A.p + A.layer];
-                const double cbv = csd.x, sbv = A.sign_s * csd.y;
-                const bool shifted = fabs(sbv) > fabs(cbv);  // rotate by beta - pi/2 (Ising: cot form)
-                X.cot = IS && shifted;
-                X.tq = shifted ? (R)((IS ? cbv : -cbv) / sbv) : (R)(sbv / cbv);
-                const double f = shifted ? sbv : cbv;
-                double fj = 1.0, fn = 1.0;
-                for (int i = 0; i < A.n; i++) {
-                    if (i < A.j0)
-                        fj *= f;
-                    fn *= f;
-                }
-                X.f = (R)f;
-                X.fn = (R)fn;
-                X.fn2 = (R)(fn * fn);
-                X.scale0 = (R)fj;
-                if constexpr (FUSE) {  // the second layer's rotation
-                    const double2 cs2 = A.cs[(size_t)b * A.p + A.layer2];
-                    const double c2 = cs2.x, s2 = A.sign_s * cs2.y;
-                    const bool sh2 = fabs(s2) > fabs(c2);
-                    X.cot2 = IS && sh2;
-                    X.tq2 = sh2 ? (R)((IS ? c2 : -c2) / s2) : (R)(s2 / c2);
-                    X.f2 = (R)(sh2 ? s2 : c2);
-                }
-                cur_b = (int)b;
-            }
-            X.sv0 = reinterpret_cast<C *>(buf);
-            X.sv1 = reinterpret_cast<C *>(buf + TB);
-            X.tc = &tcs[IS ? 0 : s][0][0];
-            X.tv = &tvs[IS ? s : 0][0][0];
-            X.tp = &tps[IS ? s : 0][0];
-            X.fixed = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
+                pend_b = -1;
+            };
 
-            // No barrier between tiles unless a point starts: a warp may begin
-            // this tile while others still store the previous one. The first
-            // barrier inside the tile decides a missed tile for all threads
-            // alike (stage work on an unfilled buffer only reads garbage).
-            const bool late = !mbar_wait_bounded(&full[s], (k / NS) & 1u);
-            if (sync_now) {
+            // the compiled form of each stage's butterflies for this pass's shape
+            const int d0 = due_form<G>(0, A.is_low, A.hmask, cb), d1 = due_form<G>(1, A.is_low, A.hmask, cb),
+                      d2 = due_form<G>(2, A.is_low, A.hmask, cb);
+            bool ok = true;
+            for (unsigned k = 0; k < niter; k++) {
+                unsigned b, t, mid;
+                int c4;
+                tile_coords(k, b, t, mid, c4);
+                const int s = (int)(k % NS);
+                unsigned char *buf = sm + (size_t)s * NV * TB;
+                bool sync_now = (k == 0);  // launch constants (qr) and the table need a barrier
+                if ((int)b != cur_b) {  // new parameter point: its phase table and mixer angle
+                    sync_now = true;
+                    if (cur_b >= 0 && reduce)
+                        stash(cur_b);
+                    tslot ^= 1;
+                    X.tab = tab + tslot * MAXTAB;
+                    if constexpr (MG) {  // this point's own graph
+                        if (est[0] >= 0 || est[1] >= 0) {
+                            views(b, curv);
+                            launch_consts(tslot);
+                            X.qr = &qr[tslot][0][0];
+                            X.qrf = &qrf[tslot][0][0];
+                        }
+                    }
+                    if constexpr (IS) {
+                        // this point's cost phases of the thread's and the stage's terms
+                        // (each thread writes and reads only its own per-thread entries)
+                        if (cost_phase && est[0] >= 0) {
+                            const double ang = ising_angle(b);
+                            double q, dk[G::RB], qq;
+                            ising_terms(0, est[0], q, dk, qq);
+                            ptp[tid] = unit_phase<R>(ang * q);
+                            for (int kk = 0; kk < G::RB; kk++)
+                                ptp[(1 + kk) * NTHR + tid] = unit_phase<R>(ang * dk[kk]);
+                            if (tid < (1 << G::RB))
+                                qps[tslot][tid] = unit_phase<R>(ang * qq);
+                        }
+                        X.qp = &qps[tslot][0];
+                    } else if (A.pre_phase || (A.post & (POST_PHASE_CONJ | POST_PHASE))) {
+                        const C *src = reinterpret_cast<const C *>(A.tab) + ((size_t)b * A.p + A.tab_layer) * A.tab_len;
+                        C *dst = tab + tslot * MAXTAB;
+                        for (int i = tid; i < A.tab_len; i += NTHR)
+                            dst[i] = src[i];
+                    }
+                    const double2 csd = A.cs[(size_t)b * A.p + A.layer];
+                    const double cbv = csd.x, sbv = A.sign_s * csd.y;
+                    const bool shifted = fabs(sbv) > fabs(cbv);  // rotate by beta - pi/2 (Ising: cot form)
+                    X.cot = IS && shifted;
+                    X.tq = shifted ? (R)((IS ? cbv : -cbv) / sbv) : (R)(sbv / cbv);
+                    const double f = shifted ? sbv : cbv;
+                    double fj = 1.0, fn = 1.0;
+                    for (int i = 0; i < A.n; i++) {
+                        if (i < A.j0)
+                            fj *= f;
+                        fn *= f;
+                    }
+                    X.f = (R)f;
+                    X.fn = (R)fn;
+                    X.fn2 = (R)(fn * fn);
+                    X.scale0 = (R)fj;
+                    if constexpr (FUSE) {  // the second layer's rotation
+                        const double2 cs2 = A.cs[(size_t)b * A.p + A.layer2];
+                        const double c2 = cs2.x, s2 = A.sign_s * cs2.y;
+                        const bool sh2 = fabs(s2) > fabs(c2);
+                        X.cot2 = IS && sh2;
+                        X.tq2 = sh2 ? (R)((IS ? c2 : -c2) / s2) : (R)(s2 / c2);
+                        X.f2 = (R)(sh2 ? s2 : c2);
+                    }
+                    cur_b = (int)b;
+                }
+                X.sv0 = reinterpret_cast<C *>(buf);
+                X.sv1 = reinterpret_cast<C *>(buf + TB);
+                X.tc = &tcs[IS ? 0 : s][0][0];
+                X.tv = &tvs[IS ? s : 0][0][0];
+                X.tp = &tps[IS ? s : 0][0];
+                X.fixed = ((uint64_t)mid << cb) | ((uint64_t)(t >> midbits) << (A.s + hb));
+
+                // No barrier between tiles unless a point starts: a warp may begin
+                // this tile while others still store the previous one. The first
+                // barrier inside the tile decides a missed tile for all threads
+                // alike (stage work on an unfilled buffer only reads garbage).
+                const bool late = !mbar_wait_bounded(&full[s], (k / NS) & 1u);
+                if (sync_now) {
+                    compute_sync<NTHR>();
+                    write_pending();
+                }
+
+                C a[NR], l[NR];
+                X.first = true;
+                X.run = X.scale0;
+                bool bad;
+                X.run2 = (R)1;
+                if (!FUSE && P.is_low) {
+                    run_stage_due<R, NV, 0, OPS, false, IS>(d0, P, X, a, l, acc0, acc1, acc2);
+                    X.first = false;
+                    bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
+                    if (!bad) {
+                        run_stage_due<R, NV, 1, OPS, false, IS>(d1, P, X, a, l, acc0, acc1, acc2);
+                        if (!P.skip_last)
+                            compute_sync<NTHR>();
+                    }
+                } else {  // a high pass (every fused pass is one)
+                    run_stage_due<R, NV, 1, OPS, false, IS>(d1, P, X, a, l, acc0, acc1, acc2);
+                    X.first = false;
+                    bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
+                }
+                if (bad) {  // a tile never arrived, or the producer gave up
+                    if (tid == 0) {
+                        atomicExch(A.err, 1);
+                        s_flag = 1;
+                    }
+                    ok = false;
+                    break;
+                }
+                if (FUSE) {  // layer `layer` ends in stage 2, layer2 starts there and ends in stage 1
+                    run_stage_due<R, NV, 2, OPS, true, IS>(d2, P, X, a, l, acc0, acc1, acc2);
+                    compute_sync<NTHR>();
+                    mix_stage_due<R, NV, 1, IS>(d1, P, X, a, l, acc2);
+                } else if (!P.skip_last) {  // a low pass over the qubits of stages 0 and 1 only ends here
+                    run_stage_due<R, NV, 2, OPS, false, IS>(d2, P, X, a, l, acc0, acc1, acc2);
+                }
+                // results (if any) are in the buffer: hand it to the producer
+                fence_proxy_async_smem();
+                mbar_arrive(&done[s]);
+            }
+            if (ok && reduce && cur_b >= 0) {
+                stash(cur_b);
                 compute_sync<NTHR>();
                 write_pending();
             }
-
-            C a[NR], l[NR];
-            X.first = true;
-            X.run = X.scale0;
-            bool bad;
-            X.run2 = (R)1;
-            if (!FUSE && P.is_low) {
-                run_stage_due<R, NV, 0, OPS, false, IS>(d0, P, X, a, l, acc0, acc1, acc2);
-                X.first = false;
-                bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
-                if (!bad) {
-                    run_stage_due<R, NV, 1, OPS, false, IS>(d1, P, X, a, l, acc0, acc1, acc2);
-                    if (!P.skip_last)
-                        compute_sync<NTHR>();
-                }
-            } else {  // a high pass (every fused pass is one)
-                run_stage_due<R, NV, 1, OPS, false, IS>(d1, P, X, a, l, acc0, acc1, acc2);
-                X.first = false;
-                bad = compute_sync_or<NTHR>(late || *reinterpret_cast<volatile int *>(&s_flag));
-            }
-            if (bad) {  // a tile never arrived, or the producer gave up
-                if (tid == 0) {
-                    atomicExch(A.err, 1);
-                    s_flag = 1;
-                }
-                ok = false;
-                break;
-            }
-            if (FUSE) {  // layer `layer` ends in stage 2, layer2 starts there and ends in stage 1
-                run_stage_due<R, NV, 2, OPS, true, IS>(d2, P, X, a, l, acc0, acc1, acc2);
-                compute_sync<NTHR>();
-                mix_stage_due<R, NV, 1, IS>(d1, P, X, a, l, acc2);
-            } else if (!P.skip_last) {  // a low pass over the qubits of stages 0 and 1 only ends here
-                run_stage_due<R, NV, 2, OPS, false, IS>(d2, P, X, a, l, acc0, acc1, acc2);
-            }
-            // results (if any) are in the buffer: hand it to the producer
-            fence_proxy_async_smem();
-            mbar_arrive(&done[s]);
-        }
-        if (ok && reduce && cur_b >= 0) {
-            stash(cur_b);
-            compute_sync<NTHR>();
-            write_pending();
-        }
         };
         const int fw = flag_word(A.load, A.pre_phase, A.pre_lambda, A.write, A.post);
         using std::integral_constant;
