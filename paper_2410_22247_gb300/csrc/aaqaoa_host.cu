@@ -427,11 +427,17 @@ struct Step {
     bool last_of_layer;   // the layer's mixer is complete after this pass
 };
 
-// Every layer runs its low pass first, then its high passes in order. With
-// fusion (at least two high passes and two layers) the last pass of a layer
-// also starts the next layer in the direction of travel on the same qubits,
-// and the next layer skips that group and ends on another high group, so
-// consecutive boundaries alternate between the last two high groups.
+// Every layer runs its low pass first, then its high passes in order, except
+// the forward sweep's first layer with two or more high passes: its first
+// high pass comes first, so that the pass generating |+>^n (no load, the
+// first cost phase, compute-bound) covers a high group in two register
+// stages rather than the low pass's three, and the low pass becomes a
+// streaming one. With fusion (at least two high passes and two layers) the
+// last pass of a layer also starts the next layer in the direction of
+// travel on the same qubits, and the next layer skips that group and ends on
+// another high group, so consecutive boundaries alternate between the last
+// two high groups. The last pass of a layer is always a high pass (its last
+// register stage carries the layer-end work).
 std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fuse, bool reverse)
 {
     const int np = (int)passes.size();
@@ -447,6 +453,8 @@ std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fu
         for (int k = 0; k < np; k++)
             if (k != skip)
                 order.push_back(k);
+        if (!reverse && i == 0 && np >= 3)
+            std::swap(order[0], order[1]);
         int j0 = done0;
         for (size_t o = 0; o < order.size(); o++) {
             const int k = order[o];

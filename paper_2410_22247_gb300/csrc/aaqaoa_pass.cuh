@@ -913,7 +913,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     const uint32_t base = stage_base<G, ST>((uint32_t)X.tid);
     const uint32_t sb = G::swz(base);
 
-    if (ST == 0 && !A.load) {  // |+>^n in the twisted frame: 2^(-n/2) i^|x|
+    if (X.first && !A.load) {  // |+>^n in the twisted frame: 2^(-n/2) i^|x| (first stage of the pass)
         // the four values amp * i^((c0 + j) & 3) once, then a compile-time
         // choice by the register index's own bit count
         const int c0 = (__popcll(X.fixed) + __popc(base)) & 3;
@@ -957,7 +957,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         }
     };
 
-    if (OPS && ST == 0 && A.pre_phase) {
+    if (OPS && X.first && A.pre_phase) {
         C P[NR];
         phases(P);
 #pragma unroll
@@ -1306,8 +1306,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
     // energy (last stage of the last forward pass).
     int est[2] = {-1, -1};
     if (OPS) {
-        if (A.pre_phase)
-            est[0] = 0;
+        if (A.pre_phase)  // in the pass's first stage
+            est[0] = A.is_low ? 0 : 1;
         else if (NV == 2 && (A.post & (POST_GAMMA | POST_PHASE_CONJ)))
             est[0] = G::NST - 1;
         else if (NV == 1 && (A.post & POST_PHASE))
