@@ -1058,6 +1058,16 @@ int aaqaoa_prepare_ising(int n, int num_edges, const int32_t *edges, const doubl
     if (field)
         for (int c = 0; c < num_vorbits; c++)
             pl->ifn[2].h[vorbit_rep[c]] = vorbit_weight[c] * field[vorbit_rep[c]];
+    for (IsingFn &F : pl->ifn)  // chunk sums of the couplings, in FP64
+        for (int c = 0; c < ISING_CHUNKS; c++)
+            for (int m = 0; m < 64; m++)
+                for (int u = 0; u < MAXN; u++) {
+                    double g = 0.0;
+                    for (int j = 0; j < 6 && 6 * c + j < MAXN; j++)
+                        if ((m >> j) & 1)
+                            g += F.W[6 * c + j][u];
+                    F.G[c][m][u] = g;
+                }
     *out = pl;
     return AAQAOA_OK;
 }

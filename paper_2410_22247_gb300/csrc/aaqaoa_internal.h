@@ -31,9 +31,14 @@ using CostFn = CutFn;
 // fields: the cost of an Ising plan, and its observables (H_red keeps one
 // representative edge per edge orbit and one vertex per vertex orbit, each at
 // orbit size times its weight or field).
+constexpr int ISING_CHUNKS = (MAXN + 5) / 6;  // 6-bit chunks of a basis index
 struct IsingFn {
-    double W[MAXN][MAXN];
+    double W[MAXN][MAXN];  // symmetric
     double h[MAXN];
+    // G[c][m][u] = sum of W[6c + j][u] over the set bits j of m: g_u(f) =
+    // sum_{v in f} W_vu is one entry per 6-bit chunk of f, loads that do
+    // not wait on each other, with a warp's vertices u on one row
+    double G[ISING_CHUNKS][64][MAXN];
 };
 
 // Cut functions of one graph of a batch of graphs with the same n: the cost

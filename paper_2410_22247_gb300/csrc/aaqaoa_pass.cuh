@@ -664,6 +664,10 @@ struct StageCtx {
     const typename CT<R>::T *ptp;
     const R *qv;                  // [2][32]
     const typename CT<R>::T *qp;  // [32]
+    // the register-bit pair terms of function e in this pass's cut stage are
+    // all zero (the usual case: few couplings among one stage's bits), so
+    // their per-amplitude additions (and the Ising phases' factors) are skipped
+    bool qz[2] = {false, false};
 };
 
 // ------------------------------------------------ cut values in a stage
@@ -695,7 +699,8 @@ __device__ __forceinline__ void cut_terms(const V *tc, const V *pt, int tid, V &
 
 // integer cut values (phase-table indices)
 template <typename G, int ST>
-__device__ __forceinline__ void cut_int(const int *tc, const int *pt, const int *qr, int tid, int (&v)[1 << G::RB])
+__device__ __forceinline__ void cut_int(const int *tc, const int *pt, const int *qr, bool qz, int tid,
+                                        int (&v)[1 << G::RB])
 {
     constexpr int RB = G::RB;
     int base, d[RB];
@@ -706,15 +711,16 @@ __device__ __forceinline__ void cut_int(const int *tc, const int *pt, const int 
         const int top = hibit(m);
         v[m] = v[m ^ (1 << top)] + d[top];
     }
+    if (!qz)
 #pragma unroll
-    for (int m = 1; m < (1 << RB); m++)
-        v[m] += qr[m];
+        for (int m = 1; m < (1 << RB); m++)
+            v[m] += qr[m];
 }
 
 // cut values as multipliers of type R (exact: integers below 2^24)
 template <typename G, typename R, int ST>
-__device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int *qr, const float *qrf, int tid,
-                                         R (&v)[1 << G::RB])
+__device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int *qr, const float *qrf, bool qz,
+                                         int tid, R (&v)[1 << G::RB])
 {
     constexpr int RB = G::RB;
     int base, d[RB];
@@ -730,9 +736,10 @@ __device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int
             const int top = hibit(m);
             v[m] = v[m ^ (1 << top)] + df[top];
         }
+        if (!qz)
 #pragma unroll
-        for (int m = 1; m < (1 << RB); m++)
-            v[m] += qrf[m];
+            for (int m = 1; m < (1 << RB); m++)
+                v[m] += qrf[m];
     } else {
         int iv[1 << RB];
         iv[0] = base;
@@ -741,9 +748,13 @@ __device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int
             const int top = hibit(m);
             iv[m] = iv[m ^ (1 << top)] + d[top];
         }
+        if (!qz)
+#pragma unroll
+            for (int m = 1; m < (1 << RB); m++)
+                iv[m] += qr[m];
 #pragma unroll
         for (int m = 0; m < (1 << RB); m++)
-            v[m] = (R)(iv[m] + qr[m]);
+            v[m] = (R)iv[m];
     }
 }
 
@@ -751,7 +762,8 @@ __device__ __forceinline__ void cut_real(const int *tc, const int *pt, const int
 // fields. Values O(x) of the thread's 2^RB states from constants rounded
 // once to R (tile: tc[15] = O(f), tc[L] = h_L(f); thread: pt; stage: q).
 template <typename G, typename R, int ST>
-__device__ __forceinline__ void ising_vals(const R *tc, const R *pt, const R *q, int tid, R (&v)[1 << G::RB])
+__device__ __forceinline__ void ising_vals(const R *tc, const R *pt, const R *q, bool qz, int tid,
+                                           R (&v)[1 << G::RB])
 {
     constexpr int RB = G::RB;
     R base, d[RB];
@@ -762,9 +774,10 @@ __device__ __forceinline__ void ising_vals(const R *tc, const R *pt, const R *q,
         const int top = hibit(m);
         v[m] = v[m ^ (1 << top)] + d[top];
     }
+    if (!qz)
 #pragma unroll
-    for (int m = 1; m < (1 << RB); m++)
-        v[m] += q[m];
+        for (int m = 1; m < (1 << RB); m++)
+            v[m] += q[m];
 }
 
 // Ising phases P[m] = scale * exp(-i s gamma O(x)) of the thread's states as
@@ -773,7 +786,8 @@ __device__ __forceinline__ void ising_vals(const R *tc, const R *pt, const R *q,
 // pp[0] (thread-bit pairs), pp[(1 + k) NTHR] (register bit k with the thread
 // bits) per thread; qp[m] (register-bit pairs) per stage.
 template <typename G, typename C, int ST>
-__device__ __forceinline__ void ising_phases(const C *tp, const C *pp, const C *qp, int tid, C (&P)[1 << G::RB])
+__device__ __forceinline__ void ising_phases(const C *tp, const C *pp, const C *qp, bool qz, int tid,
+                                             C (&P)[1 << G::RB])
 {
     constexpr int RB = G::RB, NTB = G::T - G::RB;
     C base = cmul(tp[15], pp[0]);
@@ -791,10 +805,11 @@ __device__ __forceinline__ void ising_phases(const C *tp, const C *pp, const C *
         const int top = hibit(m);
         P[m] = cmul(P[m ^ (1 << top)], d[top]);
     }
+    if (!qz)
 #pragma unroll
-    for (int m = 1; m < (1 << RB); m++)
-        if (m & (m - 1))
-            P[m] = cmul(P[m], qp[m]);
+        for (int m = 1; m < (1 << RB); m++)
+            if (m & (m - 1))
+                P[m] = cmul(P[m], qp[m]);
 }
 
 // A thread's running sum over its tiles, in FP64 for both precisions: each
@@ -940,17 +955,18 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     // the values O_e(x) of the thread's states (real; exact integers for cut functions)
     auto values = [&](int e, R (&v)[NR]) {
         if constexpr (IS)
-            ising_vals<G, R, ST>(X.tv + 16 * e, X.ptv + e * (RB + 1) * G::NTHR + X.tid, X.qv + 32 * e, X.tid, v);
+            ising_vals<G, R, ST>(X.tv + 16 * e, X.ptv + e * (RB + 1) * G::NTHR + X.tid, X.qv + 32 * e, X.qz[e], X.tid,
+                                 v);
         else
-            cut_real<G, R, ST>(e ? tc1 : tc0, e ? pt1 : pt0, X.qr + 32 * e, X.qrf + 32 * e, X.tid, v);
+            cut_real<G, R, ST>(e ? tc1 : tc0, e ? pt1 : pt0, X.qr + 32 * e, X.qrf + 32 * e, X.qz[e], X.tid, v);
     };
     // the cost layer's phase factors of the thread's states (this pass's table)
     auto phases = [&](C (&P)[NR]) {
         if constexpr (IS) {
-            ising_phases<G, C, ST>(X.tp, X.ptp + X.tid, X.qp, X.tid, P);
+            ising_phases<G, C, ST>(X.tp, X.ptp + X.tid, X.qp, X.qz[0], X.tid, P);
         } else {
             int cv[NR];
-            cut_int<G, ST>(tc0, pt0, X.qr, X.tid, cv);
+            cut_int<G, ST>(tc0, pt0, X.qr, X.qz[0], X.tid, cv);
 #pragma unroll
             for (int m = 0; m < NR; m++)
                 P[m] = X.tab[cv[m]];
@@ -1413,7 +1429,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 const IsingFn *F = ising_fn(e);
                 double d = F->h[u];
                 for (int v = 0; v < A.n; v++)
-                    d += F->W[u][v];
+                    d += F->W[v][u];  // symmetric: lanes read one row
                 isd[e][u] = d;
             }
         }
@@ -1457,7 +1473,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         // d_u = h_u + sum_v W_uv (the flip cost of u from an all-zero state):
         //   O(f) = sum_{u in f} (d_u - g_u(f)),   h_u(f) = d_u - 2 g_u(f),
         // since [f_u != f_v] = f_u + f_v - 2 f_u f_v. Lanes take vertices;
-        // every lane loops over the same set bits of f.
+        // g_u(f) adds one precomputed chunk sum per 6 bits of f (IsingFn::G:
+        // a walk over the set bits of f waited on each load in turn).
         auto tile_consts_ising = [&](unsigned k, int s) {
             unsigned b, t, mid;
             int c4;
@@ -1472,10 +1489,12 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                     const int u = lane + 32 * j;
                     if (u >= A.n)
                         continue;
-                    double g = 0.0;
+                    double g = 0.0;  // g_u(f): one chunk sum per 6 bits of f
                     const double d = isd[e][u];
-                    for (uint64_t rest = f; rest; rest &= rest - 1)
-                        g += F->W[u][__ffsll((long long)rest) - 1];
+#pragma unroll
+                    for (int c = 0; c < ISING_CHUNKS; c++)
+                        if (6 * c < A.n)
+                            g += F->G[c][(f >> (6 * c)) & 63u][u];
                     if ((f >> u) & 1ull)
                         os += d - g;
                     hl[j] = d - 2.0 * g;
@@ -1780,6 +1799,15 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 if (sync_now) {
                     compute_sync<NTHR>();
                     write_pending();
+                    if constexpr (OPS) {  // this point's register-bit pair terms, now visible
+#pragma unroll
+                        for (int e = 0; e < 2; e++) {
+                            bool z = true;
+                            for (int m = 1; m < NR; m++)
+                                z = z && (IS ? X.qv[32 * e + m] == (R)0 : X.qr[32 * e + m] == 0);
+                            X.qz[e] = z;
+                        }
+                    }
                 }
 
                 C a[NR], l[NR];
