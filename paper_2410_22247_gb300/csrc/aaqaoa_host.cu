@@ -117,7 +117,7 @@ struct aaqaoa_plan {
     bool ising = false;
     std::vector<double> ising_w, ising_h;   // per edge; per vertex (empty: no fields)
     std::vector<int32_t> vorbit_rep, vorbit_weight;
-    IsingFn ifn[3]{};                       // cost, H_C, H_red
+    std::vector<IsingFn> ifn;               // Ising plans: cost, H_C, H_red (1.1 MB; empty otherwise)
     const double *cur_gamma = nullptr;      // device gamma of the call being enqueued
     cudaStream_t stream = nullptr;
     // workspace
@@ -1042,7 +1042,8 @@ int aaqaoa_prepare_ising(int n, int num_edges, const int32_t *edges, const doubl
         pl->ising_h.assign(field, field + n);
     pl->vorbit_rep.assign(vorbit_rep, vorbit_rep + num_vorbits);
     pl->vorbit_weight.assign(vorbit_weight, vorbit_weight + num_vorbits);
-    memset(pl->ifn, 0, sizeof pl->ifn);
+    pl->ifn.clear();
+    pl->ifn.resize(3);  // zeroed in place (no 1.1 MB temporary)
     for (int i = 0; i < num_edges; i++) {
         const int u = pl->edges[2 * i], v = pl->edges[2 * i + 1];
         pl->ifn[0].W[u][v] = pl->ifn[0].W[v][u] = edge_weight[i];
@@ -1141,7 +1142,8 @@ int aaqaoa_set_workspace(aaqaoa_plan *pl, void *device_ptr, size_t bytes, int ba
         return r;
     CK(cudaMemsetAsync(pl->ws + L.ctrl, 0, 256, pl->stream));
     if (pl->ising)
-        CK(cudaMemcpyAsync(pl->ws + L.ising, pl->ifn, sizeof pl->ifn, cudaMemcpyHostToDevice, pl->stream));
+        CK(cudaMemcpyAsync(pl->ws + L.ising, pl->ifn.data(), pl->ifn.size() * sizeof(IsingFn), cudaMemcpyHostToDevice,
+                           pl->stream));
     CK(cudaStreamSynchronize(pl->stream));
     return AAQAOA_OK;
 }
