@@ -291,6 +291,26 @@ def test_full_size_k16_p1():
     assert e_rel(SYM.energy(SYM.complete_graph_model(16), g, b), Ec) < 1e-12
 
 
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_dense_k16_p2_gradient_matches_oracle(precision):
+    """Every pair of register bits of every stage is coupled (the pair terms
+    the passes skip when they vanish are all present), through tiled passes
+    with a fused boundary, against the FP64 oracle."""
+    n, e = W.complete_graph(16)
+    g, b = [0.37, -0.52], [0.21, 0.93]
+    pl, orb = plan_for(n, e, 2, precision)
+    Er, dgr, dbr = O.energy_grad(n, e, g, b)
+    for obs in ("red", "full"):
+        E, dg, db = pl.grad(g, b, obs)
+        assert e_rel(E, Er) < TOL[precision]
+        assert g_rel(dg, dgr, Er, precision) < TOL[precision]
+        assert g_rel(db, dbr, Er, precision) < TOL[precision]
+    psi = pl.statevector(g, b)
+    ref = O.qaoa_state(n, e, g, b)
+    assert np.max(np.abs(psi.astype(np.complex128) - ref)) / np.max(np.abs(ref)) < TOL[precision]
+    pl.close()
+
+
 def _release_cached_device_memory(torch):
     import gc
     gc.collect()
