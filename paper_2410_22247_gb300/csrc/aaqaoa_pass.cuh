@@ -1863,22 +1863,20 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                 compiled = true;
             }
         };
-        // cut-function modes 1 and 3 (compiling the same words for the Ising
-        // modes 4 and 5 gained nothing measurable: 58.6 vs 58.5 ms for the
-        // n = 30 Ising energy + gradient)
+        // cut-function modes 1 and 3 and their Ising counterparts 4 and 5
         constexpr bool F32 = std::is_same<R, float>::value;
-        if constexpr (F32 && MODE == 1 && NV == 1) {
+        if constexpr (F32 && (MODE == 1 || MODE == 4) && NV == 1) {
             run_if(integral_constant<int, FW_FWD_FIRST>{});
             run_if(integral_constant<int, FW_FWD_LAST>{});
             run_if(integral_constant<int, FW_FWD_ENERGY>{});
         }
-        if constexpr (F32 && MODE == 3 && NV == 1)
+        if constexpr (F32 && (MODE == 3 || MODE == 5) && NV == 1)
             run_if(integral_constant<int, FW_FWD_FUSED>{});
-        if constexpr (F32 && MODE == 1 && NV == 2) {
+        if constexpr (F32 && (MODE == 1 || MODE == 4) && NV == 2) {
             run_if(integral_constant<int, FW_ADJ_FIRST>{});
             run_if(integral_constant<int, FW_ADJ_LAST>{});
         }
-        if constexpr (F32 && MODE == 3 && NV == 2)
+        if constexpr (F32 && (MODE == 3 || MODE == 5) && NV == 2)
             run_if(integral_constant<int, FW_ADJ_BOUNDARY>{});
         if (!compiled)
             compute(integral_constant<int, -1>{});
