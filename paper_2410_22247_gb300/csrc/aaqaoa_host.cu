@@ -428,17 +428,18 @@ struct Step {
 };
 
 // Every layer runs its low pass first, then its high passes in order, except
-// the forward sweep's first layer with two or more high passes: its first
-// high pass comes first, so that the pass generating |+>^n (no load, the
-// first cost phase, compute-bound) covers a high group in two register
-// stages rather than the low pass's three, and the low pass becomes a
-// streaming one. With fusion (at least two high passes and two layers) the
+// (gen_high: complex64 forward sweeps) the first layer with two or more high
+// passes: its first high pass comes first, so that the pass generating
+// |+>^n (no load, the first cost phase, compute-bound) covers a high group
+// in two register stages rather than the low pass's three, and the low pass
+// becomes a streaming one. (Complex128 passes are bound by FP64 arithmetic
+// either way, and their kernels keep generation in stage 0.) With fusion (at least two high passes and two layers) the
 // last pass of a layer also starts the next layer in the direction of
 // travel on the same qubits, and the next layer skips that group and ends on
 // another high group, so consecutive boundaries alternate between the last
 // two high groups. The last pass of a layer is always a high pass (its last
 // register stage carries the layer-end work).
-std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fuse, bool reverse)
+std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fuse, bool reverse, bool gen_high)
 {
     const int np = (int)passes.size();
     fuse = fuse && np >= 3 && p >= 2;
@@ -453,7 +454,7 @@ std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fu
         for (int k = 0; k < np; k++)
             if (k != skip)
                 order.push_back(k);
-        if (!reverse && i == 0 && np >= 3)
+        if (gen_high && !reverse && i == 0 && np >= 3)
             std::swap(order[0], order[1]);
         int j0 = done0;
         for (size_t o = 0; o < order.size(); o++) {
@@ -520,7 +521,7 @@ int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
     const long long total = (long long)pl->tiles() * B;
     const int grid = pass_grid(total);
     const int chunk = B > 1 ? (int)((total + grid - 1) / grid) : 0;
-    const std::vector<Step> sched = layer_schedule(pl->p, pl->passes, plan_fuses(pl), false);
+    const std::vector<Step> sched = layer_schedule(pl->p, pl->passes, plan_fuses(pl), false, !pl->c128);
     for (size_t i = 0; i < sched.size(); i++) {
         const Step &sp = sched[i];
         PassArgs a = forward_args(pl, obs, B, sp, i, sched.size(), mode);
@@ -548,7 +549,7 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
     // Each layer runs its passes low pass first, so the cut-function work at
     // the layer's end (dE/dgamma, inverse phase) falls in a high pass and the
     // low pass can stop after two register stages.
-    const std::vector<Step> sched = layer_schedule(pl->p, pl->bwd_passes, plan_fuses(pl), true);
+    const std::vector<Step> sched = layer_schedule(pl->p, pl->bwd_passes, plan_fuses(pl), true, false);
     for (size_t i = 0; i < sched.size(); i++) {
         const Step &sp = sched[i];
         const Pass &ps = pl->bwd_passes[sp.k];
@@ -1223,7 +1224,7 @@ int aaqaoa_get_schedule(aaqaoa_plan *pl, int adjoint, int32_t *steps, int cap, i
     if (!pl || !count || cap < 0 || (cap > 0 && !steps))
         return fail(AAQAOA_ERR_INVALID_ARG, "plan/count is NULL, cap < 0 or steps is NULL");
     const std::vector<Pass> &passes = adjoint ? pl->bwd_passes : pl->passes;
-    const std::vector<Step> sched = layer_schedule(pl->p, passes, plan_fuses(pl), adjoint != 0);
+    const std::vector<Step> sched = layer_schedule(pl->p, passes, plan_fuses(pl), adjoint != 0, !adjoint && !pl->c128);
     *count = (int)sched.size();
     for (int i = 0; i < cap && i < (int)sched.size(); i++) {
         const Pass &ps = passes[sched[i].k];
@@ -1966,7 +1967,7 @@ extern "C" int aaqaoa_expect_static(aaqaoa_plan *pl, const double *gamma, const 
                               1, &wide[k])))
                 return r;
         const int grid = pass_grid(pl->tiles());
-        const std::vector<Step> sched = layer_schedule(p, pl->passes, plan_fuses(pl), false);
+        const std::vector<Step> sched = layer_schedule(p, pl->passes, plan_fuses(pl), false, !pl->c128);
         for (size_t i = 0; i < sched.size(); i++) {
             const int k = sched[i].k;
             // the plan's own pass arguments, pointed at the static scratch

@@ -805,7 +805,9 @@ __device__ __forceinline__ void ising_phases(const C *tp, const C *pp, const C *
         const int top = hibit(m);
         P[m] = cmul(P[m ^ (1 << top)], d[top]);
     }
-    if (!qz)
+    // (complex128 keeps the loop unconditional: the branch there costs the
+    // 255-register forward pass spills)
+    if (!(qz && std::is_same<C, float2>::value))
 #pragma unroll
         for (int m = 1; m < (1 << RB); m++)
             if (m & (m - 1))
@@ -928,7 +930,10 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     const uint32_t base = stage_base<G, ST>((uint32_t)X.tid);
     const uint32_t sb = G::swz(base);
 
-    if (X.first && !A.load) {  // |+>^n in the twisted frame: 2^(-n/2) i^|x| (first stage of the pass)
+    // the stage a pass starts with: stage 0 of a low pass, or stage 1 of a
+    // complex64 high pass (the generating pass of a forward sweep may be one)
+    constexpr bool MAY_START = ST == 0 || (ST == 1 && std::is_same<R, float>::value);
+    if (MAY_START && X.first && !A.load) {  // |+>^n in the twisted frame: 2^(-n/2) i^|x|
         // the four values amp * i^((c0 + j) & 3) once, then a compile-time
         // choice by the register index's own bit count
         const int c0 = (__popcll(X.fixed) + __popc(base)) & 3;
@@ -973,7 +978,7 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         }
     };
 
-    if (OPS && X.first && A.pre_phase) {
+    if (OPS && MAY_START && X.first && A.pre_phase) {
         C P[NR];
         phases(P);
 #pragma unroll

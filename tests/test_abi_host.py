@@ -144,11 +144,11 @@ def test_prepare_multi_names_the_bad_graph():
             N.aaqaoa_destroy_multi(h)
 
 
-def _handle(n, edges, p):
+def _handle(n, edges, p, flags=0):
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
     h = ctypes.c_void_p()
     assert N.aaqaoa_prepare(n, len(e) // 2, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0, None, None, None,
-                            p, 0, None, ctypes.byref(h)) == 0
+                            p, flags, None, ctypes.byref(h)) == 0
     return h
 
 
@@ -188,7 +188,7 @@ def _schedule(h, adjoint):
     return [tuple(int(v) for v in r) for r in out[:cnt.value]]
 
 
-def _check_schedule(steps, n, p, adjoint, fused):
+def _check_schedule(steps, n, p, adjoint, fused, c128=False):
     """The launches realise Eq. (1) layer by layer: flattened into (layer,
     qubit group) mixer steps (a fused launch is two steps with the next
     layer's diagonal step between them) the layers come in order, each layer
@@ -213,7 +213,7 @@ def _check_schedule(steps, n, p, adjoint, fused):
         assert covered == list(range(n)), l
     assert steps[-1][0] > 0 and steps[-1][3] == -1
     groups = {(s, q) for s, q, *_ in steps}
-    if not adjoint and len(groups) >= 3:
+    if not adjoint and not c128 and len(groups) >= 3:
         # the generating pass takes the first high group, then the low pass
         assert steps[0][0] > 0 and steps[1][0] == 0 and steps[0][2] == steps[1][2] == 0
     else:
@@ -245,6 +245,20 @@ def test_fused_schedule_realises_the_layers_in_order(n, p, plan4):
             assert len(steps) == p * (K + 1)
     finally:
         N.aaqaoa_destroy(h)
+
+
+def test_complex128_forward_starts_with_the_low_pass():
+    """complex128 sweeps keep the low pass first (their kernels generate the
+    state in stage 0); complex64 forward sweeps start on the first high group."""
+    for flags, first_low in ((N.AAQAOA_C128, True), (0, False)):
+        h = _handle(*W.star_graph(30), p=3, flags=flags)
+        try:
+            steps = _schedule(h, 0)
+            _check_schedule(steps, 30, 3, 0, fused=True, c128=bool(flags))
+            assert (steps[0][0] == 0) == first_low
+            assert _schedule(h, 1)[0][0] == 0
+        finally:
+            N.aaqaoa_destroy(h)
 
 
 def test_schedule_without_fusion_cases():
