@@ -468,8 +468,11 @@ int aaqaoa_get_layer_fusion(aaqaoa_plan *plan, int *enable);
  * [cap][5]): the pass's first qubit s, its qubit count, the layer l whose
  * mixer it applies there, the second layer of a fused pass or -1, and the
  * number of layer l's qubits mixed by earlier passes. The forward sweep runs
- * layers 0..p-1, the adjoint p-1..0. *count (host int) receives the number of
- * passes; at most cap rows are written. Needs no device. Plans small enough
+ * layers 0..p-1, the adjoint p-1..0; within a layer the low pass comes first,
+ * except the first layer of a complex64 forward sweep with two or more high
+ * passes, which starts on its first high group (the pass that generates the
+ * state), and a layer always ends on a high pass. *count (host int)
+ * receives the number of passes; at most cap rows are written. Needs no device. Plans small enough
  * for the whole-circuit kernel have no tiled passes (*count = 0).
  * INVALID_ARG for NULL plan/count, cap < 0 or steps NULL with cap > 0.
  */
