@@ -472,8 +472,9 @@ int aaqaoa_get_layer_fusion(aaqaoa_plan *plan, int *enable);
  * except the first layer of a complex64 forward sweep with two or more high
  * passes, which starts on its first high group (the pass that generates the
  * state), and a layer always ends on a high pass. *count (host int)
- * receives the number of passes; at most cap rows are written. Needs no device. Plans small enough
- * for the whole-circuit kernel have no tiled passes (*count = 0).
+ * receives the number of passes; at most cap rows are written. Needs no
+ * device. Plans small enough for the whole-circuit kernel have no tiled
+ * passes (*count = 0).
  * INVALID_ARG for NULL plan/count, cap < 0 or steps NULL with cap > 0.
  */
 int aaqaoa_get_schedule(aaqaoa_plan *plan, int adjoint, int32_t *steps, int cap, int *count);
