@@ -19,13 +19,14 @@
 //    and exchanges through (swizzled, bank-conflict-free) shared memory between
 //    register stages.
 //  * The cost phase of layer l is folded into the first register stage of the
-//    layer's first pass; the reduction (energy), lambda = O psi, dE/dgamma and
-//    the inverse cost phase are folded into the last stage of a pass. C(x) is
-//    computed exactly in integers: per thread one cut value by popcount over
-//    neighbour masks, then each of the thread's 2^RB amplitudes by flipping
-//    register bits (cut change of a flipped vertex, corrected for flipped
-//    neighbour pairs). The phase is a table lookup T_l[C(x)] of exp(-i gamma_l c)
-//    built in FP64 with the argument reduced mod 2 pi.
+//    layer's first pass (or, with layer-boundary fusion, into the end of the
+//    pass that ends layer l-1); the reduction (energy), lambda = O psi,
+//    dE/dgamma and the inverse cost phase are folded into the last stage of a
+//    pass. C(x) is computed exactly in integers: per thread one cut value by
+//    popcount over neighbour masks, then each of the thread's 2^RB amplitudes
+//    by flipping register bits (cut change of a flipped vertex, corrected for
+//    flipped neighbour pairs). The phase is a table lookup T_l[C(x)] of
+//    exp(-i gamma_l c) built in FP64 with the argument reduced mod 2 pi.
 //  * Reductions accumulate per thread in FP64 and are summed in a fixed order
 //    by the last block of the grid, so results are bit-reproducible.
 //
@@ -1320,7 +1321,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
         return;
 
     // The register stage that evaluates each cut function in this pass, or -1:
-    // C for the phase of a forward low pass (stage 0), for the next layer's
+    // C for the phase of a layer's first forward pass (its first stage: 0 for
+    // a low pass, 1 for the generating high pass), for the next layer's
     // phase in a fused forward pass and for the gradient and inverse phase of
     // the last adjoint pass of a layer (last stage); O for
     // lambda = O phi (first stage of the first adjoint pass) and for the
