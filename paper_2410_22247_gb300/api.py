@@ -189,16 +189,20 @@ class Plan:
     def set_layer_fusion(self, enable):
         N.check(N.aaqaoa_set_layer_fusion(self.handle, 1 if enable else 0), "aaqaoa_set_layer_fusion")
 
-    def schedule(self, adjoint=False):
-        """The tiled passes of one forward (or adjoint) sweep, in launch order:
-        a list of (first qubit, qubits, layer, fused second layer or -1,
-        qubits of the layer mixed before this pass)."""
+    def schedule(self, adjoint=False, gradient=False):
+        """The tiled passes of one sweep, in launch order: a list of (first
+        qubit, qubits, layer, fused second layer or -1, qubits of the layer
+        mixed before this pass). adjoint: the adjoint sweep of a gradient
+        evaluation (a first row whose second layer equals its layer is the
+        turnaround pass); gradient: the forward sweep of a gradient
+        evaluation (it ends before the turnaround's group); neither: the
+        forward sweep of an energy evaluation."""
+        mode = 1 if adjoint else (2 if gradient else 0)
         cnt = ctypes.c_int()
-        N.check(N.aaqaoa_get_schedule(self.handle, int(bool(adjoint)), None, 0, ctypes.byref(cnt)),
-                "aaqaoa_get_schedule")
+        N.check(N.aaqaoa_get_schedule(self.handle, mode, None, 0, ctypes.byref(cnt)), "aaqaoa_get_schedule")
         out = np.zeros((max(cnt.value, 1), 5), dtype=np.int32)
-        N.check(N.aaqaoa_get_schedule(self.handle, int(bool(adjoint)), _ptr(out, ctypes.c_int32), cnt.value,
-                                      ctypes.byref(cnt)), "aaqaoa_get_schedule")
+        N.check(N.aaqaoa_get_schedule(self.handle, mode, _ptr(out, ctypes.c_int32), cnt.value, ctypes.byref(cnt)),
+                "aaqaoa_get_schedule")
         return [tuple(int(v) for v in r) for r in out[:cnt.value]]
 
     def profile_launches(self):

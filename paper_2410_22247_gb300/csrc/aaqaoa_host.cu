@@ -330,8 +330,11 @@ int make_cluster_map(CUtensorMap *map, void *base, int n, int B, bool load)
 // streaming bandwidth. Returns false when (L, K) does not give valid tiles.
 // cluster_low: the geometry allows a low pass of CLUSTER_LOW_QUBITS qubits by
 // a cluster of 4 CTAs (the complex64 two-vector tiles), chosen by L = 14.
+// big_last (the adjoint's passes): the larger high groups come last, so that
+// the adjoint's last group can be the forward's last, smaller one (the pair a
+// turnaround pass takes).
 bool layer_passes(int n, int T, int cbmin, int hbmax, int L2, int L, int K, std::vector<Pass> &v,
-                  bool cluster_low = false)
+                  bool cluster_low = false, bool big_last = false)
 {
     v.clear();
     const bool cl = cluster_low && L == CLUSTER_LOW_QUBITS && T + 2 == CLUSTER_LOW_QUBITS;
@@ -345,7 +348,7 @@ bool layer_passes(int n, int T, int cbmin, int hbmax, int L2, int L, int K, std:
     const int r = n - L;
     int s = L;
     for (int k = 0; k < K; k++) {
-        const int h = r / K + (k < r % K ? 1 : 0);
+        const int h = r / K + ((big_last ? k >= K - r % K : k < r % K) ? 1 : 0);
         if (h > hbmax || T - h > s || T - h < cbmin)  // contiguous bits stay below the rows
             return false;
         Pass hp{s, T - h, 0, (1 << h) - 1, 0};
@@ -359,11 +362,11 @@ bool layer_passes(int n, int T, int cbmin, int hbmax, int L2, int L, int K, std:
 // The default plan: the fewest high passes, K = ceil((n-T)/hbmax); the low
 // pass covers T qubits unless those K passes can take all but the L2 qubits
 // of its first two register stages, in which case it skips its third stage.
-void default_layer(int n, int T, int cbmin, int hbmax, int L2, int *L, int *K)
+void default_layer(int n, int T, int cbmin, int hbmax, int L2, int *L, int *K, bool big_last = false)
 {
     *K = (n - T + hbmax - 1) / hbmax;
     std::vector<Pass> v;
-    *L = (L2 < T && layer_passes(n, T, cbmin, hbmax, L2, L2, *K, v)) ? L2 : T;
+    *L = (L2 < T && layer_passes(n, T, cbmin, hbmax, L2, L2, *K, v, false, big_last)) ? L2 : T;
 }
 
 void build_passes(aaqaoa_plan *pl)
@@ -376,8 +379,8 @@ void build_passes(aaqaoa_plan *pl)
         int T, CB, HB, L, K;
         pass_geometry(pl->c128, nv, &T, &CB, &HB);
         const int L2 = low_two_stage_bits(pl->c128, nv);
-        default_layer(pl->n, T, CB, HB, L2, &L, &K);
-        layer_passes(pl->n, T, CB, HB, L2, L, K, nv == 1 ? pl->passes : pl->bwd_passes);
+        default_layer(pl->n, T, CB, HB, L2, &L, &K, nv == 2);
+        layer_passes(pl->n, T, CB, HB, L2, L, K, nv == 1 ? pl->passes : pl->bwd_passes, false, nv == 2);
     }
 }
 
@@ -427,35 +430,35 @@ struct Step {
     bool last_of_layer;   // the layer's mixer is complete after this pass
 };
 
-// Every layer runs its low pass first, then its high passes in order, except
-// (gen_high: complex64 forward sweeps) the first layer with two or more high
-// passes: its first high pass comes first, so that the pass generating
-// |+>^n (no load, the first cost phase, compute-bound) covers a high group
-// in two register stages rather than the low pass's three, and the low pass
-// becomes a streaming one. (Complex128 passes are bound by FP64 arithmetic
-// either way, and their kernels keep generation in stage 0.) With fusion (at least two high passes and two layers) the
-// last pass of a layer also starts the next layer in the direction of
-// travel on the same qubits, and the next layer skips that group and ends on
-// another high group, so consecutive boundaries alternate between the last
-// two high groups. The last pass of a layer is always a high pass (its last
-// register stage carries the layer-end work).
-std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fuse, bool reverse, bool gen_high)
+// Every layer runs its low pass first, then its high passes in order. With
+// fusion (at least two high passes and two layers) the last pass of a layer
+// also starts the next layer in the direction of travel on the same qubits,
+// and the next layer skips that group and ends on another high group, so
+// consecutive boundaries alternate between the last two high groups. The last
+// pass of a layer is always a high pass (its last register stage carries the
+// layer-end work). first (optional) overrides the first layer's order;
+// start_skip is a group the first layer's mixer already has (the adjoint
+// after a turnaround pass), its qubits counted in j0.
+std::vector<Step> layer_schedule_from(int p, const std::vector<Pass> &passes, bool fuse, bool reverse,
+                                      const std::vector<int> &first, int start_skip)
 {
     const int np = (int)passes.size();
     fuse = fuse && np >= 3 && p >= 2;
     std::vector<Step> out;
-    int skip = -1;   // group already applied for this layer by the previous fused pass
-    int done0 = 0;   // its qubits
+    int skip = start_skip;                                         // group this layer already has
+    int done0 = start_skip >= 0 ? passes[start_skip].qubits : 0;  // its qubits
     for (int i = 0; i < p; i++) {
         const int l = reverse ? p - 1 - i : i;
         const bool more = i + 1 < p;
         const int next = reverse ? l - 1 : l + 1;
         std::vector<int> order;
-        for (int k = 0; k < np; k++)
-            if (k != skip)
-                order.push_back(k);
-        if (gen_high && !reverse && i == 0 && np >= 3)
-            std::swap(order[0], order[1]);
+        if (i == 0 && !first.empty()) {
+            order = first;
+        } else {
+            for (int k = 0; k < np; k++)
+                if (k != skip)
+                    order.push_back(k);
+        }
         int j0 = done0;
         for (size_t o = 0; o < order.size(); o++) {
             const int k = order[o];
@@ -464,6 +467,8 @@ std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fu
             j0 += passes[k].qubits;
             out.push_back(st);
         }
+        skip = -1;
+        done0 = 0;
         if (fuse && more) {
             skip = order.back();
             done0 = passes[skip].qubits;
@@ -472,7 +477,84 @@ std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fu
     return out;
 }
 
+// The sweep's schedule. gen_high (complex64 forward sweeps): the first layer
+// with two or more high passes starts on a high group, so that the pass
+// generating |+>^n (no load, the first cost phase, compute-bound) covers a
+// high group in two register stages rather than the low pass's three, and
+// the low pass becomes a streaming one (complex128 passes are bound by FP64
+// arithmetic either way, and their kernels keep generation in stage 0).
+// end_k >= 0: the forward sweep must end on group end_k (the turnaround's
+// group); the first layer's order is chosen for that, and an empty schedule
+// says no order ends there.
+std::vector<Step> layer_schedule(int p, const std::vector<Pass> &passes, bool fuse, bool reverse, bool gen_high,
+                                 int end_k = -1, int start_skip = -1)
+{
+    const int np = (int)passes.size();
+    std::vector<int> dflt;
+    for (int k = 0; k < np; k++)
+        if (k != start_skip)
+            dflt.push_back(k);
+    if (gen_high && !reverse && np >= 3 && start_skip < 0)
+        std::swap(dflt[0], dflt[1]);
+    if (end_k < 0)
+        return layer_schedule_from(p, passes, fuse, reverse, dflt, start_skip);
+    // candidate first-layer orders: the default, then the same with the two
+    // high groups at its ends exchanged (the first layer's last group fixes
+    // where every later layer ends)
+    std::vector<std::vector<int>> cands{dflt};
+    if (np >= 3) {
+        std::vector<int> alt = dflt;
+        const int a = gen_high ? 0 : 1;  // the first high group of the order
+        std::swap(alt[a], alt.back());
+        cands.push_back(alt);
+    }
+    for (const auto &c : cands) {
+        if (passes[c.back()].is_low)
+            continue;
+        std::vector<Step> st = layer_schedule_from(p, passes, fuse, reverse, c, start_skip);
+        if (!st.empty() && st.back().k == end_k)
+            return st;
+    }
+    return {};
+}
+
 bool plan_fuses(const aaqaoa_plan *pl) { return pl->fuse && !pl->pt_dev; }
+
+// The turnaround of a fused gradient evaluation: one two-vector pass takes
+// the forward's last group (mixed forward on phi alone, then the energy and
+// lambda = O phi of the exact final state) and the adjoint's first (both
+// vectors mixed back with the dE/dbeta terms), so phi is read once and the
+// final state never stored: the forward's last pass and the adjoint's first
+// (2 S of traffic) become one launch (3 S). It needs the forward's last
+// group to be one of the adjoint's high groups (same first qubit and size)
+// and a forward order that ends there. kf, kb: those groups, or -1.
+struct Turn {
+    int kf = -1, kb = -1;
+};
+Turn turnaround(const aaqaoa_plan *pl)
+{
+    Turn t;
+    // the adjoint's first layer keeps a high pass after the turnaround's group
+    // (its last stage carries dE/dgamma and the inverse phase)
+    if (!plan_fuses(pl) || pl->small() || pl->passes.size() < 3 || pl->bwd_passes.size() < 3)
+        return t;
+    for (size_t kb = 0; kb < pl->bwd_passes.size(); kb++) {
+        const Pass &b = pl->bwd_passes[kb];
+        if (b.is_low || b.cluster)
+            continue;
+        for (size_t kf = 0; kf < pl->passes.size(); kf++) {
+            const Pass &f = pl->passes[kf];
+            if (f.is_low || f.s != b.s || f.qubits != b.qubits)
+                continue;
+            if (layer_schedule(pl->p, pl->passes, true, false, !pl->c128, (int)kf).empty())
+                continue;
+            t.kf = (int)kf;
+            t.kb = (int)kb;
+            return t;
+        }
+    }
+    return t;
+}
 
 enum FwdMode { FWD_ENERGY, FWD_GRAD, FWD_STATE };
 
@@ -516,15 +598,20 @@ PassArgs forward_args(const aaqaoa_plan *pl, int obs, int B, const Step &sp, siz
     return a;
 }
 
+// The forward sweep; for a gradient evaluation with a turnaround it ends
+// one pass early (the turnaround applies the last group).
 int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
 {
     const long long total = (long long)pl->tiles() * B;
     const int grid = pass_grid(total);
     const int chunk = B > 1 ? (int)((total + grid - 1) / grid) : 0;
-    const std::vector<Step> sched = layer_schedule(pl->p, pl->passes, plan_fuses(pl), false, !pl->c128);
+    const Turn tn = mode == FWD_GRAD ? turnaround(pl) : Turn{};
+    std::vector<Step> sched = layer_schedule(pl->p, pl->passes, plan_fuses(pl), false, !pl->c128, tn.kf);
+    if (tn.kf >= 0)
+        sched.pop_back();
     for (size_t i = 0; i < sched.size(); i++) {
         const Step &sp = sched[i];
-        PassArgs a = forward_args(pl, obs, B, sp, i, sched.size(), mode);
+        PassArgs a = forward_args(pl, obs, B, sp, i, sched.size() + (tn.kf >= 0 ? 1 : 0), mode);
         a.chunk = chunk;
         if (pl->inject == AAQAOA_FAULT_DROP_TILE && a.load) {
             a.drop_first_load = 1;
@@ -538,7 +625,8 @@ int enqueue_forward(aaqaoa_plan *pl, int B, int obs, FwdMode mode)
     return AAQAOA_OK;
 }
 
-// adjoint passes on (phi, lambda); the first one forms lambda = O phi itself
+// adjoint passes on (phi, lambda); the first one forms lambda = O phi itself,
+// or the turnaround pass does (it also finishes the forward sweep)
 int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
 {
     int T, CB, HB;
@@ -546,15 +634,54 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
     const int tiles = 1 << (pl->n - T);
     const int grid = pass_grid((long long)tiles * B);
     const int chunk = B > 1 ? (int)(((long long)tiles * B + grid - 1) / grid) : 0;
+    const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
+    const Turn tn = turnaround(pl);
+    const int lp = pl->p - 1;  // the last layer: the adjoint's first
+    if (tn.kb >= 0) {
+        // load phi before the layer's last group, mix it forward (phi alone),
+        // rescale, energy, lambda = O phi, mix both back: a fused pass whose
+        // two layers are the same layer with opposite signs
+        const Pass &ps = pl->bwd_passes[tn.kb];
+        PassArgs a = base_args(pl, obs);
+        a.B = B;
+        a.chunk = chunk;
+        a.tiles = tiles;
+        a.s = ps.s;
+        a.cb = ps.cb;
+        a.wide_rows = ps.wide;
+        a.is_low = 0;
+        a.hmask = ps.hmask;
+        a.layer = a.layer2 = a.tab_layer = lp;
+        a.sign_s = 1.0;
+        a.sign2 = -1.0;
+        a.tab = tab_kind(pl, pl->d_tab(), B, 1);
+        a.j0 = pl->n - ps.qubits;
+        a.load = 1;
+        a.nvec_io = 1;
+        a.write = 1;
+        a.post = POST_REDUCE | POST_RESCALE | POST_LAMBDA;
+        a.fuse = 1;
+        a.slot_idx[0] = 0;  // the energy
+        a.slot_scale[0] = 1.0;
+        a.slot_idx[2] = 1 + pl->p + lp;  // dE/dbeta of the last layer, this group's share
+        a.slot_scale[2] = 2.0;
+        if (pl->inject == AAQAOA_FAULT_DROP_TILE) {
+            a.drop_first_load = 1;
+            pl->inject = 0;
+        }
+        ProfScope ps_(pl, PK_ADJ, S * 3, pass_flags(a));
+        CKL(launch_pass(pl->c128, 2, pl->map_bphi[tn.kb], pl->map_blam[tn.kb], a, grid, pl->stream), "turnaround pass");
+        pl->launches++;
+    }
     // Each layer runs its passes low pass first, so the cut-function work at
     // the layer's end (dE/dgamma, inverse phase) falls in a high pass and the
     // low pass can stop after two register stages.
-    const std::vector<Step> sched = layer_schedule(pl->p, pl->bwd_passes, plan_fuses(pl), true, false);
+    const std::vector<Step> sched = layer_schedule(pl->p, pl->bwd_passes, plan_fuses(pl), true, false, -1, tn.kb);
     for (size_t i = 0; i < sched.size(); i++) {
         const Step &sp = sched[i];
         const Pass &ps = pl->bwd_passes[sp.k];
         const int l = sp.layer;
-        const bool first = i == 0;
+        const bool first = i == 0 && tn.kb < 0;
         PassArgs a = base_args(pl, obs);
         a.B = B;
         a.chunk = chunk;
@@ -588,7 +715,6 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
             a.slot_idx[2] = 1 + pl->p + sp.layer2;
             a.slot_scale[2] = 2.0;
         }
-        const double S = (double)B * (double)((size_t)1 << pl->n) * (double)pl->amp();
         if (ps.cluster) {  // one launch per point, each over that point's cluster tiles
             for (int b = 0; b < B; b++) {
                 PassArgs ab = a;
@@ -1162,12 +1288,12 @@ static int set_layers(aaqaoa_plan *pl, const int plan4[4])
         int T, CB, HB, L, K;
         pass_geometry(pl->c128, nv, &T, &CB, &HB);
         const int L2 = low_two_stage_bits(pl->c128, nv);
-        default_layer(pl->n, T, CB, HB, L2, &L, &K);
+        default_layer(pl->n, T, CB, HB, L2, &L, &K, nv == 2);
         if (plan4[2 * (nv - 1)] > 0)
             L = plan4[2 * (nv - 1)];
         if (plan4[2 * (nv - 1) + 1] > 0)
             K = plan4[2 * (nv - 1) + 1];
-        if (!layer_passes(pl->n, T, CB, HB, L2, L, K, v[nv - 1], nv == 2 && !pl->c128))
+        if (!layer_passes(pl->n, T, CB, HB, L2, L, K, v[nv - 1], nv == 2 && !pl->c128, nv == 2))
             return fail(AAQAOA_ERR_INVALID_ARG, "%s plan: low pass of %d qubits + %d high passes does not tile n=%d",
                         nv == 1 ? "forward" : "adjoint", L, K, pl->n);
     }
@@ -1221,10 +1347,17 @@ int aaqaoa_get_layer_fusion(aaqaoa_plan *pl, int *enable)
 
 int aaqaoa_get_schedule(aaqaoa_plan *pl, int adjoint, int32_t *steps, int cap, int *count)
 {
-    if (!pl || !count || cap < 0 || (cap > 0 && !steps))
-        return fail(AAQAOA_ERR_INVALID_ARG, "plan/count is NULL, cap < 0 or steps is NULL");
-    const std::vector<Pass> &passes = adjoint ? pl->bwd_passes : pl->passes;
-    const std::vector<Step> sched = layer_schedule(pl->p, passes, plan_fuses(pl), adjoint != 0, !adjoint && !pl->c128);
+    if (!pl || !count || cap < 0 || (cap > 0 && !steps) || adjoint < 0 || adjoint > 2)
+        return fail(AAQAOA_ERR_INVALID_ARG, "plan/count is NULL, cap < 0, steps is NULL or adjoint not 0/1/2");
+    const bool bwd = adjoint == 1;
+    const std::vector<Pass> &passes = bwd ? pl->bwd_passes : pl->passes;
+    const Turn tn = adjoint ? turnaround(pl) : Turn{};  // gradient evaluations only
+    std::vector<Step> sched = bwd ? layer_schedule(pl->p, passes, plan_fuses(pl), true, false, -1, tn.kb)
+                                  : layer_schedule(pl->p, passes, plan_fuses(pl), false, !pl->c128, tn.kf);
+    if (adjoint == 2 && tn.kf >= 0)
+        sched.pop_back();  // the turnaround applies the forward's last group
+    if (bwd && tn.kb >= 0)  // the turnaround first: the last layer on its group, forward then back
+        sched.insert(sched.begin(), Step{tn.kb, pl->p - 1, pl->p - 1, 0, true, false});
     *count = (int)sched.size();
     for (int i = 0; i < cap && i < (int)sched.size(); i++) {
         const Pass &ps = passes[sched[i].k];
@@ -1258,13 +1391,13 @@ std::vector<std::array<int, 2>> layer_candidates(const aaqaoa_plan *pl, int nv)
     int T, CB, HB, L, K;
     pass_geometry(pl->c128, nv, &T, &CB, &HB);
     const int L2 = low_two_stage_bits(pl->c128, nv);
-    default_layer(pl->n, T, CB, HB, L2, &L, &K);
+    default_layer(pl->n, T, CB, HB, L2, &L, &K, nv == 2);
     std::vector<std::array<int, 2>> c;
     const bool cl = nv == 2 && !pl->c128;
     for (int k = (cl && K > 1 ? K - 1 : K); k <= K + 1; k++)
         for (int l : {T, L2, CLUSTER_LOW_QUBITS}) {
             std::vector<Pass> v;
-            if (layer_passes(pl->n, T, CB, HB, L2, l, k, v, cl) &&
+            if (layer_passes(pl->n, T, CB, HB, L2, l, k, v, cl, nv == 2) &&
                 std::find(c.begin(), c.end(), std::array<int, 2>{l, k}) == c.end())
                 c.push_back({l, k});
         }

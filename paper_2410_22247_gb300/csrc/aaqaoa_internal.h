@@ -55,6 +55,9 @@ enum PostOp : int {
     POST_GAMMA = 4,       // acc1 += C(x) Im(conj(lambda) phi)     (dE/dgamma)
     POST_PHASE_CONJ = 8,  // phi, lambda *= inverse-layer table    (undo cost layer)
     POST_PHASE = 16,      // phi *= forward table of layer tab_layer (next cost layer)
+    POST_LAMBDA = 32,     // two-vector pass: lambda = O(x) phi formed after the energy
+                          // (the pass's first mixer acts on phi alone: lambda does not
+                          // exist before; the turnaround of a gradient evaluation)
 };
 
 struct PassArgs {
@@ -83,6 +86,7 @@ struct PassArgs {
     int p;            // number of layers
     int tab_len;      // |E| + 1
     double sign_s;    // +1: exp(-i beta H_M); -1: its inverse
+    double sign2;     // the second layer of a fused pass: the same, or 0 for sign_s
     double amp0;      // 2^(-n/2) for the generated |+>^n
     const void *tab;  // this pass's phase tables [B][p][tab_len]: forward-scaled or inverse
     const double2 *cs;  // [B][p] (cos beta_l, sin beta_l)

@@ -844,7 +844,7 @@ __host__ __device__ constexpr int first_owned(int st)
     return k;
 }
 
-template <typename R, int NV, int ST, bool COT, int DUE>
+template <typename R, int NV, int ST, bool COT, int DUE, bool PHI = false>
 __device__ __forceinline__ void mix_regs_form(const PassRegs &A, int cb, R tq, R f, R &run,
                                               typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                               typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc)
@@ -873,7 +873,7 @@ __device__ __forceinline__ void mix_regs_form(const PassRegs &A, int cb, R tq, R
             if (m & (1 << k))
                 continue;
             const int m1 = m | (1 << k);
-            if constexpr (NV == 2) {
+            if constexpr (NV == 2 && !PHI) {
                 const int c = (m >> (k == 0 ? 1 : 0)) & 1;
                 dot_acc(ipp[c], l[m1], a[m]);
                 dot_acc(ipn[c], l[m], a[m1]);
@@ -887,29 +887,29 @@ __device__ __forceinline__ void mix_regs_form(const PassRegs &A, int cb, R tq, R
             else
                 rot(a[m], a[m1], tq);
         }
-        if constexpr (NV == 2) {
+        if constexpr (NV == 2 && !PHI) {
             const R q = ((ipp[0].x + ipp[0].y) + (ipp[1].x + ipp[1].y)) - ((ipn[0].x + ipn[0].y) + (ipn[1].x + ipn[1].y));
             gb = fma(q, sc * sc, gb);
         }
         sc *= f;
     }
     run = sc;
-    if constexpr (NV == 2)
+    if constexpr (NV == 2 && !PHI)
         acc.add(gb);
 }
 
 // cot (Ising plans only, decided per layer) selects the butterfly form once
 // for the whole stage, outside the unrolled loops
-template <typename R, int NV, int ST, bool IS = false, int DUE = -1>
+template <typename R, int NV, int ST, bool IS = false, int DUE = -1, bool PHI = false>
 __device__ __forceinline__ void mix_regs(const PassRegs &A, int cb, R tq, R f, R &run,
                                          typename CT<R>::T (&a)[1 << Geo<R, NV>::RB],
                                          typename CT<R>::T (&l)[1 << Geo<R, NV>::RB], Acc<R> &acc,
                                          bool cot = false)
 {
     if (IS && cot)
-        mix_regs_form<R, NV, ST, true, DUE>(A, cb, tq, f, run, a, l, acc);
+        mix_regs_form<R, NV, ST, true, DUE, PHI>(A, cb, tq, f, run, a, l, acc);
     else
-        mix_regs_form<R, NV, ST, false, DUE>(A, cb, tq, f, run, a, l, acc);
+        mix_regs_form<R, NV, ST, false, DUE, PHI>(A, cb, tq, f, run, a, l, acc);
 }
 
 // One register stage of a pass over the tile(s) in sv0 (and sv1 for NV = 2).
@@ -950,8 +950,8 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
             a[m] = zc[__popc(m) & 3];
     } else {
         load_regs<R, NV, ST>(X.sv0, sb, a);
-        if constexpr (NV == 2)
-            if (!(OPS && X.first && A.pre_lambda))
+        if constexpr (NV == 2)  // lambda exists unless this pass forms it
+            if (!(OPS && X.first && A.pre_lambda) && !(OPS && (A.post & POST_LAMBDA)))
                 load_regs<R, NV, ST>(X.sv1, sb, l);
     }
 
@@ -996,7 +996,10 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         }
     }
 
-    mix_regs<R, NV, ST, IS, DUE>(A, X.cb, X.tq, X.f, X.run, a, l, acc0, X.cot);
+    if (NV == 2 && OPS && (A.post & POST_LAMBDA))  // phi alone (lambda is formed below)
+        mix_regs<R, NV, ST, IS, DUE, true>(A, X.cb, X.tq, X.f, X.run, a, l, acc0, X.cot);
+    else
+        mix_regs<R, NV, ST, IS, DUE>(A, X.cb, X.tq, X.f, X.run, a, l, acc0, X.cot);
 
     if (OPS && LAST && (A.post & POST_RESCALE)) {  // the stored state is the exact one
 #pragma unroll
@@ -1014,6 +1017,13 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         for (int m = 0; m < NR; m++)
             e += (a[m].x * a[m].x + a[m].y * a[m].y) * ov[m];
         acc0.add((A.post & POST_RESCALE) ? e : e * X.fn2);
+        if constexpr (NV == 2) {
+            if (A.post & POST_LAMBDA) {  // lambda = O phi of the exact final state
+#pragma unroll
+                for (int m = 0; m < NR; m++)
+                    l[m] = mkc<C>(a[m].x * ov[m], a[m].y * ov[m]);
+            }
+        }
     }
     if constexpr (NV == 2) {
         if (OPS && LAST && (A.post & (POST_GAMMA | POST_PHASE_CONJ))) {
@@ -1051,7 +1061,8 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
     if (!LAST || A.write) {
         store_regs<R, NV, ST>(X.sv0, sb, a);
         if constexpr (NV == 2)
-            store_regs<R, NV, ST>(X.sv1, sb, l);
+            if (LAST || !(OPS && (A.post & POST_LAMBDA)))  // lambda exists from the last stage on
+                store_regs<R, NV, ST>(X.sv1, sb, l);
     }
 }
 
@@ -1237,6 +1248,7 @@ constexpr int FW_FWD_FUSED = flag_word(1, 0, 0, 1, POST_PHASE);
 constexpr int FW_ADJ_FIRST = flag_word(1, 0, 1, 1, 0);                          // lambda = O phi
 constexpr int FW_ADJ_LAST = flag_word(1, 0, 0, 0, POST_GAMMA);                  // layer 0 ends
 constexpr int FW_ADJ_BOUNDARY = flag_word(1, 0, 0, 1, POST_GAMMA | POST_PHASE_CONJ);
+constexpr int FW_TURN = flag_word(1, 0, 0, 1, POST_REDUCE | POST_RESCALE | POST_LAMBDA);  // forward ends, adjoint starts
 
 // Persistent tiled pass over A.B statevectors, warp-specialised. CTA c takes
 // tiles c, c+G, c+2G, ... (G = gridDim.x) of the B x tiles sequence. The last
@@ -1783,7 +1795,7 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                     X.scale0 = (R)fj;
                     if constexpr (FUSE) {  // the second layer's rotation
                         const double2 cs2 = A.cs[(size_t)b * A.p + A.layer2];
-                        const double c2 = cs2.x, s2 = A.sign_s * cs2.y;
+                        const double c2 = cs2.x, s2 = (A.sign2 != 0.0 ? A.sign2 : A.sign_s) * cs2.y;
                         const bool sh2 = fabs(s2) > fabs(c2);
                         X.cot2 = IS && sh2;
                         X.tq2 = sh2 ? (R)((IS ? c2 : -c2) / s2) : (R)(s2 / c2);
@@ -1883,8 +1895,10 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             run_if(integral_constant<int, FW_ADJ_FIRST>{});
             run_if(integral_constant<int, FW_ADJ_LAST>{});
         }
-        if constexpr (F32 && (MODE == 3 || MODE == 5) && NV == 2)
+        if constexpr (F32 && (MODE == 3 || MODE == 5) && NV == 2) {
             run_if(integral_constant<int, FW_ADJ_BOUNDARY>{});
+            run_if(integral_constant<int, FW_TURN>{});
+        }
         if (!compiled)
             compute(integral_constant<int, -1>{});
     }

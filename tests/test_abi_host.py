@@ -188,19 +188,28 @@ def _schedule(h, adjoint):
     return [tuple(int(v) for v in r) for r in out[:cnt.value]]
 
 
-def _check_schedule(steps, n, p, adjoint, fused, c128=False):
+def _check_schedule(steps, n, p, adjoint, fused, c128=False, turn_group=None):
     """The launches realise Eq. (1) layer by layer: flattened into (layer,
     qubit group) mixer steps (a fused launch is two steps with the next
     layer's diagonal step between them) the layers come in order, each layer
     mixes every qubit exactly once, j0 counts the layer's qubits mixed
     before, and the sweep's last launch is a high pass (it carries the
-    last-stage work: energy, or dE/dgamma of layer 0)."""
-    order = list(range(p - 1, -1, -1)) if adjoint else list(range(p))
+    last-stage work: energy, or dE/dgamma of layer 0). adjoint: 0 the
+    forward sweep of an energy evaluation, 1 the adjoint sweep, 2 the forward
+    sweep of a gradient evaluation. A turnaround pass (a row whose second
+    layer is its own layer) opens the adjoint sweep: it mixes the last
+    layer's group forward and back, and the gradient's forward sweep leaves
+    that group of the last layer to it (turn_group receives (s, q))."""
+    order = list(range(p - 1, -1, -1)) if adjoint == 1 else list(range(p))
+    turn = adjoint == 1 and len(steps) > 0 and steps[0][2] == steps[0][3]
     flat = []
-    for s, q, l, l2, j0 in steps:
+    for i, (s, q, l, l2, j0) in enumerate(steps):
         done = sum(qq for (ll, ss, qq) in flat if ll == l)
         assert j0 == done
         flat.append((l, s, q))
+        if turn and i == 0:
+            assert s > 0 and l == p - 1, "the turnaround is a high pass of the last layer"
+            continue
         if l2 >= 0:
             assert s > 0, "fused launches are high passes"
             assert order.index(l2) == order.index(l) + 1
@@ -210,16 +219,22 @@ def _check_schedule(steps, n, p, adjoint, fused, c128=False):
     assert pos == sorted(pos)
     for l in range(p):
         covered = sorted(b for (ll, s, q) in flat if ll == l for b in range(s, s + q))
+        if adjoint == 2 and turn_group is not None and l == p - 1:
+            covered = sorted(covered + list(range(turn_group[0], turn_group[0] + turn_group[1])))
         assert covered == list(range(n)), l
-    assert steps[-1][0] > 0 and steps[-1][3] == -1
+    if not (adjoint == 2 and turn_group is not None):  # else the turnaround ends the sweep
+        assert steps[-1][0] > 0 and steps[-1][3] == -1
     groups = {(s, q) for s, q, *_ in steps}
-    if not adjoint and not c128 and len(groups) >= 3:
-        # the generating pass takes the first high group, then the low pass
+    if adjoint != 1 and not c128 and len(groups) >= 3:
+        # the generating pass takes a high group, then the low pass
         assert steps[0][0] > 0 and steps[1][0] == 0 and steps[0][2] == steps[1][2] == 0
+    elif turn:
+        assert steps[1][0] == 0, "the turnaround, then the low pass"
     else:
         assert steps[0][0] == 0, "the sweep starts with the low pass"
-    nf = sum(1 for st in steps if st[3] >= 0)
+    nf = sum(1 for i, st in enumerate(steps) if st[3] >= 0 and not (turn and i == 0))
     assert nf == (p - 1 if fused else 0)
+    return turn
 
 
 @pytest.mark.parametrize("n,p,plan4", [(30, 2, (0, 0, 0, 0)), (30, 4, (0, 0, 0, 0)), (30, 5, (9, 3, 12, 3)),
@@ -232,19 +247,41 @@ def test_fused_schedule_realises_the_layers_in_order(n, p, plan4):
         assert N.aaqaoa_get_pass_plan(h, plan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))) == 0
         en = ctypes.c_int()
         assert N.aaqaoa_get_layer_fusion(h, ctypes.byref(en)) == 0 and en.value == 1
-        for adjoint in (0, 1):
-            K = int(plan[2 * adjoint + 1])
-            steps = _schedule(h, adjoint)
-            _check_schedule(steps, n, p, adjoint, fused=K >= 2)
-            assert len(steps) == p * (K + 1) - (p - 1 if K >= 2 else 0)
+        Kf, Kb = int(plan[1]), int(plan[3])
+        steps = _schedule(h, 0)
+        _check_schedule(steps, n, p, 0, fused=Kf >= 2)
+        assert len(steps) == p * (Kf + 1) - (p - 1 if Kf >= 2 else 0)
+        adj = _schedule(h, 1)
+        turn = _check_schedule(adj, n, p, 1, fused=Kb >= 2)
+        assert len(adj) == p * (Kb + 1) - (p - 1 if Kb >= 2 else 0)  # the turnaround takes the place of a pass
+        gf = _schedule(h, 2)
+        _check_schedule(gf, n, p, 2, fused=Kf >= 2, turn_group=adj[0][:2] if turn else None)
+        assert len(gf) == len(steps) - (1 if turn else 0)
         assert N.aaqaoa_set_layer_fusion(h, 0) == 0
-        for adjoint in (0, 1):
-            K = int(plan[2 * adjoint + 1])
-            steps = _schedule(h, adjoint)
-            _check_schedule(steps, n, p, adjoint, fused=False)
+        for mode in (0, 1, 2):
+            K = Kb if mode == 1 else Kf
+            steps = _schedule(h, mode)
+            assert not (mode == 1 and steps[0][2] == steps[0][3]), "no turnaround without fusion"
+            _check_schedule(steps, n, p, mode, fused=False)
             assert len(steps) == p * (K + 1)
     finally:
         N.aaqaoa_destroy(h)
+
+
+def test_turnaround_takes_the_forward_last_group_at_n30():
+    """The n = 30 gradient evaluation: the forward's 8-qubit group 22-29 is
+    also the adjoint's last group, so one turnaround pass ends the forward
+    sweep and opens the adjoint one (p = 2, 3)."""
+    for p in (2, 3):
+        h = _handle(*W.star_graph(30), p=p)
+        try:
+            adj, gf, fe = _schedule(h, 1), _schedule(h, 2), _schedule(h, 0)
+            assert adj[0][:4] == (22, 8, p - 1, p - 1) and adj[0][4] == 0
+            assert gf[-1][:2] != (22, 8) and len(gf) == len(fe) - 1
+            assert _check_schedule(adj, 30, p, 1, fused=True)
+            _check_schedule(gf, 30, p, 2, fused=True, turn_group=(22, 8))
+        finally:
+            N.aaqaoa_destroy(h)
 
 
 def test_complex128_forward_starts_with_the_low_pass():
@@ -256,7 +293,9 @@ def test_complex128_forward_starts_with_the_low_pass():
             steps = _schedule(h, 0)
             _check_schedule(steps, 30, 3, 0, fused=True, c128=bool(flags))
             assert (steps[0][0] == 0) == first_low
-            assert _schedule(h, 1)[0][0] == 0
+            adj = _schedule(h, 1)
+            turn = adj[0][2] == adj[0][3]  # a turnaround first, then the low pass
+            assert adj[1 if turn else 0][0] == 0
         finally:
             N.aaqaoa_destroy(h)
 
@@ -269,8 +308,8 @@ def test_schedule_without_fusion_cases():
             assert N.aaqaoa_set_pass_plan(h, *plan4) == 0
             for adjoint in (0, 1):
                 steps = _schedule(h, adjoint)
-                assert all(st[3] == -1 for st in steps)
-                _check_schedule(steps, n, p, adjoint, fused=False)
+                turn = _check_schedule(steps, n, p, adjoint, fused=False)
+                assert all(st[3] == -1 for st in steps[(1 if turn else 0):])  # a turnaround may open the adjoint
         finally:
             N.aaqaoa_destroy(h)
     h = _handle(*W.cycle_graph(10), p=3)  # whole-circuit kernel: no tiled passes
@@ -363,7 +402,8 @@ def test_cluster_low_pass_plan_and_schedule():
             assert N.aaqaoa_get_schedule(h, 1, steps, 16, ctypes.byref(cnt)) == 0
             rows = [list(steps[5 * i:5 * i + 5]) for i in range(cnt.value)]
             assert cnt.value == 5  # 3 passes per layer, one boundary fused
-            assert rows[0][:2] == [0, 14]
+            turn = rows[0][2] == rows[0][3]  # a turnaround (group 22-29) may open the sweep
+            assert rows[1 if turn else 0][:2] == [0, 14]
             for layer in (0, 1):
                 mixed = set()
                 for s0, q, l, l2, j0 in rows:

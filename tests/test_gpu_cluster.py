@@ -46,7 +46,8 @@ def test_cluster_low_pass_gradient_matches_oracle(n, p, fuse):
     pl, orb = cluster_plan(n, e, p)
     pl.set_layer_fusion(fuse)
     launches = pl.schedule(True)
-    assert launches[0][1] == 14
+    turn = launches[0][2] == launches[0][3]  # a turnaround pass may open the sweep
+    assert launches[1 if turn else 0][1] == 14
     for obs in ("red", "full"):
         oobs = O.full_observable(e) if obs == "full" else O.reduced_observable(e, orb.rep, orb.weight)
         Er, dgr, dbr = O.energy_grad(n, e, g, b, oobs)

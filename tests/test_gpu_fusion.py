@@ -206,7 +206,8 @@ def test_profile_records_each_launch_of_the_schedule():
     g, b = W.random_angles(p, 97)
     pl = _plan(n, e, p, "c64")
     pl.set_pass_plan(*PLANS["c64"][0])
-    fwd, adj = pl.schedule(False), pl.schedule(True)
+    fwd, adj = pl.schedule(False, gradient=True), pl.schedule(True)
+    turn = adj[0][2] == adj[0][3]  # the turnaround pass opens the adjoint sweep
     N.check(N.aaqaoa_profile_enable(pl.handle, 1), "profile")
     pl.grad(g, b, "red")
     recs = pl.profile_launches()
@@ -215,8 +216,70 @@ def test_profile_records_each_launch_of_the_schedule():
     assert kinds == [4] + [0] * len(fwd) + [1] * len(adj)
     fused = [r["fused"] for r in recs[1:]]
     assert fused == [st[3] >= 0 for st in fwd] + [st[3] >= 0 for st in adj]
-    assert sum(fused) == 2 * (p - 1)
-    assert recs[1]["cut_work"] and recs[len(fwd)]["cut_work"]  # phase first, energy last
+    assert sum(fused) == 2 * (p - 1) + (1 if turn else 0)
+    # phase first; the energy in the forward's last pass or in the turnaround
+    assert recs[1]["cut_work"] and recs[len(fwd) + (1 if turn else 0)]["cut_work"]
     assert all(r["ms"] > 0 for r in recs[1:])
     S = (1 << n) * 8
     assert recs[1]["bytes"] == S and recs[len(fwd) + 1]["bytes"] == 3 * S  # |+> store; phi in, phi and lambda out
+
+
+# pass plans at n = 18..24 whose gradient schedule opens the adjoint with a
+# turnaround pass (the forward's last group is one of the adjoint's groups),
+# read off the host schedule
+TURN_PLANS = [("c64", 18, (8, 2, 8, 2)), ("c64", 20, (7, 2, 8, 2)), ("c64", 22, (7, 2, 8, 2)),
+              ("c64", 24, (7, 3, 9, 3)), ("c128", 18, (7, 2, 8, 2)), ("c128", 20, (5, 2, 6, 2)),
+              ("c128", 22, (5, 2, 6, 2))]
+
+
+@pytest.mark.parametrize("precision,n,plan4", TURN_PLANS)
+def test_turnaround_gradient_matches_oracle_and_the_unfused_sweeps(n, plan4, precision):
+    """The turnaround pass (the forward's last group mixed forward on phi,
+    the energy and lambda = O phi, then both vectors mixed back) gives the
+    oracle's energy and gradient, for H_red and H_C, p = 1..3, and the same
+    as the sweeps without fusion (no turnaround)."""
+    _, e = W.prufer_tree(n, 5)
+    for p in (1, 2, 3):
+        g, b = W.random_angles(p, 40 + n + p)
+        pl = _plan(n, e, p, precision)
+        pl.set_pass_plan(*plan4)
+        adj = pl.schedule(True)
+        assert adj[0][2] == adj[0][3], (n, plan4, adj[0])
+        orb = ORB.edge_orbits(n, e)
+        for obs in ("red", "full"):
+            oobs = O.full_observable(e) if obs == "full" else O.reduced_observable(e, orb.rep, orb.weight)
+            Er, dgr, dbr = O.energy_grad(n, e, g, b, oobs)
+            E, dg, db = pl.grad(g, b, obs)
+            gs = max(abs(Er), 1.0) * (1.0 if precision == "c64" else 1e-3)
+            assert abs(E - Er) <= TOL[precision] * max(abs(Er), 1.0), (obs, E, Er)
+            assert _rel(dg, dgr, gs) < TOL[precision] and _rel(db, dbr, gs) < TOL[precision], obs
+        E1, dg1, db1 = pl.grad(g, b, "red")
+        pl.set_layer_fusion(False)
+        assert not pl.schedule(True)[0][2] == pl.schedule(True)[0][3]
+        E0, dg0, db0 = pl.grad(g, b, "red")
+        sc = max(abs(E0), 1.0)
+        assert abs(E1 - E0) <= TOL[precision] * sc
+        assert np.max(np.abs(np.concatenate([dg1 - dg0, db1 - db0]))) <= TOL[precision] * sc
+        pl.close()
+
+
+def test_turnaround_batch_and_boundary_angles_c64():
+    """Batched gradients through the turnaround (each point its own
+    parameters) and angles with |sin beta| > |cos beta| (the shifted
+    rotation in both halves of the turnaround), against the oracle."""
+    n, e = W.prufer_tree(20, 3)
+    p, B = 2, 5
+    rng = W.rng(21)
+    gs = rng.uniform(-np.pi, np.pi, size=(B, p))
+    bs = rng.uniform(-np.pi / 2, np.pi / 2, size=(B, p))
+    gs[0], bs[0] = [0.9, 1.3], [np.pi / 2 - 0.1, -np.pi / 4 - 0.2]
+    pl = _plan(n, e, p, "c64", batch=3)
+    pl.set_pass_plan(7, 2, 8, 2)
+    assert pl.schedule(True)[0][2] == pl.schedule(True)[0][3]
+    E, dg, db = pl.grad_batch(gs, bs, "red")
+    for k in range(B):
+        Er, dgr, dbr = O.energy_grad(n, e, gs[k], bs[k])
+        sc = max(abs(Er), 1.0)
+        assert abs(E[k] - Er) <= 1e-5 * sc
+        assert _rel(dg[k], dgr, sc) < 1e-5 and _rel(db[k], dbr, sc) < 1e-5, k
+    pl.close()
