@@ -333,13 +333,15 @@ def run_native(args, rank, world, local):
                 "profile read")
         if c.value:
             prof[nm] = {"ms": t.value, "launches": c.value, "bytes": by.value}
-    # the tiled passes by class: mixer only, with cut-function work, fused boundary
+    # the tiled passes by class: mixer only, with cut-function work, fused
+    # boundary, the turnaround (the forward's last group and the adjoint's first)
     classes = {}
     for r in plan.profile_launches():
         if r["kind"] not in (0, 1):
             continue
         cls = ("forward" if r["kind"] == 0 else "adjoint") + (
-            "_fused" if r["fused"] else "_cut_work" if r["cut_work"] else "_mixer_only")
+            "_turnaround" if r.get("turnaround") else "_fused" if r["fused"] else "_cut_work" if r["cut_work"]
+            else "_mixer_only")
         c = classes.setdefault(cls, {"launches": 0, "ms": 0.0, "bytes": 0.0})
         c["launches"] += 1
         c["ms"] += r["ms"]

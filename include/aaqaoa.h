@@ -558,9 +558,9 @@ int aaqaoa_stats(aaqaoa_plan *plan, aaqaoa_stats_t *out);
  * aaqaoa_profile_launches -- the recorded launches one by one, in launch
  * order: per launch its kind (as above), flags (bit 0: the pass carries
  * cut-function work -- phase, lambda = O phi, energy, dE/dgamma, inverse
- * phase; bit 1: a fused layer boundary; bit 2: the cluster low pass), event
- * duration (ms) and bytes to
- * move. kind, flags, ms, bytes: host arrays of at least max entries, each may
+ * phase; bit 1: a fused layer boundary; bit 2: the cluster low pass; bit 3:
+ * the turnaround pass of a gradient evaluation), event duration (ms) and
+ * bytes to move. kind, flags, ms, bytes: host arrays of at least max entries, each may
  * be NULL. *count (host int) receives the number of records, also when it
  * exceeds max. Synchronises the plan's stream. INVALID_ARG for a NULL plan
  * or count, or max < 0.

@@ -209,7 +209,7 @@ class Plan:
         """The launches recorded since profiling was enabled
         (aaqaoa_profile_enable), in order: dicts of kind (0 forward pass,
         1 adjoint pass, 2 whole circuit, 3 aggregation, 4 parameter tables),
-        cut_work, fused, ms and bytes."""
+        cut_work, fused, cluster, turnaround, ms and bytes."""
         cnt = ctypes.c_int()
         N.check(N.aaqaoa_profile_launches(self.handle, 0, ctypes.byref(cnt), None, None, None, None),
                 "aaqaoa_profile_launches")
@@ -222,7 +222,7 @@ class Plan:
                                           _ptr(flags, ctypes.c_int32), _ptr(ms, ctypes.c_double),
                                           _ptr(by, ctypes.c_double)), "aaqaoa_profile_launches")
         return [{"kind": int(kind[i]), "cut_work": bool(flags[i] & 1), "fused": bool(flags[i] & 2),
-                 "cluster": bool(flags[i] & 4),
+                 "cluster": bool(flags[i] & 4), "turnaround": bool(flags[i] & 8),
                  "ms": float(ms[i]), "bytes": float(by[i])} for i in range(n)]
 
     def autotune(self):
