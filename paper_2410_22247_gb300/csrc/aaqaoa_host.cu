@@ -459,15 +459,6 @@ std::vector<Step> layer_schedule_from(int p, const std::vector<Pass> &passes, bo
                 if (k != skip)
                     order.push_back(k);
         }
-        if (reverse && !more && order.size() >= 2) {
-            // the adjoint's last pass (read-only, dE/dgamma of layer 0) is
-            // compute-bound: end on the smallest high group
-            size_t best = order.size() - 1;
-            for (size_t o = 0; o + 1 < order.size(); o++)
-                if (!passes[order[o]].is_low && passes[order[o]].qubits < passes[order[best]].qubits)
-                    best = o;
-            std::rotate(order.begin() + best, order.begin() + best + 1, order.end());
-        }
         int j0 = done0;
         for (size_t o = 0; o < order.size(); o++) {
             const int k = order[o];
