@@ -594,15 +594,20 @@ def batch_extras(dev, stream):
 
 
 def traffic_from_profiles():
-    """dram bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+    """dram bytes per launch of the dominant kernel from the committed ncu
+    summary, and a note: the figure is null when the summary marks its
+    counters as taken on an earlier form of the kernel."""
     path = os.path.join(ROOT, "profiles", "adjoint_pass_n30_c64_traffic.txt")
+    val, note = None, None
     try:
         for ln in open(path):
             if ln.startswith("dram_bytes_per_launch:"):
-                return float(ln.split(":")[1])
+                val = float(ln.split(":")[1])
+            elif ln.startswith("traffic_note:"):
+                note = ln.split(":", 1)[1].strip()
     except OSError:
         pass
-    return None
+    return val, note
 
 
 def profile_case(n, precision="c64"):
@@ -702,6 +707,7 @@ def main():
     # written once and phi, lambda read and written once per layer
     adj_alg = (4 * P_LAYERS + 1) * S
     adj_alg_gbps = adj_alg * K / (adj["ms"] / 1000.0) / 1e9 if adj else None
+    traffic = traffic_from_profiles()
     step_gbps = B_alg / (result["ms"] / K / 1000.0) / 1e9
     cpu = cpu_baseline()
     errs = error_vs_oracle(result["rows"], result["angles"], RESULTS_FOR_ORACLE)
@@ -735,7 +741,7 @@ def main():
                      "algorithmic_bytes_per_step": adj_alg, "algorithmic_bytes_per_launch": adj_alg / (d["launches"] / K),
                      "achieved_streamed": achieved, "frac_streamed": achieved / peak,
                      "streamed_basis": "bytes the kernel streams (vectors loaded + stored per launch)",
-                     "traffic": traffic_from_profiles(),
+                     "traffic": traffic[0], "traffic_note": traffic[1],
                      "streamed_bytes_per_launch": d["bytes"] / d["launches"], "launches": d["launches"]},
         "step_algorithmic": {"bytes": B_alg, "formula": "(6p+1)*2^n*8", "GBps": step_gbps,
                              "frac": step_gbps / peak},

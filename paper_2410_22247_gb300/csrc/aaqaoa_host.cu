@@ -525,7 +525,8 @@ bool plan_fuses(const aaqaoa_plan *pl) { return pl->fuse && !pl->pt_dev; }
 // lambda = O phi of the exact final state) and the adjoint's first (both
 // vectors mixed back with the dE/dbeta terms), so phi is read once and the
 // final state never stored: the forward's last pass and the adjoint's first
-// (2 S of traffic) become one launch (3 S). It needs the forward's last
+// (5 S of traffic) become one launch (complex64: 2 S, phi is left as
+// loaded, see enqueue_backward; complex128: 3 S). It needs the forward's last
 // group to be one of the adjoint's high groups (same first qubit and size)
 // and a forward order that ends there. kf, kb: those groups, or -1.
 struct Turn {
@@ -640,7 +641,10 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
     if (tn.kb >= 0) {
         // load phi before the layer's last group, mix it forward (phi alone),
         // rescale, energy, lambda = O phi, mix both back: a fused pass whose
-        // two layers are the same layer with opposite signs
+        // two layers are the same layer with opposite signs. Mixed back, phi
+        // is the loaded phi times a known factor, so complex64 does not store
+        // it: the kernel stores lambda times that factor instead (2 S moved,
+        // not 3 S; complex128 stores both)
         const Pass &ps = pl->bwd_passes[tn.kb];
         PassArgs a = base_args(pl, obs);
         a.B = B;
@@ -669,7 +673,7 @@ int enqueue_backward(aaqaoa_plan *pl, int B, int obs)
             a.drop_first_load = 1;
             pl->inject = 0;
         }
-        ProfScope ps_(pl, PK_ADJ, S * 3, pass_flags(a));
+        ProfScope ps_(pl, PK_ADJ, S * (pl->c128 ? 3 : 2), pass_flags(a));
         CKL(launch_pass(pl->c128, 2, pl->map_bphi[tn.kb], pl->map_blam[tn.kb], a, grid, pl->stream), "turnaround pass");
         pl->launches++;
     }

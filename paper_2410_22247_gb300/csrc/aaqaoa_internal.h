@@ -57,7 +57,9 @@ enum PostOp : int {
     POST_PHASE = 16,      // phi *= forward table of layer tab_layer (next cost layer)
     POST_LAMBDA = 32,     // two-vector pass: lambda = O(x) phi formed after the energy
                           // (the pass's first mixer acts on phi alone: lambda does not
-                          // exist before; the turnaround of a gradient evaluation)
+                          // exist before; the turnaround of a gradient evaluation;
+                          // complex64: phi stays as loaded, lambda is stored scaled
+                          // to match it)
 };
 
 struct PassArgs {

@@ -637,6 +637,12 @@ struct PassRegs {
     double amp0;
 };
 
+// The turnaround pass (POST_LAMBDA) leaves phi as loaded and stores lambda
+// scaled to match it (complex64; complex128 passes are FP64-bound and store
+// both vectors, the extra state would cost them spills).
+template <typename R>
+constexpr bool turn_keeps_phi = std::is_same<R, float>::value;
+
 template <typename R>
 struct StageCtx {
     typename CT<R>::T *sv0, *sv1;
@@ -654,6 +660,11 @@ struct StageCtx {
     R scale0;      // f^j0: butterflies of this layer applied by earlier passes
     R run;         // f^j for the current tile (advanced by every butterfly)
     R amp0;        // 2^(-n/2), the amplitude of the generated |+>^n
+    // turnaround pass (POST_LAMBDA, turn_keeps_phi): phi is not stored back,
+    // the stored lambda carries kap = f^(2 j0 - n) instead (see run_stage),
+    // and the pass's dE/dbeta sums are multiplied by 1/kap once per point
+    R kap;
+    double ikap;
     R tq2, f2;     // fused pass: rotation of the second layer
     R run2;        // its f^j (the second layer starts on exact vectors: j = 0)
     bool cot, cot2;  // Ising plans: the layer (second layer) uses the cot form
@@ -1019,9 +1030,17 @@ __device__ __forceinline__ void run_stage(const PassRegs &A, StageCtx<R> &X,
         acc0.add((A.post & POST_RESCALE) ? e : e * X.fn2);
         if constexpr (NV == 2) {
             if (A.post & POST_LAMBDA) {  // lambda = O phi of the exact final state
+                // Mixing this pass's q qubits forward (t), rescaling by f^n and
+                // mixing them back (-t) multiplies phi by f^n (1 + t^2)^q =
+                // f^(n - 2q) = 1/kap: the phi this pass would store is the one
+                // it loaded times 1/kap. It is not stored; lambda is stored
+                // times kap, so every later product of the two is unchanged
+                // (complex64; complex128 stores both as they are).
 #pragma unroll
-                for (int m = 0; m < NR; m++)
-                    l[m] = mkc<C>(a[m].x * ov[m], a[m].y * ov[m]);
+                for (int m = 0; m < NR; m++) {
+                    const R w = turn_keeps_phi<R> ? ov[m] * X.kap : ov[m];
+                    l[m] = mkc<C>(a[m].x * w, a[m].y * w);
+                }
             }
         }
     }
@@ -1079,7 +1098,8 @@ __device__ __forceinline__ void mix_stage(const PassRegs &A, StageCtx<R> &X,
     if constexpr (NV == 2)
         load_regs<R, NV, ST>(X.sv1, sb, l);
     mix_regs<R, NV, ST, IS, DUE>(A, X.cb, X.tq2, X.f2, X.run2, a, l, acc2, X.cot2);
-    store_regs<R, NV, ST>(X.sv0, sb, a);
+    if (!(turn_keeps_phi<R> && NV == 2 && (A.post & POST_LAMBDA)))  // the turnaround keeps the loaded phi
+        store_regs<R, NV, ST>(X.sv0, sb, a);
     if constexpr (NV == 2)
         store_regs<R, NV, ST>(X.sv1, sb, l);
 }
@@ -1627,7 +1647,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                     tile_coords(k, b, t, mid, c4);
                     unsigned char *buf = sm + (size_t)s * NV * TB;
                     const int c1 = A.wide_rows ? 0 : (int)mid, c2 = A.wide_rows ? (int)mid : 0;
-                    tma_store_5d(&map0, buf, 0, c1, c2, 0, c4);
+                    if (!(turn_keeps_phi<R> && NV == 2 && (A.post & POST_LAMBDA)))  // the turnaround keeps phi
+                        tma_store_5d(&map0, buf, 0, c1, c2, 0, c4);
                     if (NV == 2)
                         tma_store_5d(&map1, buf + TB, 0, c1, c2, 0, c4);
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
@@ -1698,6 +1719,8 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
             int pend_b = -1, tslot = 1, par = 1;
             auto stash = [&](int b) {
                 double s0 = acc0.get(), s1 = acc1.get(), s2 = acc2.get();
+                if (turn_keeps_phi<R> && NV == 2 && (P.post & POST_LAMBDA))  // lambda carried kap
+                    s2 *= X.ikap;
     #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -1793,6 +1816,10 @@ __global__ void __maxnreg__((Geo<R, NV>::MAXREG))
                     X.fn = (R)fn;
                     X.fn2 = (R)(fn * fn);
                     X.scale0 = (R)fj;
+                    if constexpr (turn_keeps_phi<R> && NV == 2) {
+                        X.kap = (R)(fj * fj / fn);  // f^(2 j0 - n), j0 = n - q
+                        X.ikap = fn / (fj * fj);
+                    }
                     if constexpr (FUSE) {  // the second layer's rotation
                         const double2 cs2 = A.cs[(size_t)b * A.p + A.layer2];
                         const double c2 = cs2.x, s2 = (A.sign2 != 0.0 ? A.sign2 : A.sign_s) * cs2.y;

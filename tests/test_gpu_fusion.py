@@ -221,7 +221,9 @@ def test_profile_records_each_launch_of_the_schedule():
     assert recs[1]["cut_work"] and recs[len(fwd) + (1 if turn else 0)]["cut_work"]
     assert all(r["ms"] > 0 for r in recs[1:])
     S = (1 << n) * 8
-    assert recs[1]["bytes"] == S and recs[len(fwd) + 1]["bytes"] == 3 * S  # |+> store; phi in, phi and lambda out
+    # |+> store; the adjoint's first launch: phi in, phi and lambda out, or
+    # the complex64 turnaround: phi in, lambda out (phi stays as loaded)
+    assert recs[1]["bytes"] == S and recs[len(fwd) + 1]["bytes"] == (2 if turn else 3) * S
 
 
 # pass plans at n = 18..24 whose gradient schedule opens the adjoint with a
@@ -263,19 +265,26 @@ def test_turnaround_gradient_matches_oracle_and_the_unfused_sweeps(n, plan4, pre
         pl.close()
 
 
-def test_turnaround_batch_and_boundary_angles_c64():
+@pytest.mark.parametrize("n", [20, 21])
+def test_turnaround_batch_and_boundary_angles_c64(n):
     """Batched gradients through the turnaround (each point its own
     parameters) and angles with |sin beta| > |cos beta| (the shifted
-    rotation in both halves of the turnaround), against the oracle."""
-    n, e = W.prufer_tree(20, 3)
+    rotation in both halves of the turnaround), against the oracle. The
+    complex64 turnaround stores lambda times f^(n - 2q) and leaves phi as
+    loaded (f the factor one butterfly drops, q the pass's qubits): at
+    n = 21 the exponent is odd, and the last layer's f is negative in both
+    rotation forms (beta = -pi/4 - 0.2 shifted, beta = 2.8 not)."""
+    e = W.prufer_tree(n, 3)[1]
     p, B = 2, 5
     rng = W.rng(21)
     gs = rng.uniform(-np.pi, np.pi, size=(B, p))
     bs = rng.uniform(-np.pi / 2, np.pi / 2, size=(B, p))
     gs[0], bs[0] = [0.9, 1.3], [np.pi / 2 - 0.1, -np.pi / 4 - 0.2]
+    bs[1, 1] = 2.8
     pl = _plan(n, e, p, "c64", batch=3)
     pl.set_pass_plan(7, 2, 8, 2)
-    assert pl.schedule(True)[0][2] == pl.schedule(True)[0][3]
+    turn = pl.schedule(True)[0]
+    assert turn[2] == turn[3]  # a turnaround over q = 6 (n = 20) or 7 (n = 21) qubits
     E, dg, db = pl.grad_batch(gs, bs, "red")
     for k in range(B):
         Er, dgr, dbr = O.energy_grad(n, e, gs[k], bs[k])
