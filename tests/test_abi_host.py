@@ -224,7 +224,11 @@ def _check_schedule(steps, n, p, adjoint, fused, c128=False, turn_group=None):
         assert covered == list(range(n)), l
     if not (adjoint == 2 and turn_group is not None):  # else the turnaround ends the sweep
         assert steps[-1][0] > 0 and steps[-1][3] == -1
+    # a layer's qubit groups (at p = 1 the gradient's forward sweep holds
+    # all but the one the turnaround takes)
     groups = {(s, q) for s, q, *_ in steps}
+    if adjoint == 2 and turn_group is not None:
+        groups.add(tuple(turn_group))
     if adjoint != 1 and not c128 and len(groups) >= 3:
         # the generating pass takes a high group, then the low pass
         assert steps[0][0] > 0 and steps[1][0] == 0 and steps[0][2] == steps[1][2] == 0
@@ -266,6 +270,40 @@ def test_fused_schedule_realises_the_layers_in_order(n, p, plan4):
             assert len(steps) == p * (K + 1)
     finally:
         N.aaqaoa_destroy(h)
+
+
+def test_random_pass_plans_schedule_every_layer_once():
+    """400 seeded pass plans (n = 14..34, p = 1..4, both precisions, layer
+    fusion on and off): every sweep the host schedules -- energy, adjoint,
+    the gradient's forward sweep -- realises Eq. (1) layer by layer, with
+    the launch counts the plan implies; no device needed."""
+    rng = np.random.default_rng(7)
+    tried = 0
+    while tried < 400:
+        n, p = int(rng.integers(14, 35)), int(rng.integers(1, 5))
+        plan4 = (int(rng.integers(5, 14)), int(rng.integers(1, 4)), int(rng.integers(5, 13)), int(rng.integers(1, 4)))
+        for flags in (0, 1):
+            h = _handle(*W.star_graph(n), p=p, flags=flags)
+            try:
+                if N.aaqaoa_set_pass_plan(h, *plan4) != 0:
+                    continue
+                tried += 1
+                Kf, Kb = plan4[1], plan4[3]
+                for fuse in (1, 0):
+                    assert N.aaqaoa_set_layer_fusion(h, fuse) == 0
+                    ff, fb = bool(fuse) and Kf >= 2, bool(fuse) and Kb >= 2
+                    fwd = _schedule(h, 0)
+                    _check_schedule(fwd, n, p, 0, fused=ff, c128=bool(flags))
+                    assert len(fwd) == p * (Kf + 1) - (p - 1 if ff else 0)
+                    adj = _schedule(h, 1)
+                    turn = _check_schedule(adj, n, p, 1, fused=fb, c128=bool(flags))
+                    assert len(adj) == p * (Kb + 1) - (p - 1 if fb else 0)
+                    assert not turn or fuse, (n, p, plan4)
+                    gf = _schedule(h, 2)
+                    _check_schedule(gf, n, p, 2, fused=ff, c128=bool(flags), turn_group=adj[0][:2] if turn else None)
+                    assert len(gf) == len(fwd) - (1 if turn else 0)
+            finally:
+                N.aaqaoa_destroy(h)
 
 
 def test_turnaround_takes_the_forward_last_group_at_n30():
