@@ -703,8 +703,8 @@ def main():
     B_alg = (6 * P_LAYERS + 1) * S
     K = args.steps
     adj = prof.get("adjoint_pass")
-    # algorithmic bytes of the adjoint per step (Sec. 8(d) model): lambda
-    # written once and phi, lambda read and written once per layer
+    # algorithmic bytes of the adjoint per step: lambda written once and
+    # phi, lambda read and written once per layer
     adj_alg = (4 * P_LAYERS + 1) * S
     adj_alg_gbps = adj_alg * K / (adj["ms"] / 1000.0) / 1e9 if adj else None
     traffic = traffic_from_profiles()
