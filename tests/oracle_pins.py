@@ -185,12 +185,57 @@ def check_invariants():
     return worst
 
 
+def check_max_cut():
+    """C_max by exhaustion against textbook values: a tree (bipartite) cuts
+    every edge; K_n cuts floor(n/2) * ceil(n/2); a cycle cuts n edges if n
+    is even, n - 1 if odd; K_{a,b} cuts a*b; the Petersen graph's maximum cut
+    is 12. The maximiser returned is the smallest: on C_6, x = 0b010101 and
+    every smaller x cuts less. Returns the largest violation (in edges)."""
+    worst = 0.0
+    for n, e in (W.prufer_tree(12, 4), W.heap_binary_tree(15), W.balanced_tree(3, 2), W.star_graph(9)):
+        c, x = O.max_cut(n, e)
+        worst = max(worst, abs(c - len(e)), abs(O.cut_value(e, x) - c))
+    for n in range(2, 10):
+        worst = max(worst, abs(O.max_cut(*W.complete_graph(n))[0] - (n // 2) * ((n + 1) // 2)))
+    for n in range(3, 12):
+        worst = max(worst, abs(O.max_cut(*W.cycle_graph(n))[0] - (n - n % 2)))
+    kab = W.canonical_edges([(i, 3 + j) for i in range(3) for j in range(4)])
+    worst = max(worst, abs(O.max_cut(7, kab)[0] - 12), abs(O.max_cut(*W.generalized_petersen(5, 2))[0] - 12))
+    n, e = W.cycle_graph(6)
+    c, x = O.max_cut(n, e)
+    worst = max(worst, float(x != 0b010101), float(any(O.cut_value(e, y) >= c for y in range(x))))
+    return float(worst)
+
+
+def check_sampler():
+    """Inverse-CDF sampling with given uniforms: a basis state always
+    returns itself; |+>^6 returns floor(u 2^6); 100000 stratified uniforms
+    reproduce every probability of an unnormalised random state to one
+    count. Returns the largest violation (in states or counts)."""
+    n = 6
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[37] = 1.0
+    worst = float(np.max(np.abs(O.sample(psi, np.linspace(0.0, 0.999, 50)).astype(np.int64) - 37)))
+    u = (np.arange(640) + 0.37) / 640
+    got = O.sample(O.plus_state(n), u).astype(np.int64)
+    worst = max(worst, float(np.max(np.abs(got - np.floor(u * 64).astype(np.int64)))))
+    rng = W.rng(3)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    pr = np.abs(psi) ** 2 / np.sum(np.abs(psi) ** 2)
+    K = 100000
+    counts = np.bincount(O.sample(psi, (np.arange(K) + 0.5) / K).astype(np.int64), minlength=1 << n)
+    worst = max(worst, float(np.max(np.abs(counts - K * pr))) - 1.0 - 1e-9)
+    return max(worst, 0.0)
+
+
 ALL_CHECKS = {
     "bruteforce": check_bruteforce,
     "closed_form": check_closed_form,
     "symmetric": check_symmetric,
     "finite_difference": check_finite_difference,
     "invariants": check_invariants,
+    "max_cut": check_max_cut,
+    "sampler": check_sampler,
 }
 
 

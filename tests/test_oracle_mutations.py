@@ -38,6 +38,12 @@ MUTATIONS = {
     "ising_gamma_grad_uses_observable": (
         "im_sum += cimag(conj(lam[x]) * oracle_ising_value(m, edges, w, n, h, x) * phi[x]);",
         "im_sum += cimag(conj(lam[x]) * oracle_ising_value(k, oedges, ow, n, oh, x) * phi[x]);"),
+    "terms_zz_sign": ("s += w[e] * 0.5 * (1.0 - oracle_zz(", "s += w[e] * 0.5 * (1.0 + oracle_zz("),
+    "max_cut_comparison_flipped": ("if (c > best) {", "if (c < best) {"),
+    "max_cut_ties_take_the_last": ("if (c > best) {", "if (c >= best) {"),
+    "sampler_exclusive_cdf": ("        s += a * a + b * b;\n        cdf[x] = s;",
+                              "        cdf[x] = s;\n        s += a * a + b * b;"),
+    "sampler_unnormalised": ("const double t = u[k] * s;", "const double t = u[k];"),
 }
 
 

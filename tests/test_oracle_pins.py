@@ -61,42 +61,15 @@ def test_single_qubit_rx_by_hand(oracle_lib):
 
 
 def test_max_cut_closed_forms(oracle_lib):
-    """C_max by exhaustion against textbook values: a tree (bipartite) cuts every
-    edge; K_n cuts floor(n/2) * ceil(n/2); a cycle cuts n edges if n is even,
-    n - 1 if odd; K_{a,b} cuts a*b; the Petersen graph's maximum cut is 12."""
-    for n, e in (W.prufer_tree(12, 4), W.heap_binary_tree(15), W.balanced_tree(3, 2), W.star_graph(9)):
-        c, x = O.max_cut(n, e)
-        assert c == len(e) and O.cut_value(e, x) == c
-    for n in range(2, 10):
-        assert O.max_cut(*W.complete_graph(n))[0] == (n // 2) * ((n + 1) // 2)
-    for n in range(3, 12):
-        assert O.max_cut(*W.cycle_graph(n))[0] == n - (n % 2)
-    kab = W.canonical_edges([(i, 3 + j) for i in range(3) for j in range(4)])
-    assert O.max_cut(7, kab)[0] == 12
-    assert O.max_cut(*W.generalized_petersen(5, 2))[0] == 12
-    # the smallest maximiser: x = 0 never cuts, so it is the first x that does
-    n, e = W.cycle_graph(6)
-    c, x = O.max_cut(n, e)
-    assert x == 0b010101 and all(O.cut_value(e, y) < c for y in range(x))
+    """Tree, K_n, cycle, K_{a,b} and Petersen maxima and the smallest
+    maximiser (oracle_pins.check_max_cut)."""
+    assert P.check_max_cut() == 0
 
 
 def test_inverse_cdf_sampler(oracle_lib):
-    """A basis state always returns itself; |+>^n returns floor(u 2^n);
-    stratified uniforms reproduce every probability to one count."""
-    n = 6
-    psi = np.zeros(1 << n, dtype=np.complex128)
-    psi[37] = 1.0
-    assert set(O.sample(psi, np.linspace(0.0, 0.999, 50)).tolist()) == {37}
-    plus = O.plus_state(n)
-    u = (np.arange(640) + 0.37) / 640
-    assert np.array_equal(O.sample(plus, u), np.floor(u * 64).astype(np.uint64))
-    rng = W.rng(3)
-    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
-    p = np.abs(psi) ** 2 / np.sum(np.abs(psi) ** 2)
-    K = 100000
-    x = O.sample(psi, (np.arange(K) + 0.5) / K)
-    counts = np.bincount(x.astype(np.int64), minlength=1 << n)
-    assert np.all(np.abs(counts - K * p) <= 1.0 + 1e-9)
+    """Basis state, |+>^n and stratified uniforms on a random state
+    (oracle_pins.check_sampler)."""
+    assert P.check_sampler() == 0
 
 
 def test_weighted_oracle_matches_dense_and_scaling(oracle_lib):
