@@ -463,19 +463,27 @@ int aaqaoa_set_layer_fusion(aaqaoa_plan *plan, int enable);
 int aaqaoa_get_layer_fusion(aaqaoa_plan *plan, int *enable);
 
 /*
- * aaqaoa_get_schedule -- the tiled passes one forward (adjoint = 0) or adjoint
- * (adjoint = 1) sweep launches, in order, as 5 ints each (host, row-major
- * [cap][5]): the pass's first qubit s, its qubit count, the layer l whose
- * mixer it applies there, the second layer of a fused pass or -1, and the
- * number of layer l's qubits mixed by earlier passes. The forward sweep runs
- * layers 0..p-1, the adjoint p-1..0; within a layer the low pass comes first,
- * except the first layer of a complex64 forward sweep with two or more high
- * passes, which starts on its first high group (the pass that generates the
- * state), and a layer always ends on a high pass. *count (host int)
- * receives the number of passes; at most cap rows are written. Needs no
- * device. Plans small enough for the whole-circuit kernel have no tiled
- * passes (*count = 0).
- * INVALID_ARG for NULL plan/count, cap < 0 or steps NULL with cap > 0.
+ * aaqaoa_get_schedule -- the tiled passes one sweep launches, in order, as
+ * 5 ints each (host, row-major [cap][5]): the pass's first qubit s, its
+ * qubit count, the layer l whose mixer it applies there, the second layer of
+ * a fused pass or -1, and the number of layer l's qubits mixed by earlier
+ * passes. adjoint = 0: the forward sweep of an energy evaluation; 1: the
+ * adjoint sweep of a gradient evaluation; 2: the forward sweep of a gradient
+ * evaluation. Forward sweeps run layers 0..p-1, the adjoint p-1..0; within
+ * a layer the low pass comes first, except the first layer of a complex64
+ * forward sweep with two or more high passes, which starts on a high group
+ * (the pass that generates the state), and a layer ends on a high pass.
+ * With layer fusion, when the forward's last group is one of the adjoint's
+ * high groups, a gradient evaluation joins the forward's last pass and the
+ * adjoint's first into one turnaround pass: it is the adjoint sweep's first
+ * row, its second layer equal to its layer (the last layer, mixed forward on
+ * phi, then back on phi and lambda), and the gradient's forward sweep
+ * (adjoint = 2) leaves that group of the last layer to it (its last row may
+ * then be a low pass). *count (host int) receives the number of passes; at
+ * most cap rows are written. Needs no device. Plans small enough for the
+ * whole-circuit kernel have no tiled passes (*count = 0).
+ * INVALID_ARG for NULL plan/count, cap < 0, steps NULL with cap > 0, or
+ * adjoint not 0, 1 or 2.
  */
 int aaqaoa_get_schedule(aaqaoa_plan *plan, int adjoint, int32_t *steps, int cap, int *count);
 
