@@ -453,8 +453,11 @@ int aaqaoa_autotune(aaqaoa_plan *plan, int *plan4);
  * meet at a diagonal step). With p >= 2 and at least two high passes per
  * layer, the pass that ends layer l also applies the next layer's cost phase
  * (the inverse phase in the adjoint) and its mixer on the same qubits, so the
- * statevector is read and written once less per layer boundary. Results are
- * the same up to rounding order. enable: 1 (the default) or 0.
+ * statevector is read and written once less per layer boundary. The same
+ * setting enables the turnaround pass of gradient evaluations (the forward's
+ * last pass and the adjoint's first in one launch, see aaqaoa_get_schedule;
+ * any p >= 1). Results are the same up to rounding order. enable: 1 (the
+ * default) or 0.
  * aaqaoa_get_layer_fusion writes the setting to *enable (host int).
  * INVALID_ARG for a NULL plan/pointer or enable not 0/1. The stored state
  * becomes invalid.
