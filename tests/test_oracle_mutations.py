@@ -98,3 +98,38 @@ def test_lightcone_pin_catches_planted_mistake(name, oracle_lib):
 
 def test_lightcone_unmutated_copy_passes(oracle_lib):
     assert P.check_lightcone(_load_mutated_lightcone(open(LC_SRC).read(), "copy")) < 1e-11
+
+
+# Planted mistakes in a copy of oracle/oracle.py's integer-weight route
+# (weighted MaxCut as the plain cut of the edge list in which edge e appears
+# w_e times, with (edges, w) as the observable); the copy runs on the same
+# compiled oracle.
+OR_MUTATIONS = {
+    "weighted_cost_ignores_weights": ("return _edges(np.repeat(e, w, axis=0))", "return _edges(e)"),
+    "weighted_observable_unit_weights": ("return _edges(edges), _f64(weights)",
+                                         "return _edges(edges), np.ones(len(_edges(edges)))"),
+}
+
+
+def _load_mutated_oracle(src, tag):
+    import types
+    mod = types.ModuleType(f"oracle.oracle_{tag}")
+    mod.__dict__.update(__file__=O.__file__, __package__="oracle")
+    exec(compile(src, f"oracle_{tag}.py", "exec"), mod.__dict__)
+    mod._lib = O._load()
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(OR_MUTATIONS))
+def test_weighted_pin_catches_planted_mistake(name, monkeypatch, oracle_lib):
+    old, new = OR_MUTATIONS[name]
+    src = open(O.__file__).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    monkeypatch.setattr(P, "O", _load_mutated_oracle(src.replace(old, new), name))
+    worst = P.check_weighted()
+    assert worst > 1e-3, worst
+
+
+def test_weighted_unmutated_copy_passes(monkeypatch, oracle_lib):
+    monkeypatch.setattr(P, "O", _load_mutated_oracle(open(O.__file__).read(), "copy"))
+    assert P.check_weighted() < 1e-11
